@@ -1,0 +1,191 @@
+/*
+ * spand.h -- C ABI of the GB300 spaND (sparsified nested dissection) library.
+ *
+ * Problem (Sec. 1, Eq. (1)): solve A x = b for a sparse symmetric
+ * positive-definite A in R^{N x N}.  The only required input is A; vertex
+ * coordinates are optional and, when given, drive the geometric vertex
+ * separator (Sec. 2.3, last paragraph).  The library
+ *   1. analyzes A on the host: modified nested-dissection ordering and
+ *      clustering (Algorithm 3, Sec. 2.3) plus the symbolic structure of every
+ *      elimination step (fill, Sec. 2.4; merge maps, Sec. 2.7; colouring of
+ *      the sparsification order);
+ *   2. factorizes on the GPU, level by level (Algorithm 2, "OrthS"): block
+ *      Cholesky elimination of every separator (Sec. 2.4), block-diagonal
+ *      scaling of every interface (Sec. 2.5), orthogonal sparsification by
+ *      column-pivoted QR truncated at eps (Sec. 2.6.1; truncation rule of
+ *      Sec. 4), merge (Sec. 2.7), giving M with M^T A M ~ I (Sec. 2.8);
+ *   3. solves with preconditioned CG on the GPU, the preconditioner being
+ *      z = M M^T r (Sec. 2.8), to ||b - A x||_2 / ||b||_2 <= tol (Sec. 4).
+ *
+ * Conventions for every call:
+ *   - Return value: SPAND_OK (0) or one of the SPAND_ERR_* codes below; no C++
+ *     exception crosses this boundary.  spand_last_error() gives a message.
+ *   - The caller owns every array it passes; the library copies what it keeps.
+ *   - CSR: rowptr int64[n+1] (rowptr[0] = 0), colind int32[nnz] strictly
+ *     increasing within each row, every diagonal entry present, symmetric
+ *     pattern; vals float64[nnz] of a symmetric matrix.
+ *   - Pointers are host pointers unless a call says otherwise.  Vector
+ *     arguments of spand_solve may be host or device memory (detected with
+ *     cudaPointerGetAttributes).
+ *   - cuda_stream is a cudaStream_t (NULL = legacy default stream).  Every
+ *     call that takes a stream returns after its work on that stream is done.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef SPAND_H
+#define SPAND_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  SPAND_OK = 0,
+  SPAND_ERR_INVALID_ARG = 1,   /* bad size, null pointer, malformed CSR */
+  SPAND_ERR_NOT_SPD = 2,       /* a pivot block is not positive definite */
+  SPAND_ERR_NO_CONVERGENCE = 3,/* PCG reached maxit above tol */
+  SPAND_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+  SPAND_ERR_OOM = 5,           /* device or host allocation failed */
+  SPAND_ERR_STATE = 6          /* call out of order (e.g. solve before factorize) */
+};
+
+/* precision of the factorization (the PCG recurrences, its dot products
+ * and the SpMV always run in FP64) */
+enum {
+  SPAND_FP64 = 0,  /* plain: every factor kernel in FP64 */
+  SPAND_FP32 = 1   /* mixed: factor blocks, Schur GEMMs, QR and the
+                      preconditioner apply in FP32; scaling pivots in FP64 */
+};
+
+typedef struct spand_handle_s* spand_handle;
+
+typedef struct {
+  int32_t levels;     /* L of Algorithm 3: 2^(L-1) leaves; L >= 1 */
+  double eps;         /* sparsification tolerance, >= 0 (0 = exact ND Cholesky) */
+  int32_t skip;       /* no scaling / sparsification for the first `skip`
+                         elimination steps counted from the leaves (Sec. 4.4) */
+  int32_t precision;  /* SPAND_FP64 or SPAND_FP32 */
+  int32_t maxit;      /* PCG iteration cap (paper: 500) */
+  double tol;         /* PCG relative residual target (paper: 1e-12) */
+} spand_opts;
+
+/* Fills *opts with levels 8, eps 1e-2, skip 0, FP64, maxit 500, tol 1e-10. */
+void spand_default_opts(spand_opts* opts);
+
+/*
+ * spand_analyze -- host-only analysis (Algorithm 3, Sec. 2.3; clusters and
+ * cluster trees, Sec. 2.3/2.7).
+ *   n, rowptr, colind, vals : CSR of A (see conventions); vals is copied and
+ *                             used by the next spand_factorize.
+ *   coords                  : NULL, or n*dim float64 row-major vertex
+ *                             coordinates (geometric separator); with NULL a
+ *                             BFS level-set bisection is used.
+ *   dim                     : coordinate dimension (ignored if coords NULL).
+ *   opts                    : options (copied).
+ *   out                     : receives a new handle (NULL on error).
+ * Errors: SPAND_ERR_INVALID_ARG for a malformed CSR or options.
+ */
+int spand_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
+                  const double* coords, int32_t dim, const spand_opts* opts, spand_handle* out);
+
+/*
+ * spand_factorize -- numeric factorization on the current CUDA device
+ * (Algorithm 2).  vals: NULL to use the values given to spand_analyze, or a
+ * new float64[nnz] array for the same pattern (host or device memory).
+ * Errors: SPAND_ERR_NOT_SPD (spand_get_stats gives the failing step/cluster),
+ * SPAND_ERR_CUDA, SPAND_ERR_OOM.  A failed factorization leaves the handle
+ * unfactorized.
+ */
+int spand_factorize(spand_handle h, const double* vals, void* cuda_stream);
+
+/*
+ * spand_solve -- PCG (Sec. 4) with z = M M^T r (Sec. 2.8).
+ *   b       : float64[n] right-hand side (host or device), original ordering.
+ *   x       : float64[n] solution (host or device), original ordering.
+ *   iters   : optional, receives the number of products A p.
+ *   relres  : optional, receives ||b - A x|| / ||b|| (true residual).
+ * Errors: SPAND_ERR_STATE before a successful factorize;
+ *         SPAND_ERR_NO_CONVERGENCE if maxit is reached above tol (x, iters and
+ *         relres are still written).
+ */
+int spand_solve(spand_handle h, const double* b, double* x, int32_t* iters, double* relres,
+                void* cuda_stream);
+
+/*
+ * spand_apply -- z = M M^T r, the preconditioner alone (Sec. 2.8), on device
+ * vectors in the ORIGINAL ordering.  r and z are device float64[n]; they may
+ * alias.
+ */
+int spand_apply(spand_handle h, const double* r_dev, double* z_dev, void* cuda_stream);
+
+/*
+ * spand_get_tree -- the ordering and clusters (integer output of analyze).
+ *   perm        : int32[n], perm[i] = vertex at position i (may be NULL)
+ *   cluster_ptr : int32[n_clusters+1] (may be NULL)
+ *   cluster_key : int32[3*n_clusters], (S, L, R) heap labels, none = -1
+ *                 (may be NULL)
+ *   n_clusters  : receives the number of clusters (required)
+ *   n_steps     : receives L (may be NULL)
+ * Call once with NULL arrays to size them.
+ */
+int spand_get_tree(spand_handle h, int32_t* perm, int32_t* cluster_ptr, int32_t* cluster_key,
+                   int32_t* n_clusters, int32_t* n_steps);
+
+/*
+ * spand_get_step -- symbolic structure of elimination step t (1 = leaves ..
+ * L = root).  Cluster indices are into that step's list.
+ *   counts[5] (required): n_t, #children entries, #adj entries, #adjf entries,
+ *                         #colours
+ *   keys[3 n_t], child_ptr[n_t+1] / child_idx (indices into step t-1's list;
+ *   step 1: the initial clusters), elim[n_t] (1 = eliminated at t),
+ *   colour[n_t] (-1 if eliminated), adj_ptr[n_t+1] / adj_idx (cluster graph
+ *   before the step), adjf_ptr[n_t+1] / adjf_idx (remaining clusters after the
+ *   step's fill).  Any array may be NULL.
+ */
+int spand_get_step(spand_handle h, int32_t t, int32_t* counts, int32_t* keys, int32_t* child_ptr,
+                   int32_t* child_idx, int32_t* elim, int32_t* colour, int32_t* adj_ptr,
+                   int32_t* adj_idx, int32_t* adjf_ptr, int32_t* adjf_idx);
+
+/*
+ * spand_get_ranks -- after spand_factorize: cluster sizes of step t at its
+ * start (sizes_before[n_t]) and after its sparsification (sizes_after[n_t];
+ * equal to sizes_before where nothing was sparsified; 0 for eliminated
+ * clusters).  Either array may be NULL.
+ */
+int spand_get_ranks(spand_handle h, int32_t t, int32_t* sizes_before, int32_t* sizes_after);
+
+typedef struct {
+  double t_analyze_s;     /* host analysis wall time */
+  double t_factor_s;      /* last factorize wall time (stream-synchronous) */
+  double t_solve_s;       /* last solve wall time */
+  int32_t n_cg;           /* last solve iteration count */
+  double relres;          /* last solve true relative residual */
+  int64_t size_top;       /* size of the root separator right before elimination */
+  int64_t mem_f;          /* stored factor entries (Sec. 4: mem_F) */
+  double factor_flops;    /* algorithmic flops of the last factorization */
+  double apply_bytes;     /* algorithmic bytes of one preconditioner apply */
+  int32_t fail_step;      /* NOT_SPD: elimination step (1-based), else 0 */
+  int32_t fail_cluster;   /* NOT_SPD: cluster index in that step, else -1 */
+  int64_t device_bytes;   /* device memory held by the handle */
+} spand_stats;
+
+int spand_get_stats(spand_handle h, spand_stats* st);
+
+/* Per-phase device timings of the last factorization, summed over steps (ms):
+ * out[0] eliminate, out[1] scale, out[2] sparsify, out[3] merge+assembly;
+ * out[4] one preconditioner apply (last solve, mean), out[5] one SpMV + PCG
+ * vector update (last solve, mean). */
+int spand_get_phase_times(spand_handle h, double* out6);
+
+void spand_destroy(spand_handle h);
+
+const char* spand_error_string(int code);
+/* Message of the last failed call on this thread ("" if none). */
+const char* spand_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPAND_H */

@@ -311,6 +311,7 @@ class Factor:
     ops: list = field(default_factory=list)   # ('E', s_slots, Ls, [(n_slots, Xt)]), ('S', p_slots, Lp), ('Q', p_slots, Q)
     ranks: List[Dict[int, int]] = field(default_factory=list)  # per step: cluster -> r
     sizes_before: List[np.ndarray] = field(default_factory=list)  # per step: cluster sizes at step start
+    sizes_after: List[np.ndarray] = field(default_factory=list)   # per step: sizes after sparsification (0 = eliminated)
     size_top: int = 0
     mem_f: int = 0
 
@@ -461,6 +462,9 @@ def factorize(prob_rowptr, prob_colind, prob_vals, tree: Tree, eps: float, skip:
             if trace is not None:
                 trace.append((t, "post", frozenset(blocks)))
         F.ranks.append(ranks)
+        after = size.copy()
+        after[st.elim == 1] = 0
+        F.sizes_after.append(after)
         if t == L:
             break
         # ---- merge (Sec. 2.7)

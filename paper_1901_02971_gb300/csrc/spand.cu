@@ -1,0 +1,1333 @@
+// C-ABI entry points, device memory management, the level scheduler of the
+// numeric factorization (Algorithm 2) and the PCG driver (Sec. 4).
+#include "spand.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <type_traits>
+#include <numeric>
+#include <stdexcept>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "factor_kernels.cuh"
+#include "solve_kernels.cuh"
+#include "spand_internal.h"
+
+namespace spand {
+
+thread_local std::string g_err;
+
+struct Fail {
+  int code;
+  std::string msg;
+};
+
+#define CK(expr)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (expr);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      throw Fail{e_ == cudaErrorMemoryAllocation ? SPAND_ERR_OOM : SPAND_ERR_CUDA,            \
+                 std::string(#expr) + ": " + cudaGetErrorString(e_)};                         \
+  } while (0)
+
+#define CKLAUNCH() CK(cudaGetLastError())
+
+static inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Chunked bump allocator over cudaMalloc; reset() keeps the chunks for reuse.
+class DevArena {
+  struct Chunk {
+    char* p;
+    size_t cap, used;
+  };
+  std::vector<Chunk> chunks_;
+  size_t cur_ = 0;
+
+ public:
+  size_t bytes_held = 0;
+  void* alloc(size_t bytes) {
+    bytes = align256(std::max<size_t>(bytes, 1));
+    while (cur_ < chunks_.size()) {
+      Chunk& c = chunks_[cur_];
+      if (c.used + bytes <= c.cap) {
+        void* p = c.p + c.used;
+        c.used += bytes;
+        return p;
+      }
+      ++cur_;
+    }
+    size_t cap = std::max<size_t>(bytes, size_t(64) << 20);
+    char* p = nullptr;
+    CK(cudaMalloc(&p, cap));
+    chunks_.push_back({p, cap, bytes});
+    bytes_held += cap;
+    cur_ = chunks_.size() - 1;
+    return p;
+  }
+  void reset() {
+    for (auto& c : chunks_) c.used = 0;
+    cur_ = 0;
+  }
+  void release() {
+    for (auto& c : chunks_) cudaFree(c.p);
+    chunks_.clear();
+    cur_ = 0;
+    bytes_held = 0;
+  }
+  ~DevArena() { release(); }
+};
+
+// Grow-only contiguous device buffer.
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  void* ensure(size_t bytes) {
+    if (bytes <= cap && p) return p;
+    if (p) {
+      CK(cudaDeviceSynchronize());
+      cudaFree(p);
+      p = nullptr;
+      cap = 0;
+    }
+    size_t c = align256(std::max<size_t>(bytes + bytes / 4, 256));
+    CK(cudaMalloc(&p, c));
+    cap = c;
+    return p;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+  ~DevBuf() { release(); }
+};
+
+// Host-side packer for one upload of descriptor arrays.
+struct Packer {
+  std::vector<char> buf;
+  template <typename X>
+  size_t add(const std::vector<X>& v) {
+    size_t off = align256(buf.size());
+    buf.resize(off + v.size() * sizeof(X));
+    if (!v.empty()) std::memcpy(buf.data() + off, v.data(), v.size() * sizeof(X));
+    return off;
+  }
+};
+
+template <typename TF>
+struct ApplyStep {
+  int n_elim = 0, n_scale = 0, n_q = 0;
+  const ElimOp<TF>* elim = nullptr;
+  const ScaleOp<TF>* scale = nullptr;
+  const QOp<TF>* q = nullptr;
+  const int32_t* slots = nullptr;
+  int64_t ntgt = 0;
+  const int32_t* tslot = nullptr;
+  const int64_t* tptr = nullptr;
+  const int64_t* tidx = nullptr;
+  size_t sm_elim_fwd = 0, sm_elim_bwd = 0, sm_scale = 0, sm_q_fwd = 0, sm_q_bwd = 0;
+};
+
+// Highest dynamic shared memory requested so far, per kernel.
+static void ensure_smem(const void* fn, size_t bytes) {
+  static std::unordered_map<const void*, size_t> done;
+  if (bytes <= 48 * 1024) return;
+  auto it = done.find(fn);
+  if (it != done.end() && it->second >= bytes) return;
+  CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  done[fn] = bytes;
+}
+
+}  // namespace spand
+
+using namespace spand;
+
+struct spand_handle_s {
+  spand_opts opts{};
+  int64_t n = 0, nnz = 0;
+  std::vector<int64_t> rowptr;
+  std::vector<int32_t> colind;
+  std::vector<double> vals;
+  Tree tree;
+  // step-1 assembly: original nnz e -> (cluster row, offset in that row)
+  std::vector<int32_t> asm_row;
+  std::vector<int64_t> asm_off;
+  // A in the cluster order (for the SpMV of PCG)
+  std::vector<int64_t> prow;
+  std::vector<int32_t> pcol;
+  std::vector<int64_t> pval_src;
+  // device
+  int device = -1;
+  bool consts_ready = false;
+  DevArena persist, descs;
+  DevBuf scratch[2];
+  DevBuf d_vals, d_asm_row, d_asm_off, d_prow, d_pcol, d_pval, d_pval_src, d_perm;
+  DevBuf d_vec, d_tmp, d_save, d_bin, d_bout;
+  int fprec = -1;
+  bool factored = false;
+  std::vector<ApplyStep<double>> apply64;
+  std::vector<ApplyStep<float>> apply32;
+  int64_t tmp_len = 0, save_len = 0;
+  spand_stats st{};
+  double phase_ms[6] = {0, 0, 0, 0, 0, 0};
+  std::vector<std::vector<int32_t>> sizes_before, sizes_after;
+};
+
+namespace spand {
+
+// ---------------------------------------------------------------- layouts
+
+template <typename T>
+struct Layout {
+  std::vector<T*> row;
+  std::vector<int32_t> ld, W;
+  std::vector<int32_t> nptr, nidx, noff;  // neighbour lists with column offsets
+  int32_t off_of(int i, int q) const {
+    if (q == i) return 0;
+    const int32_t* b = nidx.data() + nptr[i];
+    const int32_t* e = nidx.data() + nptr[i + 1];
+    const int32_t* it = std::lower_bound(b, e, q);
+    if (it == e || *it != q) return -1;
+    return noff[nptr[i] + (it - b)];
+  }
+  int32_t first_upper(int i) const {  // column where the blocks of neighbours q > i start
+    for (int32_t e = nptr[i]; e < nptr[i + 1]; ++e)
+      if (nidx[e] > i) return noff[e];
+    return W[i];
+  }
+};
+
+// Row layout of step t: eliminated clusters keep their pre-elimination
+// neighbours (cluster graph before the step), the others the graph after the
+// step's fill.  Separator rows go to the persistent arena (they are factor
+// data), the others to the step's scratch buffer.
+template <typename T>
+static Layout<T> make_layout(spand_handle h, int t, const std::vector<int32_t>& sz, cudaStream_t s) {
+  const StepStruct& st = h->tree.steps[t - 1];
+  Layout<T> lay;
+  const int n = st.n;
+  lay.row.assign(n, nullptr);
+  lay.ld.resize(n);
+  lay.W.resize(n);
+  lay.nptr.assign(1, 0);
+  for (int i = 0; i < n; ++i) {
+    const int32_t* b = st.elim[i] ? &st.adj_idx[st.adj_ptr[i]] : &st.adjf_idx[st.adjf_ptr[i]];
+    const int32_t* e = st.elim[i] ? &st.adj_idx[st.adj_ptr[i + 1]] : &st.adjf_idx[st.adjf_ptr[i + 1]];
+    int32_t w = sz[i];
+    for (const int32_t* q = b; q < e; ++q) {
+      lay.nidx.push_back(*q);
+      lay.noff.push_back(w);
+      w += sz[*q];
+    }
+    lay.nptr.push_back((int32_t)lay.nidx.size());
+    lay.W[i] = w;
+    lay.ld[i] = std::max<int32_t>(sz[i], 1);
+  }
+  size_t pers = 0, scr = 0;
+  for (int i = 0; i < n; ++i) {
+    size_t b = align256((size_t)lay.ld[i] * std::max(lay.W[i], 1) * sizeof(T));
+    (st.elim[i] ? pers : scr) += b;
+  }
+  char* pbase = pers ? (char*)h->persist.alloc(pers) : nullptr;
+  char* sbase = scr ? (char*)h->scratch[t & 1].ensure(scr) : nullptr;
+  size_t po = 0, so = 0;
+  for (int i = 0; i < n; ++i) {
+    size_t b = align256((size_t)lay.ld[i] * std::max(lay.W[i], 1) * sizeof(T));
+    if (st.elim[i]) { lay.row[i] = (T*)(pbase + po); po += b; }
+    else { lay.row[i] = (T*)(sbase + so); so += b; }
+  }
+  if (pers) CK(cudaMemsetAsync(pbase, 0, pers, s));
+  if (scr) CK(cudaMemsetAsync(sbase, 0, scr, s));
+  return lay;
+}
+
+template <typename T>
+static void* upload(spand_handle h, const Packer& pk, cudaStream_t s) {
+  if (pk.buf.empty()) return nullptr;
+  void* d = h->descs.alloc(pk.buf.size());
+  CK(cudaMemcpyAsync(d, pk.buf.data(), pk.buf.size(), cudaMemcpyHostToDevice, s));
+  return d;
+}
+
+template <typename X>
+static X* at(void* base, size_t off) { return reinterpret_cast<X*>((char*)base + off); }
+
+// Tiled upper Cholesky of a batch of diagonal blocks (right-looking over 64x64 tiles).
+template <typename T>
+static void potrf_batch(spand_handle h, const std::vector<RowDesc<T>>& rows, int* d_info, cudaStream_t s) {
+  if (rows.empty()) return;
+  Packer pk;
+  size_t o = pk.add(rows);
+  void* d = upload<T>(h, pk, s);
+  const RowDesc<T>* dr = at<const RowDesc<T>>(d, o);
+  int nmax = 0;
+  for (auto& r : rows) nmax = std::max(nmax, r.n);
+  const int nt = (nmax + TB - 1) / TB;
+  const size_t sm1 = sizeof(SqTile<T>), sm2 = 2 * sizeof(SqTile<T>);
+  ensure_smem((const void*)k_potrf_diag<T>, sm1);
+  ensure_smem((const void*)k_potrf_trsm<T>, sm2);
+  const int nb = (int)rows.size();
+  for (int k = 0; k < nt; ++k) {
+    k_potrf_diag<T><<<nb, NT, sm1, s>>>(dr, k, d_info);
+    CKLAUNCH();
+    const int m = nt - k - 1;
+    if (m > 0) {
+      k_potrf_trsm<T><<<dim3(m, nb), NT, sm2, s>>>(dr, k);
+      CKLAUNCH();
+      k_potrf_update<T><<<dim3(m * (m + 1) / 2, nb), NT, 0, s>>>(dr, k);
+      CKLAUNCH();
+    }
+  }
+}
+
+template <typename T>
+static void trsm_batch(spand_handle h, const std::vector<TrsmTask<T>>& tasks, cudaStream_t s) {
+  if (tasks.empty()) return;
+  Packer pk;
+  size_t o = pk.add(tasks);
+  void* d = upload<T>(h, pk, s);
+  const size_t sm = 2 * sizeof(SqTile<T>) + sizeof(TileSmem<T>);
+  ensure_smem((const void*)k_trsm_cols<T>, sm);
+  k_trsm_cols<T><<<(unsigned)tasks.size(), NT, sm, s>>>(at<const TrsmTask<T>>(d, o));
+  CKLAUNCH();
+}
+
+template <typename T>
+static void add_panels(std::vector<TrsmTask<T>>& out, T* R, int n, int ld, int c0, int c1) {
+  if (n <= 0) return;
+  for (int c = c0; c < c1; c += TB) out.push_back({R, n, ld, c, std::min(c + TB, c1)});
+}
+
+template <typename T>
+static void copy_batch(spand_handle h, const std::vector<CopyTask<T>>& tasks, cudaStream_t s) {
+  if (tasks.empty()) return;
+  std::vector<CopyTile> tiles;
+  for (int32_t i = 0; i < (int32_t)tasks.size(); ++i)
+    for (int r0 = 0; r0 < tasks[i].rows; r0 += 32)
+      for (int c0 = 0; c0 < tasks[i].cols; c0 += 32) tiles.push_back({i, r0, c0});
+  if (tiles.empty()) return;
+  Packer pk;
+  size_t ot = pk.add(tasks), oi = pk.add(tiles);
+  void* d = upload<T>(h, pk, s);
+  const size_t nt = tiles.size();
+  for (size_t b = 0; b < nt; b += 1u << 30) {
+    const unsigned cnt = (unsigned)std::min<size_t>(nt - b, 1u << 30);
+    k_copy<T><<<cnt, NT, 0, s>>>(at<const CopyTile>(d, oi) + b, at<const CopyTask<T>>(d, ot));
+    CKLAUNCH();
+  }
+}
+
+struct StepTimer {
+  cudaEvent_t ev[5];
+  StepTimer() { for (auto& e : ev) CK(cudaEventCreate(&e)); }
+  ~StepTimer() { for (auto& e : ev) cudaEventDestroy(e); }
+};
+
+template <typename T>
+static int factorize_impl(spand_handle h, cudaStream_t s) {
+  const Tree& tr = h->tree;
+  const int L = tr.L;
+  const double eps = h->opts.eps;
+  const int skip = h->opts.skip;
+  h->persist.reset();
+  h->descs.reset();
+  std::vector<ApplyStep<T>> apply;
+  h->sizes_before.assign(L, {});
+  h->sizes_after.assign(L, {});
+  for (double& v : h->phase_ms) v = 0;
+  spand_stats& stt = h->st;
+  stt.size_top = 0;
+  stt.mem_f = 0;
+  stt.factor_flops = 0;
+  stt.fail_step = 0;
+  stt.fail_cluster = -1;
+  StepTimer tm;
+  // info flag + cur_size scratch
+  int* d_info = (int*)h->descs.alloc(sizeof(int));
+  CK(cudaMemsetAsync(d_info, 0, sizeof(int), s));
+
+  const int nc0 = (int)tr.cluster_ptr.size() - 1;
+  std::vector<int32_t> sz(nc0);
+  std::vector<std::vector<int32_t>> slots(nc0);
+  for (int i = 0; i < nc0; ++i) {
+    sz[i] = tr.cluster_ptr[i + 1] - tr.cluster_ptr[i];
+    slots[i].resize(sz[i]);
+    std::iota(slots[i].begin(), slots[i].end(), tr.cluster_ptr[i]);
+  }
+  CK(cudaEventRecord(tm.ev[0], s));
+  Layout<T> lay = make_layout<T>(h, 1, sz, s);
+  {  // assemble A into the step-1 rows
+    Packer pk;
+    size_t orow = pk.add(lay.row);
+    void* d = upload<T>(h, pk, s);
+    const int64_t nnz = h->nnz;
+    if (nnz > 0) {
+      const int g = (int)std::min<int64_t>((nnz + 255) / 256, 4096);
+      k_assemble<T><<<g, 256, 0, s>>>((const double*)h->d_vals.p, (const int32_t*)h->d_asm_row.p,
+                                      (const int64_t*)h->d_asm_off.p, at<T* const>(d, orow), nnz);
+      CKLAUNCH();
+    }
+  }
+  CK(cudaEventRecord(tm.ev[1], s));
+  {
+    float ms = 0;
+    CK(cudaEventSynchronize(tm.ev[1]));
+    CK(cudaEventElapsedTime(&ms, tm.ev[0], tm.ev[1]));
+    h->phase_ms[3] += ms;
+  }
+
+  int32_t* d_cur = nullptr;
+  for (int t = 1; t <= L; ++t) {
+    const StepStruct& st = tr.steps[t - 1];
+    const int n = st.n;
+    h->sizes_before[t - 1] = sz;
+    if (t == L)
+      for (int i = 0; i < n; ++i)
+        if (st.elim[i]) stt.size_top += sz[i];
+    CK(cudaEventRecord(tm.ev[0], s));
+    // ------------------------------------------------ eliminate (Sec. 2.4)
+    std::vector<int> seps, rems;
+    for (int i = 0; i < n; ++i) (st.elim[i] ? seps : rems).push_back(i);
+    {
+      std::vector<RowDesc<T>> diag;
+      std::vector<int> diag_cl;
+      std::vector<TrsmTask<T>> tr_tasks;
+      for (int sidx : seps) {
+        if (sz[sidx] <= 0) continue;
+        diag.push_back({lay.row[sidx], sz[sidx], lay.ld[sidx]});
+        diag_cl.push_back(sidx);
+        add_panels(tr_tasks, lay.row[sidx], sz[sidx], lay.ld[sidx], sz[sidx], lay.W[sidx]);
+        const double ns = sz[sidx], m = lay.W[sidx] - sz[sidx];
+        stt.factor_flops += ns * ns * ns / 3 + ns * ns * m + ns * m * m;
+      }
+      potrf_batch<T>(h, diag, d_info, s);
+      int info = 0;
+      CK(cudaMemcpyAsync(&info, d_info, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (info) {
+        stt.fail_step = t;
+        stt.fail_cluster = diag_cl[info - 1];
+        throw Fail{SPAND_ERR_NOT_SPD, "pivot block not positive definite at step " + std::to_string(t)};
+      }
+      trsm_batch<T>(h, tr_tasks, s);
+      // pull-form Schur update of every pair of neighbours
+      std::vector<SchurBlock<T>> blocks;
+      std::vector<std::vector<SchurContrib<T>>> contr;
+      std::unordered_map<int64_t, int32_t> bid;
+      for (int sidx : seps) {
+        if (sz[sidx] <= 0) continue;
+        const int32_t nb0 = lay.nptr[sidx], nb1 = lay.nptr[sidx + 1];
+        for (int32_t ea = nb0; ea < nb1; ++ea) {
+          const int32_t a = lay.nidx[ea];
+          if (sz[a] <= 0) continue;
+          for (int32_t eb = ea; eb < nb1; ++eb) {
+            const int32_t b = lay.nidx[eb];
+            if (sz[b] <= 0) continue;
+            const int64_t key = (int64_t)a * n + b;
+            auto it = bid.find(key);
+            int32_t id;
+            if (it == bid.end()) {
+              id = (int32_t)blocks.size();
+              bid.emplace(key, id);
+              const int32_t oab = lay.off_of(a, b), oba = lay.off_of(b, a);
+              if (oab < 0 || oba < 0) throw Fail{SPAND_ERR_STATE, "fill block missing from the layout"};
+              SchurBlock<T> bl;
+              bl.C1 = lay.row[a] + (size_t)oab * lay.ld[a];
+              bl.C2 = (a == b) ? nullptr : lay.row[b] + (size_t)oba * lay.ld[b];
+              bl.ld1 = lay.ld[a];
+              bl.ld2 = lay.ld[b];
+              bl.rows = sz[a];
+              bl.cols = sz[b];
+              blocks.push_back(bl);
+              contr.emplace_back();
+            } else {
+              id = it->second;
+            }
+            SchurContrib<T> c;
+            c.Xa = lay.row[sidx] + (size_t)lay.noff[ea] * lay.ld[sidx];
+            c.Xb = lay.row[sidx] + (size_t)lay.noff[eb] * lay.ld[sidx];
+            c.lds = lay.ld[sidx];
+            c.ns = sz[sidx];
+            contr[id].push_back(c);
+          }
+        }
+      }
+      if (!blocks.empty()) {
+        std::vector<SchurContrib<T>> flat;
+        std::vector<SchurTile> tiles;
+        for (size_t b = 0; b < blocks.size(); ++b) {
+          blocks[b].cbeg = (int32_t)flat.size();
+          flat.insert(flat.end(), contr[b].begin(), contr[b].end());
+          blocks[b].cend = (int32_t)flat.size();
+          for (int i0 = 0; i0 < blocks[b].rows; i0 += TB)
+            for (int j0 = 0; j0 < blocks[b].cols; j0 += TB) tiles.push_back({(int32_t)b, i0, j0});
+        }
+        Packer pk;
+        size_t ob = pk.add(blocks), oc = pk.add(flat), ot = pk.add(tiles);
+        void* d = upload<T>(h, pk, s);
+        k_schur<T><<<(unsigned)tiles.size(), NT, 0, s>>>(at<const SchurTile>(d, ot), at<const SchurBlock<T>>(d, ob),
+                                                        at<const SchurContrib<T>>(d, oc));
+        CKLAUNCH();
+      }
+    }
+    CK(cudaEventRecord(tm.ev[1], s));
+    // ------------------------------------------------ apply ops of the elimination
+    ApplyStep<T> ap;
+    std::vector<int32_t> aslots;
+    std::vector<ElimOp<T>> eops;
+    std::vector<std::pair<int32_t, int64_t>> tgt;  // (target slot, tmp index)
+    int64_t tmp_off = 0;
+    size_t sm_ef = 0, sm_eb = 0;
+    for (int sidx : seps) {
+      if (sz[sidx] <= 0) continue;
+      ElimOp<T> o;
+      o.R = lay.row[sidx];
+      o.ns = sz[sidx];
+      o.m = lay.W[sidx] - sz[sidx];
+      o.slot = (int64_t)aslots.size();
+      o.tmp = tmp_off;
+      aslots.insert(aslots.end(), slots[sidx].begin(), slots[sidx].end());
+      int64_t j = 0;
+      for (int32_t e = lay.nptr[sidx]; e < lay.nptr[sidx + 1]; ++e) {
+        const int32_t q = lay.nidx[e];
+        for (int32_t k = 0; k < sz[q]; ++k, ++j) {
+          aslots.push_back(slots[q][k]);
+          tgt.push_back({slots[q][k], tmp_off + j});
+        }
+      }
+      tmp_off += o.m;
+      eops.push_back(o);
+      stt.mem_f += (int64_t)o.ns * (o.ns + 1) / 2 + (int64_t)o.ns * o.m;
+      sm_ef = std::max(sm_ef, (size_t)o.ns * sizeof(double));
+      sm_eb = std::max(sm_eb, (size_t)(o.ns + o.m) * sizeof(double));
+    }
+    h->tmp_len = std::max(h->tmp_len, tmp_off);
+    std::stable_sort(tgt.begin(), tgt.end(),
+                     [](const std::pair<int32_t, int64_t>& a, const std::pair<int32_t, int64_t>& b) { return a.first < b.first; });
+    std::vector<int32_t> tslot;
+    std::vector<int64_t> tptr(1, 0), tidx;
+    for (size_t i = 0; i < tgt.size(); ++i) {
+      if (i == 0 || tgt[i].first != tgt[i - 1].first) {
+        if (i) tptr.push_back((int64_t)tidx.size());
+        tslot.push_back(tgt[i].first);
+      }
+      tidx.push_back(tgt[i].second);
+    }
+    if (!tgt.empty()) tptr.push_back((int64_t)tidx.size());
+
+    // ------------------------------------------------ scale + sparsify
+    std::vector<int32_t> sz_after = sz;
+    for (int sidx : seps) sz_after[sidx] = 0;
+    std::vector<ScaleOp<T>> sops;
+    std::vector<QOp<T>> qops;
+    size_t sm_s = 0, sm_qf = 0, sm_qb = 0;
+    const bool sparsify = (skip < t) && (t < L);
+    std::vector<int> cp_cluster;           // sparsified clusters (task order)
+    std::vector<T*> cp_qc;                 // their Q_pc scratch
+    if (sparsify) {
+      std::vector<RowDesc<T>> diag;
+      std::vector<int> diag_cl;
+      std::vector<TrsmTask<T>> up, lo;
+      std::vector<CopyTask<T>> m_up, m_lo, usave;
+      std::vector<RowDesc<T>> idr;
+      for (int p : rems) {
+        if (sz[p] <= 0) continue;
+        diag.push_back({lay.row[p], sz[p], lay.ld[p]});
+        diag_cl.push_back(p);
+        const int fu = lay.first_upper(p);
+        add_panels(up, lay.row[p], sz[p], lay.ld[p], fu, lay.W[p]);
+        add_panels(lo, lay.row[p], sz[p], lay.ld[p], sz[p], fu);
+        for (int32_t e = lay.nptr[p]; e < lay.nptr[p + 1]; ++e) {
+          const int32_t q = lay.nidx[e];
+          if (q <= p || sz[q] <= 0) continue;
+          const int32_t oqp = lay.off_of(q, p);
+          CopyTask<T> c;
+          c.src = lay.row[p] + (size_t)lay.noff[e] * lay.ld[p];
+          c.dst = lay.row[q] + (size_t)oqp * lay.ld[q];
+          c.lds = lay.ld[p];
+          c.ldd = lay.ld[q];
+          c.rows = sz[q];
+          c.cols = sz[p];
+          c.trans = 1;
+          c.pad = 0;
+          m_up.push_back(c);
+          CopyTask<T> b = c;
+          b.src = c.dst;
+          b.dst = const_cast<T*>(c.src);
+          b.lds = lay.ld[q];
+          b.ldd = lay.ld[p];
+          b.rows = sz[p];
+          b.cols = sz[q];
+          m_lo.push_back(b);
+        }
+        T* U = (T*)h->persist.alloc((size_t)sz[p] * sz[p] * sizeof(T));
+        usave.push_back({lay.row[p], U, lay.ld[p], sz[p], sz[p], sz[p], 0, 0});
+        idr.push_back({lay.row[p], sz[p], lay.ld[p]});
+        ScaleOp<T> so;
+        so.U = U;
+        so.np = sz[p];
+        so.pad = 0;
+        so.slot = 0;  // set below
+        sops.push_back(so);
+        const double np_ = sz[p], m = lay.W[p] - sz[p];
+        stt.factor_flops += np_ * np_ * np_ / 3 + np_ * np_ * m;
+        stt.mem_f += (int64_t)sz[p] * (sz[p] + 1) / 2;
+        sm_s = std::max(sm_s, (size_t)sz[p] * sizeof(double));
+      }
+      potrf_batch<T>(h, diag, d_info, s);
+      int info = 0;
+      CK(cudaMemcpyAsync(&info, d_info, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (info) {
+        stt.fail_step = t;
+        stt.fail_cluster = diag_cl[info - 1];
+        throw Fail{SPAND_ERR_NOT_SPD, "interface block not positive definite at step " + std::to_string(t)};
+      }
+      trsm_batch<T>(h, up, s);
+      copy_batch<T>(h, m_up, s);
+      trsm_batch<T>(h, lo, s);
+      copy_batch<T>(h, m_lo, s);
+      copy_batch<T>(h, usave, s);
+      if (!idr.empty()) {
+        Packer pk;
+        size_t o = pk.add(idr);
+        void* d = upload<T>(h, pk, s);
+        k_set_identity<T><<<dim3(8, (unsigned)idr.size()), 256, 0, s>>>(at<const RowDesc<T>>(d, o), (int)idr.size());
+        CKLAUNCH();
+      }
+      CK(cudaEventRecord(tm.ev[2], s));
+      // ---- sparsify, colour by colour (Sec. 2.6.1)
+      d_cur = (int32_t*)h->descs.alloc((size_t)n * sizeof(int32_t));
+      CK(cudaMemcpyAsync(d_cur, sz.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      std::vector<CpqrTask<T>> tasks;
+      std::vector<CpqrNbr<T>> nbrs;
+      const int ncol = st.ncolours();
+      std::vector<std::vector<int32_t>> by_colour(std::max(ncol, 1));
+      size_t wbytes = 0;
+      struct WOff { size_t w, nrm, piv, qc; };
+      std::vector<WOff> woff;
+      int nnb_max = 0, np_max = 0;
+      for (int p : rems) {
+        if (sz[p] <= 0) continue;
+        if (lay.nptr[p + 1] == lay.nptr[p]) continue;  // no neighbours: nothing to compress against
+        CpqrTask<T> tk{};
+        tk.p = p;
+        tk.np = sz[p];
+        tk.ldp = lay.ld[p];
+        tk.Rp = lay.row[p];
+        tk.nbeg = (int32_t)nbrs.size();
+        int mm = 0;
+        for (int32_t e = lay.nptr[p]; e < lay.nptr[p + 1]; ++e) {
+          const int32_t q = lay.nidx[e];
+          CpqrNbr<T> nb;
+          nb.Rq = lay.row[q];
+          nb.q = q;
+          nb.off_pq = lay.noff[e];
+          nb.off_qp = lay.off_of(q, p);
+          if (nb.off_qp < 0) throw Fail{SPAND_ERR_STATE, "asymmetric block pattern"};
+          nb.ldq = lay.ld[q];
+          nbrs.push_back(nb);
+          mm += sz[q];
+        }
+        tk.nend = (int32_t)nbrs.size();
+        tk.m_max = mm;
+        WOff w;
+        w.w = wbytes; wbytes += align256((size_t)sz[p] * std::max(mm, 1) * sizeof(T));
+        w.nrm = wbytes; wbytes += align256((size_t)std::max(mm, 1) * sizeof(T));
+        w.piv = wbytes; wbytes += align256((size_t)std::max(mm, 1) * sizeof(int32_t));
+        w.qc = wbytes; wbytes += align256((size_t)sz[p] * sz[p] * sizeof(T));
+        woff.push_back(w);
+        by_colour[st.colour[p]].push_back((int32_t)tasks.size());
+        tasks.push_back(tk);
+        cp_cluster.push_back(p);
+        nnb_max = std::max(nnb_max, tk.nend - tk.nbeg);
+        np_max = std::max(np_max, (int)sz[p]);
+      }
+      if (!tasks.empty()) {
+        char* wb = (char*)h->scratch[(t + 1) & 1].ensure(wbytes);
+        for (size_t i = 0; i < tasks.size(); ++i) {
+          tasks[i].work = (T*)(wb + woff[i].w);
+          tasks[i].norms = (T*)(wb + woff[i].nrm);
+          tasks[i].piv = (int32_t*)(wb + woff[i].piv);
+          tasks[i].Qc = (T*)(wb + woff[i].qc);
+          cp_qc.push_back(tasks[i].Qc);
+        }
+        std::vector<int32_t> list;
+        std::vector<size_t> cbeg;
+        for (auto& v : by_colour) {
+          cbeg.push_back(list.size());
+          list.insert(list.end(), v.begin(), v.end());
+        }
+        cbeg.push_back(list.size());
+        Packer pk;
+        size_t ot = pk.add(tasks), on = pk.add(nbrs), ol = pk.add(list);
+        void* d = upload<T>(h, pk, s);
+        const size_t sm = align256(sizeof(int) * (nnb_max + 1)) + (size_t)np_max * sizeof(T);
+        ensure_smem((const void*)k_cpqr<T>, sm);
+        for (size_t c = 0; c + 1 < cbeg.size(); ++c) {
+          const unsigned cnt = (unsigned)(cbeg[c + 1] - cbeg[c]);
+          if (!cnt) continue;
+          k_cpqr<T><<<cnt, NT, sm, s>>>(at<const CpqrTask<T>>(d, ot), at<const int32_t>(d, ol) + cbeg[c],
+                                        at<const CpqrNbr<T>>(d, on), d_cur, (T)eps);
+          CKLAUNCH();
+        }
+        CK(cudaMemcpyAsync(sz_after.data(), d_cur, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      }
+      CK(cudaStreamSynchronize(s));
+      for (int sidx : seps) sz_after[sidx] = 0;
+      // compact Q_pc (|p| x r) into the factor
+      std::vector<CopyTask<T>> qcopy;
+      for (size_t i = 0; i < cp_cluster.size(); ++i) {
+        const int p = cp_cluster[i];
+        const int r = sz_after[p];
+        QOp<T> q;
+        q.np = sz[p];
+        q.r = r;
+        T* Q = r > 0 ? (T*)h->persist.alloc((size_t)sz[p] * r * sizeof(T)) : nullptr;
+        q.Q = Q;
+        if (r > 0) qcopy.push_back({cp_qc[i], Q, sz[p], sz[p], sz[p], r, 0, 0});
+        q.slot = 0;
+        q.save = 0;
+        qops.push_back(q);
+        const double np_ = sz[p], m = lay.W[p] - sz[p], rr = r;
+        stt.factor_flops += 4 * np_ * m * rr - 2 * rr * rr * (np_ + m) + 4 * rr * rr * rr / 3;
+        stt.mem_f += (int64_t)sz[p] * r;
+        sm_qf = std::max(sm_qf, (size_t)sz[p] * sizeof(double));
+        sm_qb = std::max(sm_qb, (size_t)std::max(r, 1) * sizeof(double));
+      }
+      copy_batch<T>(h, qcopy, s);
+    } else {
+      CK(cudaEventRecord(tm.ev[2], s));
+    }
+    CK(cudaEventRecord(tm.ev[3], s));
+    // slots of the scaling / sparsification ops (step-t slot lists)
+    {
+      size_t k = 0;
+      if (sparsify)
+        for (int p : rems) {
+          if (sz[p] <= 0) continue;
+          sops[k].slot = (int64_t)aslots.size();
+          aslots.insert(aslots.end(), slots[p].begin(), slots[p].end());
+          ++k;
+        }
+      int64_t save = h->save_len;
+      for (size_t i = 0; i < cp_cluster.size(); ++i) {
+        const int p = cp_cluster[i];
+        qops[i].slot = (int64_t)aslots.size();
+        aslots.insert(aslots.end(), slots[p].begin(), slots[p].end());
+        qops[i].save = save;
+        save += qops[i].np + qops[i].r;
+      }
+      h->save_len = save;
+    }
+    h->sizes_after[t - 1] = sz_after;
+    {  // upload the step's apply program
+      Packer pk;
+      size_t oe = pk.add(eops), os = pk.add(sops), oq = pk.add(qops), osl = pk.add(aslots);
+      size_t ots = pk.add(tslot), otp = pk.add(tptr), oti = pk.add(tidx);
+      void* d = nullptr;
+      if (!pk.buf.empty()) {
+        d = h->persist.alloc(pk.buf.size());
+        CK(cudaMemcpyAsync(d, pk.buf.data(), pk.buf.size(), cudaMemcpyHostToDevice, s));
+      }
+      ap.n_elim = (int)eops.size();
+      ap.n_scale = (int)sops.size();
+      ap.n_q = (int)qops.size();
+      ap.elim = at<const ElimOp<T>>(d, oe);
+      ap.scale = at<const ScaleOp<T>>(d, os);
+      ap.q = at<const QOp<T>>(d, oq);
+      ap.slots = at<const int32_t>(d, osl);
+      ap.ntgt = (int64_t)tslot.size();
+      ap.tslot = at<const int32_t>(d, ots);
+      ap.tptr = at<const int64_t>(d, otp);
+      ap.tidx = at<const int64_t>(d, oti);
+      ap.sm_elim_fwd = sm_ef;
+      ap.sm_elim_bwd = sm_eb;
+      ap.sm_scale = sm_s;
+      ap.sm_q_fwd = sm_qf;
+      ap.sm_q_bwd = sm_qb;
+      apply.push_back(ap);
+    }
+    // ------------------------------------------------ merge (Sec. 2.7)
+    Layout<T> nxt;
+    if (t < L) {
+      const StepStruct& ns = tr.steps[t];
+      std::vector<int32_t> nsz(ns.n, 0), pof(n, -1), ro(n, 0);
+      std::vector<std::vector<int32_t>> nslots(ns.n);
+      for (int P = 0; P < ns.n; ++P) {
+        int32_t o = 0;
+        for (int32_t e = ns.child_ptr[P]; e < ns.child_ptr[P + 1]; ++e) {
+          const int32_t a = ns.child_idx[e];
+          pof[a] = P;
+          ro[a] = o;
+          o += sz_after[a];
+          nslots[P].insert(nslots[P].end(), slots[a].begin(), slots[a].begin() + sz_after[a]);
+        }
+        nsz[P] = o;
+      }
+      nxt = make_layout<T>(h, t + 1, nsz, s);
+      std::vector<CopyTask<T>> cps;
+      for (int a : rems) {
+        if (sz_after[a] <= 0) continue;
+        const int P = pof[a];
+        auto add = [&](int b, int32_t src_col) {
+          if (sz_after[b] <= 0) return;
+          const int Q = pof[b];
+          int32_t tc;
+          if (Q == P) tc = ro[b];
+          else {
+            const int32_t o = nxt.off_of(P, Q);
+            if (o < 0) return;
+            tc = o + ro[b];
+          }
+          CopyTask<T> c;
+          c.src = lay.row[a] + (size_t)src_col * lay.ld[a];
+          c.dst = nxt.row[P] + ro[a] + (size_t)tc * nxt.ld[P];
+          c.lds = lay.ld[a];
+          c.ldd = nxt.ld[P];
+          c.rows = sz_after[a];
+          c.cols = sz_after[b];
+          c.trans = 0;
+          c.pad = 0;
+          cps.push_back(c);
+        };
+        add(a, 0);
+        for (int32_t e = lay.nptr[a]; e < lay.nptr[a + 1]; ++e) add(lay.nidx[e], lay.noff[e]);
+      }
+      copy_batch<T>(h, cps, s);
+      sz = nsz;
+      slots = std::move(nslots);
+    }
+    CK(cudaEventRecord(tm.ev[4], s));
+    CK(cudaEventSynchronize(tm.ev[4]));
+    float ms[4];
+    for (int k = 0; k < 4; ++k) CK(cudaEventElapsedTime(&ms[k], tm.ev[k], tm.ev[k + 1]));
+    h->phase_ms[0] += ms[0];
+    h->phase_ms[1] += ms[1];
+    h->phase_ms[2] += ms[2];
+    h->phase_ms[3] += ms[3];
+    if (t < L) lay = std::move(nxt);
+  }
+  if constexpr (std::is_same<T, double>::value) {
+    h->apply64 = std::move(apply);
+    h->apply32.clear();
+  } else {
+    h->apply32 = std::move(apply);
+    h->apply64.clear();
+  }
+  return SPAND_OK;
+}
+
+// ---------------------------------------------------------------- apply / PCG
+
+template <typename TF>
+static void apply_prec(spand_handle h, const std::vector<ApplyStep<TF>>& steps, double* x, cudaStream_t s) {
+  double* tmp = (double*)h->d_tmp.p;
+  double* save = (double*)h->d_save.p;
+  for (const ApplyStep<TF>& a : steps) {
+    if (a.n_elim) {
+      ensure_smem((const void*)k_elim_fwd<TF>, a.sm_elim_fwd);
+      k_elim_fwd<TF><<<a.n_elim, AT, a.sm_elim_fwd, s>>>(a.elim, a.slots, x, tmp);
+      CKLAUNCH();
+      if (a.ntgt) {
+        k_scatter_sub<<<(unsigned)std::min<int64_t>((a.ntgt + 255) / 256, 4096), 256, 0, s>>>(a.tslot, a.tptr, a.tidx,
+                                                                                              tmp, x, a.ntgt);
+        CKLAUNCH();
+      }
+    }
+    if (a.n_scale) {
+      ensure_smem((const void*)k_scale_fwd<TF>, a.sm_scale);
+      k_scale_fwd<TF><<<a.n_scale, AT, a.sm_scale, s>>>(a.scale, a.slots, x);
+      CKLAUNCH();
+    }
+    if (a.n_q) {
+      ensure_smem((const void*)k_q_fwd<TF>, a.sm_q_fwd);
+      k_q_fwd<TF><<<a.n_q, AT, a.sm_q_fwd, s>>>(a.q, a.slots, x, save);
+      CKLAUNCH();
+    }
+  }
+  for (auto it = steps.rbegin(); it != steps.rend(); ++it) {
+    const ApplyStep<TF>& a = *it;
+    if (a.n_q) {
+      ensure_smem((const void*)k_q_bwd<TF>, a.sm_q_bwd);
+      k_q_bwd<TF><<<a.n_q, AT, a.sm_q_bwd, s>>>(a.q, a.slots, x, save);
+      CKLAUNCH();
+    }
+    if (a.n_scale) {
+      ensure_smem((const void*)k_scale_bwd<TF>, a.sm_scale);
+      k_scale_bwd<TF><<<a.n_scale, AT, a.sm_scale, s>>>(a.scale, a.slots, x);
+      CKLAUNCH();
+    }
+    if (a.n_elim) {
+      ensure_smem((const void*)k_elim_bwd<TF>, a.sm_elim_bwd);
+      k_elim_bwd<TF><<<a.n_elim, AT, a.sm_elim_bwd, s>>>(a.elim, a.slots, x);
+      CKLAUNCH();
+    }
+  }
+}
+
+static void apply_any(spand_handle h, double* x, cudaStream_t s) {
+  if (h->fprec == SPAND_FP64) apply_prec<double>(h, h->apply64, x, s);
+  else apply_prec<float>(h, h->apply32, x, s);
+}
+
+static void ensure_solve_buffers(spand_handle h) {
+  const int64_t n = std::max<int64_t>(h->n, 1);
+  h->d_vec.ensure((size_t)(7 * n + RED_BLOCKS + 16) * sizeof(double));
+  h->d_tmp.ensure((size_t)std::max<int64_t>(h->tmp_len, 1) * sizeof(double));
+  h->d_save.ensure((size_t)std::max<int64_t>(h->save_len, 1) * sizeof(double));
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace spand
+
+// ==================================================================== C ABI
+
+#define API_BEGIN try {
+#define API_END                                              \
+  }                                                          \
+  catch (const Fail& f) {                                    \
+    g_err = f.msg;                                           \
+    return f.code;                                           \
+  }                                                          \
+  catch (const std::bad_alloc&) {                            \
+    g_err = "host allocation failed";                        \
+    return SPAND_ERR_OOM;                                    \
+  }                                                          \
+  catch (const std::exception& e) {                          \
+    g_err = e.what();                                        \
+    return SPAND_ERR_INVALID_ARG;                            \
+  }                                                          \
+  catch (...) {                                              \
+    g_err = "unknown error";                                 \
+    return SPAND_ERR_INVALID_ARG;                            \
+  }
+
+extern "C" {
+
+void spand_default_opts(spand_opts* o) {
+  if (!o) return;
+  o->levels = 8;
+  o->eps = 1e-2;
+  o->skip = 0;
+  o->precision = SPAND_FP64;
+  o->maxit = 500;
+  o->tol = 1e-10;
+}
+
+const char* spand_error_string(int code) {
+  switch (code) {
+    case SPAND_OK: return "ok";
+    case SPAND_ERR_INVALID_ARG: return "invalid argument";
+    case SPAND_ERR_NOT_SPD: return "matrix (or a pivot block) is not positive definite";
+    case SPAND_ERR_NO_CONVERGENCE: return "PCG did not converge within maxit";
+    case SPAND_ERR_CUDA: return "CUDA error";
+    case SPAND_ERR_OOM: return "out of memory";
+    case SPAND_ERR_STATE: return "call out of order";
+    default: return "unknown error code";
+  }
+}
+
+const char* spand_last_error(void) { return g_err.c_str(); }
+
+int spand_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals, const double* coords,
+                  int32_t dim, const spand_opts* opts, spand_handle* out) {
+  if (!out) { g_err = "out is NULL"; return SPAND_ERR_INVALID_ARG; }
+  *out = nullptr;
+  API_BEGIN
+  g_err.clear();
+  if (!opts) throw Fail{SPAND_ERR_INVALID_ARG, "opts is NULL"};
+  if (opts->levels < 1 || opts->levels > 30) throw Fail{SPAND_ERR_INVALID_ARG, "levels must be in [1, 30]"};
+  if (!(opts->eps >= 0.0)) throw Fail{SPAND_ERR_INVALID_ARG, "eps must be >= 0"};
+  if (opts->skip < 0) throw Fail{SPAND_ERR_INVALID_ARG, "skip must be >= 0"};
+  if (opts->precision != SPAND_FP64 && opts->precision != SPAND_FP32)
+    throw Fail{SPAND_ERR_INVALID_ARG, "unknown precision"};
+  if (opts->maxit < 1 || !(opts->tol > 0.0)) throw Fail{SPAND_ERR_INVALID_ARG, "maxit >= 1 and tol > 0 required"};
+  if (n > INT32_MAX - 1) throw Fail{SPAND_ERR_INVALID_ARG, "n too large"};
+  if (coords && (dim < 1 || dim > 8)) throw Fail{SPAND_ERR_INVALID_ARG, "dim must be in [1, 8]"};
+  std::string err;
+  if (validate_csr(n, rowptr, colind, err)) throw Fail{SPAND_ERR_INVALID_ARG, err};
+  const int64_t nnz = n ? rowptr[n] : 0;
+  if (nnz && !vals) throw Fail{SPAND_ERR_INVALID_ARG, "vals is NULL"};
+  auto t0 = std::chrono::steady_clock::now();
+  std::unique_ptr<spand_handle_s> h(new spand_handle_s());
+  h->opts = *opts;
+  h->n = n;
+  h->nnz = nnz;
+  h->rowptr.assign(rowptr, rowptr + n + 1);
+  h->colind.assign(colind, colind + nnz);
+  h->vals.assign(vals, vals + nnz);
+  if (analyze_tree(n, rowptr, colind, coords, dim, opts->levels, h->tree, err))
+    throw Fail{SPAND_ERR_INVALID_ARG, err};
+  const Tree& tr = h->tree;
+  // position of every vertex, its cluster and local index
+  std::vector<int32_t> pos(n), cl(n), loc(n);
+  for (int64_t i = 0; i < n; ++i) pos[tr.perm[i]] = (int32_t)i;
+  const int nc = (int)tr.cluster_ptr.size() - 1;
+  for (int c = 0; c < nc; ++c)
+    for (int32_t i = tr.cluster_ptr[c]; i < tr.cluster_ptr[c + 1]; ++i) {
+      cl[tr.perm[i]] = c;
+      loc[tr.perm[i]] = i - tr.cluster_ptr[c];
+    }
+  // step-1 assembly map (same row layout rule as the factorization)
+  const StepStruct& s1 = tr.steps.empty() ? StepStruct() : tr.steps[0];
+  h->asm_row.assign(nnz, -1);
+  h->asm_off.assign(nnz, 0);
+  if (n > 0) {
+    std::vector<int32_t> csz(nc);
+    for (int c = 0; c < nc; ++c) csz[c] = tr.cluster_ptr[c + 1] - tr.cluster_ptr[c];
+    std::vector<std::vector<std::pair<int32_t, int32_t>>> coff(nc);  // (neighbour, col offset)
+    for (int c = 0; c < nc; ++c) {
+      const bool el = s1.elim[c];
+      const int32_t b = el ? s1.adj_ptr[c] : s1.adjf_ptr[c];
+      const int32_t e = el ? s1.adj_ptr[c + 1] : s1.adjf_ptr[c + 1];
+      int32_t w = csz[c];
+      for (int32_t k = b; k < e; ++k) {
+        const int32_t q = el ? s1.adj_idx[k] : s1.adjf_idx[k];
+        coff[c].push_back({q, w});
+        w += csz[q];
+      }
+    }
+    for (int64_t v = 0; v < n; ++v)
+      for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+        const int32_t w = colind[e];
+        const int32_t ci = cl[v], cj = cl[w];
+        int32_t col = -1;
+        if (ci == cj) col = 0;
+        else {
+          auto& l = coff[ci];
+          auto it = std::lower_bound(l.begin(), l.end(), std::make_pair(cj, INT32_MIN));
+          if (it != l.end() && it->first == cj) col = it->second;
+        }
+        if (col < 0) continue;  // entry (n, s) of an eliminated s: held in s's row only
+        const int64_t ld = std::max<int32_t>(csz[ci], 1);
+        h->asm_row[e] = ci;
+        h->asm_off[e] = loc[v] + (int64_t)(col + loc[w]) * ld;
+      }
+  }
+  // A in cluster order
+  h->prow.assign(n + 1, 0);
+  h->pcol.resize(nnz);
+  h->pval_src.resize(nnz);
+  {
+    std::vector<std::pair<int32_t, int64_t>> rowbuf;
+    int64_t o = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      const int32_t v = tr.perm[i];
+      rowbuf.clear();
+      for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) rowbuf.push_back({pos[colind[e]], e});
+      std::sort(rowbuf.begin(), rowbuf.end());
+      for (auto& pr : rowbuf) {
+        h->pcol[o] = pr.first;
+        h->pval_src[o] = pr.second;
+        ++o;
+      }
+      h->prow[i + 1] = o;
+    }
+  }
+  h->st.t_analyze_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  *out = h.release();
+  return SPAND_OK;
+  API_END
+}
+
+int spand_factorize(spand_handle h, const double* vals, void* cuda_stream) {
+  if (!h) { g_err = "null handle"; return SPAND_ERR_INVALID_ARG; }
+  API_BEGIN
+  g_err.clear();
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  auto t0 = std::chrono::steady_clock::now();
+  h->factored = false;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (h->device >= 0 && h->device != dev) throw Fail{SPAND_ERR_STATE, "handle was factorized on another device"};
+  h->device = dev;
+  const int64_t n = h->n, nnz = h->nnz;
+  if (!h->consts_ready) {
+    h->d_asm_row.ensure(std::max<int64_t>(nnz, 1) * sizeof(int32_t));
+    h->d_asm_off.ensure(std::max<int64_t>(nnz, 1) * sizeof(int64_t));
+    h->d_prow.ensure((n + 1) * sizeof(int64_t));
+    h->d_pcol.ensure(std::max<int64_t>(nnz, 1) * sizeof(int32_t));
+    h->d_pval_src.ensure(std::max<int64_t>(nnz, 1) * sizeof(int64_t));
+    h->d_perm.ensure(std::max<int64_t>(n, 1) * sizeof(int32_t));
+    if (nnz) {
+      CK(cudaMemcpy(h->d_asm_row.p, h->asm_row.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(h->d_asm_off.p, h->asm_off.data(), nnz * sizeof(int64_t), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(h->d_pcol.p, h->pcol.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(h->d_pval_src.p, h->pval_src.data(), nnz * sizeof(int64_t), cudaMemcpyHostToDevice));
+    }
+    CK(cudaMemcpy(h->d_prow.p, h->prow.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+    if (n) CK(cudaMemcpy(h->d_perm.p, h->tree.perm.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+    h->consts_ready = true;
+  }
+  h->d_vals.ensure(std::max<int64_t>(nnz, 1) * sizeof(double));
+  h->d_pval.ensure(std::max<int64_t>(nnz, 1) * sizeof(double));
+  if (nnz) {
+    const double* src = vals ? vals : h->vals.data();
+    const bool dsrc = vals && is_device_ptr(vals);
+    CK(cudaMemcpyAsync(h->d_vals.p, src, nnz * sizeof(double), dsrc ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    if (vals && !dsrc) std::memcpy(h->vals.data(), vals, nnz * sizeof(double));
+    // permuted values for the SpMV: pval[k] = vals[pval_src[k]]
+    k_gather_vals<<<(unsigned)std::min<int64_t>((nnz + 255) / 256, 4096), 256, 0, s>>>(
+        nnz, (const int64_t*)h->d_pval_src.p, (const double*)h->d_vals.p, (double*)h->d_pval.p);
+    CKLAUNCH();
+  }
+  h->tmp_len = 0;
+  h->save_len = 0;
+  int rc;
+  if (h->opts.precision == SPAND_FP64) rc = factorize_impl<double>(h, s);
+  else rc = factorize_impl<float>(h, s);
+  h->fprec = h->opts.precision;
+  CK(cudaStreamSynchronize(s));
+  h->st.t_factor_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  h->st.device_bytes = (int64_t)(h->persist.bytes_held + h->descs.bytes_held + h->scratch[0].cap + h->scratch[1].cap);
+  const size_t esz = h->fprec == SPAND_FP64 ? 8 : 4;
+  h->st.apply_bytes = 2.0 * (double)h->st.mem_f * esz;
+  h->factored = rc == SPAND_OK;
+  return rc;
+  API_END
+}
+
+
+int spand_apply(spand_handle h, const double* r_dev, double* z_dev, void* cuda_stream) {
+  if (!h) { g_err = "null handle"; return SPAND_ERR_INVALID_ARG; }
+  API_BEGIN
+  g_err.clear();
+  if (!h->factored) throw Fail{SPAND_ERR_STATE, "spand_apply before a successful spand_factorize"};
+  if (h->n && (!r_dev || !z_dev)) throw Fail{SPAND_ERR_INVALID_ARG, "null vector"};
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  ensure_solve_buffers(h);
+  const int64_t n = h->n;
+  if (n == 0) return SPAND_OK;
+  double* w = (double*)h->d_vec.p;
+  const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+  k_permute<<<g, 256, 0, s>>>(n, (const int32_t*)h->d_perm.p, r_dev, w, 1);
+  CKLAUNCH();
+  apply_any(h, w, s);
+  k_permute<<<g, 256, 0, s>>>(n, (const int32_t*)h->d_perm.p, w, z_dev, 0);
+  CKLAUNCH();
+  CK(cudaStreamSynchronize(s));
+  return SPAND_OK;
+  API_END
+}
+
+int spand_solve(spand_handle h, const double* b, double* x, int32_t* iters, double* relres, void* cuda_stream) {
+  if (!h) { g_err = "null handle"; return SPAND_ERR_INVALID_ARG; }
+  API_BEGIN
+  g_err.clear();
+  if (!h->factored) throw Fail{SPAND_ERR_STATE, "spand_solve before a successful spand_factorize"};
+  const int64_t n = h->n;
+  if (n && (!b || !x)) throw Fail{SPAND_ERR_INVALID_ARG, "null vector"};
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  auto t0 = std::chrono::steady_clock::now();
+  ensure_solve_buffers(h);
+  if (n == 0) {
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0;
+    return SPAND_OK;
+  }
+  double* V = (double*)h->d_vec.p;
+  double *bp = V, *xv = V + n, *r = V + 2 * n, *z = V + 3 * n, *p = V + 4 * n, *q = V + 5 * n, *io = V + 6 * n;
+  double* part = V + 7 * n;
+  double* sc = part + RED_BLOCKS;  // scalars
+  const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+  CK(cudaMemcpyAsync(io, b, n * sizeof(double), bdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+  const int32_t* perm = (const int32_t*)h->d_perm.p;
+  const int64_t* rp = (const int64_t*)h->d_prow.p;
+  const int32_t* ci = (const int32_t*)h->d_pcol.p;
+  const double* va = (const double*)h->d_pval.p;
+  k_permute<<<g, 256, 0, s>>>(n, perm, io, bp, 1);
+  CKLAUNCH();
+  CK(cudaMemsetAsync(xv, 0, n * sizeof(double), s));
+  auto dot = [&](const double* a, const double* c, double* out) {
+    k_dot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, a, c, part);
+    CKLAUNCH();
+    k_reduce<<<1, RED_THREADS, 0, s>>>(part, RED_BLOCKS, out);
+    CKLAUNCH();
+  };
+  auto read = [&](const double* d) {
+    double v = 0;
+    CK(cudaMemcpyAsync(&v, d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return v;
+  };
+  cudaEvent_t e0, e1, e2;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventCreate(&e2));
+  double apply_ms = 0, spmv_ms = 0;
+  int napply = 0;
+  auto precond = [&](const double* src, double* dst) {
+    k_copy_vec<<<g, 256, 0, s>>>(n, src, dst);
+    CKLAUNCH();
+    CK(cudaEventRecord(e0, s));
+    apply_any(h, dst, s);
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    apply_ms += ms;
+    ++napply;
+  };
+  // sc: [0] rz, [1] pq, [2] rr, [3] rz_new, [4] bb
+  dot(bp, bp, sc + 4);
+  const double bnorm = std::sqrt(read(sc + 4));
+  int it = 0;
+  double rel = 0.0;
+  const double tol = h->opts.tol;
+  const int maxit = h->opts.maxit;
+  if (bnorm == 0.0) {
+    CK(cudaMemsetAsync(xv, 0, n * sizeof(double), s));
+  } else {
+    k_copy_vec<<<g, 256, 0, s>>>(n, bp, r);
+    CKLAUNCH();
+    precond(r, z);
+    k_copy_vec<<<g, 256, 0, s>>>(n, z, p);
+    CKLAUNCH();
+    int irz = 0, irzn = 3;
+    dot(r, z, sc + irz);
+    while (it < maxit) {
+      CK(cudaEventRecord(e2, s));
+      k_spmv_dot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, rp, ci, va, p, q, part);
+      CKLAUNCH();
+      k_reduce<<<1, RED_THREADS, 0, s>>>(part, RED_BLOCKS, sc + 1);
+      CKLAUNCH();
+      // alpha = rz / pq
+      if (irz != 0) {
+        k_copy_vec<<<1, 32, 0, s>>>(1, sc + irz, sc + 0);
+        CKLAUNCH();
+        irz = 0;
+        irzn = 3;
+      }
+      k_update_xr<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, sc, xv, r, p, q, part);
+      CKLAUNCH();
+      k_reduce<<<1, RED_THREADS, 0, s>>>(part, RED_BLOCKS, sc + 2);
+      CKLAUNCH();
+      CK(cudaEventRecord(e1, s));
+      ++it;
+      const double rr = read(sc + 2);
+      {
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, e2, e1));
+        spmv_ms += ms;
+      }
+      if (std::sqrt(rr) / bnorm <= tol) {
+        k_residual<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, rp, ci, va, xv, bp, r);
+        CKLAUNCH();
+        dot(r, r, sc + 2);
+        if (std::sqrt(read(sc + 2)) / bnorm <= tol) break;
+        precond(r, z);
+        k_copy_vec<<<g, 256, 0, s>>>(n, z, p);
+        CKLAUNCH();
+        dot(r, z, sc + 0);
+        continue;
+      }
+      precond(r, z);
+      dot(r, z, sc + irzn);
+      k_update_p<<<g, 256, 0, s>>>(n, sc + irzn, sc + irz, z, p);
+      CKLAUNCH();
+      std::swap(irz, irzn);
+    }
+    k_residual<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, rp, ci, va, xv, bp, q);
+    CKLAUNCH();
+    dot(q, q, sc + 2);
+    rel = std::sqrt(read(sc + 2)) / bnorm;
+  }
+  k_permute<<<g, 256, 0, s>>>(n, perm, xv, io, 0);
+  CKLAUNCH();
+  CK(cudaMemcpyAsync(x, io, n * sizeof(double), xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaEventDestroy(e2);
+  if (iters) *iters = it;
+  if (relres) *relres = rel;
+  h->st.n_cg = it;
+  h->st.relres = rel;
+  h->st.t_solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  h->phase_ms[4] = napply ? apply_ms / napply : 0.0;
+  h->phase_ms[5] = it ? spmv_ms / it : 0.0;
+  if (bnorm != 0.0 && !(rel <= tol)) {
+    g_err = "PCG stopped at maxit with relative residual " + std::to_string(rel);
+    return SPAND_ERR_NO_CONVERGENCE;
+  }
+  return SPAND_OK;
+  API_END
+}
+
+int spand_get_tree(spand_handle h, int32_t* perm, int32_t* cluster_ptr, int32_t* cluster_key, int32_t* n_clusters,
+                   int32_t* n_steps) {
+  if (!h || !n_clusters) { g_err = "null argument"; return SPAND_ERR_INVALID_ARG; }
+  const Tree& t = h->tree;
+  const int nc = (int)t.cluster_ptr.size() - 1;
+  *n_clusters = nc;
+  if (n_steps) *n_steps = t.L;
+  if (perm) std::copy(t.perm.begin(), t.perm.end(), perm);
+  if (cluster_ptr) std::copy(t.cluster_ptr.begin(), t.cluster_ptr.end(), cluster_ptr);
+  if (cluster_key) std::copy(t.keys.begin(), t.keys.end(), cluster_key);
+  return SPAND_OK;
+}
+
+int spand_get_step(spand_handle h, int32_t t, int32_t* counts, int32_t* keys, int32_t* child_ptr, int32_t* child_idx,
+                   int32_t* elim, int32_t* colour, int32_t* adj_ptr, int32_t* adj_idx, int32_t* adjf_ptr,
+                   int32_t* adjf_idx) {
+  if (!h || !counts) { g_err = "null argument"; return SPAND_ERR_INVALID_ARG; }
+  if (t < 1 || t > (int32_t)h->tree.steps.size()) { g_err = "step out of range"; return SPAND_ERR_INVALID_ARG; }
+  const StepStruct& s = h->tree.steps[t - 1];
+  counts[0] = s.n;
+  counts[1] = (int32_t)s.child_idx.size();
+  counts[2] = (int32_t)s.adj_idx.size();
+  counts[3] = (int32_t)s.adjf_idx.size();
+  counts[4] = s.ncolours();
+  auto cp = [](const std::vector<int32_t>& v, int32_t* d) { if (d) std::copy(v.begin(), v.end(), d); };
+  cp(s.keys, keys);
+  cp(s.child_ptr, child_ptr);
+  cp(s.child_idx, child_idx);
+  cp(s.elim, elim);
+  cp(s.colour, colour);
+  cp(s.adj_ptr, adj_ptr);
+  cp(s.adj_idx, adj_idx);
+  cp(s.adjf_ptr, adjf_ptr);
+  cp(s.adjf_idx, adjf_idx);
+  return SPAND_OK;
+}
+
+int spand_get_ranks(spand_handle h, int32_t t, int32_t* sizes_before, int32_t* sizes_after) {
+  if (!h) { g_err = "null handle"; return SPAND_ERR_INVALID_ARG; }
+  if (!h->factored) { g_err = "not factorized"; return SPAND_ERR_STATE; }
+  if (t < 1 || t > (int32_t)h->sizes_before.size()) { g_err = "step out of range"; return SPAND_ERR_INVALID_ARG; }
+  if (sizes_before) std::copy(h->sizes_before[t - 1].begin(), h->sizes_before[t - 1].end(), sizes_before);
+  if (sizes_after) std::copy(h->sizes_after[t - 1].begin(), h->sizes_after[t - 1].end(), sizes_after);
+  return SPAND_OK;
+}
+
+int spand_get_stats(spand_handle h, spand_stats* st) {
+  if (!h || !st) { g_err = "null argument"; return SPAND_ERR_INVALID_ARG; }
+  *st = h->st;
+  return SPAND_OK;
+}
+
+int spand_get_phase_times(spand_handle h, double* out6) {
+  if (!h || !out6) { g_err = "null argument"; return SPAND_ERR_INVALID_ARG; }
+  for (int i = 0; i < 6; ++i) out6[i] = h->phase_ms[i];
+  return SPAND_OK;
+}
+
+void spand_destroy(spand_handle h) { delete h; }
+
+}  // extern "C"

@@ -1,0 +1,79 @@
+"""Convenience wrapper over the C ABI (argument marshalling only)."""
+from __future__ import annotations
+
+from typing import Optional
+
+import numpy as np
+
+from . import _lib as L
+
+
+def _addr(a):
+    """Address of a contiguous float64 numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+        return a.ctypes.data
+    assert str(a.dtype) == "torch.float64" and a.is_contiguous()
+    return a.data_ptr()
+
+
+class Solver:
+    """analyze -> factorize -> solve on one CSR matrix.
+
+    Parameters follow ``spand_opts``: levels (L of Algorithm 3), eps, skip,
+    precision ("fp64" or "fp32"), maxit, tol.
+    """
+
+    def __init__(self, rowptr, colind, vals, coords=None, levels: int = 8, eps: float = 1e-2, skip: int = 0,
+                 precision: str = "fp64", maxit: int = 500, tol: float = 1e-10):
+        prec = {"fp64": L.SPAND_FP64, "fp32": L.SPAND_FP32}[precision]
+        self.opts = L.default_opts(levels=levels, eps=eps, skip=skip, precision=prec, maxit=maxit, tol=tol)
+        self.n = int(np.asarray(rowptr).size - 1)
+        self.h = L.spand_analyze(rowptr, colind, vals, coords, self.opts)
+
+    @classmethod
+    def from_problem(cls, prob, use_coords: bool = True, **kw):
+        return cls(prob.rowptr, prob.colind, prob.vals, prob.coords if use_coords else None, **kw)
+
+    def factorize(self, vals=None, stream: int = 0):
+        L.spand_factorize(self.h, None if vals is None else _addr(vals), stream)
+        return self
+
+    def solve(self, b, x=None, stream: int = 0, check: bool = True):
+        """b: float64 numpy array (host) or torch CUDA tensor; returns (x, iters, relres)."""
+        if x is None:
+            x = np.empty(self.n) if isinstance(b, np.ndarray) else b.new_empty(b.shape)
+        rc, it, rr = L.spand_solve(self.h, _addr(b), _addr(x), stream, check=check)
+        return x, it, rr
+
+    def apply(self, r, z=None, stream: int = 0):
+        if z is None:
+            z = r.new_empty(r.shape)
+        L.spand_apply(self.h, _addr(r), _addr(z), stream)
+        return z
+
+    def tree(self) -> dict:
+        return L.spand_get_tree(self.h)
+
+    def step(self, t: int) -> dict:
+        return L.spand_get_step(self.h, t)
+
+    def ranks(self, t: int):
+        return L.spand_get_ranks(self.h, t)
+
+    def stats(self):
+        return L.spand_get_stats(self.h)
+
+    def phase_times(self):
+        return L.spand_get_phase_times(self.h)
+
+    def close(self):
+        if self.h:
+            L.spand_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,90 @@
+"""The C ABI loads, exports every declared symbol, and rejects bad input on
+the host (no GPU needed for these checks)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1901_02971_gb300 import _lib as L
+from paper_1901_02971_gb300 import inputs as I
+
+HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "spand.h")
+
+
+def declared():
+    txt = open(HDR).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(spand_[a-z_]+)\s*\(", txt)))
+
+
+def test_header_and_binding_agree():
+    assert declared() == sorted(L.EXPORTS)
+
+
+def test_every_symbol_exported(spand_lib):
+    for name in declared():
+        assert hasattr(spand_lib, name), name
+
+
+def test_error_strings(spand_lib):
+    for code in range(7):
+        assert spand_lib.spand_error_string(code)
+
+
+def _analyze_rc(rowptr, colind, vals, levels=3):
+    o = L.default_opts(levels=levels)
+    h = C.c_void_p()
+    rowptr = np.ascontiguousarray(rowptr, np.int64)
+    colind = np.ascontiguousarray(colind, np.int32)
+    vals = np.ascontiguousarray(vals, np.float64)
+    rc = L.lib().spand_analyze(rowptr.size - 1, rowptr.ctypes.data, colind.ctypes.data, vals.ctypes.data, None, 0,
+                               C.byref(o), C.byref(h))
+    if h.value:
+        L.spand_destroy(h.value)
+    return rc
+
+
+def test_malformed_csr_rejected(spand_lib):
+    p = I.laplacian_2d(4)
+    assert _analyze_rc(p.rowptr, p.colind, p.vals) == L.SPAND_OK
+    # non-symmetric pattern: drop one off-diagonal entry of row 0
+    rp, ci, va = p.rowptr.copy(), p.colind.copy(), p.vals.copy()
+    k = int(rp[0]) + 1
+    ci2 = np.delete(ci, k)
+    va2 = np.delete(va, k)
+    rp2 = rp.copy()
+    rp2[1:] -= 1
+    assert _analyze_rc(rp2, ci2, va2) == L.SPAND_ERR_INVALID_ARG
+    # unsorted columns in a row
+    ci3 = ci.copy()
+    ci3[rp[1]], ci3[rp[1] + 1] = ci3[rp[1] + 1], ci3[rp[1]]
+    assert _analyze_rc(rp, ci3, va) == L.SPAND_ERR_INVALID_ARG
+    # column out of range
+    ci4 = ci.copy()
+    ci4[-1] = p.n
+    assert _analyze_rc(rp, ci4, va) == L.SPAND_ERR_INVALID_ARG
+    # bad levels
+    assert _analyze_rc(rp, ci, va, levels=0) == L.SPAND_ERR_INVALID_ARG
+    assert "levels" in L.lib().spand_last_error().decode()
+
+
+def test_missing_diagonal_rejected(spand_lib):
+    rowptr = np.array([0, 1, 2], np.int64)
+    colind = np.array([1, 0], np.int32)
+    assert _analyze_rc(rowptr, colind, np.ones(2)) == L.SPAND_ERR_INVALID_ARG
+
+
+def test_solve_before_factorize_is_state_error(spand_lib):
+    p = I.laplacian_2d(4)
+    h = L.spand_analyze(p.rowptr, p.colind, p.vals, p.coords, L.default_opts(levels=2))
+    try:
+        b = np.ones(p.n)
+        x = np.zeros(p.n)
+        rc, _, _ = L.spand_solve(h, b.ctypes.data, x.ctypes.data, check=False)
+        assert rc == L.SPAND_ERR_STATE
+        with pytest.raises(L.SpandError):
+            L.spand_get_ranks(h, 1)
+    finally:
+        L.spand_destroy(h)

@@ -1,0 +1,52 @@
+"""Host analysis (C++, in libspand.so) against the oracle's independent
+implementation of Algorithm 3 and the per-step symbolic structure: every
+integer output must match bit for bit."""
+import numpy as np
+import pytest
+
+from oracle import spand_oracle as O
+from paper_1901_02971_gb300 import _lib as L
+from paper_1901_02971_gb300 import inputs as I
+
+
+def _compare(p, levels, geo=True):
+    coords = p.coords if geo else None
+    ref = O.flat_tree(O.analyze(p.n, p.rowptr, p.colind, coords, levels))
+    h = L.spand_analyze(p.rowptr, p.colind, p.vals, coords, L.default_opts(levels=levels))
+    try:
+        got = L.spand_get_tree(h)
+        for k in ("perm", "cluster_ptr", "keys"):
+            assert np.array_equal(got[k], ref[k]), k
+        assert got["n_steps"] == levels
+        for t in range(1, levels + 1):
+            gs = L.spand_get_step(h, t)
+            rs = ref[f"step{t}"]
+            for k in rs:
+                assert np.array_equal(gs[k], rs[k]), (t, k)
+    finally:
+        L.spand_destroy(h)
+
+
+CASES = [
+    ("lapl2d_8_L3", lambda: I.laplacian_2d(8), 3, True),
+    ("lapl2d_64_L8", lambda: I.laplacian_2d(64), 8, True),
+    ("lapl2d_37_L6", lambda: I.laplacian_2d(37), 6, True),
+    ("lapl2d_5_L7", lambda: I.laplacian_2d(5), 7, True),
+    ("lapl3d_16_L6", lambda: I.laplacian_3d(16), 6, True),
+    ("diff3d_12_L5", lambda: I.diffusion_3d(12, 2, block=3), 5, True),
+    ("diff2d_30_L6_nogeo", lambda: I.diffusion_2d(30, 4), 6, False),
+    ("knn_3000_L7", lambda: I.knn_laplacian(3000, 10, 3), 7, False),
+    ("lapl2d_1_L1", lambda: I.laplacian_2d(1), 1, True),
+    ("lapl2d_2_L3", lambda: I.laplacian_2d(2), 3, True),
+]
+
+
+@pytest.mark.parametrize("name,gen,levels,geo", CASES, ids=[c[0] for c in CASES])
+def test_analyze_bitexact(spand_lib, name, gen, levels, geo):
+    _compare(gen(), levels, geo)
+
+
+@pytest.mark.slow
+def test_analyze_bitexact_3d_64(spand_lib):
+    """The benchmark workload itself: 7-point Laplacian on 64^3, L = 10."""
+    _compare(I.laplacian_3d(64), 10, True)
