@@ -178,6 +178,29 @@ int spand_get_stats(spand_handle h, spand_stats* st);
  * vector update (last solve, mean). */
 int spand_get_phase_times(spand_handle h, double* out6);
 
+/*
+ * Kernel-family profile (for roofline reporting; not part of the method).
+ * spand_set_profiling(h, 1) makes later factorize/solve/apply calls bracket
+ * each batch of launches of one family with a CUDA event pair on the
+ * launching stream (adds a few microseconds per batch).  Families:
+ */
+enum {
+  SPAND_K_POTRF = 0,  /* pivot Cholesky tiles (Sec. 2.4, 2.5) */
+  SPAND_K_TRSM = 1,   /* block-row triangular solves and pivot inverses */
+  SPAND_K_SCHUR = 2,  /* Schur-complement update (Sec. 2.4) */
+  SPAND_K_CPQR = 3,   /* sparsification QR (Sec. 2.6.1), all colours of a level */
+  SPAND_K_COPY = 4,   /* merge gathers and transpose mirrors (Sec. 2.7) */
+  SPAND_K_APPLY = 5,  /* one z = M M^T r (Sec. 2.8) */
+  SPAND_K_PCG = 6     /* SpMV + fused PCG vector update, one iteration */
+};
+int spand_set_profiling(spand_handle h, int32_t on);
+/* out4: batches' launches, summed device ms, algorithmic flops, algorithmic
+ * bytes, accumulated since the last reset. */
+int spand_get_kernel_profile(spand_handle h, int32_t family, double* out4);
+int spand_reset_kernel_profile(spand_handle h);
+/* Kernels launched by this handle since it was created (always counted). */
+int spand_get_launch_count(spand_handle h, int64_t* launches);
+
 void spand_destroy(spand_handle h);
 
 const char* spand_error_string(int code);

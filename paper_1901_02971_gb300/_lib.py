@@ -30,7 +30,10 @@ SPAND_FP32 = 1
 # every function declared in include/spand.h
 EXPORTS = ["spand_default_opts", "spand_analyze", "spand_factorize", "spand_solve", "spand_apply",
            "spand_get_tree", "spand_get_step", "spand_get_ranks", "spand_get_stats",
-           "spand_get_phase_times", "spand_destroy", "spand_error_string", "spand_last_error"]
+           "spand_get_phase_times", "spand_set_profiling", "spand_get_kernel_profile",
+           "spand_reset_kernel_profile", "spand_get_launch_count", "spand_destroy", "spand_error_string",
+           "spand_last_error"]
+KERNEL_FAMILIES = ["potrf", "trsm", "schur", "cpqr", "copy", "apply", "pcg"]
 
 
 class Opts(C.Structure):
@@ -75,6 +78,10 @@ def lib():
     L.spand_get_ranks.argtypes = [C.c_void_p, C.c_int32, P, P]
     L.spand_get_stats.argtypes = [C.c_void_p, C.POINTER(Stats)]
     L.spand_get_phase_times.argtypes = [C.c_void_p, P]
+    L.spand_set_profiling.argtypes = [C.c_void_p, C.c_int32]
+    L.spand_get_kernel_profile.argtypes = [C.c_void_p, C.c_int32, P]
+    L.spand_reset_kernel_profile.argtypes = [C.c_void_p]
+    L.spand_get_launch_count.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
     L.spand_destroy.argtypes = [C.c_void_p]
     L.spand_destroy.restype = None
     L.spand_error_string.argtypes = [C.c_int]
@@ -190,6 +197,30 @@ def spand_get_phase_times(h: int) -> np.ndarray:
     out = np.zeros(6, dtype=np.float64)
     _check(lib().spand_get_phase_times(h, _ptr(out)))
     return out
+
+
+def spand_set_profiling(h: int, on: bool):
+    _check(lib().spand_set_profiling(h, 1 if on else 0))
+
+
+def spand_get_kernel_profile(h: int) -> dict:
+    """family -> dict(launches, ms, flops, bytes)."""
+    out = {}
+    buf = np.zeros(4)
+    for i, name in enumerate(KERNEL_FAMILIES):
+        _check(lib().spand_get_kernel_profile(h, i, _ptr(buf)))
+        out[name] = {"launches": int(buf[0]), "ms": float(buf[1]), "flops": float(buf[2]), "bytes": float(buf[3])}
+    return out
+
+
+def spand_reset_kernel_profile(h: int):
+    _check(lib().spand_reset_kernel_profile(h))
+
+
+def spand_get_launch_count(h: int) -> int:
+    v = C.c_int64(0)
+    _check(lib().spand_get_launch_count(h, C.byref(v)))
+    return v.value
 
 
 def spand_destroy(h: int):

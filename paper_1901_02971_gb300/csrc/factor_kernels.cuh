@@ -18,9 +18,10 @@ struct RowDesc {      // a cluster's block row or its diagonal block
 };
 
 template <typename T>
-struct TrsmTask {     // X = U^{-T} B for columns [c0, c1) of a block row (U = its diag block)
-  T* R;
-  int32_t n, ld, c0, c1;
+struct TrsmTask {     // B <- U^{-T} B: U upper n x n, B n x nc (rows < i_start of B are zero)
+  const T* U;
+  T* B;
+  int32_t n, ldu, ldb, nc, i_start, pad;
 };
 
 template <typename T>
@@ -51,22 +52,6 @@ struct CopyTask {     // dst[r + c*ldd] = src[r + c*lds] (trans = 0) or src[c + 
 
 struct CopyTile {
   int32_t task, r0, c0;
-};
-
-template <typename T>
-struct CpqrNbr {      // neighbour q of p in the sparsified row A_pn (Sec. 2.6.1)
-  T* Rq;              // q's block row (leading dimension ldq)
-  int32_t q, off_pq, off_qp, ldq;
-};
-
-template <typename T>
-struct CpqrTask {
-  T* Rp;              // p's block row
-  T* work;            // |p| x m_max workspace
-  T* norms;           // m_max
-  int32_t* piv;       // m_max
-  T* Qc;              // |p| x |p| capacity (first r columns = Q_pc on exit)
-  int32_t p, np, ldp, nbeg, nend, m_max;
 };
 
 // ---------------------------------------------------------------- assembly
@@ -143,8 +128,9 @@ __global__ void __launch_bounds__(NT) k_potrf_update(const RowDesc<T>* __restric
   sub_store(acc, d.R + i0 + (size_t)j0 * d.ld, d.ld, mi, nj);
 }
 
-// X = U^{-T} B for one 64-column panel of a block row: left-looking over the
-// row tiles (B_i -= sum_{l<i} U_li^T X_l; X_i = U_ii^{-T} B_i).
+// B <- U^{-T} B for one panel of at most 64 columns, left-looking over the
+// row tiles (B_i -= sum_{l<i} U_li^T X_l; X_i = U_ii^{-T} B_i).  Rows of B
+// above i_start are zero (identity right-hand sides) and are skipped.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_trsm_cols(const TrsmTask<T>* __restrict__ tasks) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -152,17 +138,18 @@ __global__ void __launch_bounds__(NT) k_trsm_cols(const TrsmTask<T>* __restrict_
   SqTile<T>& B = *reinterpret_cast<SqTile<T>*>(smraw + sizeof(SqTile<T>));
   TileSmem<T>& sm = *reinterpret_cast<TileSmem<T>*>(smraw + 2 * sizeof(SqTile<T>));
   const TrsmTask<T> d = tasks[blockIdx.x];
-  const int nc = d.c1 - d.c0;
+  const int nc = d.nc;
   if (nc <= 0 || d.n <= 0) return;
-  T* X = d.R + (size_t)d.c0 * d.ld;
+  T* X = d.B;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  for (int i0 = 0; i0 < d.n; i0 += TB) {
+  const int is = (d.i_start / TB) * TB;
+  for (int i0 = is; i0 < d.n; i0 += TB) {
     const int nb = min(TB, d.n - i0);
     T acc[4][4];
     zero_acc(acc);
-    if (i0 > 0) tn_acc(acc, d.R + (size_t)i0 * d.ld, d.ld, nb, X, d.ld, nc, i0, sm);
-    load_tile(U, d.R + i0 + (size_t)i0 * d.ld, d.ld, nb, nb);
-    load_tile(B, X + i0, d.ld, nb, nc);
+    if (i0 > is) tn_acc(acc, d.U + is + (size_t)i0 * d.ldu, d.ldu, nb, X + is, d.ldb, nc, i0 - is, sm);
+    load_tile(U, d.U + i0 + (size_t)i0 * d.ldu, d.ldu, nb, nb);
+    load_tile(B, X + i0, d.ldb, nb, nc);
     __syncthreads();
 #pragma unroll
     for (int ii = 0; ii < 4; ++ii)
@@ -173,7 +160,7 @@ __global__ void __launch_bounds__(NT) k_trsm_cols(const TrsmTask<T>* __restrict_
       }
     __syncthreads();
     trsm_tile_upperT(U, B, nb, nc);
-    store_tile(B, X + i0, d.ld, nb, nc);
+    store_tile(B, X + i0, d.ldb, nb, nc);
     __syncthreads();
   }
 }
@@ -252,230 +239,6 @@ __global__ void k_set_identity(const RowDesc<T>* __restrict__ rows, int nrows) {
     const int i = (int)(e % d.n), j = (int)(e / d.n);
     d.R[i + (size_t)j * d.ld] = (i == j) ? T(1) : T(0);
   }
-}
-
-// ---------------------------------------------------------------- sparsification
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Orthogonal sparsification of one scaled interface p (Sec. 2.6.1), one CTA:
-//   gather A_pn (all current neighbour columns, in neighbour order) ->
-//   Householder QR with column pivoting (largest remaining column norm, lowest
-//   index on ties; norms recomputed exactly after every reflector) ->
-//   stop at the first k with |R_kk| < eps |R_00| (truncation rule of Sec. 4) ->
-//   write W_cn = R[0:r, :] P^T into p's row and its transpose into the rows of
-//   the neighbours, set A_cc = I, form Q_pc = H_0 ... H_{r-1} [I_r; 0].
-// The fine dofs f are dropped (their coupling W_fn is O(eps)).
-template <typename T>
-__global__ void __launch_bounds__(NT) k_cpqr(const CpqrTask<T>* __restrict__ tasks,
-                                            const int32_t* __restrict__ list,
-                                            const CpqrNbr<T>* __restrict__ nbrs,
-                                            int32_t* __restrict__ cur_size, T eps) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const CpqrTask<T> d = tasks[list[blockIdx.x]];
-  const int np = d.np;
-  const int nnb = d.nend - d.nbeg;
-  // shared: cstart[nnb+1] ints, v[np] T, red scratch
-  int* cstart = reinterpret_cast<int*>(smraw);
-  T* sv = reinterpret_cast<T*>(smraw + ((sizeof(int) * (nnb + 1) + 15) & ~size_t(15)));
-  __shared__ T red_v[NT / 32];
-  __shared__ int red_i[NT / 32];
-  __shared__ T s_beta, s_tau, s_r00;
-  __shared__ int s_piv, s_stop;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NT / 32;
-  if (tid == 0) {
-    int m = 0;
-    for (int e = 0; e < nnb; ++e) {
-      cstart[e] = m;
-      m += cur_size[nbrs[d.nbeg + e].q];
-    }
-    cstart[nnb] = m;
-  }
-  __syncthreads();
-  const int m = cstart[nnb];
-  if (m == 0) {  // every neighbour already reduced to nothing: no coupling left, p is kept
-    for (int64_t x = tid; x < (int64_t)np * np; x += NT) {
-      const int i = (int)(x % np), j = (int)(x / np);
-      d.Qc[i + (size_t)j * np] = (i == j) ? T(1) : T(0);
-    }
-    if (tid == 0) cur_size[d.p] = np;
-    return;
-  }
-  T* W = d.work;  // np x m, ld = np
-  // gather
-  for (int e = 0; e < nnb; ++e) {
-    const CpqrNbr<T> nb = nbrs[d.nbeg + e];
-    const int w = cstart[e + 1] - cstart[e];
-    const T* src = d.Rp + (size_t)nb.off_pq * d.ldp;
-    T* dst = W + (size_t)cstart[e] * np;
-    for (int64_t x = tid; x < (int64_t)np * w; x += NT) {
-      const int i = (int)(x % np), j = (int)(x / np);
-      dst[i + (size_t)j * np] = src[i + (size_t)j * d.ldp];
-    }
-  }
-  __syncthreads();
-  // column norms (squared) and identity pivots
-  for (int j = warp; j < m; j += nw) {
-    T s = 0;
-    for (int i = lane; i < np; i += 32) {
-      const T x = W[i + (size_t)j * np];
-      s += x * x;
-    }
-    s = warp_sum(s);
-    if (lane == 0) { d.norms[j] = s; d.piv[j] = j; }
-  }
-  __syncthreads();
-  const int kmax = min(np, m);
-  int r = kmax;
-  for (int k = 0; k < kmax; ++k) {
-    // pivot: argmax norms[j], j >= k (lowest j on ties)
-    T best = T(-1);
-    int bj = m;
-    for (int j = k + tid; j < m; j += NT) {
-      const T v = d.norms[j];
-      if (v > best) { best = v; bj = j; }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const T ov = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-      if (ov > best || (ov == best && oj < bj)) { best = ov; bj = oj; }
-    }
-    if (lane == 0) { red_v[warp] = best; red_i[warp] = bj; }
-    __syncthreads();
-    if (tid == 0) {
-      T bv = red_v[0];
-      int bi = red_i[0];
-      for (int w = 1; w < nw; ++w)
-        if (red_v[w] > bv || (red_v[w] == bv && red_i[w] < bi)) { bv = red_v[w]; bi = red_i[w]; }
-      s_piv = (bi >= k && bi < m) ? bi : k;
-    }
-    __syncthreads();
-    const int pj = s_piv;
-    if (pj != k) {  // swap columns k and pj
-      for (int i = tid; i < np; i += NT) {
-        const T a = W[i + (size_t)k * np];
-        W[i + (size_t)k * np] = W[i + (size_t)pj * np];
-        W[i + (size_t)pj * np] = a;
-      }
-      if (tid == 0) {
-        const T a = d.norms[k]; d.norms[k] = d.norms[pj]; d.norms[pj] = a;
-        const int b = d.piv[k]; d.piv[k] = d.piv[pj]; d.piv[pj] = b;
-      }
-    }
-    __syncthreads();
-    // Householder vector of W[k:np, k]
-    T s = 0;
-    for (int i = k + 1 + tid; i < np; i += NT) {
-      const T x = W[i + (size_t)k * np];
-      s += x * x;
-    }
-    s = warp_sum(s);
-    if (lane == 0) red_v[warp] = s;
-    __syncthreads();
-    if (tid == 0) {
-      T sig = 0;
-      for (int w = 0; w < nw; ++w) sig += red_v[w];
-      const T alpha = W[k + (size_t)k * np];
-      T beta, tau;
-      if (sig == T(0)) {
-        beta = alpha;
-        tau = T(0);
-      } else {
-        const T nrm = sqrt(alpha * alpha + sig);
-        beta = alpha >= T(0) ? -nrm : nrm;
-        tau = (beta - alpha) / beta;
-      }
-      const T rkk = fabs(beta);
-      if (k == 0) s_r00 = rkk;
-      // prefix rule |R_kk| >= eps |R_00|; R_00 = 0 means A_pn = 0 (r = 0)
-      s_stop = (s_r00 == T(0)) || (rkk < eps * s_r00);
-      s_beta = beta;
-      s_tau = tau;
-      sv[k] = T(1);
-    }
-    __syncthreads();
-    if (s_stop) { r = k; break; }
-    const T beta = s_beta, tau = s_tau;
-    const T alpha = W[k + (size_t)k * np];
-    const T scal = (tau == T(0)) ? T(0) : T(1) / (alpha - beta);
-    for (int i = k + 1 + tid; i < np; i += NT) {
-      const T v = W[i + (size_t)k * np] * scal;
-      W[i + (size_t)k * np] = v;
-      sv[i] = v;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      W[k + (size_t)k * np] = beta;
-      d.norms[k] = tau;  // column k is done: keep tau where its norm was
-    }
-    // apply H = I - tau v v^T to columns j > k; refresh their trailing norms
-    for (int j = k + 1 + warp; j < m; j += nw) {
-      T* col = W + (size_t)j * np;
-      T wdot = 0;
-      for (int i = k + lane; i < np; i += 32) wdot += sv[i] * col[i];
-      wdot = warp_sum(wdot) * tau;
-      T nrm = 0;
-      for (int i = k + lane; i < np; i += 32) {
-        const T x = col[i] - wdot * sv[i];
-        col[i] = x;
-        if (i > k) nrm += x * x;
-      }
-      nrm = warp_sum(nrm);
-      if (lane == 0) d.norms[j] = nrm;
-    }
-    __syncthreads();
-  }
-  // ---- write back W_cn = R[0:r, :] P^T into p's row and the transposes
-  // column position j holds original column piv[j]
-  for (int64_t x = tid; x < (int64_t)r * m; x += NT) {
-    const int i = (int)(x % r), j = (int)(x / r);
-    const T val = (j < r && i > j) ? T(0) : W[i + (size_t)j * np];
-    const int oc = d.piv[j];
-    // neighbour owning original column oc
-    int lo = 0, hi = nnb - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (cstart[mid] <= oc) lo = mid; else hi = mid - 1;
-    }
-    const CpqrNbr<T> nb = nbrs[d.nbeg + lo];
-    const int cc = oc - cstart[lo];
-    d.Rp[i + (size_t)(nb.off_pq + cc) * d.ldp] = val;
-    nb.Rq[cc + (size_t)(nb.off_qp + i) * nb.ldq] = val;
-  }
-  // A_cc = I
-  for (int64_t x = tid; x < (int64_t)r * r; x += NT) {
-    const int i = (int)(x % r), j = (int)(x / r);
-    d.Rp[i + (size_t)j * d.ldp] = (i == j) ? T(1) : T(0);
-  }
-  __syncthreads();
-  // Q_pc = H_0 H_1 ... H_{r-1} [I_r; 0]   (applied right to left)
-  T* G = d.Qc;
-  for (int64_t x = tid; x < (int64_t)np * r; x += NT) {
-    const int i = (int)(x % np), j = (int)(x / np);
-    G[i + (size_t)j * np] = (i == j) ? T(1) : T(0);
-  }
-  __syncthreads();
-  for (int k = r - 1; k >= 0; --k) {
-    const T tau = d.norms[k];
-    if (tau != T(0)) {
-      for (int j = k + warp; j < r; j += nw) {
-        T* col = G + (size_t)j * np;
-        T wdot = (lane == 0) ? col[k] : T(0);  // v_k[k] = 1
-        for (int i = k + 1 + lane; i < np; i += 32) wdot += W[i + (size_t)k * np] * col[i];
-        wdot = warp_sum(wdot);
-        if (lane == 0) col[k] -= tau * wdot;
-        for (int i = k + 1 + lane; i < np; i += 32) col[i] -= tau * wdot * W[i + (size_t)k * np];
-      }
-    }
-    __syncthreads();
-  }
-  if (tid == 0) cur_size[d.p] = r;
 }
 
 }  // namespace spand

@@ -9,7 +9,9 @@
 // sparsification transform is kept as the explicit coarse basis Q_pc: since
 // the fine dofs are identity in M^T A M, Q_p [c; f] = r_p + Q_pc (c - c_old)
 // with r_p the forward input, so only Q_pc (|p| x r) and the forward input
-// (saved per apply) are needed.
+// (saved per apply) are needed.  Triangular solves with the pivot factors use
+// their explicit inverses Y = U^{-T} (formed once by the factorization), so
+// every step of the apply is a set of independent, coalesced GEMVs.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -22,6 +24,7 @@ constexpr int AT = 256;  // threads per CTA of the apply kernels
 template <typename TF>
 struct ElimOp {
   const TF* R;       // [U_s | X^T], ns x (ns + m), ld = ns
+  const TF* Y;       // U_s^{-T} (lower, ns x ns, ld = ns)
   int32_t ns, m;
   int64_t slot;      // ns slots of s, then m slots of the neighbour columns
   int64_t tmp;       // m entries of the forward update
@@ -29,7 +32,7 @@ struct ElimOp {
 
 template <typename TF>
 struct ScaleOp {
-  const TF* U;       // np x np upper, ld = np
+  const TF* Y;       // U_p^{-T} (lower, np x np, ld = np)
   int32_t np, pad;
   int64_t slot;
 };
@@ -48,59 +51,23 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// Solve U^T y = b in place (y in shared memory), U upper n x n, ld = n.
+// y = Y x, Y lower n x n (ld n): one thread per row (coalesced over rows).
 template <typename TF>
-__device__ void trsv_upperT_cta(const TF* __restrict__ U, int n, double* y) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int b0 = 0; b0 < n; b0 += 32) {
-    const int nb = min(32, n - b0);
-    if (warp == 0) {
-      double bj = lane < nb ? y[b0 + lane] : 0.0;
-      for (int i = 0; i < nb; ++i) {
-        double yi = 0.0;
-        if (lane == i) yi = bj / (double)U[(b0 + i) + (size_t)(b0 + i) * n];
-        yi = __shfl_sync(0xffffffffu, yi, i);
-        if (lane == i) bj = yi;
-        else if (lane > i && lane < nb) bj -= (double)U[(b0 + i) + (size_t)(b0 + lane) * n] * yi;
-      }
-      if (lane < nb) y[b0 + lane] = bj;
-    }
-    __syncthreads();
-    for (int l = b0 + nb + warp; l < n; l += nw) {
-      double s = lane < nb ? (double)U[(b0 + lane) + (size_t)l * n] * y[b0 + lane] : 0.0;
-      s = warp_sum_d(s);
-      if (lane == 0) y[l] -= s;
-    }
-    __syncthreads();
+__device__ __forceinline__ void trmv_lower_cta(const TF* __restrict__ Y, int n, const double* x, double* y) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j <= i; ++j) s += (double)Y[i + (size_t)j * n] * x[j];
+    y[i] = s;
   }
 }
 
-// Solve U y = b in place (y in shared memory), U upper n x n, ld = n.
+// y_j = sum_{i >= j} Y[i, j] x_i  (y = Y^T x): one warp per output.
 template <typename TF>
-__device__ void trsv_upper_cta(const TF* __restrict__ U, int n, double* y) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nblk = (n + 31) / 32;
-  for (int bk = nblk - 1; bk >= 0; --bk) {
-    const int b0 = bk * 32, nb = min(32, n - b0);
-    if (warp == 0) {
-      double bj = lane < nb ? y[b0 + lane] : 0.0;
-      for (int i = nb - 1; i >= 0; --i) {
-        double yi = 0.0;
-        if (lane == i) yi = bj / (double)U[(b0 + i) + (size_t)(b0 + i) * n];
-        yi = __shfl_sync(0xffffffffu, yi, i);
-        if (lane == i) bj = yi;
-        else if (lane < i) bj -= (double)U[(b0 + lane) + (size_t)(b0 + i) * n] * yi;
-      }
-      if (lane < nb) y[b0 + lane] = bj;
-    }
-    __syncthreads();
-    for (int l = threadIdx.x; l < b0; l += blockDim.x) {
-      double s = 0.0;
-      for (int i = 0; i < nb; ++i) s += (double)U[l + (size_t)(b0 + i) * n] * y[b0 + i];
-      y[l] -= s;
-    }
-    __syncthreads();
-  }
+__device__ __forceinline__ void trmv_lowerT_warp(const TF* __restrict__ Y, int n, const double* x, int j, double& out) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int i = j + lane; i < n; i += 32) s += (double)Y[i + (size_t)j * n] * x[i];
+  out = warp_sum_d(s);
 }
 
 // ---------------------------------------------------------------- forward sweep
@@ -108,16 +75,19 @@ __device__ void trsv_upper_cta(const TF* __restrict__ U, int n, double* y) {
 template <typename TF>
 __global__ void __launch_bounds__(AT) k_elim_fwd(const ElimOp<TF>* __restrict__ ops, const int32_t* __restrict__ slots,
                                                 double* __restrict__ x, double* __restrict__ tmp) {
-  extern __shared__ double ys[];
+  extern __shared__ double sh[];
   const ElimOp<TF> o = ops[blockIdx.x];
   const int32_t* sl = slots + o.slot;
-  for (int i = threadIdx.x; i < o.ns; i += blockDim.x) ys[i] = x[sl[i]];
+  double* xs = sh;
+  double* ys = sh + o.ns;
+  for (int i = threadIdx.x; i < o.ns; i += blockDim.x) xs[i] = x[sl[i]];
   __syncthreads();
-  trsv_upperT_cta(o.R, o.ns, ys);
+  trmv_lower_cta(o.Y, o.ns, xs, ys);  // y_s = U_s^{-T} x_s
+  __syncthreads();
   for (int i = threadIdx.x; i < o.ns; i += blockDim.x) x[sl[i]] = ys[i];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const TF* XT = o.R + (size_t)o.ns * o.ns;
-  for (int j = warp; j < o.m; j += nw) {
+  for (int j = warp; j < o.m; j += nw) {  // u = X_ns y_s
     double s = 0.0;
     for (int i = lane; i < o.ns; i += 32) s += (double)XT[i + (size_t)j * o.ns] * ys[i];
     s = warp_sum_d(s);
@@ -139,13 +109,16 @@ __global__ void k_scatter_sub(const int32_t* __restrict__ tslot, const int64_t* 
 template <typename TF>
 __global__ void __launch_bounds__(AT) k_scale_fwd(const ScaleOp<TF>* __restrict__ ops, const int32_t* __restrict__ slots,
                                                  double* __restrict__ x) {
-  extern __shared__ double ys[];
+  extern __shared__ double xs[];
   const ScaleOp<TF> o = ops[blockIdx.x];
   const int32_t* sl = slots + o.slot;
-  for (int i = threadIdx.x; i < o.np; i += blockDim.x) ys[i] = x[sl[i]];
+  for (int i = threadIdx.x; i < o.np; i += blockDim.x) xs[i] = x[sl[i]];
   __syncthreads();
-  trsv_upperT_cta(o.U, o.np, ys);
-  for (int i = threadIdx.x; i < o.np; i += blockDim.x) x[sl[i]] = ys[i];
+  for (int i = threadIdx.x; i < o.np; i += blockDim.x) {  // x_p <- U_p^{-T} x_p
+    double s = 0.0;
+    for (int j = 0; j <= i; ++j) s += (double)o.Y[i + (size_t)j * o.np] * xs[j];
+    x[sl[i]] = s;
+  }
 }
 
 template <typename TF>
@@ -194,13 +167,17 @@ __global__ void __launch_bounds__(AT) k_q_bwd(const QOp<TF>* __restrict__ ops, c
 template <typename TF>
 __global__ void __launch_bounds__(AT) k_scale_bwd(const ScaleOp<TF>* __restrict__ ops, const int32_t* __restrict__ slots,
                                                  double* __restrict__ x) {
-  extern __shared__ double ys[];
+  extern __shared__ double xs[];
   const ScaleOp<TF> o = ops[blockIdx.x];
   const int32_t* sl = slots + o.slot;
-  for (int i = threadIdx.x; i < o.np; i += blockDim.x) ys[i] = x[sl[i]];
+  for (int i = threadIdx.x; i < o.np; i += blockDim.x) xs[i] = x[sl[i]];
   __syncthreads();
-  trsv_upper_cta(o.U, o.np, ys);
-  for (int i = threadIdx.x; i < o.np; i += blockDim.x) x[sl[i]] = ys[i];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = warp; j < o.np; j += nw) {  // x_p <- U_p^{-1} x_p = Y^T x_p
+    double v;
+    trmv_lowerT_warp(o.Y, o.np, xs, j, v);
+    if (lane == 0) x[sl[j]] = v;
+  }
 }
 
 template <typename TF>
@@ -209,19 +186,23 @@ __global__ void __launch_bounds__(AT) k_elim_bwd(const ElimOp<TF>* __restrict__ 
   extern __shared__ double sh[];
   const ElimOp<TF> o = ops[blockIdx.x];
   const int32_t* sl = slots + o.slot;
-  double* ys = sh;
+  double* acc = sh;
   double* xn = sh + o.ns;
   for (int j = threadIdx.x; j < o.m; j += blockDim.x) xn[j] = x[sl[o.ns + j]];
   __syncthreads();
   const TF* XT = o.R + (size_t)o.ns * o.ns;
-  for (int i = threadIdx.x; i < o.ns; i += blockDim.x) {
+  for (int i = threadIdx.x; i < o.ns; i += blockDim.x) {  // acc = x_s - X_ns^T x_n
     double s = x[sl[i]];
     for (int j = 0; j < o.m; ++j) s -= (double)XT[i + (size_t)j * o.ns] * xn[j];
-    ys[i] = s;
+    acc[i] = s;
   }
   __syncthreads();
-  trsv_upper_cta(o.R, o.ns, ys);
-  for (int i = threadIdx.x; i < o.ns; i += blockDim.x) x[sl[i]] = ys[i];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = warp; j < o.ns; j += nw) {  // x_s = U_s^{-1} acc
+    double v;
+    trmv_lowerT_warp(o.Y, o.ns, acc, j, v);
+    if (lane == 0) x[sl[j]] = v;
+  }
 }
 
 // ---------------------------------------------------------------- PCG pieces

@@ -15,6 +15,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "cpqr_cluster.cuh"
 #include "factor_kernels.cuh"
 #include "solve_kernels.cuh"
 #include "spand_internal.h"
@@ -39,6 +40,10 @@ struct Fail {
 #define CKLAUNCH() CK(cudaGetLastError())
 
 static inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+constexpr size_t kCpqrChunkBudget = 160 * 1024;  // shared-memory chunk per CTA
+constexpr int kCpqrMaxCluster = 8;              // portable thread-block cluster size
+constexpr int kAuxStreams = 4;
 
 // Chunked bump allocator over cudaMalloc; reset() keeps the chunks for reuse.
 class DevArena {
@@ -144,6 +149,77 @@ static void ensure_smem(const void* fn, size_t bytes) {
   done[fn] = bytes;
 }
 
+// Kernel-family profiler: launch counts always; with profiling on, a CUDA
+// event pair on the launching stream around each batch of launches of one
+// family, plus its algorithmic flops and bytes.
+enum Family { F_POTRF = 0, F_TRSM, F_SCHUR, F_CPQR, F_COPY, F_APPLY, F_PCG, F_NFAM };
+
+struct KProf {
+  bool on = false;
+  int64_t launches = 0;
+  double ms[F_NFAM] = {}, flops[F_NFAM] = {}, bytes[F_NFAM] = {};
+  int64_t count[F_NFAM] = {};
+  struct Pend {
+    int fam;
+    cudaEvent_t a, b;
+    double flops, bytes;
+    int64_t nl;
+  };
+  std::vector<Pend> pend;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    return e;
+  }
+  int begin(int fam, cudaStream_t s) {
+    if (!on) return -1;
+    Pend p{fam, get(), get(), 0.0, 0.0, 0};
+    CK(cudaEventRecord(p.a, s));
+    pend.push_back(p);
+    return (int)pend.size() - 1;
+  }
+  void end(int id, cudaStream_t s, double flops, double bytes, int64_t nl) {
+    if (id < 0) return;
+    Pend& p = pend[id];
+    p.flops += flops;
+    p.bytes += bytes;
+    p.nl += nl;
+    CK(cudaEventRecord(p.b, s));
+  }
+  void add(int id, double flops, double bytes) {
+    if (id < 0) return;
+    pend[id].flops += flops;
+    pend[id].bytes += bytes;
+  }
+  void flush() {  // call after a synchronisation point
+    for (auto& p : pend) {
+      float t = 0;
+      CK(cudaEventSynchronize(p.b));
+      CK(cudaEventElapsedTime(&t, p.a, p.b));
+      ms[p.fam] += t;
+      flops[p.fam] += p.flops;
+      bytes[p.fam] += p.bytes;
+      count[p.fam] += p.nl;
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pend.clear();
+  }
+  void reset() {
+    for (int f = 0; f < F_NFAM; ++f) ms[f] = flops[f] = bytes[f] = 0, count[f] = 0;
+  }
+  ~KProf() {
+    for (auto& p : pend) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
 }  // namespace spand
 
 using namespace spand;
@@ -177,6 +253,16 @@ struct spand_handle_s {
   spand_stats st{};
   double phase_ms[6] = {0, 0, 0, 0, 0, 0};
   std::vector<std::vector<int32_t>> sizes_before, sizes_after;
+  cudaStream_t aux[kAuxStreams] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kAuxStreams] = {};
+  KProf prof;
+  ~spand_handle_s() {
+    for (auto& a : aux)
+      if (a) cudaStreamDestroy(a);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    for (auto& e : ev_join)
+      if (e) cudaEventDestroy(e);
+  }
 };
 
 namespace spand {
@@ -247,6 +333,13 @@ static Layout<T> make_layout(spand_handle h, int t, const std::vector<int32_t>& 
   return lay;
 }
 
+static void ensure_streams(spand_handle h) {
+  if (h->ev_fork) return;
+  for (auto& a : h->aux) CK(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  for (auto& e : h->ev_join) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+}
+
 template <typename T>
 static void* upload(spand_handle h, const Packer& pk, cudaStream_t s) {
   if (pk.buf.empty()) return nullptr;
@@ -273,7 +366,15 @@ static void potrf_batch(spand_handle h, const std::vector<RowDesc<T>>& rows, int
   ensure_smem((const void*)k_potrf_diag<T>, sm1);
   ensure_smem((const void*)k_potrf_trsm<T>, sm2);
   const int nb = (int)rows.size();
+  double fl = 0, by = 0;
+  for (auto& r : rows) {
+    fl += (double)r.n * r.n * r.n / 3;
+    by += 2.0 * r.n * r.n * sizeof(T);
+  }
+  const int pid = h->prof.begin(F_POTRF, s);
+  int64_t nl = 0;
   for (int k = 0; k < nt; ++k) {
+    nl += (nt - k - 1 > 0) ? 3 : 1;
     k_potrf_diag<T><<<nb, NT, sm1, s>>>(dr, k, d_info);
     CKLAUNCH();
     const int m = nt - k - 1;
@@ -284,6 +385,8 @@ static void potrf_batch(spand_handle h, const std::vector<RowDesc<T>>& rows, int
       CKLAUNCH();
     }
   }
+  h->prof.launches += nl;
+  h->prof.end(pid, s, fl, by, nl);
 }
 
 template <typename T>
@@ -294,15 +397,56 @@ static void trsm_batch(spand_handle h, const std::vector<TrsmTask<T>>& tasks, cu
   void* d = upload<T>(h, pk, s);
   const size_t sm = 2 * sizeof(SqTile<T>) + sizeof(TileSmem<T>);
   ensure_smem((const void*)k_trsm_cols<T>, sm);
+  double fl = 0, by = 0;
+  for (auto& t : tasks) {
+    const double nn = t.n - (t.i_start / TB) * TB;
+    fl += nn * nn * t.nc;
+    by += (nn * nn / 2 + 2.0 * nn * t.nc) * sizeof(T);
+  }
+  const int pid = h->prof.begin(F_TRSM, s);
   k_trsm_cols<T><<<(unsigned)tasks.size(), NT, sm, s>>>(at<const TrsmTask<T>>(d, o));
   CKLAUNCH();
+  h->prof.launches += 1;
+  h->prof.end(pid, s, fl, by, 1);
 }
 
+// Panels of at most 64 columns [c0, c1) of a block row: B <- U^{-T} B.
 template <typename T>
 static void add_panels(std::vector<TrsmTask<T>>& out, T* R, int n, int ld, int c0, int c1) {
   if (n <= 0) return;
-  for (int c = c0; c < c1; c += TB) out.push_back({R, n, ld, c, std::min(c + TB, c1)});
+  for (int c = c0; c < c1; c += TB) {
+    TrsmTask<T> t;
+    t.U = R;
+    t.B = R + (size_t)c * ld;
+    t.n = n;
+    t.ldu = ld;
+    t.ldb = ld;
+    t.nc = std::min(c + TB, c1) - c;
+    t.i_start = 0;
+    t.pad = 0;
+    out.push_back(t);
+  }
 }
+
+// Y = U^{-T} (lower): the same solve on identity panels (Y must hold I).
+template <typename T>
+static void add_inverse(std::vector<TrsmTask<T>>& out, const T* U, int n, int ldu, T* Y) {
+  for (int c = 0; c < n; c += TB) {
+    TrsmTask<T> t;
+    t.U = U;
+    t.B = Y + (size_t)c * n;
+    t.n = n;
+    t.ldu = ldu;
+    t.ldb = n;
+    t.nc = std::min(c + TB, n) - c;
+    t.i_start = c;
+    t.pad = 0;
+    out.push_back(t);
+  }
+}
+
+template <typename T>
+static void set_identity(spand_handle h, const std::vector<RowDesc<T>>& rows, cudaStream_t s);
 
 template <typename T>
 static void copy_batch(spand_handle h, const std::vector<CopyTask<T>>& tasks, cudaStream_t s) {
@@ -316,11 +460,29 @@ static void copy_batch(spand_handle h, const std::vector<CopyTask<T>>& tasks, cu
   size_t ot = pk.add(tasks), oi = pk.add(tiles);
   void* d = upload<T>(h, pk, s);
   const size_t nt = tiles.size();
+  double by = 0;
+  for (auto& t : tasks) by += 2.0 * t.rows * t.cols * sizeof(T);
+  const int pid = h->prof.begin(F_COPY, s);
+  int64_t nl = 0;
   for (size_t b = 0; b < nt; b += 1u << 30) {
     const unsigned cnt = (unsigned)std::min<size_t>(nt - b, 1u << 30);
     k_copy<T><<<cnt, NT, 0, s>>>(at<const CopyTile>(d, oi) + b, at<const CopyTask<T>>(d, ot));
     CKLAUNCH();
+    ++nl;
   }
+  h->prof.launches += nl;
+  h->prof.end(pid, s, 0.0, by, nl);
+}
+
+template <typename T>
+static void set_identity(spand_handle h, const std::vector<RowDesc<T>>& rows, cudaStream_t s) {
+  if (rows.empty()) return;
+  Packer pk;
+  size_t o = pk.add(rows);
+  void* d = upload<T>(h, pk, s);
+  k_set_identity<T><<<dim3(8, (unsigned)rows.size()), 256, 0, s>>>(at<const RowDesc<T>>(d, o), (int)rows.size());
+  CKLAUNCH();
+  h->prof.launches += 1;
 }
 
 struct StepTimer {
@@ -372,6 +534,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       k_assemble<T><<<g, 256, 0, s>>>((const double*)h->d_vals.p, (const int32_t*)h->d_asm_row.p,
                                       (const int64_t*)h->d_asm_off.p, at<T* const>(d, orow), nnz);
       CKLAUNCH();
+      h->prof.launches += 1;
     }
   }
   CK(cudaEventRecord(tm.ev[1], s));
@@ -394,8 +557,9 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
     // ------------------------------------------------ eliminate (Sec. 2.4)
     std::vector<int> seps, rems;
     for (int i = 0; i < n; ++i) (st.elim[i] ? seps : rems).push_back(i);
+    std::vector<T*> ysep(n, nullptr);
     {
-      std::vector<RowDesc<T>> diag;
+      std::vector<RowDesc<T>> diag, ident;
       std::vector<int> diag_cl;
       std::vector<TrsmTask<T>> tr_tasks;
       for (int sidx : seps) {
@@ -403,9 +567,14 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         diag.push_back({lay.row[sidx], sz[sidx], lay.ld[sidx]});
         diag_cl.push_back(sidx);
         add_panels(tr_tasks, lay.row[sidx], sz[sidx], lay.ld[sidx], sz[sidx], lay.W[sidx]);
+        T* Y = (T*)h->persist.alloc((size_t)sz[sidx] * sz[sidx] * sizeof(T));
+        ysep[sidx] = Y;
+        ident.push_back({Y, sz[sidx], sz[sidx]});
+        add_inverse(tr_tasks, lay.row[sidx], sz[sidx], lay.ld[sidx], Y);
         const double ns = sz[sidx], m = lay.W[sidx] - sz[sidx];
         stt.factor_flops += ns * ns * ns / 3 + ns * ns * m + ns * m * m;
       }
+      set_identity<T>(h, ident, s);
       potrf_batch<T>(h, diag, d_info, s);
       int info = 0;
       CK(cudaMemcpyAsync(&info, d_info, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -471,9 +640,19 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         Packer pk;
         size_t ob = pk.add(blocks), oc = pk.add(flat), ot = pk.add(tiles);
         void* d = upload<T>(h, pk, s);
+        double fl = 0, by = 0;
+        for (auto& bl : blocks) {
+          double ksum = 0;
+          for (int32_t c = bl.cbeg; c < bl.cend; ++c) ksum += flat[c].ns;
+          fl += 2.0 * bl.rows * bl.cols * ksum;
+          by += ((double)(bl.rows + bl.cols) * ksum + (bl.C2 ? 3.0 : 2.0) * bl.rows * bl.cols) * sizeof(T);
+        }
+        const int pid = h->prof.begin(F_SCHUR, s);
         k_schur<T><<<(unsigned)tiles.size(), NT, 0, s>>>(at<const SchurTile>(d, ot), at<const SchurBlock<T>>(d, ob),
                                                         at<const SchurContrib<T>>(d, oc));
         CKLAUNCH();
+        h->prof.launches += 1;
+        h->prof.end(pid, s, fl, by, 1);
       }
     }
     CK(cudaEventRecord(tm.ev[1], s));
@@ -488,6 +667,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       if (sz[sidx] <= 0) continue;
       ElimOp<T> o;
       o.R = lay.row[sidx];
+      o.Y = ysep[sidx];
       o.ns = sz[sidx];
       o.m = lay.W[sidx] - sz[sidx];
       o.slot = (int64_t)aslots.size();
@@ -504,7 +684,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       tmp_off += o.m;
       eops.push_back(o);
       stt.mem_f += (int64_t)o.ns * (o.ns + 1) / 2 + (int64_t)o.ns * o.m;
-      sm_ef = std::max(sm_ef, (size_t)o.ns * sizeof(double));
+      sm_ef = std::max(sm_ef, (size_t)2 * o.ns * sizeof(double));
       sm_eb = std::max(sm_eb, (size_t)(o.ns + o.m) * sizeof(double));
     }
     h->tmp_len = std::max(h->tmp_len, tmp_off);
@@ -528,13 +708,14 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
     std::vector<QOp<T>> qops;
     size_t sm_s = 0, sm_qf = 0, sm_qb = 0;
     const bool sparsify = (skip < t) && (t < L);
+    int cpqr_pid = -1;
     std::vector<int> cp_cluster;           // sparsified clusters (task order)
     std::vector<T*> cp_qc;                 // their Q_pc scratch
     if (sparsify) {
-      std::vector<RowDesc<T>> diag;
+      std::vector<RowDesc<T>> diag, ident;
       std::vector<int> diag_cl;
       std::vector<TrsmTask<T>> up, lo;
-      std::vector<CopyTask<T>> m_up, m_lo, usave;
+      std::vector<CopyTask<T>> m_up, m_lo;
       std::vector<RowDesc<T>> idr;
       for (int p : rems) {
         if (sz[p] <= 0) continue;
@@ -566,11 +747,12 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
           b.cols = sz[q];
           m_lo.push_back(b);
         }
-        T* U = (T*)h->persist.alloc((size_t)sz[p] * sz[p] * sizeof(T));
-        usave.push_back({lay.row[p], U, lay.ld[p], sz[p], sz[p], sz[p], 0, 0});
+        T* Y = (T*)h->persist.alloc((size_t)sz[p] * sz[p] * sizeof(T));
+        ident.push_back({Y, sz[p], sz[p]});
+        add_inverse(up, lay.row[p], sz[p], lay.ld[p], Y);
         idr.push_back({lay.row[p], sz[p], lay.ld[p]});
         ScaleOp<T> so;
-        so.U = U;
+        so.Y = Y;
         so.np = sz[p];
         so.pad = 0;
         so.slot = 0;  // set below
@@ -580,6 +762,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         stt.mem_f += (int64_t)sz[p] * (sz[p] + 1) / 2;
         sm_s = std::max(sm_s, (size_t)sz[p] * sizeof(double));
       }
+      set_identity<T>(h, ident, s);
       potrf_batch<T>(h, diag, d_info, s);
       int info = 0;
       CK(cudaMemcpyAsync(&info, d_info, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -589,30 +772,23 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         stt.fail_cluster = diag_cl[info - 1];
         throw Fail{SPAND_ERR_NOT_SPD, "interface block not positive definite at step " + std::to_string(t)};
       }
-      trsm_batch<T>(h, up, s);
+      trsm_batch<T>(h, up, s);   // upper blocks U_p^{-T} A_pq and the inverses Y_p
       copy_batch<T>(h, m_up, s);
       trsm_batch<T>(h, lo, s);
       copy_batch<T>(h, m_lo, s);
-      copy_batch<T>(h, usave, s);
-      if (!idr.empty()) {
-        Packer pk;
-        size_t o = pk.add(idr);
-        void* d = upload<T>(h, pk, s);
-        k_set_identity<T><<<dim3(8, (unsigned)idr.size()), 256, 0, s>>>(at<const RowDesc<T>>(d, o), (int)idr.size());
-        CKLAUNCH();
-      }
+      set_identity<T>(h, idr, s);
       CK(cudaEventRecord(tm.ev[2], s));
       // ---- sparsify, colour by colour (Sec. 2.6.1)
       d_cur = (int32_t*)h->descs.alloc((size_t)n * sizeof(int32_t));
       CK(cudaMemcpyAsync(d_cur, sz.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
       std::vector<CpqrTask<T>> tasks;
       std::vector<CpqrNbr<T>> nbrs;
+      std::vector<int> tclass;  // cluster size of each task
       const int ncol = st.ncolours();
-      std::vector<std::vector<int32_t>> by_colour(std::max(ncol, 1));
       size_t wbytes = 0;
-      struct WOff { size_t w, nrm, piv, qc; };
+      struct WOff { size_t nrm, v, tau, qc, gw; };
       std::vector<WOff> woff;
-      int nnb_max = 0, np_max = 0;
+      const size_t CB = kCpqrChunkBudget;
       for (int p : rems) {
         if (sz[p] <= 0) continue;
         if (lay.nptr[p + 1] == lay.nptr[p]) continue;  // no neighbours: nothing to compress against
@@ -637,46 +813,102 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         }
         tk.nend = (int32_t)nbrs.size();
         tk.m_max = mm;
+        // smallest cluster whose per-CTA chunk fits in shared memory, and at
+        // most ~2 columns per thread
+        int C = kCpqrMaxCluster;
+        for (int c = 1; c <= kCpqrMaxCluster; c *= 2)
+          if ((size_t)sz[p] * ((mm + c - 1) / c) * sizeof(T) <= CB) { C = c; break; }
+        while (C < kCpqrMaxCluster && (mm + C - 1) / C > 2 * CQ_NT) C *= 2;
+        const bool resident = (size_t)sz[p] * ((mm + C - 1) / C) * sizeof(T) <= CB;
         WOff w;
-        w.w = wbytes; wbytes += align256((size_t)sz[p] * std::max(mm, 1) * sizeof(T));
         w.nrm = wbytes; wbytes += align256((size_t)std::max(mm, 1) * sizeof(T));
-        w.piv = wbytes; wbytes += align256((size_t)std::max(mm, 1) * sizeof(int32_t));
+        w.v = wbytes; wbytes += align256((size_t)sz[p] * sz[p] * sizeof(T));
+        w.tau = wbytes; wbytes += align256((size_t)sz[p] * sizeof(T));
         w.qc = wbytes; wbytes += align256((size_t)sz[p] * sz[p] * sizeof(T));
+        w.gw = wbytes;
+        if (!resident) wbytes += align256((size_t)C * sz[p] * ((mm + C - 1) / C) * sizeof(T));
         woff.push_back(w);
-        by_colour[st.colour[p]].push_back((int32_t)tasks.size());
         tasks.push_back(tk);
+        tclass.push_back(C);
         cp_cluster.push_back(p);
-        nnb_max = std::max(nnb_max, tk.nend - tk.nbeg);
-        np_max = std::max(np_max, (int)sz[p]);
       }
       if (!tasks.empty()) {
         char* wb = (char*)h->scratch[(t + 1) & 1].ensure(wbytes);
         for (size_t i = 0; i < tasks.size(); ++i) {
-          tasks[i].work = (T*)(wb + woff[i].w);
           tasks[i].norms = (T*)(wb + woff[i].nrm);
-          tasks[i].piv = (int32_t*)(wb + woff[i].piv);
+          tasks[i].V = (T*)(wb + woff[i].v);
+          tasks[i].tau = (T*)(wb + woff[i].tau);
           tasks[i].Qc = (T*)(wb + woff[i].qc);
+          tasks[i].gwork = (T*)(wb + woff[i].gw);
           cp_qc.push_back(tasks[i].Qc);
         }
+        // launch groups: (colour, cluster size)
+        struct Group { int colour, C; std::vector<int32_t> ids; size_t smem = 0; size_t chunk = 0; };
+        std::vector<Group> groups;
+        for (int c = 0; c < std::max(ncol, 1); ++c)
+          for (int C = 1; C <= kCpqrMaxCluster; C *= 2) {
+            Group g;
+            g.colour = c;
+            g.C = C;
+            for (size_t i = 0; i < tasks.size(); ++i)
+              if (st.colour[tasks[i].p] == c && tclass[i] == C) {
+                g.ids.push_back((int32_t)i);
+                const int np_ = tasks[i].np, mm = tasks[i].m_max;
+                const size_t chunk = (size_t)np_ * ((mm + C - 1) / C) * sizeof(T);
+                const size_t fixed = ((sizeof(CqShared<T>) + 15) & ~size_t(15)) +
+                                     (((size_t)(tasks[i].nend - tasks[i].nbeg + 1) * sizeof(int) + 15) & ~size_t(15)) +
+                                     (((size_t)np_ * sizeof(T) + 15) & ~size_t(15));
+                g.smem = std::max(g.smem, fixed);
+                if (chunk <= CB) g.chunk = std::max(g.chunk, chunk);
+              }
+            if (!g.ids.empty()) groups.push_back(std::move(g));
+          }
         std::vector<int32_t> list;
-        std::vector<size_t> cbeg;
-        for (auto& v : by_colour) {
-          cbeg.push_back(list.size());
-          list.insert(list.end(), v.begin(), v.end());
+        std::vector<size_t> gbeg;
+        for (auto& g : groups) {
+          gbeg.push_back(list.size());
+          list.insert(list.end(), g.ids.begin(), g.ids.end());
         }
-        cbeg.push_back(list.size());
         Packer pk;
         size_t ot = pk.add(tasks), on = pk.add(nbrs), ol = pk.add(list);
         void* d = upload<T>(h, pk, s);
-        const size_t sm = align256(sizeof(int) * (nnb_max + 1)) + (size_t)np_max * sizeof(T);
-        ensure_smem((const void*)k_cpqr<T>, sm);
-        for (size_t c = 0; c + 1 < cbeg.size(); ++c) {
-          const unsigned cnt = (unsigned)(cbeg[c + 1] - cbeg[c]);
-          if (!cnt) continue;
-          k_cpqr<T><<<cnt, NT, sm, s>>>(at<const CpqrTask<T>>(d, ot), at<const int32_t>(d, ol) + cbeg[c],
-                                        at<const CpqrNbr<T>>(d, on), d_cur, (T)eps);
-          CKLAUNCH();
+        ensure_streams(h);
+        cpqr_pid = h->prof.begin(F_CPQR, s);
+        size_t gi = 0;
+        while (gi < groups.size()) {  // one colour at a time; its groups run side by side
+          size_t ge = gi;
+          while (ge < groups.size() && groups[ge].colour == groups[gi].colour) ++ge;
+          CK(cudaEventRecord(h->ev_fork, s));
+          for (size_t g = gi; g < ge; ++g) {
+            cudaStream_t as = h->aux[(g - gi) % kAuxStreams];
+            CK(cudaStreamWaitEvent(as, h->ev_fork, 0));
+            const Group& G = groups[g];
+            const size_t smem = G.smem + G.chunk;
+            const void* fn = (const void*)k_cpqr_cluster<T>;
+            ensure_smem(fn, smem);
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)(G.ids.size() * G.C), 1, 1);
+            cfg.blockDim = dim3(CQ_NT, 1, 1);
+            cfg.dynamicSmemBytes = smem;
+            cfg.stream = as;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = (unsigned)G.C;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            CK(cudaLaunchKernelEx(&cfg, k_cpqr_cluster<T>, at<const CpqrTask<T>>(d, ot),
+                                  at<const int32_t>(d, ol) + gbeg[g], at<const CpqrNbr<T>>(d, on), d_cur, (T)eps,
+                                  (int32_t)G.chunk));
+            CK(cudaEventRecord(h->ev_join[(g - gi) % kAuxStreams], as));
+          }
+          for (size_t g = gi; g < std::min(ge, gi + (size_t)kAuxStreams); ++g)
+            CK(cudaStreamWaitEvent(s, h->ev_join[(g - gi) % kAuxStreams], 0));
+          gi = ge;
         }
+        h->prof.launches += (int64_t)groups.size();
+        h->prof.end(cpqr_pid, s, 0.0, 0.0, (int64_t)groups.size());
         CK(cudaMemcpyAsync(sz_after.data(), d_cur, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       }
       CK(cudaStreamSynchronize(s));
@@ -696,7 +928,10 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         q.save = 0;
         qops.push_back(q);
         const double np_ = sz[p], m = lay.W[p] - sz[p], rr = r;
-        stt.factor_flops += 4 * np_ * m * rr - 2 * rr * rr * (np_ + m) + 4 * rr * rr * rr / 3;
+        const double qfl = 4 * np_ * m * rr - 2 * rr * rr * (np_ + m) + 4 * rr * rr * rr / 3;
+        stt.factor_flops += qfl;
+        // algorithmic bytes: A_pn read once, W written twice, Q_pc written
+        h->prof.add(cpqr_pid, qfl, (np_ * m + 2 * rr * m + np_ * rr) * sizeof(T));
         stt.mem_f += (int64_t)sz[p] * r;
         sm_qf = std::max(sm_qf, (size_t)sz[p] * sizeof(double));
         sm_qb = std::max(sm_qb, (size_t)std::max(r, 1) * sizeof(double));
@@ -806,6 +1041,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
     }
     CK(cudaEventRecord(tm.ev[4], s));
     CK(cudaEventSynchronize(tm.ev[4]));
+    h->prof.flush();
     float ms[4];
     for (int k = 0; k < 4; ++k) CK(cudaEventElapsedTime(&ms[k], tm.ev[k], tm.ev[k + 1]));
     h->phase_ms[0] += ms[0];
@@ -830,6 +1066,10 @@ template <typename TF>
 static void apply_prec(spand_handle h, const std::vector<ApplyStep<TF>>& steps, double* x, cudaStream_t s) {
   double* tmp = (double*)h->d_tmp.p;
   double* save = (double*)h->d_save.p;
+  const int pid = h->prof.begin(F_APPLY, s);
+  int64_t nl = 0;
+  for (const ApplyStep<TF>& a : steps) nl += 2 * (a.n_elim ? 2 : 0) + 2 * (a.n_scale ? 1 : 0) + 2 * (a.n_q ? 1 : 0) -
+                                             (a.n_elim && !a.ntgt ? 1 : 0);
   for (const ApplyStep<TF>& a : steps) {
     if (a.n_elim) {
       ensure_smem((const void*)k_elim_fwd<TF>, a.sm_elim_fwd);
@@ -870,6 +1110,8 @@ static void apply_prec(spand_handle h, const std::vector<ApplyStep<TF>>& steps, 
       CKLAUNCH();
     }
   }
+  h->prof.launches += nl;
+  h->prof.end(pid, s, 0.0, h->st.apply_bytes, nl);
 }
 
 static void apply_any(spand_handle h, double* x, cudaStream_t s) {
@@ -1085,6 +1327,7 @@ int spand_factorize(spand_handle h, const double* vals, void* cuda_stream) {
     k_gather_vals<<<(unsigned)std::min<int64_t>((nnz + 255) / 256, 4096), 256, 0, s>>>(
         nnz, (const int64_t*)h->d_pval_src.p, (const double*)h->d_vals.p, (double*)h->d_pval.p);
     CKLAUNCH();
+    h->prof.launches += 1;
   }
   h->tmp_len = 0;
   h->save_len = 0;
@@ -1120,6 +1363,7 @@ int spand_apply(spand_handle h, const double* r_dev, double* z_dev, void* cuda_s
   apply_any(h, w, s);
   k_permute<<<g, 256, 0, s>>>(n, (const int32_t*)h->d_perm.p, w, z_dev, 0);
   CKLAUNCH();
+  h->prof.launches += 2;
   CK(cudaStreamSynchronize(s));
   return SPAND_OK;
   API_END
@@ -1153,19 +1397,23 @@ int spand_solve(spand_handle h, const double* b, double* x, int32_t* iters, doub
   const double* va = (const double*)h->d_pval.p;
   k_permute<<<g, 256, 0, s>>>(n, perm, io, bp, 1);
   CKLAUNCH();
+  h->prof.launches += 1;
   CK(cudaMemsetAsync(xv, 0, n * sizeof(double), s));
   auto dot = [&](const double* a, const double* c, double* out) {
     k_dot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, a, c, part);
     CKLAUNCH();
     k_reduce<<<1, RED_THREADS, 0, s>>>(part, RED_BLOCKS, out);
     CKLAUNCH();
+    h->prof.launches += 2;
   };
   auto read = [&](const double* d) {
     double v = 0;
     CK(cudaMemcpyAsync(&v, d, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    h->prof.flush();
     return v;
   };
+  const double pcg_bytes = (double)h->nnz * 12 + (double)(n + 1) * 8 + 9.0 * n * 8;
   cudaEvent_t e0, e1, e2;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -1175,6 +1423,7 @@ int spand_solve(spand_handle h, const double* b, double* x, int32_t* iters, doub
   auto precond = [&](const double* src, double* dst) {
     k_copy_vec<<<g, 256, 0, s>>>(n, src, dst);
     CKLAUNCH();
+    h->prof.launches += 1;
     CK(cudaEventRecord(e0, s));
     apply_any(h, dst, s);
     CK(cudaEventRecord(e1, s));
@@ -1196,6 +1445,7 @@ int spand_solve(spand_handle h, const double* b, double* x, int32_t* iters, doub
   } else {
     k_copy_vec<<<g, 256, 0, s>>>(n, bp, r);
     CKLAUNCH();
+    h->prof.launches += 1;
     precond(r, z);
     k_copy_vec<<<g, 256, 0, s>>>(n, z, p);
     CKLAUNCH();
@@ -1203,14 +1453,17 @@ int spand_solve(spand_handle h, const double* b, double* x, int32_t* iters, doub
     dot(r, z, sc + irz);
     while (it < maxit) {
       CK(cudaEventRecord(e2, s));
+      const int pid = h->prof.begin(F_PCG, s);
       k_spmv_dot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, rp, ci, va, p, q, part);
       CKLAUNCH();
+      h->prof.launches += 4;
       k_reduce<<<1, RED_THREADS, 0, s>>>(part, RED_BLOCKS, sc + 1);
       CKLAUNCH();
       // alpha = rz / pq
       if (irz != 0) {
         k_copy_vec<<<1, 32, 0, s>>>(1, sc + irz, sc + 0);
         CKLAUNCH();
+        h->prof.launches += 1;
         irz = 0;
         irzn = 3;
       }
@@ -1218,6 +1471,7 @@ int spand_solve(spand_handle h, const double* b, double* x, int32_t* iters, doub
       CKLAUNCH();
       k_reduce<<<1, RED_THREADS, 0, s>>>(part, RED_BLOCKS, sc + 2);
       CKLAUNCH();
+      h->prof.end(pid, s, 2.0 * h->nnz + 6.0 * n, pcg_bytes, 4);
       CK(cudaEventRecord(e1, s));
       ++it;
       const double rr = read(sc + 2);
@@ -1229,11 +1483,13 @@ int spand_solve(spand_handle h, const double* b, double* x, int32_t* iters, doub
       if (std::sqrt(rr) / bnorm <= tol) {
         k_residual<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, rp, ci, va, xv, bp, r);
         CKLAUNCH();
+        h->prof.launches += 1;
         dot(r, r, sc + 2);
         if (std::sqrt(read(sc + 2)) / bnorm <= tol) break;
         precond(r, z);
         k_copy_vec<<<g, 256, 0, s>>>(n, z, p);
         CKLAUNCH();
+        h->prof.launches += 1;
         dot(r, z, sc + 0);
         continue;
       }
@@ -1241,15 +1497,18 @@ int spand_solve(spand_handle h, const double* b, double* x, int32_t* iters, doub
       dot(r, z, sc + irzn);
       k_update_p<<<g, 256, 0, s>>>(n, sc + irzn, sc + irz, z, p);
       CKLAUNCH();
+      h->prof.launches += 1;
       std::swap(irz, irzn);
     }
     k_residual<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, rp, ci, va, xv, bp, q);
     CKLAUNCH();
+    h->prof.launches += 1;
     dot(q, q, sc + 2);
     rel = std::sqrt(read(sc + 2)) / bnorm;
   }
   k_permute<<<g, 256, 0, s>>>(n, perm, xv, io, 0);
   CKLAUNCH();
+  h->prof.launches += 1;
   CK(cudaMemcpyAsync(x, io, n * sizeof(double), xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   cudaEventDestroy(e0);
@@ -1268,6 +1527,34 @@ int spand_solve(spand_handle h, const double* b, double* x, int32_t* iters, doub
   }
   return SPAND_OK;
   API_END
+}
+
+int spand_set_profiling(spand_handle h, int32_t on) {
+  if (!h) { g_err = "null handle"; return SPAND_ERR_INVALID_ARG; }
+  h->prof.on = on != 0;
+  return SPAND_OK;
+}
+
+int spand_get_kernel_profile(spand_handle h, int32_t family, double* out4) {
+  if (!h || !out4) { g_err = "null argument"; return SPAND_ERR_INVALID_ARG; }
+  if (family < 0 || family >= F_NFAM) { g_err = "unknown kernel family"; return SPAND_ERR_INVALID_ARG; }
+  out4[0] = (double)h->prof.count[family];
+  out4[1] = h->prof.ms[family];
+  out4[2] = h->prof.flops[family];
+  out4[3] = h->prof.bytes[family];
+  return SPAND_OK;
+}
+
+int spand_reset_kernel_profile(spand_handle h) {
+  if (!h) { g_err = "null handle"; return SPAND_ERR_INVALID_ARG; }
+  h->prof.reset();
+  return SPAND_OK;
+}
+
+int spand_get_launch_count(spand_handle h, int64_t* launches) {
+  if (!h || !launches) { g_err = "null argument"; return SPAND_ERR_INVALID_ARG; }
+  *launches = h->prof.launches;
+  return SPAND_OK;
 }
 
 int spand_get_tree(spand_handle h, int32_t* perm, int32_t* cluster_ptr, int32_t* cluster_key, int32_t* n_clusters,

@@ -67,6 +67,18 @@ class Solver:
     def phase_times(self):
         return L.spand_get_phase_times(self.h)
 
+    def set_profiling(self, on: bool = True):
+        L.spand_set_profiling(self.h, on)
+
+    def kernel_profile(self) -> dict:
+        return L.spand_get_kernel_profile(self.h)
+
+    def reset_kernel_profile(self):
+        L.spand_reset_kernel_profile(self.h)
+
+    def launch_count(self) -> int:
+        return L.spand_get_launch_count(self.h)
+
     def close(self):
         if self.h:
             L.spand_destroy(self.h)
