@@ -192,12 +192,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--grid", type=int, default=GRID, help="cube edge (small cases for profiling only)")
+    ap.add_argument("--levels", type=int, default=LEVELS)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     rank, world, local = dist_env()
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and (args.grid, args.levels) == (GRID, LEVELS):
         cpu = oracle_sample_seconds()  # before any CUDA work in this process
     import numpy as np
     import torch
@@ -212,8 +214,12 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    p = I.laplacian_3d(GRID)
+    p = I.laplacian_3d(args.grid)
     b = I.rhs(p.n, SEED)
+    levels = args.levels
+    workload = WORKLOAD if (args.grid, levels) == (GRID, LEVELS) else f"lapl3d_{args.grid}^3_7pt_L{levels}_eps1e-2"
+    if workload != WORKLOAD:
+        args.no_cpu_baseline = True
     vals_d = torch.from_numpy(p.vals).cuda()
     b_d = torch.from_numpy(b).cuda()
     x_d = torch.empty_like(b_d)
@@ -227,7 +233,7 @@ def main():
         torch.cuda.synchronize()
 
     def run_form(precision, steps, warmup, timed_clocks=False):
-        s = Solver.from_problem(p, levels=LEVELS, eps=EPS, precision=precision)
+        s = Solver.from_problem(p, levels=levels, eps=EPS, precision=precision)
         for _ in range(warmup):
             s.factorize(vals_d)
             s.solve(b_d, x_d)
@@ -304,7 +310,7 @@ def main():
         "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": p.n, "nnz": p.nnz, "levels": LEVELS, "eps": EPS,
+        "config": {"workload": workload, "N": p.n, "nnz": p.nnz, "levels": levels, "eps": EPS,
                    "factor": "fp32 (mixed), PCG fp64", "parallelism": f"replicas x{world}",
                    "l2": "256 MB L2 flush between timed steps; factor data > 129 MB"},
         "forms": {

@@ -40,7 +40,6 @@ template <typename T>
 struct CpqrTask {
   T* Rp;              // p's block row (leading dimension ldp)
   T* gwork;           // global fallback for the chunks: C * np * cols_per
-  T* norms;           // m_max: squared trailing column norms, -1 once pivoted
   T* V;               // np x np capacity, column k = v_k (v_k[k] = 1, zero above)
   T* tau;             // np
   T* Qc;              // np x np capacity; first r columns = Q_pc on exit
@@ -49,14 +48,30 @@ struct CpqrTask {
 
 template <typename T>
 struct CqShared {     // fixed part of the dynamic shared memory
-  T cand_v;
-  int cand_j;
-  T beta, tau;
-  int stop;
+  T cand_v[16];       // pivot candidate of every CTA of the cluster (pushed by its owner)
+  int cand_j[16];
+  T alpha, beta, tau;  // reflector of the current step (pushed by the pivot's owner)
 };
 
+// one barrier for the whole cluster (a plain block barrier when C == 1)
+__device__ __forceinline__ void cq_sync(cg::cluster_group& cl, int C) {
+  if (C == 1) __syncthreads();
+  else cl.sync();
+}
+
 // dynamic shared memory layout:
-//   [CqShared][cstart: (nnb+1) ints][vbuf: np T][chunk: np * ldc T (if resident)]
+//   [CqShared][cstart: (nnb+1) ints][vbuf: np T][norms: cols_per T][chunk: np * ldc T (if resident)]
+// `norms` holds the squared trailing norms of the CTA's columns (-1 once the
+// column has been a pivot).  Per reflector step k:
+//   1. every CTA finds its best column (largest norm, lowest index on ties)
+//      and pushes it into every CTA's candidate slots; barrier;
+//   2. every thread reduces the C candidates: pivot j*, |R_kk| = sqrt(norm j*)
+//      (norms are recomputed exactly, so this is the 2-norm of the pivot's
+//      trailing column); the truncation rule is checked here, uniformly;
+//   3. the owner of j* forms the reflector (beta = -sign(alpha) |R_kk|,
+//      tau = (beta - alpha) / beta, v = x / (alpha - beta)) and pushes alpha,
+//      beta, tau and v into every CTA; it retires the column; barrier;
+//   4. every CTA applies H_k to its live columns and refreshes their norms.
 template <typename T>
 __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __restrict__ tasks,
                                                        const int32_t* __restrict__ list,
@@ -76,7 +91,8 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
   off += ((size_t)(nnb + 1) * sizeof(int) + 15) & ~size_t(15);
   T* vbuf = reinterpret_cast<T*>(smraw + off);
   off += ((size_t)np * sizeof(T) + 15) & ~size_t(15);
-  T* schunk = reinterpret_cast<T*>(smraw + off);
+  T* snorm = reinterpret_cast<T*>(smraw + off);
+  const size_t norm_off = off;
   __shared__ T red_v[CQ_NT / 32];
   __shared__ int red_j[CQ_NT / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -105,6 +121,7 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
   const int j0 = min(m, rank * cols_per);
   const int nc = min(m, j0 + cols_per) - j0;
   const int ldc = max(cols_per, 1);
+  T* schunk = reinterpret_cast<T*>(smraw + norm_off + (((size_t)ldc * sizeof(T) + 15) & ~size_t(15)));
   const bool resident = (int64_t)np * ldc * (int64_t)sizeof(T) <= (int64_t)chunk_smem_bytes;
   T* chunk = resident ? schunk : d.gwork + (size_t)rank * np * ldc;
 
@@ -132,7 +149,7 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) d.norms[j] = s;
+    if (lane == 0) snorm[jl] = s;
   }
   __syncthreads();
 
@@ -140,11 +157,11 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
   int r = kmax;
   T r00 = T(0);
   for (int k = 0; k < kmax; ++k) {
-    // (a) local pivot candidate: largest norm, lowest global column on ties
+    // 1. local pivot candidate
     T bv = T(-1);
     int bj = INT_MAX;
     for (int jl = tid; jl < nc; jl += CQ_NT) {
-      const T v = d.norms[j0 + jl];
+      const T v = snorm[jl];
       if (v > bv) { bv = v; bj = j0 + jl; }
     }
 #pragma unroll
@@ -155,103 +172,90 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
     }
     if (lane == 0) { red_v[warp] = bv; red_j[warp] = bj; }
     __syncthreads();
-    if (tid == 0) {
-      for (int w = 1; w < CQ_NT / 32; ++w)
-        if (red_v[w] > bv || (red_v[w] == bv && red_j[w] < bj)) { bv = red_v[w]; bj = red_j[w]; }
-      sh.cand_v = bv;
-      sh.cand_j = bj;
-    }
-    cluster.sync();
-    // every CTA reduces the C candidates in the same order -> same pivot
-    T gv = T(-1);
-    int gj = INT_MAX;
-    for (int q = 0; q < C; ++q) {
-      const CqShared<T>* o = cluster.map_shared_rank(&sh, q);
-      const T v = o->cand_v;
-      const int j = o->cand_j;
-      if (v > gv || (v == gv && j < gj)) { gv = v; gj = j; }
+    bv = red_v[0];
+    bj = red_j[0];
+    for (int w = 1; w < CQ_NT / 32; ++w)
+      if (red_v[w] > bv || (red_v[w] == bv && red_j[w] < bj)) { bv = red_v[w]; bj = red_j[w]; }
+    T gv = bv;
+    int gj = bj;
+    if (C > 1) {
+      if (tid < C) {  // push my candidate into slot `rank` of CTA `tid`
+        CqShared<T>* o = cluster.map_shared_rank(&sh, tid);
+        o->cand_v[rank] = bv;
+        o->cand_j[rank] = bj;
+      }
+      cluster.sync();
+      gv = T(-1);
+      gj = INT_MAX;
+      for (int q = 0; q < C; ++q) {
+        const T v = sh.cand_v[q];
+        const int j = sh.cand_j[q];
+        if (v > gv || (v == gv && j < gj)) { gv = v; gj = j; }
+      }
     }
     if (gj == INT_MAX) gj = 0;  // unreachable: k < kmax <= m leaves a column
-    const int owner = min(C - 1, gj / max(cols_per, 1));
-    // (b) the owner forms the Householder reflector of its pivot column
-    if (rank == owner) {
-      const int jl = gj - j0;
-      T s = 0;
-      for (int i = k + 1 + tid; i < np; i += CQ_NT) {
-        const T x = chunk[(size_t)i * ldc + jl];
-        s += x * x;
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      __syncthreads();
-      if (lane == 0) red_v[warp] = s;
-      __syncthreads();
-      if (tid == 0) {
-        T sig = 0;
-        for (int w = 0; w < CQ_NT / 32; ++w) sig += red_v[w];
-        const T alpha = chunk[(size_t)k * ldc + jl];
-        T beta, tau;
-        if (sig == T(0)) {
-          beta = alpha;
-          tau = T(0);
-        } else {
-          const T nrm = sqrt(alpha * alpha + sig);
-          beta = alpha >= T(0) ? -nrm : nrm;
-          tau = (beta - alpha) / beta;
-        }
-        sh.beta = beta;
-        sh.tau = tau;
-        vbuf[k] = T(1);
-        d.norms[gj] = T(-1);
-        d.tau[k] = tau;
-      }
-      __syncthreads();
-      const T alpha = chunk[(size_t)k * ldc + jl];
-      const T beta = sh.beta, tau = sh.tau;
-      const T scal = (tau == T(0)) ? T(0) : T(1) / (alpha - beta);
-      for (int i = k + 1 + tid; i < np; i += CQ_NT) {
-        const T v = chunk[(size_t)i * ldc + jl] * scal;
-        vbuf[i] = v;
-        chunk[(size_t)i * ldc + jl] = T(0);
-      }
-      __syncthreads();  // vbuf entries come from other threads
-      for (int i = tid; i < np; i += CQ_NT) d.V[i + (size_t)k * np] = i < k ? T(0) : (i == k ? T(1) : vbuf[i]);
-      __syncthreads();
-      if (tid == 0) chunk[(size_t)k * ldc + jl] = beta;
-    }
-    cluster.sync();
-    // (c) everyone takes the reflector from the owner and checks the rule
-    const CqShared<T>* osh = cluster.map_shared_rank(&sh, owner);
-    const T beta = osh->beta, tau = osh->tau;
-    const T rkk = fabs(beta);
+    // 2. |R_kk| and the truncation rule (same values in every thread)
+    const T rkk = sqrt(gv > T(0) ? gv : T(0));
     if (k == 0) r00 = rkk;
     if (r00 == T(0) || rkk < eps * r00) {
       r = k;
-      break;  // uniform: every CTA read the same beta
+      break;
     }
-    if (rank != owner) {
-      const T* ov = cluster.map_shared_rank(vbuf, owner);
-      for (int i = k + tid; i < np; i += CQ_NT) vbuf[i] = ov[i];
+    const int owner = min(C - 1, gj / max(cols_per, 1));
+    // 3. the owner forms the reflector and pushes it to every CTA
+    if (rank == owner) {
+      const int jl = gj - j0;
+      const T alpha = chunk[(size_t)k * ldc + jl];
+      T beta, tau, scal;
+      if (rkk == T(0)) {
+        beta = T(0);
+        tau = T(0);
+        scal = T(0);
+      } else {
+        beta = alpha >= T(0) ? -rkk : rkk;
+        tau = (beta - alpha) / beta;
+        scal = T(1) / (alpha - beta);
+      }
+      for (int i = k + tid; i < np; i += CQ_NT) {
+        const T v = (i == k) ? T(1) : chunk[(size_t)i * ldc + jl] * scal;
+        for (int q = 0; q < C; ++q) cluster.map_shared_rank(vbuf, q)[i] = v;
+        d.V[i + (size_t)k * np] = v;
+      }
+      for (int i = tid; i < k; i += CQ_NT) d.V[i + (size_t)k * np] = T(0);
+      if (tid < C) {
+        CqShared<T>* o = cluster.map_shared_rank(&sh, tid);
+        o->alpha = alpha;
+        o->beta = beta;
+        o->tau = tau;
+      }
+      if (tid == 0) d.tau[k] = tau;
     }
-    __syncthreads();
-    // (d) apply H_k to my remaining columns, refresh their trailing norms
+    cq_sync(cluster, C);
+    const T tau = sh.tau;
+    if (rank == owner) {  // retire the pivot column: R_kk = beta, zeros below
+      const int jl = gj - j0;
+      for (int i = k + tid; i < np; i += CQ_NT) chunk[(size_t)i * ldc + jl] = (i == k) ? sh.beta : T(0);
+      if (tid == 0) snorm[jl] = T(-1);
+    }
+    // 4. apply H_k to my live columns, refresh their trailing norms
     for (int jl = tid; jl < nc; jl += CQ_NT) {
-      if (d.norms[j0 + jl] < T(0)) continue;
+      if (jl == gj - j0) continue;
+      if (snorm[jl] < T(0)) continue;
       T w = 0;
       for (int i = k; i < np; ++i) w += vbuf[i] * chunk[(size_t)i * ldc + jl];
       w *= tau;
-      T s = 0;
+      T sq = 0;
       for (int i = k; i < np; ++i) {
         const T x = chunk[(size_t)i * ldc + jl] - w * vbuf[i];
         chunk[(size_t)i * ldc + jl] = x;
-        if (i > k) s += x * x;
+        if (i > k) sq += x * x;
       }
-      d.norms[j0 + jl] = s;
+      snorm[jl] = sq;
     }
     __syncthreads();
   }
-  // the owner of step r may have retired a column that is not kept: its top r
-  // rows are untouched, so every column's rows 0..r-1 hold W_cn.
+  // Rows 0..r-1 of every column now hold W_cn in the original column order
+  // (the pivot found at step r, if any, was not touched).
   // ---- write back W_cn into p's row and the transposes into the neighbours
   for (int64_t x = tid; x < (int64_t)r * nc; x += CQ_NT) {
     const int i = (int)(x % r), jl = (int)(x / r);
@@ -268,6 +272,7 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
       const int i = (int)(x % r), j = (int)(x / r);
       d.Rp[i + (size_t)j * d.ldp] = (i == j) ? T(1) : T(0);
     }
+  if (C > 1) cluster.sync();  // every V column and tau is visible cluster-wide
   // ---- Q_pc e_c = H_0 ... H_c e_c (H_k e_c = e_c for k > c), one warp per column
   for (int c = rank * (CQ_NT / 32) + warp; c < r; c += C * (CQ_NT / 32)) {
     T* col = d.Qc + (size_t)c * np;
@@ -287,7 +292,7 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
     }
   }
   if (rank == 0 && tid == 0) cur_size[d.p] = r;
-  cluster.sync();  // keep every CTA's shared memory alive until all DSMEM reads are done
+  if (C > 1) cluster.sync();  // no CTA leaves while others may still write into its shared memory
 }
 
 }  // namespace spand

@@ -137,6 +137,35 @@ __device__ bool potrf_tile_upper(SqTile<T>& s, int nb) {
   return true;
 }
 
+// B <- D B with D = U^{-T} the stored inverse of a diagonal tile (lower,
+// zero above the diagonal), i.e. B <- U^{-T} B as one small GEMM instead of a
+// serial substitution.  D, B in shared memory; each thread produces a 4x4
+// patch; starts and ends synchronised.
+template <typename T>
+__device__ void apply_inv_tile(const SqTile<T>& D, SqTile<T>& B, int nb) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  T acc[4][4];
+  zero_acc(acc);
+  for (int l = 0; l < nb; ++l) {
+    T dv[4], bv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      dv[q] = D.v[tx + 16 * q][l];
+      bv[q] = B.v[l][ty + 16 * q];
+    }
+#pragma unroll
+    for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) acc[ii][jj] = fma(dv[ii], bv[jj], acc[ii][jj]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) B.v[tx + 16 * ii][ty + 16 * jj] = acc[ii][jj];
+  __syncthreads();
+}
+
 // In place: B <- U^{-T} B, U upper nb x nb, B nb x ncols (both in shared memory).
 template <typename T>
 __device__ void trsm_tile_upperT(const SqTile<T>& U, SqTile<T>& B, int nb, int ncols) {

@@ -15,11 +15,13 @@ struct RowDesc {      // a cluster's block row or its diagonal block
   T* R;               // column-major, leading dimension ld
   int32_t n;          // rows (cluster size)
   int32_t ld;
+  T* dinv;            // ceil(n/64) tiles of 64x64: inverses U_kk^{-T} of the diagonal tiles
 };
 
 template <typename T>
 struct TrsmTask {     // B <- U^{-T} B: U upper n x n, B n x nc (rows < i_start of B are zero)
   const T* U;
+  const T* dinv;      // inverses of U's diagonal 64x64 tiles (see RowDesc)
   T* B;
   int32_t n, ldu, ldb, nc, i_start, pad;
 };
@@ -68,17 +70,24 @@ __global__ void k_assemble(const double* __restrict__ vals, const int32_t* __res
 
 // ---------------------------------------------------------------- tiled Cholesky
 
-// Tile step k, phase 1: factor diagonal tile (k, k) of every block.
+// Tile step k, phase 1: factor diagonal tile (k, k) of every block and store
+// the inverse of its factor, U_kk^{-T}, for the tile solves of phase 2 and of
+// k_trsm_cols.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_potrf_diag(const RowDesc<T>* __restrict__ rows, int k, int* info) {
   extern __shared__ __align__(16) unsigned char smraw[];
   SqTile<T>& s = *reinterpret_cast<SqTile<T>*>(smraw);
+  SqTile<T>& Id = *reinterpret_cast<SqTile<T>*>(smraw + sizeof(SqTile<T>));
   const RowDesc<T> d = rows[blockIdx.x];
   const int k0 = k * TB;
   if (k0 >= d.n) return;
   const int nb = min(TB, d.n - k0);
   T* P = d.R + k0 + (size_t)k0 * d.ld;
   load_tile(s, P, d.ld, nb, nb);
+  for (int e = threadIdx.x; e < TB * TB; e += NT) {
+    const int i = e & (TB - 1), j = e >> 6;
+    Id.v[i][j] = (i == j) ? T(1) : T(0);
+  }
   __syncthreads();
   const bool ok = potrf_tile_upper(s, nb);
   if (!ok) {
@@ -86,23 +95,25 @@ __global__ void __launch_bounds__(NT) k_potrf_diag(const RowDesc<T>* __restrict_
     return;
   }
   store_tile(s, P, d.ld, nb, nb);
+  trsm_tile_upperT(s, Id, nb, nb);
+  store_tile(Id, d.dinv + (size_t)k * TB * TB, TB, TB, TB);
 }
 
 // Tile step k, phase 2: U_kj = U_kk^{-T} A_kj for the tiles j > k of the diagonal block.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_potrf_trsm(const RowDesc<T>* __restrict__ rows, int k) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  SqTile<T>& U = *reinterpret_cast<SqTile<T>*>(smraw);
+  SqTile<T>& D = *reinterpret_cast<SqTile<T>*>(smraw);
   SqTile<T>& B = *reinterpret_cast<SqTile<T>*>(smraw + sizeof(SqTile<T>));
   const RowDesc<T> d = rows[blockIdx.y];
   const int k0 = k * TB;
   const int j0 = k0 + TB * (1 + blockIdx.x);
   if (j0 >= d.n) return;
   const int nb = min(TB, d.n - k0), nc = min(TB, d.n - j0);
-  load_tile(U, d.R + k0 + (size_t)k0 * d.ld, d.ld, nb, nb);
+  load_tile(D, d.dinv + (size_t)k * TB * TB, TB, TB, TB);
   load_tile(B, d.R + k0 + (size_t)j0 * d.ld, d.ld, nb, nc);
   __syncthreads();
-  trsm_tile_upperT(U, B, nb, nc);
+  apply_inv_tile(D, B, nb);
   store_tile(B, d.R + k0 + (size_t)j0 * d.ld, d.ld, nb, nc);
 }
 
@@ -148,7 +159,7 @@ __global__ void __launch_bounds__(NT) k_trsm_cols(const TrsmTask<T>* __restrict_
     T acc[4][4];
     zero_acc(acc);
     if (i0 > is) tn_acc(acc, d.U + is + (size_t)i0 * d.ldu, d.ldu, nb, X + is, d.ldb, nc, i0 - is, sm);
-    load_tile(U, d.U + i0 + (size_t)i0 * d.ldu, d.ldu, nb, nb);
+    load_tile(U, d.dinv + (size_t)(i0 / TB) * TB * TB, TB, TB, TB);  // U_ii^{-T}
     load_tile(B, X + i0, d.ldb, nb, nc);
     __syncthreads();
 #pragma unroll
@@ -159,7 +170,7 @@ __global__ void __launch_bounds__(NT) k_trsm_cols(const TrsmTask<T>* __restrict_
         B.v[r][c] -= acc[ii][jj];
       }
     __syncthreads();
-    trsm_tile_upperT(U, B, nb, nc);
+    apply_inv_tile(U, B, nb);
     store_tile(B, X + i0, d.ldb, nb, nc);
     __syncthreads();
   }

@@ -27,7 +27,11 @@ struct ElimOp {
   const TF* Y;       // U_s^{-T} (lower, ns x ns, ld = ns)
   int32_t ns, m;
   int64_t slot;      // ns slots of s, then m slots of the neighbour columns
-  int64_t tmp;       // m entries of the forward update
+  int64_t ty, tu, ta;  // temp offsets: y_s (ns), u = X_ns y_s (m), backward acc (ns)
+};
+
+struct ApplyItem {   // one CTA's share of an operation: op index and first row / column
+  int32_t op, first;
 };
 
 template <typename TF>
@@ -51,76 +55,133 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// y = Y x, Y lower n x n (ld n): one thread per row (coalesced over rows).
-template <typename TF>
-__device__ __forceinline__ void trmv_lower_cta(const TF* __restrict__ Y, int n, const double* x, double* y) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double s = 0.0;
-    for (int j = 0; j <= i; ++j) s += (double)Y[i + (size_t)j * n] * x[j];
-    y[i] = s;
-  }
-}
-
-// y_j = sum_{i >= j} Y[i, j] x_i  (y = Y^T x): one warp per output.
-template <typename TF>
-__device__ __forceinline__ void trmv_lowerT_warp(const TF* __restrict__ Y, int n, const double* x, int j, double& out) {
-  const int lane = threadIdx.x & 31;
-  double s = 0.0;
-  for (int i = j + lane; i < n; i += 32) s += (double)Y[i + (size_t)j * n] * x[i];
-  out = warp_sum_d(s);
-}
-
 // ---------------------------------------------------------------- forward sweep
 
+// warp-wide sum_{i in [i0, n)} a[i] * x[i] (a contiguous), lanes over i,
+// four independent accumulators (128 elements per iteration)
 template <typename TF>
-__global__ void __launch_bounds__(AT) k_elim_fwd(const ElimOp<TF>* __restrict__ ops, const int32_t* __restrict__ slots,
-                                                double* __restrict__ x, double* __restrict__ tmp) {
-  extern __shared__ double sh[];
-  const ElimOp<TF> o = ops[blockIdx.x];
+__device__ __forceinline__ double dot_warp(const TF* __restrict__ a, const double* x, int i0, int n) {
+  const int lane = threadIdx.x & 31;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int i = i0 + lane;
+  for (; i + 96 < n; i += 128) {
+    s0 += (double)a[i] * x[i];
+    s1 += (double)a[i + 32] * x[i + 32];
+    s2 += (double)a[i + 64] * x[i + 64];
+    s3 += (double)a[i + 96] * x[i + 96];
+  }
+  for (; i < n; i += 32) s0 += (double)a[i] * x[i];
+  return warp_sum_d((s0 + s1) + (s2 + s3));
+}
+
+constexpr int RB = 32;       // rows per block of the row-dot kernels (one per lane)
+constexpr int AP_COLS = 32;  // outputs per CTA of the warp-per-column kernels
+
+// Row dots of a 32-row block: sum_{k < K} A[r0 + lane + k*ld] x[k], with the K
+// range split over the CTA's 8 warps (lanes cover consecutive rows, so every
+// load is coalesced) and the 8 partial sums added in a fixed order.  All
+// threads must call it; the result is valid in warp 0 for row r0 + lane.
+template <typename TF>
+__device__ __forceinline__ double rowblock_dot(const TF* __restrict__ A, size_t ld, int r0, int nrows,
+                                               const double* x, int K, double (*part)[RB + 1]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = AT / 32;
+  const int row = r0 + lane;
+  const int kc = (K + nw - 1) / nw;
+  const int k0 = warp * kc, k1 = min(K, k0 + kc);
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  if (row < nrows) {
+    const TF* a = A + row;
+    int k = k0;
+    for (; k + 4 <= k1; k += 4) {
+      s0 += (double)a[(size_t)k * ld] * x[k];
+      s1 += (double)a[(size_t)(k + 1) * ld] * x[k + 1];
+      s2 += (double)a[(size_t)(k + 2) * ld] * x[k + 2];
+      s3 += (double)a[(size_t)(k + 3) * ld] * x[k + 3];
+    }
+    for (; k < k1; ++k) s0 += (double)a[(size_t)k * ld] * x[k];
+  }
+  part[warp][lane] = (s0 + s1) + (s2 + s3);
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0)
+    for (int w = 0; w < nw; ++w) t += part[w][lane];
+  __syncthreads();
+  return t;
+}
+
+// forward, part 1: y_s = U_s^{-T} x_s = Y x_s for one 32-row block -> tmp[ty]
+// (Y is exactly zero above its diagonal, so the block reads columns < r0 + 32)
+template <typename TF>
+__global__ void __launch_bounds__(AT) k_elim_fwd_y(const ElimOp<TF>* __restrict__ ops, const ApplyItem* __restrict__ items,
+                                                  const int32_t* __restrict__ slots, const double* __restrict__ x,
+                                                  double* __restrict__ tmp) {
+  extern __shared__ double xs[];
+  __shared__ double part[AT / 32][RB + 1];
+  const ApplyItem it = items[blockIdx.x];
+  const ElimOp<TF> o = ops[it.op];
   const int32_t* sl = slots + o.slot;
-  double* xs = sh;
-  double* ys = sh + o.ns;
-  for (int i = threadIdx.x; i < o.ns; i += blockDim.x) xs[i] = x[sl[i]];
+  const int K = min(o.ns, it.first + RB);
+  for (int j = threadIdx.x; j < K; j += AT) xs[j] = x[sl[j]];
   __syncthreads();
-  trmv_lower_cta(o.Y, o.ns, xs, ys);  // y_s = U_s^{-T} x_s
+  const double v = rowblock_dot(o.Y, (size_t)o.ns, it.first, o.ns, xs, K, part);
+  const int i = it.first + (threadIdx.x & 31);
+  if (threadIdx.x < 32 && i < o.ns) tmp[o.ty + i] = v;
+}
+
+// forward, part 2: u = X_ns y_s (X_ns = (X^T)^T), AP_COLS outputs per CTA -> tmp[tu]
+template <typename TF>
+__global__ void __launch_bounds__(AT) k_elim_fwd_u(const ElimOp<TF>* __restrict__ ops, const ApplyItem* __restrict__ items,
+                                                  double* __restrict__ tmp) {
+  extern __shared__ double ys[];
+  const ApplyItem it = items[blockIdx.x];
+  const ElimOp<TF> o = ops[it.op];
+  for (int i = threadIdx.x; i < o.ns; i += AT) ys[i] = tmp[o.ty + i];
   __syncthreads();
-  for (int i = threadIdx.x; i < o.ns; i += blockDim.x) x[sl[i]] = ys[i];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const TF* XT = o.R + (size_t)o.ns * o.ns;
-  for (int j = warp; j < o.m; j += nw) {  // u = X_ns y_s
-    double s = 0.0;
-    for (int i = lane; i < o.ns; i += 32) s += (double)XT[i + (size_t)j * o.ns] * ys[i];
-    s = warp_sum_d(s);
-    if (lane == 0) tmp[o.tmp + j] = s;
+  const int hi = min(o.m, it.first + AP_COLS);
+  for (int j = it.first + warp; j < hi; j += AT / 32) {
+    const double v = dot_warp(XT + (size_t)j * o.ns, ys, 0, o.ns);
+    if (lane == 0) tmp[o.tu + j] = v;
   }
 }
 
-// x[slot_t] -= sum of the forward updates aimed at it (fixed order).
-__global__ void k_scatter_sub(const int32_t* __restrict__ tslot, const int64_t* __restrict__ ptr,
-                              const int64_t* __restrict__ idx, const double* __restrict__ tmp,
-                              double* __restrict__ x, int64_t ntgt) {
+// forward, part 3: x_s = y_s (assign targets) and x_n -= sum of the u's aimed
+// at it (pull form, fixed order).  Targets [0, nassign) are assignments with
+// exactly one source.
+__global__ void k_scatter(const int32_t* __restrict__ tslot, const int64_t* __restrict__ ptr,
+                          const int64_t* __restrict__ idx, const double* __restrict__ tmp, double* __restrict__ x,
+                          int64_t nassign, int64_t ntgt) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntgt; t += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int64_t e = ptr[t]; e < ptr[t + 1]; ++e) s += tmp[idx[e]];
-    x[tslot[t]] -= s;
+    if (t < nassign) {
+      x[tslot[t]] = tmp[idx[ptr[t]]];
+    } else {
+      double s = 0.0;
+      for (int64_t e = ptr[t]; e < ptr[t + 1]; ++e) s += tmp[idx[e]];
+      x[tslot[t]] -= s;
+    }
   }
 }
 
+// x_p <- U_p^{-T} x_p = Y x_p (one CTA per cluster; 32-row blocks)
 template <typename TF>
 __global__ void __launch_bounds__(AT) k_scale_fwd(const ScaleOp<TF>* __restrict__ ops, const int32_t* __restrict__ slots,
                                                  double* __restrict__ x) {
   extern __shared__ double xs[];
+  __shared__ double part[AT / 32][RB + 1];
   const ScaleOp<TF> o = ops[blockIdx.x];
   const int32_t* sl = slots + o.slot;
-  for (int i = threadIdx.x; i < o.np; i += blockDim.x) xs[i] = x[sl[i]];
+  for (int i = threadIdx.x; i < o.np; i += AT) xs[i] = x[sl[i]];
   __syncthreads();
-  for (int i = threadIdx.x; i < o.np; i += blockDim.x) {  // x_p <- U_p^{-T} x_p
-    double s = 0.0;
-    for (int j = 0; j <= i; ++j) s += (double)o.Y[i + (size_t)j * o.np] * xs[j];
-    x[sl[i]] = s;
+  for (int r0 = 0; r0 < o.np; r0 += RB) {
+    const double v = rowblock_dot(o.Y, (size_t)o.np, r0, o.np, xs, min(o.np, r0 + RB), part);
+    const int i = r0 + (threadIdx.x & 31);
+    if (threadIdx.x < 32 && i < o.np) x[sl[i]] = v;
   }
 }
 
+// c = Q_pc^T x_p (the coarse values go to the first r slots; the forward
+// input and c are saved for the backward sweep)
 template <typename TF>
 __global__ void __launch_bounds__(AT) k_q_fwd(const QOp<TF>* __restrict__ ops, const int32_t* __restrict__ slots,
                                              double* __restrict__ x, double* __restrict__ save) {
@@ -128,17 +189,15 @@ __global__ void __launch_bounds__(AT) k_q_fwd(const QOp<TF>* __restrict__ ops, c
   const QOp<TF> o = ops[blockIdx.x];
   const int32_t* sl = slots + o.slot;
   double* sv = save + o.save;
-  for (int i = threadIdx.x; i < o.np; i += blockDim.x) {
+  for (int i = threadIdx.x; i < o.np; i += AT) {
     const double v = x[sl[i]];
     ys[i] = v;
     sv[i] = v;
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = AT / 32;
   for (int k = warp; k < o.r; k += nw) {
-    double s = 0.0;
-    for (int i = lane; i < o.np; i += 32) s += (double)o.Q[i + (size_t)k * o.np] * ys[i];
-    s = warp_sum_d(s);
+    const double s = dot_warp(o.Q + (size_t)k * o.np, ys, 0, o.np);
     if (lane == 0) {
       sv[o.np + k] = s;
       x[sl[k]] = s;
@@ -148,59 +207,73 @@ __global__ void __launch_bounds__(AT) k_q_fwd(const QOp<TF>* __restrict__ ops, c
 
 // ---------------------------------------------------------------- backward sweep
 
+// x_p = (forward input) + Q_pc (c - c_old)
 template <typename TF>
 __global__ void __launch_bounds__(AT) k_q_bwd(const QOp<TF>* __restrict__ ops, const int32_t* __restrict__ slots,
                                              double* __restrict__ x, const double* __restrict__ save) {
   extern __shared__ double dc[];
+  __shared__ double part[AT / 32][RB + 1];
   const QOp<TF> o = ops[blockIdx.x];
   const int32_t* sl = slots + o.slot;
   const double* sv = save + o.save;
-  for (int k = threadIdx.x; k < o.r; k += blockDim.x) dc[k] = x[sl[k]] - sv[o.np + k];
+  for (int k = threadIdx.x; k < o.r; k += AT) dc[k] = x[sl[k]] - sv[o.np + k];
   __syncthreads();
-  for (int i = threadIdx.x; i < o.np; i += blockDim.x) {
-    double s = sv[i];
-    for (int k = 0; k < o.r; ++k) s += (double)o.Q[i + (size_t)k * o.np] * dc[k];
-    x[sl[i]] = s;
+  for (int r0 = 0; r0 < o.np; r0 += RB) {
+    const double v = rowblock_dot(o.Q, (size_t)o.np, r0, o.np, dc, o.r, part);
+    const int i = r0 + (threadIdx.x & 31);
+    if (threadIdx.x < 32 && i < o.np) x[sl[i]] = sv[i] + v;
   }
 }
 
+// x_p <- U_p^{-1} x_p = Y^T x_p
 template <typename TF>
 __global__ void __launch_bounds__(AT) k_scale_bwd(const ScaleOp<TF>* __restrict__ ops, const int32_t* __restrict__ slots,
                                                  double* __restrict__ x) {
   extern __shared__ double xs[];
   const ScaleOp<TF> o = ops[blockIdx.x];
   const int32_t* sl = slots + o.slot;
-  for (int i = threadIdx.x; i < o.np; i += blockDim.x) xs[i] = x[sl[i]];
+  for (int i = threadIdx.x; i < o.np; i += AT) xs[i] = x[sl[i]];
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = warp; j < o.np; j += nw) {  // x_p <- U_p^{-1} x_p = Y^T x_p
-    double v;
-    trmv_lowerT_warp(o.Y, o.np, xs, j, v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = AT / 32;
+  for (int j = warp; j < o.np; j += nw) {
+    const double v = dot_warp(o.Y + (size_t)j * o.np, xs, j, o.np);
     if (lane == 0) x[sl[j]] = v;
   }
 }
 
+// backward, part 1: acc = x_s - X_ns^T x_n for one 32-row block -> tmp[ta]
 template <typename TF>
-__global__ void __launch_bounds__(AT) k_elim_bwd(const ElimOp<TF>* __restrict__ ops, const int32_t* __restrict__ slots,
-                                                double* __restrict__ x) {
-  extern __shared__ double sh[];
-  const ElimOp<TF> o = ops[blockIdx.x];
+__global__ void __launch_bounds__(AT) k_elim_bwd_acc(const ElimOp<TF>* __restrict__ ops, const ApplyItem* __restrict__ items,
+                                                    const int32_t* __restrict__ slots, const double* __restrict__ x,
+                                                    double* __restrict__ tmp) {
+  extern __shared__ double xn[];
+  __shared__ double part[AT / 32][RB + 1];
+  const ApplyItem it = items[blockIdx.x];
+  const ElimOp<TF> o = ops[it.op];
   const int32_t* sl = slots + o.slot;
-  double* acc = sh;
-  double* xn = sh + o.ns;
-  for (int j = threadIdx.x; j < o.m; j += blockDim.x) xn[j] = x[sl[o.ns + j]];
+  for (int j = threadIdx.x; j < o.m; j += AT) xn[j] = x[sl[o.ns + j]];
   __syncthreads();
   const TF* XT = o.R + (size_t)o.ns * o.ns;
-  for (int i = threadIdx.x; i < o.ns; i += blockDim.x) {  // acc = x_s - X_ns^T x_n
-    double s = x[sl[i]];
-    for (int j = 0; j < o.m; ++j) s -= (double)XT[i + (size_t)j * o.ns] * xn[j];
-    acc[i] = s;
-  }
+  const double v = rowblock_dot(XT, (size_t)o.ns, it.first, o.ns, xn, o.m, part);
+  const int i = it.first + (threadIdx.x & 31);
+  if (threadIdx.x < 32 && i < o.ns) tmp[o.ta + i] = x[sl[i]] - v;
+}
+
+// backward, part 2: x_s = U_s^{-1} acc = Y^T acc, AP_COLS outputs per CTA
+template <typename TF>
+__global__ void __launch_bounds__(AT) k_elim_bwd_x(const ElimOp<TF>* __restrict__ ops, const ApplyItem* __restrict__ items,
+                                                  const int32_t* __restrict__ slots, const double* __restrict__ tmp,
+                                                  double* __restrict__ x) {
+  extern __shared__ double acc[];
+  const ApplyItem it = items[blockIdx.x];
+  const ElimOp<TF> o = ops[it.op];
+  const int32_t* sl = slots + o.slot;
+  for (int i = threadIdx.x; i < o.ns; i += AT) acc[i] = tmp[o.ta + i];
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = warp; j < o.ns; j += nw) {  // x_s = U_s^{-1} acc
-    double v;
-    trmv_lowerT_warp(o.Y, o.ns, acc, j, v);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int hi = min(o.ns, it.first + AP_COLS);
+  for (int j = it.first + warp; j < hi; j += AT / 32) {
+    const double v = dot_warp(o.Y + (size_t)j * o.ns, acc, j, o.ns);
     if (lane == 0) x[sl[j]] = v;
   }
 }

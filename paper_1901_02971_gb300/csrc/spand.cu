@@ -132,11 +132,15 @@ struct ApplyStep {
   const ScaleOp<TF>* scale = nullptr;
   const QOp<TF>* q = nullptr;
   const int32_t* slots = nullptr;
-  int64_t ntgt = 0;
+  // per-CTA work items of the split elimination GEMVs
+  int n_fy = 0, n_fu = 0, n_ba = 0, n_bx = 0;
+  const ApplyItem *fy = nullptr, *fu = nullptr, *ba = nullptr, *bx = nullptr;
+  // forward scatter: [0, nassign) assignments x_s = y_s, then subtractions
+  int64_t ntgt = 0, nassign = 0;
   const int32_t* tslot = nullptr;
   const int64_t* tptr = nullptr;
   const int64_t* tidx = nullptr;
-  size_t sm_elim_fwd = 0, sm_elim_bwd = 0, sm_scale = 0, sm_q_fwd = 0, sm_q_bwd = 0;
+  size_t sm_ns = 0, sm_m = 0, sm_scale = 0, sm_q_fwd = 0, sm_q_bwd = 0;
 };
 
 // Highest dynamic shared memory requested so far, per kernel.
@@ -362,7 +366,7 @@ static void potrf_batch(spand_handle h, const std::vector<RowDesc<T>>& rows, int
   int nmax = 0;
   for (auto& r : rows) nmax = std::max(nmax, r.n);
   const int nt = (nmax + TB - 1) / TB;
-  const size_t sm1 = sizeof(SqTile<T>), sm2 = 2 * sizeof(SqTile<T>);
+  const size_t sm1 = 2 * sizeof(SqTile<T>), sm2 = 2 * sizeof(SqTile<T>);
   ensure_smem((const void*)k_potrf_diag<T>, sm1);
   ensure_smem((const void*)k_potrf_trsm<T>, sm2);
   const int nb = (int)rows.size();
@@ -412,11 +416,12 @@ static void trsm_batch(spand_handle h, const std::vector<TrsmTask<T>>& tasks, cu
 
 // Panels of at most 64 columns [c0, c1) of a block row: B <- U^{-T} B.
 template <typename T>
-static void add_panels(std::vector<TrsmTask<T>>& out, T* R, int n, int ld, int c0, int c1) {
+static void add_panels(std::vector<TrsmTask<T>>& out, T* R, const T* dinv, int n, int ld, int c0, int c1) {
   if (n <= 0) return;
   for (int c = c0; c < c1; c += TB) {
     TrsmTask<T> t;
     t.U = R;
+    t.dinv = dinv;
     t.B = R + (size_t)c * ld;
     t.n = n;
     t.ldu = ld;
@@ -430,10 +435,11 @@ static void add_panels(std::vector<TrsmTask<T>>& out, T* R, int n, int ld, int c
 
 // Y = U^{-T} (lower): the same solve on identity panels (Y must hold I).
 template <typename T>
-static void add_inverse(std::vector<TrsmTask<T>>& out, const T* U, int n, int ldu, T* Y) {
+static void add_inverse(std::vector<TrsmTask<T>>& out, const T* U, const T* dinv, int n, int ldu, T* Y) {
   for (int c = 0; c < n; c += TB) {
     TrsmTask<T> t;
     t.U = U;
+    t.dinv = dinv;
     t.B = Y + (size_t)c * n;
     t.n = n;
     t.ldu = ldu;
@@ -447,6 +453,13 @@ static void add_inverse(std::vector<TrsmTask<T>>& out, const T* U, int n, int ld
 
 template <typename T>
 static void set_identity(spand_handle h, const std::vector<RowDesc<T>>& rows, cudaStream_t s);
+
+// Storage for the inverses of the diagonal 64x64 tiles of an n x n pivot block.
+template <typename T>
+static T* alloc_dinv(spand_handle h, int n) {
+  const size_t nt = (size_t)(n + TB - 1) / TB;
+  return (T*)h->descs.alloc(std::max<size_t>(nt, 1) * TB * TB * sizeof(T));
+}
 
 template <typename T>
 static void copy_batch(spand_handle h, const std::vector<CopyTask<T>>& tasks, cudaStream_t s) {
@@ -564,13 +577,14 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       std::vector<TrsmTask<T>> tr_tasks;
       for (int sidx : seps) {
         if (sz[sidx] <= 0) continue;
-        diag.push_back({lay.row[sidx], sz[sidx], lay.ld[sidx]});
+        T* dv = alloc_dinv<T>(h, sz[sidx]);
+        diag.push_back({lay.row[sidx], sz[sidx], lay.ld[sidx], dv});
         diag_cl.push_back(sidx);
-        add_panels(tr_tasks, lay.row[sidx], sz[sidx], lay.ld[sidx], sz[sidx], lay.W[sidx]);
+        add_panels(tr_tasks, lay.row[sidx], (const T*)dv, sz[sidx], lay.ld[sidx], sz[sidx], lay.W[sidx]);
         T* Y = (T*)h->persist.alloc((size_t)sz[sidx] * sz[sidx] * sizeof(T));
         ysep[sidx] = Y;
-        ident.push_back({Y, sz[sidx], sz[sidx]});
-        add_inverse(tr_tasks, lay.row[sidx], sz[sidx], lay.ld[sidx], Y);
+        ident.push_back({Y, sz[sidx], sz[sidx], nullptr});
+        add_inverse(tr_tasks, (const T*)lay.row[sidx], (const T*)dv, sz[sidx], lay.ld[sidx], Y);
         const double ns = sz[sidx], m = lay.W[sidx] - sz[sidx];
         stt.factor_flops += ns * ns * ns / 3 + ns * ns * m + ns * m * m;
       }
@@ -660,9 +674,12 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
     ApplyStep<T> ap;
     std::vector<int32_t> aslots;
     std::vector<ElimOp<T>> eops;
-    std::vector<std::pair<int32_t, int64_t>> tgt;  // (target slot, tmp index)
+    std::vector<std::pair<int32_t, int64_t>> tgt;  // (target slot, tmp index) of the subtractions
+    std::vector<int32_t> tslot;
+    std::vector<int64_t> tptr(1, 0), tidx;
+    std::vector<ApplyItem> it_fy, it_fu, it_ba, it_bx;
     int64_t tmp_off = 0;
-    size_t sm_ef = 0, sm_eb = 0;
+    size_t sm_ns = 0, sm_m = 0;
     for (int sidx : seps) {
       if (sz[sidx] <= 0) continue;
       ElimOp<T> o;
@@ -671,27 +688,40 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       o.ns = sz[sidx];
       o.m = lay.W[sidx] - sz[sidx];
       o.slot = (int64_t)aslots.size();
-      o.tmp = tmp_off;
+      o.ty = tmp_off;
+      o.tu = tmp_off + o.ns;
+      o.ta = tmp_off + o.ns + o.m;
+      const int32_t op = (int32_t)eops.size();
       aslots.insert(aslots.end(), slots[sidx].begin(), slots[sidx].end());
+      for (int32_t i = 0; i < o.ns; ++i) {  // x_s = y_s
+        tslot.push_back(slots[sidx][i]);
+        tidx.push_back(o.ty + i);
+        tptr.push_back((int64_t)tidx.size());
+      }
       int64_t j = 0;
       for (int32_t e = lay.nptr[sidx]; e < lay.nptr[sidx + 1]; ++e) {
         const int32_t q = lay.nidx[e];
         for (int32_t k = 0; k < sz[q]; ++k, ++j) {
           aslots.push_back(slots[q][k]);
-          tgt.push_back({slots[q][k], tmp_off + j});
+          tgt.push_back({slots[q][k], o.tu + j});
         }
       }
-      tmp_off += o.m;
+      for (int32_t r0 = 0; r0 < o.ns; r0 += RB) {
+        it_fy.push_back({op, r0});
+        it_ba.push_back({op, r0});
+      }
+      for (int32_t c0 = 0; c0 < o.m; c0 += AP_COLS) it_fu.push_back({op, c0});
+      for (int32_t c0 = 0; c0 < o.ns; c0 += AP_COLS) it_bx.push_back({op, c0});
+      tmp_off += 2 * (int64_t)o.ns + o.m;
       eops.push_back(o);
       stt.mem_f += (int64_t)o.ns * (o.ns + 1) / 2 + (int64_t)o.ns * o.m;
-      sm_ef = std::max(sm_ef, (size_t)2 * o.ns * sizeof(double));
-      sm_eb = std::max(sm_eb, (size_t)(o.ns + o.m) * sizeof(double));
+      sm_ns = std::max(sm_ns, (size_t)o.ns * sizeof(double));
+      sm_m = std::max(sm_m, (size_t)o.m * sizeof(double));
     }
     h->tmp_len = std::max(h->tmp_len, tmp_off);
+    const int64_t nassign = (int64_t)tslot.size();
     std::stable_sort(tgt.begin(), tgt.end(),
                      [](const std::pair<int32_t, int64_t>& a, const std::pair<int32_t, int64_t>& b) { return a.first < b.first; });
-    std::vector<int32_t> tslot;
-    std::vector<int64_t> tptr(1, 0), tidx;
     for (size_t i = 0; i < tgt.size(); ++i) {
       if (i == 0 || tgt[i].first != tgt[i - 1].first) {
         if (i) tptr.push_back((int64_t)tidx.size());
@@ -719,11 +749,12 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       std::vector<RowDesc<T>> idr;
       for (int p : rems) {
         if (sz[p] <= 0) continue;
-        diag.push_back({lay.row[p], sz[p], lay.ld[p]});
+        T* dv = alloc_dinv<T>(h, sz[p]);
+        diag.push_back({lay.row[p], sz[p], lay.ld[p], dv});
         diag_cl.push_back(p);
         const int fu = lay.first_upper(p);
-        add_panels(up, lay.row[p], sz[p], lay.ld[p], fu, lay.W[p]);
-        add_panels(lo, lay.row[p], sz[p], lay.ld[p], sz[p], fu);
+        add_panels(up, lay.row[p], (const T*)dv, sz[p], lay.ld[p], fu, lay.W[p]);
+        add_panels(lo, lay.row[p], (const T*)dv, sz[p], lay.ld[p], sz[p], fu);
         for (int32_t e = lay.nptr[p]; e < lay.nptr[p + 1]; ++e) {
           const int32_t q = lay.nidx[e];
           if (q <= p || sz[q] <= 0) continue;
@@ -748,9 +779,9 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
           m_lo.push_back(b);
         }
         T* Y = (T*)h->persist.alloc((size_t)sz[p] * sz[p] * sizeof(T));
-        ident.push_back({Y, sz[p], sz[p]});
-        add_inverse(up, lay.row[p], sz[p], lay.ld[p], Y);
-        idr.push_back({lay.row[p], sz[p], lay.ld[p]});
+        ident.push_back({Y, sz[p], sz[p], nullptr});
+        add_inverse(up, (const T*)lay.row[p], (const T*)dv, sz[p], lay.ld[p], Y);
+        idr.push_back({lay.row[p], sz[p], lay.ld[p], nullptr});
         ScaleOp<T> so;
         so.Y = Y;
         so.np = sz[p];
@@ -821,7 +852,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         while (C < kCpqrMaxCluster && (mm + C - 1) / C > 2 * CQ_NT) C *= 2;
         const bool resident = (size_t)sz[p] * ((mm + C - 1) / C) * sizeof(T) <= CB;
         WOff w;
-        w.nrm = wbytes; wbytes += align256((size_t)std::max(mm, 1) * sizeof(T));
+        w.nrm = 0;
         w.v = wbytes; wbytes += align256((size_t)sz[p] * sz[p] * sizeof(T));
         w.tau = wbytes; wbytes += align256((size_t)sz[p] * sizeof(T));
         w.qc = wbytes; wbytes += align256((size_t)sz[p] * sz[p] * sizeof(T));
@@ -835,7 +866,6 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       if (!tasks.empty()) {
         char* wb = (char*)h->scratch[(t + 1) & 1].ensure(wbytes);
         for (size_t i = 0; i < tasks.size(); ++i) {
-          tasks[i].norms = (T*)(wb + woff[i].nrm);
           tasks[i].V = (T*)(wb + woff[i].v);
           tasks[i].tau = (T*)(wb + woff[i].tau);
           tasks[i].Qc = (T*)(wb + woff[i].qc);
@@ -857,7 +887,8 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
                 const size_t chunk = (size_t)np_ * ((mm + C - 1) / C) * sizeof(T);
                 const size_t fixed = ((sizeof(CqShared<T>) + 15) & ~size_t(15)) +
                                      (((size_t)(tasks[i].nend - tasks[i].nbeg + 1) * sizeof(int) + 15) & ~size_t(15)) +
-                                     (((size_t)np_ * sizeof(T) + 15) & ~size_t(15));
+                                     (((size_t)np_ * sizeof(T) + 15) & ~size_t(15)) +
+                                     (((size_t)std::max((mm + C - 1) / C, 1) * sizeof(T) + 15) & ~size_t(15));
                 g.smem = std::max(g.smem, fixed);
                 if (chunk <= CB) g.chunk = std::max(g.chunk, chunk);
               }
@@ -966,6 +997,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       Packer pk;
       size_t oe = pk.add(eops), os = pk.add(sops), oq = pk.add(qops), osl = pk.add(aslots);
       size_t ots = pk.add(tslot), otp = pk.add(tptr), oti = pk.add(tidx);
+      size_t ofy = pk.add(it_fy), ofu = pk.add(it_fu), oba = pk.add(it_ba), obx = pk.add(it_bx);
       void* d = nullptr;
       if (!pk.buf.empty()) {
         d = h->persist.alloc(pk.buf.size());
@@ -979,11 +1011,20 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       ap.q = at<const QOp<T>>(d, oq);
       ap.slots = at<const int32_t>(d, osl);
       ap.ntgt = (int64_t)tslot.size();
+      ap.nassign = nassign;
       ap.tslot = at<const int32_t>(d, ots);
       ap.tptr = at<const int64_t>(d, otp);
       ap.tidx = at<const int64_t>(d, oti);
-      ap.sm_elim_fwd = sm_ef;
-      ap.sm_elim_bwd = sm_eb;
+      ap.n_fy = (int)it_fy.size();
+      ap.n_fu = (int)it_fu.size();
+      ap.n_ba = (int)it_ba.size();
+      ap.n_bx = (int)it_bx.size();
+      ap.fy = at<const ApplyItem>(d, ofy);
+      ap.fu = at<const ApplyItem>(d, ofu);
+      ap.ba = at<const ApplyItem>(d, oba);
+      ap.bx = at<const ApplyItem>(d, obx);
+      ap.sm_ns = sm_ns;
+      ap.sm_m = sm_m;
       ap.sm_scale = sm_s;
       ap.sm_q_fwd = sm_qf;
       ap.sm_q_bwd = sm_qb;
@@ -1062,61 +1103,79 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
 
 // ---------------------------------------------------------------- apply / PCG
 
+// tmp: h->tmp_len doubles of per-step temporaries; save: h->save_len doubles
+// of sparsification forward inputs (both scratch; nothing needs to start at 0)
 template <typename TF>
-static void apply_prec(spand_handle h, const std::vector<ApplyStep<TF>>& steps, double* x, cudaStream_t s) {
-  double* tmp = (double*)h->d_tmp.p;
-  double* save = (double*)h->d_save.p;
+static void apply_prec(spand_handle h, const std::vector<ApplyStep<TF>>& steps, double* x, double* tmp, double* save,
+                       cudaStream_t s) {
   const int pid = h->prof.begin(F_APPLY, s);
   int64_t nl = 0;
-  for (const ApplyStep<TF>& a : steps) nl += 2 * (a.n_elim ? 2 : 0) + 2 * (a.n_scale ? 1 : 0) + 2 * (a.n_q ? 1 : 0) -
-                                             (a.n_elim && !a.ntgt ? 1 : 0);
-  for (const ApplyStep<TF>& a : steps) {
+  auto launched = [&](int k) { nl += k; };
+  for (const ApplyStep<TF>& a : steps) {  // forward: leaves -> root
     if (a.n_elim) {
-      ensure_smem((const void*)k_elim_fwd<TF>, a.sm_elim_fwd);
-      k_elim_fwd<TF><<<a.n_elim, AT, a.sm_elim_fwd, s>>>(a.elim, a.slots, x, tmp);
+      ensure_smem((const void*)k_elim_fwd_y<TF>, a.sm_ns);
+      ensure_smem((const void*)k_elim_fwd_u<TF>, a.sm_ns);
+      k_elim_fwd_y<TF><<<a.n_fy, AT, a.sm_ns, s>>>(a.elim, a.fy, a.slots, x, tmp);
       CKLAUNCH();
-      if (a.ntgt) {
-        k_scatter_sub<<<(unsigned)std::min<int64_t>((a.ntgt + 255) / 256, 4096), 256, 0, s>>>(a.tslot, a.tptr, a.tidx,
-                                                                                              tmp, x, a.ntgt);
+      launched(1);
+      if (a.n_fu) {
+        k_elim_fwd_u<TF><<<a.n_fu, AT, a.sm_ns, s>>>(a.elim, a.fu, tmp);
         CKLAUNCH();
+        launched(1);
       }
+      k_scatter<<<(unsigned)std::min<int64_t>((a.ntgt + 255) / 256, 4096), 256, 0, s>>>(a.tslot, a.tptr, a.tidx, tmp, x,
+                                                                                       a.nassign, a.ntgt);
+      CKLAUNCH();
+      launched(1);
     }
     if (a.n_scale) {
       ensure_smem((const void*)k_scale_fwd<TF>, a.sm_scale);
       k_scale_fwd<TF><<<a.n_scale, AT, a.sm_scale, s>>>(a.scale, a.slots, x);
       CKLAUNCH();
+      launched(1);
     }
     if (a.n_q) {
       ensure_smem((const void*)k_q_fwd<TF>, a.sm_q_fwd);
       k_q_fwd<TF><<<a.n_q, AT, a.sm_q_fwd, s>>>(a.q, a.slots, x, save);
       CKLAUNCH();
+      launched(1);
     }
   }
-  for (auto it = steps.rbegin(); it != steps.rend(); ++it) {
+  for (auto it = steps.rbegin(); it != steps.rend(); ++it) {  // backward: root -> leaves
     const ApplyStep<TF>& a = *it;
     if (a.n_q) {
       ensure_smem((const void*)k_q_bwd<TF>, a.sm_q_bwd);
       k_q_bwd<TF><<<a.n_q, AT, a.sm_q_bwd, s>>>(a.q, a.slots, x, save);
       CKLAUNCH();
+      launched(1);
     }
     if (a.n_scale) {
       ensure_smem((const void*)k_scale_bwd<TF>, a.sm_scale);
       k_scale_bwd<TF><<<a.n_scale, AT, a.sm_scale, s>>>(a.scale, a.slots, x);
       CKLAUNCH();
+      launched(1);
     }
     if (a.n_elim) {
-      ensure_smem((const void*)k_elim_bwd<TF>, a.sm_elim_bwd);
-      k_elim_bwd<TF><<<a.n_elim, AT, a.sm_elim_bwd, s>>>(a.elim, a.slots, x);
+      ensure_smem((const void*)k_elim_bwd_acc<TF>, a.sm_m);
+      ensure_smem((const void*)k_elim_bwd_x<TF>, a.sm_ns);
+      k_elim_bwd_acc<TF><<<a.n_ba, AT, a.sm_m, s>>>(a.elim, a.ba, a.slots, x, tmp);
       CKLAUNCH();
+      k_elim_bwd_x<TF><<<a.n_bx, AT, a.sm_ns, s>>>(a.elim, a.bx, a.slots, tmp, x);
+      CKLAUNCH();
+      launched(2);
     }
   }
   h->prof.launches += nl;
   h->prof.end(pid, s, 0.0, h->st.apply_bytes, nl);
 }
 
+static void apply_any(spand_handle h, double* x, double* tmp, double* save, cudaStream_t s) {
+  if (h->fprec == SPAND_FP64) apply_prec<double>(h, h->apply64, x, tmp, save, s);
+  else apply_prec<float>(h, h->apply32, x, tmp, save, s);
+}
+
 static void apply_any(spand_handle h, double* x, cudaStream_t s) {
-  if (h->fprec == SPAND_FP64) apply_prec<double>(h, h->apply64, x, s);
-  else apply_prec<float>(h, h->apply32, x, s);
+  apply_any(h, x, (double*)h->d_tmp.p, (double*)h->d_save.p, s);
 }
 
 static void ensure_solve_buffers(spand_handle h) {
