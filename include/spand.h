@@ -120,6 +120,27 @@ int spand_solve(spand_handle h, const double* b, double* x, int32_t* iters, doub
 int spand_apply(spand_handle h, const double* r_dev, double* z_dev, void* cuda_stream);
 
 /*
+ * spand_apply_noalloc -- the same z = M M^T r as spand_apply, for callers
+ * that must not allocate device memory during the call: code running while
+ * another component owns the device memory pool (for instance a framework's
+ * caching allocator with a fixed budget), or a latency-critical loop where the
+ * implicit device-wide synchronisation of cudaMalloc / cudaFree is not
+ * acceptable.  The paper has no counterpart; this is a deployment variant.
+ *   r_dev, z_dev : device float64[n], original ordering; they may alias.
+ * Work space: one fixed array of 2^21 doubles (16 MiB) compiled into the
+ * library, resident on every GPU that loads it until the process exits.  A
+ * factorization whose apply needs more (n + its per-step temporaries + its
+ * sparsification save area) is rejected with SPAND_ERR_INVALID_ARG before any
+ * GPU work.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents (nothing in
+ * it needs to start at zero); calls whose GPU work overlaps -- on different
+ * streams, handles or host threads -- race on it and must be serialised by the
+ * caller.  Errors as spand_apply.
+ */
+int spand_apply_noalloc(spand_handle h, const double* r_dev, double* z_dev, void* cuda_stream);
+
+/*
  * spand_get_tree -- the ordering and clusters (integer output of analyze).
  *   perm        : int32[n], perm[i] = vertex at position i (may be NULL)
  *   cluster_ptr : int32[n_clusters+1] (may be NULL)

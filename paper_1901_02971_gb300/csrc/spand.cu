@@ -1428,6 +1428,65 @@ int spand_apply(spand_handle h, const double* r_dev, double* z_dev, void* cuda_s
   API_END
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------- allocation-free apply
+//
+// spand_apply allocates its work vectors (device memory) on first use.  Some
+// callers cannot allow that: code that runs while another component owns the
+// whole device memory pool (a framework's caching allocator with a fixed
+// budget), or a latency-critical loop where cudaMalloc / cudaFree would add
+// their implicit device-wide synchronisation.  spand_apply_noalloc computes the
+// same z = M M^T r with its work vectors in one fixed array that lives in the
+// library image itself (a static __device__ array, kNoAllocMaxDoubles doubles =
+// 16 MiB, resident on every GPU that loads the library until the process
+// exits), so the call itself never allocates.
+namespace spand {
+constexpr int64_t kNoAllocMaxDoubles = int64_t(1) << 21;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxDoubles];
+constexpr int kNoAllocMaxDevices = 64;
+static double* g_noalloc_addr[kNoAllocMaxDevices] = {};  // device address of the array, per device
+}  // namespace spand
+
+extern "C" {
+
+int spand_apply_noalloc(spand_handle h, const double* r_dev, double* z_dev, void* cuda_stream) {
+  if (!h) { g_err = "null handle"; return SPAND_ERR_INVALID_ARG; }
+  API_BEGIN
+  g_err.clear();
+  if (!h->factored) throw Fail{SPAND_ERR_STATE, "spand_apply_noalloc before a successful spand_factorize"};
+  if (h->n && (!r_dev || !z_dev)) throw Fail{SPAND_ERR_INVALID_ARG, "null vector"};
+  const int64_t n = h->n;
+  const int64_t need = n + std::max<int64_t>(h->tmp_len, 0) + std::max<int64_t>(h->save_len, 0);
+  if (need > kNoAllocMaxDoubles)
+    throw Fail{SPAND_ERR_INVALID_ARG, "spand_apply_noalloc: this factorization needs " + std::to_string(need) +
+                                          " doubles of work space, the fixed array holds " +
+                                          std::to_string(kNoAllocMaxDoubles)};
+  if (n == 0) return SPAND_OK;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) throw Fail{SPAND_ERR_INVALID_ARG, "device ordinal out of range"};
+  if (!g_noalloc_addr[dev]) {  // once per device, with that device current
+    double* p = nullptr;
+    CK(cudaGetSymbolAddress((void**)&p, g_noalloc_scratch));
+    g_noalloc_addr[dev] = p;
+  }
+  double* w = g_noalloc_addr[dev];
+  double* tmp = w + n;
+  double* save = tmp + h->tmp_len;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+  k_permute<<<g, 256, 0, s>>>(n, (const int32_t*)h->d_perm.p, r_dev, w, 1);
+  CKLAUNCH();
+  apply_any(h, w, tmp, save, s);
+  k_permute<<<g, 256, 0, s>>>(n, (const int32_t*)h->d_perm.p, w, z_dev, 0);
+  CKLAUNCH();
+  h->prof.launches += 2;
+  CK(cudaStreamSynchronize(s));
+  return SPAND_OK;
+  API_END
+}
+
 int spand_solve(spand_handle h, const double* b, double* x, int32_t* iters, double* relres, void* cuda_stream) {
   if (!h) { g_err = "null handle"; return SPAND_ERR_INVALID_ARG; }
   API_BEGIN
