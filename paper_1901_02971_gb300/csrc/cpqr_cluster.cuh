@@ -273,22 +273,56 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
       d.Rp[i + (size_t)j * d.ldp] = (i == j) ? T(1) : T(0);
     }
   if (C > 1) cluster.sync();  // every V column and tau is visible cluster-wide
-  // ---- Q_pc e_c = H_0 ... H_c e_c (H_k e_c = e_c for k > c), one warp per column
-  for (int c = rank * (CQ_NT / 32) + warp; c < r; c += C * (CQ_NT / 32)) {
-    T* col = d.Qc + (size_t)c * np;
-    for (int i = lane; i < np; i += 32) col[i] = (i == c) ? T(1) : T(0);
-    __syncwarp();
+  // ---- Q_pc e_c = H_0 ... H_c e_c (H_k e_c = e_c for k > c), one warp per
+  // column, the column held in registers (lane l owns rows l, l+32, ...)
+  constexpr int QR = 16;  // rows per lane held in registers
+  if (np > 32 * QR) {     // tall interfaces: the column lives in global memory
+    for (int c = rank * (CQ_NT / 32) + warp; c < r; c += C * (CQ_NT / 32)) {
+      T* col = d.Qc + (size_t)c * np;
+      for (int i = lane; i < np; i += 32) col[i] = (i == c) ? T(1) : T(0);
+      __syncwarp();
+      for (int k = c; k >= 0; --k) {
+        const T tk = d.tau[k];
+        if (tk == T(0)) continue;
+        const T* v = d.V + (size_t)k * np;
+        T w = 0;
+        for (int i = k + lane; i < np; i += 32) w += v[i] * col[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        w *= tk;
+        for (int i = k + lane; i < np; i += 32) col[i] -= w * v[i];
+        __syncwarp();
+      }
+    }
+  }
+  for (int c = rank * (CQ_NT / 32) + warp; np <= 32 * QR && c < r; c += C * (CQ_NT / 32)) {
+    T col[QR];
+#pragma unroll
+    for (int q = 0; q < QR; ++q) col[q] = (lane + 32 * q == c) ? T(1) : T(0);
     for (int k = c; k >= 0; --k) {
       const T tk = d.tau[k];
       if (tk == T(0)) continue;
       const T* v = d.V + (size_t)k * np;
       T w = 0;
-      for (int i = k + lane; i < np; i += 32) w += v[i] * col[i];
+#pragma unroll
+      for (int q = 0; q < QR; ++q) {
+        const int i = lane + 32 * q;
+        if (i >= k && i < np) w += v[i] * col[q];
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
       w *= tk;
-      for (int i = k + lane; i < np; i += 32) col[i] -= w * v[i];
-      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < QR; ++q) {
+        const int i = lane + 32 * q;
+        if (i >= k && i < np) col[q] -= w * v[i];
+      }
+    }
+    T* out = d.Qc + (size_t)c * np;
+#pragma unroll
+    for (int q = 0; q < QR; ++q) {
+      const int i = lane + 32 * q;
+      if (i < np) out[i] = col[q];
     }
   }
   if (rank == 0 && tid == 0) cur_size[d.p] = r;

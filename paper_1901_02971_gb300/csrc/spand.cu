@@ -41,8 +41,8 @@ struct Fail {
 
 static inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-constexpr size_t kCpqrChunkBudget = 160 * 1024;  // shared-memory chunk per CTA
-constexpr int kCpqrMaxCluster = 8;              // portable thread-block cluster size
+constexpr size_t kCpqrChunkBudget = 192 * 1024;  // shared-memory chunk per CTA
+constexpr int kCpqrMaxCluster = 16;             // thread-block cluster size (16 = non-portable)
 constexpr int kAuxStreams = 4;
 
 // Chunked bump allocator over cudaMalloc; reset() keeps the chunks for reuse.
@@ -143,6 +143,14 @@ struct ApplyStep {
   size_t sm_ns = 0, sm_m = 0, sm_scale = 0, sm_q_fwd = 0, sm_q_bwd = 0;
 };
 
+// Clusters of more than 8 CTAs need an explicit opt-in per kernel.
+static void ensure_nonportable_cluster(const void* fn) {
+  static std::unordered_map<const void*, bool> done;
+  if (done.count(fn)) return;
+  CK(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  done[fn] = true;
+}
+
 // Highest dynamic shared memory requested so far, per kernel.
 static void ensure_smem(const void* fn, size_t bytes) {
   static std::unordered_map<const void*, size_t> done;
@@ -152,6 +160,37 @@ static void ensure_smem(const void* fn, size_t bytes) {
   CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   done[fn] = bytes;
 }
+
+// Largest cluster size (16 or 8) at which the sparsification kernel can be
+// resident with a full shared-memory chunk on this device.
+template <typename T>
+static int cpqr_max_cluster() {
+  static int cached[2] = {0, 0};
+  int& c = cached[sizeof(T) == 8 ? 1 : 0];
+  if (c) return c;
+  const void* fn = (const void*)k_cpqr_cluster<T>;
+  const size_t smem = kCpqrChunkBudget + 16 * 1024;
+  ensure_smem(fn, smem);
+  c = 8;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16, 1, 1);
+    cfg.blockDim = dim3(CQ_NT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 16;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) == cudaSuccess && n > 0) c = 16;
+  }
+  cudaGetLastError();  // a refused query only means 8
+  return c;
+}
+
 
 // Kernel-family profiler: launch counts always; with profiling on, a CUDA
 // event pair on the launching stream around each batch of launches of one
@@ -820,6 +859,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       struct WOff { size_t nrm, v, tau, qc, gw; };
       std::vector<WOff> woff;
       const size_t CB = kCpqrChunkBudget;
+      const int max_cluster = cpqr_max_cluster<T>();
       for (int p : rems) {
         if (sz[p] <= 0) continue;
         if (lay.nptr[p + 1] == lay.nptr[p]) continue;  // no neighbours: nothing to compress against
@@ -846,10 +886,10 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         tk.m_max = mm;
         // smallest cluster whose per-CTA chunk fits in shared memory, and at
         // most ~2 columns per thread
-        int C = kCpqrMaxCluster;
-        for (int c = 1; c <= kCpqrMaxCluster; c *= 2)
+        int C = max_cluster;
+        for (int c = 1; c <= max_cluster; c *= 2)
           if ((size_t)sz[p] * ((mm + c - 1) / c) * sizeof(T) <= CB) { C = c; break; }
-        while (C < kCpqrMaxCluster && (mm + C - 1) / C > 2 * CQ_NT) C *= 2;
+        while (C < max_cluster && (mm + C - 1) / C > 2 * CQ_NT) C *= 2;
         const bool resident = (size_t)sz[p] * ((mm + C - 1) / C) * sizeof(T) <= CB;
         WOff w;
         w.nrm = 0;
@@ -917,6 +957,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
             const size_t smem = G.smem + G.chunk;
             const void* fn = (const void*)k_cpqr_cluster<T>;
             ensure_smem(fn, smem);
+            if (G.C > 8) ensure_nonportable_cluster(fn);
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3((unsigned)(G.ids.size() * G.C), 1, 1);
             cfg.blockDim = dim3(CQ_NT, 1, 1);
