@@ -241,16 +241,43 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
     for (int jl = tid; jl < nc; jl += CQ_NT) {
       if (jl == gj - j0) continue;
       if (snorm[jl] < T(0)) continue;
-      T w = 0;
-      for (int i = k; i < np; ++i) w += vbuf[i] * chunk[(size_t)i * ldc + jl];
-      w *= tau;
-      T sq = 0;
-      for (int i = k; i < np; ++i) {
-        const T x = chunk[(size_t)i * ldc + jl] - w * vbuf[i];
-        chunk[(size_t)i * ldc + jl] = x;
-        if (i > k) sq += x * x;
+      T* __restrict__ col = chunk + jl;    // disjoint from vbuf: lets the loads run ahead of the stores
+      const T* __restrict__ vb = vbuf;
+      // w = v^T col[k:], four independent partial sums
+      T w0 = 0, w1 = 0, w2 = 0, w3 = 0;
+      int i = k;
+      for (; i + 4 <= np; i += 4) {
+        w0 += vb[i] * col[(size_t)i * ldc];
+        w1 += vb[i + 1] * col[(size_t)(i + 1) * ldc];
+        w2 += vb[i + 2] * col[(size_t)(i + 2) * ldc];
+        w3 += vb[i + 3] * col[(size_t)(i + 3) * ldc];
       }
-      snorm[jl] = sq;
+      for (; i < np; ++i) w0 += vb[i] * col[(size_t)i * ldc];
+      const T w = ((w0 + w1) + (w2 + w3)) * tau;
+      col[(size_t)k * ldc] -= w;  // v_k = 1
+      // update rows k+1.. and their squared norm
+      T q0 = 0, q1 = 0, q2 = 0, q3 = 0;
+      i = k + 1;
+      for (; i + 4 <= np; i += 4) {
+        const T x0 = col[(size_t)i * ldc] - w * vb[i];
+        const T x1 = col[(size_t)(i + 1) * ldc] - w * vb[i + 1];
+        const T x2 = col[(size_t)(i + 2) * ldc] - w * vb[i + 2];
+        const T x3 = col[(size_t)(i + 3) * ldc] - w * vb[i + 3];
+        col[(size_t)i * ldc] = x0;
+        col[(size_t)(i + 1) * ldc] = x1;
+        col[(size_t)(i + 2) * ldc] = x2;
+        col[(size_t)(i + 3) * ldc] = x3;
+        q0 += x0 * x0;
+        q1 += x1 * x1;
+        q2 += x2 * x2;
+        q3 += x3 * x3;
+      }
+      for (; i < np; ++i) {
+        const T x = col[(size_t)i * ldc] - w * vb[i];
+        col[(size_t)i * ldc] = x;
+        q0 += x * x;
+      }
+      snorm[jl] = (q0 + q1) + (q2 + q3);
     }
     __syncthreads();
   }

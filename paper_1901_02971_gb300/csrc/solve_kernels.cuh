@@ -35,18 +35,13 @@ struct ApplyItem {   // one CTA's share of an operation: op index and first row 
 };
 
 template <typename TF>
-struct ScaleOp {
+struct SqOp {        // scaling S_p followed (if p is sparsified) by Q_p^T, one cluster
   const TF* Y;       // U_p^{-T} (lower, np x np, ld = np)
-  int32_t np, pad;
-  int64_t slot;
-};
-
-template <typename TF>
-struct QOp {
-  const TF* Q;       // np x r coarse basis, ld = np
+  const TF* Q;       // coarse basis Q_pc (np x r, ld = np); nullptr: not sparsified (r = np)
   int32_t np, r;
-  int64_t slot;
-  int64_t save;      // np (forward input) + r (coarse values) entries
+  int64_t slot;      // np slots of p
+  int64_t save;      // np (scaled forward input) + r (coarse values) entries, kept per apply
+  int64_t tz;        // temp: np entries of the backward sweep
 };
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -163,80 +158,94 @@ __global__ void k_scatter(const int32_t* __restrict__ tslot, const int64_t* __re
   }
 }
 
-// x_p <- U_p^{-T} x_p = Y x_p (one CTA per cluster; 32-row blocks)
+
+
+// ---------------------------------------------------------------- backward sweep
+
+
+
+// ---------------------------------------------------------------- scaling + coarse basis
+
+// forward, part 1: y_p = U_p^{-T} x_p = Y x_p for one 32-row block -> save[0:np]
 template <typename TF>
-__global__ void __launch_bounds__(AT) k_scale_fwd(const ScaleOp<TF>* __restrict__ ops, const int32_t* __restrict__ slots,
-                                                 double* __restrict__ x) {
+__global__ void __launch_bounds__(AT) k_sq_fwd_y(const SqOp<TF>* __restrict__ ops, const ApplyItem* __restrict__ items,
+                                                const int32_t* __restrict__ slots, const double* __restrict__ x,
+                                                double* __restrict__ save) {
   extern __shared__ double xs[];
   __shared__ double part[AT / 32][RB + 1];
-  const ScaleOp<TF> o = ops[blockIdx.x];
+  const ApplyItem it = items[blockIdx.x];
+  const SqOp<TF> o = ops[it.op];
   const int32_t* sl = slots + o.slot;
-  for (int i = threadIdx.x; i < o.np; i += AT) xs[i] = x[sl[i]];
+  const int K = min(o.np, it.first + RB);
+  for (int j = threadIdx.x; j < K; j += AT) xs[j] = x[sl[j]];
   __syncthreads();
-  for (int r0 = 0; r0 < o.np; r0 += RB) {
-    const double v = rowblock_dot(o.Y, (size_t)o.np, r0, o.np, xs, min(o.np, r0 + RB), part);
-    const int i = r0 + (threadIdx.x & 31);
-    if (threadIdx.x < 32 && i < o.np) x[sl[i]] = v;
-  }
+  const double v = rowblock_dot(o.Y, (size_t)o.np, it.first, o.np, xs, K, part);
+  const int i = it.first + (threadIdx.x & 31);
+  if (threadIdx.x < 32 && i < o.np) save[o.save + i] = v;
 }
 
-// c = Q_pc^T x_p (the coarse values go to the first r slots; the forward
-// input and c are saved for the backward sweep)
+// forward, part 2: c = Q_pc^T y_p (identity when p is not sparsified), AP_COLS
+// outputs per CTA -> x[first r slots] and save[np:np+r]
 template <typename TF>
-__global__ void __launch_bounds__(AT) k_q_fwd(const QOp<TF>* __restrict__ ops, const int32_t* __restrict__ slots,
-                                             double* __restrict__ x, double* __restrict__ save) {
+__global__ void __launch_bounds__(AT) k_sq_fwd_c(const SqOp<TF>* __restrict__ ops, const ApplyItem* __restrict__ items,
+                                                const int32_t* __restrict__ slots, double* __restrict__ x,
+                                                double* __restrict__ save) {
   extern __shared__ double ys[];
-  const QOp<TF> o = ops[blockIdx.x];
+  const ApplyItem it = items[blockIdx.x];
+  const SqOp<TF> o = ops[it.op];
   const int32_t* sl = slots + o.slot;
   double* sv = save + o.save;
-  for (int i = threadIdx.x; i < o.np; i += AT) {
-    const double v = x[sl[i]];
-    ys[i] = v;
-    sv[i] = v;
-  }
+  for (int i = threadIdx.x; i < o.np; i += AT) ys[i] = sv[i];
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = AT / 32;
-  for (int k = warp; k < o.r; k += nw) {
-    const double s = dot_warp(o.Q + (size_t)k * o.np, ys, 0, o.np);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int hi = min(o.r, it.first + AP_COLS);
+  for (int k = it.first + warp; k < hi; k += AT / 32) {
+    const double c = o.Q ? dot_warp(o.Q + (size_t)k * o.np, ys, 0, o.np) : ys[k];
     if (lane == 0) {
-      sv[o.np + k] = s;
-      x[sl[k]] = s;
+      x[sl[k]] = c;
+      sv[o.np + k] = c;
     }
   }
 }
 
-// ---------------------------------------------------------------- backward sweep
-
-// x_p = (forward input) + Q_pc (c - c_old)
+// backward, part 1: z = y_p + Q_pc (c - c_old) for one 32-row block -> tmp[tz]
+// (without Q: z = x_p)
 template <typename TF>
-__global__ void __launch_bounds__(AT) k_q_bwd(const QOp<TF>* __restrict__ ops, const int32_t* __restrict__ slots,
-                                             double* __restrict__ x, const double* __restrict__ save) {
+__global__ void __launch_bounds__(AT) k_sq_bwd_z(const SqOp<TF>* __restrict__ ops, const ApplyItem* __restrict__ items,
+                                                const int32_t* __restrict__ slots, const double* __restrict__ x,
+                                                const double* __restrict__ save, double* __restrict__ tmp) {
   extern __shared__ double dc[];
   __shared__ double part[AT / 32][RB + 1];
-  const QOp<TF> o = ops[blockIdx.x];
+  const ApplyItem it = items[blockIdx.x];
+  const SqOp<TF> o = ops[it.op];
   const int32_t* sl = slots + o.slot;
   const double* sv = save + o.save;
+  const int i = it.first + (threadIdx.x & 31);
+  if (!o.Q) {
+    if (threadIdx.x < 32 && i < o.np) tmp[o.tz + i] = x[sl[i]];
+    return;
+  }
   for (int k = threadIdx.x; k < o.r; k += AT) dc[k] = x[sl[k]] - sv[o.np + k];
   __syncthreads();
-  for (int r0 = 0; r0 < o.np; r0 += RB) {
-    const double v = rowblock_dot(o.Q, (size_t)o.np, r0, o.np, dc, o.r, part);
-    const int i = r0 + (threadIdx.x & 31);
-    if (threadIdx.x < 32 && i < o.np) x[sl[i]] = sv[i] + v;
-  }
+  const double v = rowblock_dot(o.Q, (size_t)o.np, it.first, o.np, dc, o.r, part);
+  if (threadIdx.x < 32 && i < o.np) tmp[o.tz + i] = sv[i] + v;
 }
 
-// x_p <- U_p^{-1} x_p = Y^T x_p
+// backward, part 2: x_p = U_p^{-1} z = Y^T z, AP_COLS outputs per CTA
 template <typename TF>
-__global__ void __launch_bounds__(AT) k_scale_bwd(const ScaleOp<TF>* __restrict__ ops, const int32_t* __restrict__ slots,
-                                                 double* __restrict__ x) {
-  extern __shared__ double xs[];
-  const ScaleOp<TF> o = ops[blockIdx.x];
+__global__ void __launch_bounds__(AT) k_sq_bwd_x(const SqOp<TF>* __restrict__ ops, const ApplyItem* __restrict__ items,
+                                                const int32_t* __restrict__ slots, const double* __restrict__ tmp,
+                                                double* __restrict__ x) {
+  extern __shared__ double zs[];
+  const ApplyItem it = items[blockIdx.x];
+  const SqOp<TF> o = ops[it.op];
   const int32_t* sl = slots + o.slot;
-  for (int i = threadIdx.x; i < o.np; i += AT) xs[i] = x[sl[i]];
+  for (int i = threadIdx.x; i < o.np; i += AT) zs[i] = tmp[o.tz + i];
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = AT / 32;
-  for (int j = warp; j < o.np; j += nw) {
-    const double v = dot_warp(o.Y + (size_t)j * o.np, xs, j, o.np);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int hi = min(o.np, it.first + AP_COLS);
+  for (int j = it.first + warp; j < hi; j += AT / 32) {
+    const double v = dot_warp(o.Y + (size_t)j * o.np, zs, j, o.np);
     if (lane == 0) x[sl[j]] = v;
   }
 }
