@@ -141,6 +141,19 @@ int spand_apply(spand_handle h, const double* r_dev, double* z_dev, void* cuda_s
 int spand_apply_noalloc(spand_handle h, const double* r_dev, double* z_dev, void* cuda_stream);
 
 /*
+ * spand_sampled_outer -- out[e] = -lam[i] * x[j] for every stored entry e =
+ * (i, j) of A, in the CSR order given to spand_analyze.  With x = A^{-1} b and
+ * lam = A^{-1} (dL/dx) (the adjoint solve, same factorization since A is
+ * SPD), this is dL/dA restricted to A's pattern (each stored value taken as
+ * an independent parameter; for a symmetric parameterization add the entries
+ * (i, j) and (j, i)).  Not part of the paper: it makes spand_solve
+ * differentiable.
+ *   lam_dev, x_dev : device float64[n]; out_dev : device float64[nnz].
+ */
+int spand_sampled_outer(spand_handle h, const double* lam_dev, const double* x_dev, double* out_dev,
+                        void* cuda_stream);
+
+/*
  * spand_get_tree -- the ordering and clusters (integer output of analyze).
  *   perm        : int32[n], perm[i] = vertex at position i (may be NULL)
  *   cluster_ptr : int32[n_clusters+1] (may be NULL)

@@ -29,7 +29,7 @@ SPAND_FP32 = 1
 
 # every function declared in include/spand.h
 EXPORTS = ["spand_default_opts", "spand_analyze", "spand_factorize", "spand_solve", "spand_apply",
-           "spand_apply_noalloc",
+           "spand_apply_noalloc", "spand_sampled_outer",
            "spand_get_tree", "spand_get_step", "spand_get_ranks", "spand_get_stats",
            "spand_get_phase_times", "spand_set_profiling", "spand_get_kernel_profile",
            "spand_reset_kernel_profile", "spand_get_launch_count", "spand_destroy", "spand_error_string",
@@ -75,6 +75,7 @@ def lib():
     L.spand_solve.argtypes = [C.c_void_p, P, P, i32p, C.POINTER(C.c_double), P]
     L.spand_apply.argtypes = [C.c_void_p, P, P, P]
     L.spand_apply_noalloc.argtypes = [C.c_void_p, P, P, P]
+    L.spand_sampled_outer.argtypes = [C.c_void_p, P, P, P, P]
     L.spand_get_tree.argtypes = [C.c_void_p, P, P, P, i32p, i32p]
     L.spand_get_step.argtypes = [C.c_void_p, C.c_int32] + [P] * 10
     L.spand_get_ranks.argtypes = [C.c_void_p, C.c_int32, P, P]
@@ -156,6 +157,11 @@ def spand_apply_noalloc(h: int, r_ptr: int, z_ptr: int, stream: int = 0):
     """z = M M^T r on device vectors without allocating device memory (fixed
     work array inside the library; see include/spand.h)."""
     _check(lib().spand_apply_noalloc(h, r_ptr, z_ptr, stream or None))
+
+
+def spand_sampled_outer(h: int, lam_ptr: int, x_ptr: int, out_ptr: int, stream: int = 0):
+    """out[e] = -lam[i] x[j] on A's stored pattern (device pointers)."""
+    _check(lib().spand_sampled_outer(h, lam_ptr, x_ptr, out_ptr, stream or None))
 
 
 def spand_get_tree(h: int) -> dict:

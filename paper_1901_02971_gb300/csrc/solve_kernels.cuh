@@ -392,6 +392,16 @@ __global__ void k_gather_vals(int64_t nnz, const int64_t* __restrict__ src, cons
     out[k] = vals[src[k]];
 }
 
+// dL/dA on A's pattern: out[e] = -lam[row(e)] * x[col(e)] (original CSR order)
+__global__ void k_sampled_outer(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                const double* __restrict__ lam, const double* __restrict__ x, double* __restrict__ out) {
+  for (int64_t row = blockIdx.x * (int64_t)(blockDim.x / 32) + (threadIdx.x >> 5); row < n;
+       row += (int64_t)gridDim.x * (blockDim.x / 32)) {
+    const double l = -lam[row];
+    for (int64_t e = rp[row] + (threadIdx.x & 31); e < rp[row + 1]; e += 32) out[e] = l * x[ci[e]];
+  }
+}
+
 // r = b - A x
 __global__ void k_residual(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                            const double* __restrict__ va, const double* __restrict__ x, const double* __restrict__ b,

@@ -291,6 +291,7 @@ struct spand_handle_s {
   DevBuf scratch[2];
   DevBuf d_vals, d_asm_row, d_asm_off, d_prow, d_pcol, d_pval, d_pval_src, d_perm;
   DevBuf d_vec, d_tmp, d_save, d_bin, d_bout;
+  DevBuf d_rowptr, d_colind;  // original CSR pattern (gradient on A's pattern)
   int fprec = -1;
   bool factored = false;
   std::vector<ApplyStep<double>> apply64;
@@ -973,9 +974,13 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
             attr[0].val.clusterDim.z = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            CK(cudaLaunchKernelEx(&cfg, k_cpqr_cluster<T>, at<const CpqrTask<T>>(d, ot),
-                                  at<const int32_t>(d, ol) + gbeg[g], at<const CpqrNbr<T>>(d, on), d_cur, (T)eps,
-                                  (int32_t)G.chunk));
+            const CpqrTask<T>* a0 = at<const CpqrTask<T>>(d, ot);
+            const int32_t* a1 = at<const int32_t>(d, ol) + gbeg[g];
+            const CpqrNbr<T>* a2 = at<const CpqrNbr<T>>(d, on);
+            T a4 = (T)eps;
+            int32_t a5 = (int32_t)G.chunk;
+            void* args[] = {(void*)&a0, (void*)&a1, (void*)&a2, (void*)&d_cur, (void*)&a4, (void*)&a5};
+            CK(cudaLaunchKernelExC(&cfg, fn, args));
             CK(cudaEventRecord(h->ev_join[(g - gi) % kAuxStreams], as));
           }
           for (size_t g = gi; g < std::min(ge, gi + (size_t)kAuxStreams); ++g)
@@ -1773,6 +1778,31 @@ int spand_get_launch_count(spand_handle h, int64_t* launches) {
   if (!h || !launches) { g_err = "null argument"; return SPAND_ERR_INVALID_ARG; }
   *launches = h->prof.launches;
   return SPAND_OK;
+}
+
+int spand_sampled_outer(spand_handle h, const double* lam_dev, const double* x_dev, double* out_dev,
+                        void* cuda_stream) {
+  if (!h) { g_err = "null handle"; return SPAND_ERR_INVALID_ARG; }
+  API_BEGIN
+  g_err.clear();
+  const int64_t n = h->n, nnz = h->nnz;
+  if (nnz && (!lam_dev || !x_dev || !out_dev)) throw Fail{SPAND_ERR_INVALID_ARG, "null vector"};
+  if (nnz == 0) return SPAND_OK;
+  if (!h->d_rowptr.p) {  // the original pattern, copied to the device on first use
+    h->d_rowptr.ensure((n + 1) * sizeof(int64_t));
+    h->d_colind.ensure(nnz * sizeof(int32_t));
+    CK(cudaMemcpy(h->d_rowptr.p, h->rowptr.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_colind.p, h->colind.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice));
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const unsigned g = (unsigned)std::min<int64_t>((n + 7) / 8, 8192);
+  k_sampled_outer<<<g, 256, 0, s>>>(n, (const int64_t*)h->d_rowptr.p, (const int32_t*)h->d_colind.p, lam_dev, x_dev,
+                                    out_dev);
+  CKLAUNCH();
+  h->prof.launches += 1;
+  CK(cudaStreamSynchronize(s));
+  return SPAND_OK;
+  API_END
 }
 
 int spand_get_tree(spand_handle h, int32_t* perm, int32_t* cluster_ptr, int32_t* cluster_key, int32_t* n_clusters,

@@ -29,6 +29,7 @@ class Solver:
         prec = {"fp64": L.SPAND_FP64, "fp32": L.SPAND_FP32}[precision]
         self.opts = L.default_opts(levels=levels, eps=eps, skip=skip, precision=prec, maxit=maxit, tol=tol)
         self.n = int(np.asarray(rowptr).size - 1)
+        self.nnz = int(np.asarray(rowptr)[-1])
         self.h = L.spand_analyze(rowptr, colind, vals, coords, self.opts)
 
     @classmethod
@@ -43,6 +44,9 @@ class Solver:
         """b: float64 numpy array (host) or torch CUDA tensor; returns (x, iters, relres)."""
         if x is None:
             x = np.empty(self.n) if isinstance(b, np.ndarray) else b.new_empty(b.shape)
+        if stream == 0 and not isinstance(b, np.ndarray):
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
         rc, it, rr = L.spand_solve(self.h, _addr(b), _addr(x), stream, check=check)
         return x, it, rr
 
