@@ -52,238 +52,282 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 // ---------------------------------------------------------------- forward sweep
 
-// warp-wide sum_{i in [i0, n)} a[i] * x[i] (a contiguous), lanes over i,
-// four independent accumulators (128 elements per iteration)
-template <typename TF>
-__device__ __forceinline__ double dot_warp(const TF* __restrict__ a, const double* x, int i0, int n) {
-  const int lane = threadIdx.x & 31;
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int i = i0 + lane;
-  for (; i + 96 < n; i += 128) {
-    s0 += (double)a[i] * x[i];
-    s1 += (double)a[i + 32] * x[i + 32];
-    s2 += (double)a[i + 64] * x[i + 64];
-    s3 += (double)a[i + 96] * x[i + 96];
-  }
-  for (; i < n; i += 32) s0 += (double)a[i] * x[i];
-  return warp_sum_d((s0 + s1) + (s2 + s3));
-}
+constexpr int RB = 32;       // rows per item of the row-block GEMVs (one per lane)
+constexpr int AP_COLS = 32;  // columns per item of the column-dot GEMVs (four per warp)
+constexpr int SCH = 2048;    // input-vector chunk staged in shared memory (elements)
 
-constexpr int RB = 32;       // rows per block of the row-dot kernels (one per lane)
-constexpr int AP_COLS = 32;  // outputs per CTA of the warp-per-column kernels
+// Vectors written during the apply by other CTAs are read through L2 (ld.cg):
+// the L1 of an SM is not coherent with writes made by other SMs.
+__device__ __forceinline__ double ldv(const double* p) { return __ldcg(p); }
 
-// Row dots of a 32-row block: sum_{k < K} A[r0 + lane + k*ld] x[k], with the K
-// range split over the CTA's 8 warps (lanes cover consecutive rows, so every
-// load is coalesced) and the 8 partial sums added in a fixed order.  All
-// threads must call it; the result is valid in warp 0 for row r0 + lane.
-template <typename TF>
-__device__ __forceinline__ double rowblock_dot(const TF* __restrict__ A, size_t ld, int r0, int nrows,
-                                               const double* x, int K, double (*part)[RB + 1]) {
+// Row-block GEMV: out[r] = sum_{k < K} A[r + k*ld] v(k) for the 32 rows
+// r = r0 + lane, with v staged in shared memory in chunks of SCH and the
+// chunk's columns split over the 8 warps (lanes cover consecutive rows, so
+// every load is one coalesced 32-element segment; eight loads in flight per
+// thread).  Partial sums are combined in a fixed order.  All threads call it;
+// the result is valid in warp 0.
+template <typename TF, typename ACC, typename Src>
+__device__ __forceinline__ ACC rowblock_gemv(const TF* __restrict__ A, size_t ld, int r0, int nrows, int K, Src src,
+                                             ACC* vs, ACC (*part)[RB + 1]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = AT / 32;
   const int row = r0 + lane;
-  const int kc = (K + nw - 1) / nw;
-  const int k0 = warp * kc, k1 = min(K, k0 + kc);
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  if (row < nrows) {
-    const TF* a = A + row;
-    int k = k0;
-    for (; k + 4 <= k1; k += 4) {
-      s0 += (double)a[(size_t)k * ld] * x[k];
-      s1 += (double)a[(size_t)(k + 1) * ld] * x[k + 1];
-      s2 += (double)a[(size_t)(k + 2) * ld] * x[k + 2];
-      s3 += (double)a[(size_t)(k + 3) * ld] * x[k + 3];
+  const bool live = row < nrows;
+  ACC s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+  for (int k0 = 0; k0 < K; k0 += SCH) {
+    const int kn = min(SCH, K - k0);
+    __syncthreads();  // the previous chunk has been consumed
+    for (int k = threadIdx.x; k < kn; k += AT) vs[k] = (ACC)src(k0 + k);
+    __syncthreads();
+    const int kc = (kn + nw - 1) / nw;
+    const int kb = min(kn, warp * kc), ke = min(kn, kb + kc);
+    if (live) {
+      const TF* ap = A + row + (size_t)(k0 + kb) * ld;
+      int k = kb;
+      for (; k + 8 <= ke; k += 8) {
+        TF a[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] = __ldg(ap + (size_t)u * ld);
+        s0 = fma((ACC)a[0], vs[k], s0);
+        s1 = fma((ACC)a[1], vs[k + 1], s1);
+        s2 = fma((ACC)a[2], vs[k + 2], s2);
+        s3 = fma((ACC)a[3], vs[k + 3], s3);
+        s0 = fma((ACC)a[4], vs[k + 4], s0);
+        s1 = fma((ACC)a[5], vs[k + 5], s1);
+        s2 = fma((ACC)a[6], vs[k + 6], s2);
+        s3 = fma((ACC)a[7], vs[k + 7], s3);
+        ap += 8 * ld;
+      }
+      for (; k < ke; ++k, ap += ld) s0 = fma((ACC)__ldg(ap), vs[k], s0);
     }
-    for (; k < k1; ++k) s0 += (double)a[(size_t)k * ld] * x[k];
   }
   part[warp][lane] = (s0 + s1) + (s2 + s3);
   __syncthreads();
-  double t = 0.0;
+  ACC t = 0;
   if (warp == 0)
     for (int w = 0; w < nw; ++w) t += part[w][lane];
   __syncthreads();
   return t;
 }
 
-// forward, part 1: y_s = U_s^{-T} x_s = Y x_s for one 32-row block -> tmp[ty]
-// (Y is exactly zero above its diagonal, so the block reads columns < r0 + 32)
-template <typename TF>
-__global__ void __launch_bounds__(AT) k_elim_fwd_y(const ElimOp<TF>* __restrict__ ops, const ApplyItem* __restrict__ items,
-                                                  const int32_t* __restrict__ slots, const double* __restrict__ x,
-                                                  double* __restrict__ tmp) {
-  extern __shared__ double xs[];
-  __shared__ double part[AT / 32][RB + 1];
-  const ApplyItem it = items[blockIdx.x];
-  const ElimOp<TF> o = ops[it.op];
-  const int32_t* sl = slots + o.slot;
-  const int K = min(o.ns, it.first + RB);
-  for (int j = threadIdx.x; j < K; j += AT) xs[j] = x[sl[j]];
-  __syncthreads();
-  const double v = rowblock_dot(o.Y, (size_t)o.ns, it.first, o.ns, xs, K, part);
-  const int i = it.first + (threadIdx.x & 31);
-  if (threadIdx.x < 32 && i < o.ns) tmp[o.ty + i] = v;
+template <typename ACC>
+__device__ __forceinline__ ACC warp_sum(ACC v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
-// forward, part 2: u = X_ns y_s (X_ns = (X^T)^T), AP_COLS outputs per CTA -> tmp[tu]
-template <typename TF>
-__global__ void __launch_bounds__(AT) k_elim_fwd_u(const ElimOp<TF>* __restrict__ ops, const ApplyItem* __restrict__ items,
-                                                  double* __restrict__ tmp) {
-  extern __shared__ double ys[];
-  const ApplyItem it = items[blockIdx.x];
-  const ElimOp<TF> o = ops[it.op];
-  for (int i = threadIdx.x; i < o.ns; i += AT) ys[i] = tmp[o.ty + i];
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const TF* XT = o.R + (size_t)o.ns * o.ns;
-  const int hi = min(o.m, it.first + AP_COLS);
-  for (int j = it.first + warp; j < hi; j += AT / 32) {
-    const double v = dot_warp(XT + (size_t)j * o.ns, ys, 0, o.ns);
-    if (lane == 0) tmp[o.tu + j] = v;
+// Column-dot GEMV: out(j) = sum_{i in [lo_j, n)} A[i + j*ld] v(i) for the
+// columns j in [c0, c1) (at most AP_COLS), lo_j = j if `tri` (A lower
+// triangular: rows above the diagonal are never read) else 0.  Warp w owns
+// columns c0 + w + 8q (q < 4) and sweeps them together, lanes over i, so four
+// to eight loads are in flight per lane; v is staged in chunks of SCH.  All
+// threads call it; `store(j, value)` runs on lane 0 of the owning warp.
+template <typename TF, typename ACC, typename Src, typename Store>
+__device__ __forceinline__ void coldot_gemv(const TF* __restrict__ A, size_t ld, int n, int c0, int c1, bool tri,
+                                            Src src, Store store, ACC* vs) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = AT / 32;
+  int j[4];
+  bool ok[4];
+  ACC acc[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    j[q] = c0 + warp + nw * q;
+    ok[q] = j[q] < c1;
+    acc[q] = 0;
+  }
+  const int lo = tri ? c0 : 0;  // no column of this item reads rows above c0
+  for (int i0 = lo; i0 < n; i0 += SCH) {
+    const int in = min(SCH, n - i0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < in; i += AT) vs[i] = (ACC)src(i0 + i);
+    __syncthreads();
+    int i = lane;
+    for (; i + 32 < in; i += 64) {
+      TF a[4][2];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const TF* col = A + (size_t)j[q] * ld + i0;
+        const bool t0 = ok[q] && (!tri || i0 + i >= j[q]);
+        const bool t1 = ok[q] && (!tri || i0 + i + 32 >= j[q]);
+        a[q][0] = t0 ? __ldg(col + i) : TF(0);
+        a[q][1] = t1 ? __ldg(col + i + 32) : TF(0);
+      }
+      const ACC v0 = vs[i], v1 = vs[i + 32];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fma((ACC)a[q][1], v1, fma((ACC)a[q][0], v0, acc[q]));
+    }
+    for (; i < in; i += 32) {
+      const ACC v0 = vs[i];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (ok[q] && (!tri || i0 + i >= j[q])) acc[q] = fma((ACC)__ldg(A + (size_t)j[q] * ld + i0 + i), v0, acc[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const ACC v = warp_sum(acc[q]);
+    if (ok[q] && lane == 0) store(j[q], v);
   }
 }
 
-// forward, part 3: x_s = y_s (assign targets) and x_n -= sum of the u's aimed
-// at it (pull form, fixed order).  Targets [0, nassign) are assignments with
-// exactly one source.
-__global__ void k_scatter(const int32_t* __restrict__ tslot, const int64_t* __restrict__ ptr,
-                          const int64_t* __restrict__ idx, const double* __restrict__ tmp, double* __restrict__ x,
-                          int64_t nassign, int64_t ntgt) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntgt; t += (int64_t)gridDim.x * blockDim.x) {
-    if (t < nassign) {
-      x[tslot[t]] = tmp[idx[ptr[t]]];
+// ---------------------------------------------------------------- the persistent apply
+//
+// The whole apply is one cooperative launch that walks the phases of every
+// step in order (forward: leaves -> root, backward: root -> leaves) with a
+// grid-wide barrier between dependent phases; within a phase the items are
+// independent and are spread over all CTAs.
+
+enum ApplyKind : int32_t {
+  PH_FY = 0,   // E_s forward:  y_s = Y x_s                  -> tmp[ty]
+  PH_FU,       //               u = X_ns y_s                  -> tmp[tu]
+  PH_SCATTER,  //               x_s = y_s, x_n -= sum u (pull, fixed order)
+  PH_SY,       // S_p forward:  y_p = Y x_p                  -> save[0:np]
+  PH_SC,       // Q_p^T:        c = Q_pc^T y_p               -> x (coarse slots), save[np:np+r]
+  PH_SZ,       // Q_p backward: z = y_p + Q_pc (c - c_old)   -> tmp[tz]
+  PH_SX,       // S_p backward: x_p = Y^T z
+  PH_BA,       // E_s backward: acc = x_s - X_ns^T x_n       -> tmp[ta]
+  PH_BX        //               x_s = Y^T acc
+};
+
+template <typename TF>
+struct ApplyPhase {
+  int32_t kind, n;             // n = items, or scatter targets
+  const ElimOp<TF>* elim;
+  const SqOp<TF>* sq;
+  const ApplyItem* items;
+  const int32_t* slots;
+  const int32_t* tslot;        // scatter only
+  const int64_t* tptr;
+  const int64_t* tidx;
+  int64_t nassign;
+};
+
+constexpr unsigned kBarrierSpins = 1u << 24;  // with ~40 ns sleeps: well over a second
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier on a monotonically increasing arrival counter (reset to 0
+// before the launch): barrier b completes when the counter reaches
+// (b + 1) * gridDim.x.  All CTAs are co-resident (cooperative launch).  The
+// wait is bounded: on timeout *err is set and false is returned to every
+// thread of the CTA, which then leaves the kernel.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, int* err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    __threadfence();
+    atomicAdd(count, 1u);
+    unsigned spins = 0;
+    while (ld_acquire_u32(count) < target) {
+      if (++spins > kBarrierSpins) {
+        atomicExch(err, 1);
+        ok = 0;
+        break;
+      }
+      __nanosleep(40);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <typename TF>
+__global__ void __launch_bounds__(AT) k_apply(const ApplyPhase<TF>* __restrict__ phases, int nph, double* x,
+                                              double* tmp, double* save, unsigned* bar, int* err) {
+  typedef TF ACC;  // inner sums in the factor's precision
+  extern __shared__ __align__(16) unsigned char apply_smem[];
+  ACC* vs = reinterpret_cast<ACC*>(apply_smem);
+  __shared__ ACC part[AT / 32][RB + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int p = 0; p < nph; ++p) {
+    const ApplyPhase<TF> P = phases[p];
+    if (P.kind == PH_SCATTER) {
+      for (int64_t t = blockIdx.x * (int64_t)AT + threadIdx.x; t < P.n; t += (int64_t)gridDim.x * AT) {
+        if (t < P.nassign) {
+          x[P.tslot[t]] = ldv(tmp + P.tidx[P.tptr[t]]);
+        } else {
+          double s = 0.0;
+          for (int64_t e = P.tptr[t]; e < P.tptr[t + 1]; ++e) s += ldv(tmp + P.tidx[e]);
+          x[P.tslot[t]] = ldv(x + P.tslot[t]) - s;
+        }
+      }
     } else {
-      double s = 0.0;
-      for (int64_t e = ptr[t]; e < ptr[t + 1]; ++e) s += tmp[idx[e]];
-      x[tslot[t]] -= s;
+      for (int itx = blockIdx.x; itx < P.n; itx += gridDim.x) {
+        const ApplyItem it = P.items[itx];
+        if (P.kind == PH_FY || P.kind == PH_BA || P.kind == PH_FU || P.kind == PH_BX) {
+          const ElimOp<TF> o = P.elim[it.op];
+          const int32_t* sl = P.slots + o.slot;
+          const TF* XT = o.R + (size_t)o.ns * o.ns;
+          if (P.kind == PH_FY) {
+            const int K = min(o.ns, it.first + RB);
+            const ACC v = rowblock_gemv<TF, ACC>(o.Y, (size_t)o.ns, it.first, o.ns, K,
+                                                 [&](int k) { return ldv(x + sl[k]); }, vs, part);
+            const int i = it.first + lane;
+            if (warp == 0 && i < o.ns) tmp[o.ty + i] = (double)v;
+          } else if (P.kind == PH_BA) {
+            const ACC v = rowblock_gemv<TF, ACC>(XT, (size_t)o.ns, it.first, o.ns, o.m,
+                                                 [&](int k) { return ldv(x + sl[o.ns + k]); }, vs, part);
+            const int i = it.first + lane;
+            if (warp == 0 && i < o.ns) tmp[o.ta + i] = ldv(x + sl[i]) - (double)v;
+          } else if (P.kind == PH_FU) {
+            coldot_gemv<TF, ACC>(XT, (size_t)o.ns, o.ns, it.first, min(o.m, it.first + AP_COLS), false,
+                                 [&](int i) { return ldv(tmp + o.ty + i); },
+                                 [&](int j, ACC v) { tmp[o.tu + j] = (double)v; }, vs);
+          } else {  // PH_BX
+            coldot_gemv<TF, ACC>(o.Y, (size_t)o.ns, o.ns, it.first, min(o.ns, it.first + AP_COLS), true,
+                                 [&](int i) { return ldv(tmp + o.ta + i); },
+                                 [&](int j, ACC v) { x[sl[j]] = (double)v; }, vs);
+          }
+        } else {
+          const SqOp<TF> o = P.sq[it.op];
+          const int32_t* sl = P.slots + o.slot;
+          double* sv = save + o.save;
+          if (P.kind == PH_SY) {
+            const int K = min(o.np, it.first + RB);
+            const ACC v = rowblock_gemv<TF, ACC>(o.Y, (size_t)o.np, it.first, o.np, K,
+                                                 [&](int k) { return ldv(x + sl[k]); }, vs, part);
+            const int i = it.first + lane;
+            if (warp == 0 && i < o.np) sv[i] = (double)v;
+          } else if (P.kind == PH_SC) {
+            const int hi = min(o.r, it.first + AP_COLS);
+            if (o.Q) {
+              coldot_gemv<TF, ACC>(o.Q, (size_t)o.np, o.np, it.first, hi, false, [&](int i) { return ldv(sv + i); },
+                                   [&](int k, ACC c) {
+                                     x[sl[k]] = (double)c;
+                                     sv[o.np + k] = (double)c;
+                                   },
+                                   vs);
+            } else {
+              for (int k = it.first + threadIdx.x; k < hi; k += AT) {
+                const double c = ldv(sv + k);
+                x[sl[k]] = c;
+                sv[o.np + k] = c;
+              }
+            }
+          } else if (P.kind == PH_SZ) {
+            const int i = it.first + lane;
+            if (!o.Q) {
+              if (warp == 0 && i < o.np) tmp[o.tz + i] = ldv(x + sl[i]);
+            } else {
+              const ACC v = rowblock_gemv<TF, ACC>(o.Q, (size_t)o.np, it.first, o.np, o.r,
+                                                   [&](int k) { return ldv(x + sl[k]) - ldv(sv + o.np + k); }, vs, part);
+              if (warp == 0 && i < o.np) tmp[o.tz + i] = ldv(sv + i) + (double)v;
+            }
+          } else {  // PH_SX
+            coldot_gemv<TF, ACC>(o.Y, (size_t)o.np, o.np, it.first, min(o.np, it.first + AP_COLS), true,
+                                 [&](int i) { return ldv(tmp + o.tz + i); },
+                                 [&](int j, ACC v) { x[sl[j]] = (double)v; }, vs);
+          }
+        }
+      }
     }
-  }
-}
-
-
-
-// ---------------------------------------------------------------- backward sweep
-
-
-
-// ---------------------------------------------------------------- scaling + coarse basis
-
-// forward, part 1: y_p = U_p^{-T} x_p = Y x_p for one 32-row block -> save[0:np]
-template <typename TF>
-__global__ void __launch_bounds__(AT) k_sq_fwd_y(const SqOp<TF>* __restrict__ ops, const ApplyItem* __restrict__ items,
-                                                const int32_t* __restrict__ slots, const double* __restrict__ x,
-                                                double* __restrict__ save) {
-  extern __shared__ double xs[];
-  __shared__ double part[AT / 32][RB + 1];
-  const ApplyItem it = items[blockIdx.x];
-  const SqOp<TF> o = ops[it.op];
-  const int32_t* sl = slots + o.slot;
-  const int K = min(o.np, it.first + RB);
-  for (int j = threadIdx.x; j < K; j += AT) xs[j] = x[sl[j]];
-  __syncthreads();
-  const double v = rowblock_dot(o.Y, (size_t)o.np, it.first, o.np, xs, K, part);
-  const int i = it.first + (threadIdx.x & 31);
-  if (threadIdx.x < 32 && i < o.np) save[o.save + i] = v;
-}
-
-// forward, part 2: c = Q_pc^T y_p (identity when p is not sparsified), AP_COLS
-// outputs per CTA -> x[first r slots] and save[np:np+r]
-template <typename TF>
-__global__ void __launch_bounds__(AT) k_sq_fwd_c(const SqOp<TF>* __restrict__ ops, const ApplyItem* __restrict__ items,
-                                                const int32_t* __restrict__ slots, double* __restrict__ x,
-                                                double* __restrict__ save) {
-  extern __shared__ double ys[];
-  const ApplyItem it = items[blockIdx.x];
-  const SqOp<TF> o = ops[it.op];
-  const int32_t* sl = slots + o.slot;
-  double* sv = save + o.save;
-  for (int i = threadIdx.x; i < o.np; i += AT) ys[i] = sv[i];
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int hi = min(o.r, it.first + AP_COLS);
-  for (int k = it.first + warp; k < hi; k += AT / 32) {
-    const double c = o.Q ? dot_warp(o.Q + (size_t)k * o.np, ys, 0, o.np) : ys[k];
-    if (lane == 0) {
-      x[sl[k]] = c;
-      sv[o.np + k] = c;
-    }
-  }
-}
-
-// backward, part 1: z = y_p + Q_pc (c - c_old) for one 32-row block -> tmp[tz]
-// (without Q: z = x_p)
-template <typename TF>
-__global__ void __launch_bounds__(AT) k_sq_bwd_z(const SqOp<TF>* __restrict__ ops, const ApplyItem* __restrict__ items,
-                                                const int32_t* __restrict__ slots, const double* __restrict__ x,
-                                                const double* __restrict__ save, double* __restrict__ tmp) {
-  extern __shared__ double dc[];
-  __shared__ double part[AT / 32][RB + 1];
-  const ApplyItem it = items[blockIdx.x];
-  const SqOp<TF> o = ops[it.op];
-  const int32_t* sl = slots + o.slot;
-  const double* sv = save + o.save;
-  const int i = it.first + (threadIdx.x & 31);
-  if (!o.Q) {
-    if (threadIdx.x < 32 && i < o.np) tmp[o.tz + i] = x[sl[i]];
-    return;
-  }
-  for (int k = threadIdx.x; k < o.r; k += AT) dc[k] = x[sl[k]] - sv[o.np + k];
-  __syncthreads();
-  const double v = rowblock_dot(o.Q, (size_t)o.np, it.first, o.np, dc, o.r, part);
-  if (threadIdx.x < 32 && i < o.np) tmp[o.tz + i] = sv[i] + v;
-}
-
-// backward, part 2: x_p = U_p^{-1} z = Y^T z, AP_COLS outputs per CTA
-template <typename TF>
-__global__ void __launch_bounds__(AT) k_sq_bwd_x(const SqOp<TF>* __restrict__ ops, const ApplyItem* __restrict__ items,
-                                                const int32_t* __restrict__ slots, const double* __restrict__ tmp,
-                                                double* __restrict__ x) {
-  extern __shared__ double zs[];
-  const ApplyItem it = items[blockIdx.x];
-  const SqOp<TF> o = ops[it.op];
-  const int32_t* sl = slots + o.slot;
-  for (int i = threadIdx.x; i < o.np; i += AT) zs[i] = tmp[o.tz + i];
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int hi = min(o.np, it.first + AP_COLS);
-  for (int j = it.first + warp; j < hi; j += AT / 32) {
-    const double v = dot_warp(o.Y + (size_t)j * o.np, zs, j, o.np);
-    if (lane == 0) x[sl[j]] = v;
-  }
-}
-
-// backward, part 1: acc = x_s - X_ns^T x_n for one 32-row block -> tmp[ta]
-template <typename TF>
-__global__ void __launch_bounds__(AT) k_elim_bwd_acc(const ElimOp<TF>* __restrict__ ops, const ApplyItem* __restrict__ items,
-                                                    const int32_t* __restrict__ slots, const double* __restrict__ x,
-                                                    double* __restrict__ tmp) {
-  extern __shared__ double xn[];
-  __shared__ double part[AT / 32][RB + 1];
-  const ApplyItem it = items[blockIdx.x];
-  const ElimOp<TF> o = ops[it.op];
-  const int32_t* sl = slots + o.slot;
-  for (int j = threadIdx.x; j < o.m; j += AT) xn[j] = x[sl[o.ns + j]];
-  __syncthreads();
-  const TF* XT = o.R + (size_t)o.ns * o.ns;
-  const double v = rowblock_dot(XT, (size_t)o.ns, it.first, o.ns, xn, o.m, part);
-  const int i = it.first + (threadIdx.x & 31);
-  if (threadIdx.x < 32 && i < o.ns) tmp[o.ta + i] = x[sl[i]] - v;
-}
-
-// backward, part 2: x_s = U_s^{-1} acc = Y^T acc, AP_COLS outputs per CTA
-template <typename TF>
-__global__ void __launch_bounds__(AT) k_elim_bwd_x(const ElimOp<TF>* __restrict__ ops, const ApplyItem* __restrict__ items,
-                                                  const int32_t* __restrict__ slots, const double* __restrict__ tmp,
-                                                  double* __restrict__ x) {
-  extern __shared__ double acc[];
-  const ApplyItem it = items[blockIdx.x];
-  const ElimOp<TF> o = ops[it.op];
-  const int32_t* sl = slots + o.slot;
-  for (int i = threadIdx.x; i < o.ns; i += AT) acc[i] = tmp[o.ta + i];
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int hi = min(o.ns, it.first + AP_COLS);
-  for (int j = it.first + warp; j < hi; j += AT / 32) {
-    const double v = dot_warp(o.Y + (size_t)j * o.ns, acc, j, o.ns);
-    if (lane == 0) x[sl[j]] = v;
+    if (p + 1 < nph && !grid_barrier(bar, (unsigned)(p + 1) * gridDim.x, err)) return;
   }
 }
 

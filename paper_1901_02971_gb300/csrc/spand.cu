@@ -44,6 +44,7 @@ static inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 constexpr size_t kCpqrChunkBudget = 192 * 1024;  // shared-memory chunk per CTA
 constexpr int kCpqrMaxCluster = 8;              // thread-block cluster size (broadcasts to 16 CTAs cost 3.5x more)
 constexpr int kAuxStreams = 4;
+constexpr int kApplyCtasPerSm = 4;  // CTAs per SM of the cooperative apply
 
 // Chunked bump allocator over cudaMalloc; reset() keeps the chunks for reuse.
 class DevArena {
@@ -303,19 +304,17 @@ struct spand_handle_s {
   cudaStream_t aux[kAuxStreams] = {};
   cudaEvent_t ev_fork = nullptr, ev_join[kAuxStreams] = {};
   KProf prof;
-  // the preconditioner apply captured as a CUDA graph (per factorization,
-  // keyed by the vector pointers it was captured with)
-  cudaStream_t gstream = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  const void* gkey[3] = {nullptr, nullptr, nullptr};
-  int64_t g_launches = 0;
-  bool g_warm = false;
+  // the preconditioner apply program (phases of every step, on the device);
+  // one cooperative launch of k_apply runs it
+  const void* aprog = nullptr;
+  int n_aprog = 0;
+  int apply_grid = 0;
+  size_t apply_smem = 0;
+  DevBuf d_bar;  // [0] grid-barrier arrival counter, [1] barrier-timeout flag
   ~spand_handle_s() {
     for (auto& a : aux)
       if (a) cudaStreamDestroy(a);
     if (ev_fork) cudaEventDestroy(ev_fork);
-    if (gexec) cudaGraphExecDestroy(gexec);
-    if (gstream) cudaStreamDestroy(gstream);
     for (auto& e : ev_join)
       if (e) cudaEventDestroy(e);
   }
@@ -555,6 +554,76 @@ struct StepTimer {
   StepTimer() { for (auto& e : ev) CK(cudaEventCreate(&e)); }
   ~StepTimer() { for (auto& e : ev) cudaEventDestroy(e); }
 };
+
+// The apply program: the phases of every step in execution order (forward
+// sweep leaves -> root, then the backward sweep root -> leaves), uploaded once
+// per factorization, and the cooperative grid that runs it.
+template <typename TF>
+static void build_apply_program(spand_handle h, const std::vector<ApplyStep<TF>>& steps, cudaStream_t s) {
+  std::vector<ApplyPhase<TF>> ph;
+  auto items = [&](int32_t kind, const ApplyStep<TF>& a, const ApplyItem* it, int n) {
+    if (n <= 0) return;
+    ApplyPhase<TF> p = {};
+    p.kind = kind;
+    p.n = n;
+    p.elim = a.elim;
+    p.sq = a.sq;
+    p.items = it;
+    p.slots = a.slots;
+    ph.push_back(p);
+  };
+  for (const ApplyStep<TF>& a : steps) {
+    if (a.n_elim) {
+      items(PH_FY, a, a.fy, a.n_fy);
+      items(PH_FU, a, a.fu, a.n_fu);
+      if (a.ntgt > 0) {
+        ApplyPhase<TF> p = {};
+        p.kind = PH_SCATTER;
+        p.n = (int32_t)a.ntgt;
+        p.tslot = a.tslot;
+        p.tptr = a.tptr;
+        p.tidx = a.tidx;
+        p.nassign = a.nassign;
+        ph.push_back(p);
+      }
+    }
+    if (a.n_sq) {
+      items(PH_SY, a, a.sy, a.n_sy);
+      items(PH_SC, a, a.sc, a.n_sc);
+    }
+  }
+  for (auto it = steps.rbegin(); it != steps.rend(); ++it) {
+    const ApplyStep<TF>& a = *it;
+    if (a.n_sq) {
+      items(PH_SZ, a, a.sz, a.n_sz);
+      items(PH_SX, a, a.sx, a.n_sx);
+    }
+    if (a.n_elim) {
+      items(PH_BA, a, a.ba, a.n_ba);
+      items(PH_BX, a, a.bx, a.n_bx);
+    }
+  }
+  h->n_aprog = (int)ph.size();
+  h->aprog = nullptr;
+  if (!ph.empty()) {
+    void* d = h->persist.alloc(ph.size() * sizeof(ApplyPhase<TF>));
+    CK(cudaMemcpyAsync(d, ph.data(), ph.size() * sizeof(ApplyPhase<TF>), cudaMemcpyHostToDevice, s));
+    h->aprog = d;
+  }
+  h->d_bar.ensure(2 * sizeof(unsigned));
+  CK(cudaMemsetAsync(h->d_bar.p, 0, 2 * sizeof(unsigned), s));
+  const void* fn = (const void*)k_apply<TF>;
+  h->apply_smem = (size_t)SCH * sizeof(TF);
+  ensure_smem(fn, h->apply_smem);
+  int dev = 0, nsm = 0, coop = 0, per_sm = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) throw Fail{SPAND_ERR_CUDA, "device does not support cooperative launches (needed by the apply)"};
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_apply<TF>, AT, h->apply_smem));
+  if (per_sm < 1) throw Fail{SPAND_ERR_CUDA, "apply kernel cannot be resident"};
+  h->apply_grid = nsm * std::min(per_sm, kApplyCtasPerSm);
+}
 
 template <typename T>
 static int factorize_impl(spand_handle h, cudaStream_t s) {
@@ -1159,6 +1228,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
     h->phase_ms[3] += ms[3];
     if (t < L) lay = std::move(nxt);
   }
+  build_apply_program<T>(h, apply, s);
   if constexpr (std::is_same<T, double>::value) {
     h->apply64 = std::move(apply);
     h->apply32.clear();
@@ -1172,110 +1242,45 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
 // ---------------------------------------------------------------- apply / PCG
 
 // tmp: h->tmp_len doubles of per-step temporaries; save: h->save_len doubles
-// of sparsification forward inputs (both scratch; nothing needs to start at 0)
+// of sparsification forward inputs (both scratch; nothing needs to start at 0).
+// One cooperative launch runs the whole apply program; a barrier timeout is
+// recorded in d_bar[1] and reported by check_apply().
 template <typename TF>
-static void apply_prec(spand_handle h, const std::vector<ApplyStep<TF>>& steps, double* x, double* tmp, double* save,
-                       cudaStream_t s) {
+static void apply_prec(spand_handle h, double* x, double* tmp, double* save, cudaStream_t s) {
+  if (!h->n_aprog) return;
   const int pid = h->prof.begin(F_APPLY, s);
-  int64_t nl = 0;
-  auto launched = [&](int k) { nl += k; };
-  for (const ApplyStep<TF>& a : steps) {  // forward: leaves -> root
-    if (a.n_elim) {
-      ensure_smem((const void*)k_elim_fwd_y<TF>, a.sm_ns);
-      ensure_smem((const void*)k_elim_fwd_u<TF>, a.sm_ns);
-      k_elim_fwd_y<TF><<<a.n_fy, AT, a.sm_ns, s>>>(a.elim, a.fy, a.slots, x, tmp);
-      CKLAUNCH();
-      launched(1);
-      if (a.n_fu) {
-        k_elim_fwd_u<TF><<<a.n_fu, AT, a.sm_ns, s>>>(a.elim, a.fu, tmp);
-        CKLAUNCH();
-        launched(1);
-      }
-      k_scatter<<<(unsigned)std::min<int64_t>((a.ntgt + 255) / 256, 4096), 256, 0, s>>>(a.tslot, a.tptr, a.tidx, tmp, x,
-                                                                                       a.nassign, a.ntgt);
-      CKLAUNCH();
-      launched(1);
-    }
-    if (a.n_sq) {
-      ensure_smem((const void*)k_sq_fwd_y<TF>, a.sm_np);
-      ensure_smem((const void*)k_sq_fwd_c<TF>, a.sm_np);
-      k_sq_fwd_y<TF><<<a.n_sy, AT, a.sm_np, s>>>(a.sq, a.sy, a.slots, x, save);
-      CKLAUNCH();
-      launched(1);
-      if (a.n_sc) {
-        k_sq_fwd_c<TF><<<a.n_sc, AT, a.sm_np, s>>>(a.sq, a.sc, a.slots, x, save);
-        CKLAUNCH();
-        launched(1);
-      }
-    }
-  }
-  for (auto it = steps.rbegin(); it != steps.rend(); ++it) {  // backward: root -> leaves
-    const ApplyStep<TF>& a = *it;
-    if (a.n_sq) {
-      ensure_smem((const void*)k_sq_bwd_z<TF>, a.sm_r);
-      ensure_smem((const void*)k_sq_bwd_x<TF>, a.sm_np);
-      k_sq_bwd_z<TF><<<a.n_sz, AT, a.sm_r, s>>>(a.sq, a.sz, a.slots, x, save, tmp);
-      CKLAUNCH();
-      k_sq_bwd_x<TF><<<a.n_sx, AT, a.sm_np, s>>>(a.sq, a.sx, a.slots, tmp, x);
-      CKLAUNCH();
-      launched(2);
-    }
-    if (a.n_elim) {
-      ensure_smem((const void*)k_elim_bwd_acc<TF>, a.sm_m);
-      ensure_smem((const void*)k_elim_bwd_x<TF>, a.sm_ns);
-      k_elim_bwd_acc<TF><<<a.n_ba, AT, a.sm_m, s>>>(a.elim, a.ba, a.slots, x, tmp);
-      CKLAUNCH();
-      k_elim_bwd_x<TF><<<a.n_bx, AT, a.sm_ns, s>>>(a.elim, a.bx, a.slots, tmp, x);
-      CKLAUNCH();
-      launched(2);
-    }
-  }
-  h->prof.launches += nl;
-  h->prof.end(pid, s, 0.0, h->st.apply_bytes, nl);
+  unsigned* bar = (unsigned*)h->d_bar.p;
+  int* err = (int*)(bar + 1);
+  CK(cudaMemsetAsync(bar, 0, sizeof(unsigned), s));
+  const ApplyPhase<TF>* ph = (const ApplyPhase<TF>*)h->aprog;
+  int nph = h->n_aprog;
+  void* args[] = {(void*)&ph, (void*)&nph, (void*)&x, (void*)&tmp, (void*)&save, (void*)&bar, (void*)&err};
+  CK(cudaLaunchCooperativeKernel((const void*)k_apply<TF>, dim3((unsigned)h->apply_grid), dim3(AT), args,
+                                 h->apply_smem, s));
+  CKLAUNCH();
+  h->prof.launches += 1;
+  h->prof.end(pid, s, 0.0, h->st.apply_bytes, 1);
 }
 
 static void apply_any(spand_handle h, double* x, double* tmp, double* save, cudaStream_t s) {
-  if (h->fprec == SPAND_FP64) apply_prec<double>(h, h->apply64, x, tmp, save, s);
-  else apply_prec<float>(h, h->apply32, x, tmp, save, s);
+  if (h->fprec == SPAND_FP64) apply_prec<double>(h, x, tmp, save, s);
+  else apply_prec<float>(h, x, tmp, save, s);
 }
 
-// The apply replayed from a CUDA graph: the first call after a factorization
-// runs eagerly (it also sets every kernel attribute), the second captures the
-// launch sequence on a private stream, later calls replay it on `s`.  With
-// kernel profiling on, the apply always runs eagerly.
-static void apply_graph(spand_handle h, double* x, double* tmp, double* save, cudaStream_t s) {
-  const bool same = h->gexec && h->gkey[0] == x && h->gkey[1] == tmp && h->gkey[2] == save;
-  if (h->prof.on || (!same && !h->g_warm)) {
-    apply_any(h, x, tmp, save, s);
-    h->g_warm = true;
-    return;
+// Reads (after the stream has been synchronised) and clears the apply's
+// barrier-timeout flag.
+static void check_apply(spand_handle h) {
+  if (!h->d_bar.p) return;
+  int flag = 0;
+  CK(cudaMemcpy(&flag, (unsigned*)h->d_bar.p + 1, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    CK(cudaMemset((unsigned*)h->d_bar.p + 1, 0, sizeof(int)));
+    throw Fail{SPAND_ERR_CUDA, "preconditioner apply: a grid barrier timed out"};
   }
-  if (!same) {
-    if (h->gexec) {
-      CK(cudaGraphExecDestroy(h->gexec));
-      h->gexec = nullptr;
-    }
-    if (!h->gstream) CK(cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
-    const int64_t l0 = h->prof.launches;
-    cudaGraph_t g = nullptr;
-    CK(cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal));
-    apply_any(h, x, tmp, save, h->gstream);
-    CK(cudaStreamEndCapture(h->gstream, &g));
-    const cudaError_t e = cudaGraphInstantiate(&h->gexec, g, 0);
-    cudaGraphDestroy(g);
-    CK(e);
-    h->g_launches = h->prof.launches - l0;
-    h->prof.launches = l0;
-    h->gkey[0] = x;
-    h->gkey[1] = tmp;
-    h->gkey[2] = save;
-  }
-  CK(cudaGraphLaunch(h->gexec, s));
-  h->prof.launches += h->g_launches;
 }
 
 static void apply_any(spand_handle h, double* x, cudaStream_t s) {
-  apply_graph(h, x, (double*)h->d_tmp.p, (double*)h->d_save.p, s);
+  apply_any(h, x, (double*)h->d_tmp.p, (double*)h->d_save.p, s);
 }
 
 static void ensure_solve_buffers(spand_handle h) {
@@ -1453,11 +1458,6 @@ int spand_factorize(spand_handle h, const double* vals, void* cuda_stream) {
   cudaStream_t s = (cudaStream_t)cuda_stream;
   auto t0 = std::chrono::steady_clock::now();
   h->factored = false;
-  if (h->gexec) {
-    cudaGraphExecDestroy(h->gexec);
-    h->gexec = nullptr;
-  }
-  h->g_warm = false;
   int dev = 0;
   CK(cudaGetDevice(&dev));
   if (h->device >= 0 && h->device != dev) throw Fail{SPAND_ERR_STATE, "handle was factorized on another device"};
@@ -1529,6 +1529,7 @@ int spand_apply(spand_handle h, const double* r_dev, double* z_dev, void* cuda_s
   CKLAUNCH();
   h->prof.launches += 2;
   CK(cudaStreamSynchronize(s));
+  check_apply(h);
   return SPAND_OK;
   API_END
 }
@@ -1588,6 +1589,7 @@ int spand_apply_noalloc(spand_handle h, const double* r_dev, double* z_dev, void
   CKLAUNCH();
   h->prof.launches += 2;
   CK(cudaStreamSynchronize(s));
+  check_apply(h);
   return SPAND_OK;
   API_END
 }
@@ -1734,6 +1736,7 @@ int spand_solve(spand_handle h, const double* b, double* x, int32_t* iters, doub
   h->prof.launches += 1;
   CK(cudaMemcpyAsync(x, io, n * sizeof(double), xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  check_apply(h);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaEventDestroy(e2);
