@@ -109,31 +109,82 @@ __device__ __forceinline__ void store_tile(const SqTile<T>& s, T* P, int ld, int
   }
 }
 
-// In-place upper Cholesky of the nb x nb tile (upper triangle read/written).
-// Returns false (for every thread) if a pivot is not positive.
+// Upper Cholesky of the nb x nb diagonal tile s (A = U^T U, upper triangle
+// read and overwritten with U, lower triangle left as loaded) fused with the
+// inverse D = U^{-T} (lower, TB x TB, identity beyond nb).  Right-looking: at
+// step k the pivot row k of A and row k of D are published to shared memory,
+// then every thread updates the 4 x 4 elements it holds in registers
+// (rows tx + 16a, columns ty + 16b):
+//   U_kj = A_kj / sqrt(A_kk);  A_ij -= U_ki U_kj (k < i <= j);
+//   D_k. <- D_k. / U_kk;       D_i. -= U_ki D_k. (i > k)      (row ops of L^{-1}, L = U^T).
+// One block barrier per step (the row buffers alternate).  Returns false
+// (for every thread) if a pivot is not positive; nothing is stored then.
 template <typename T>
-__device__ bool potrf_tile_upper(SqTile<T>& s, int nb) {
-  __shared__ int bad;
-  if (threadIdx.x == 0) bad = 0;
-  __syncthreads();
+__device__ bool potrf_inv_tile(SqTile<T>& s, SqTile<T>& D, int nb) {
+  __shared__ T rowA[2][TB], rowD[2][TB];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  T a[4][4], d[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = tx + 16 * p, j = ty + 16 * q;
+      a[p][q] = s.v[i][j];
+      d[p][q] = (i == j) ? T(1) : T(0);
+    }
   for (int k = 0; k < nb; ++k) {
-    if (threadIdx.x == 0) {
-      const T d = s.v[k][k];
-      if (!(d > T(0))) bad = 1;
-      s.v[k][k] = sqrt(d > T(0) ? d : T(1));
+    const int par = k & 1;
+#pragma unroll
+    for (int p = 0; p < 4; ++p)  // owners of row k publish it (compile-time register indices)
+      if (tx + 16 * p == k) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          rowA[par][ty + 16 * q] = a[p][q];
+          rowD[par][ty + 16 * q] = d[p][q];
+        }
+      }
+    __syncthreads();
+    const T piv = rowA[par][k];
+    if (!(piv > T(0))) return false;  // uniform: every thread read the same pivot
+    const T ukk = sqrt(piv);
+    const T inv = T(1) / ukk;
+    T ui[4], uj[4], dk[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      ui[q] = rowA[par][tx + 16 * q] * inv;
+      uj[q] = rowA[par][ty + 16 * q] * inv;
+      dk[q] = rowD[par][ty + 16 * q] * inv;
     }
-    __syncthreads();
-    if (bad) return false;
-    const T dk = s.v[k][k];
-    for (int j = k + 1 + threadIdx.x; j < nb; j += NT) s.v[k][j] /= dk;
-    __syncthreads();
-    const int m = nb - k - 1;
-    for (int e = threadIdx.x; e < m * m; e += NT) {
-      const int i = k + 1 + e % m, j = k + 1 + e / m;
-      if (i <= j) s.v[i][j] -= s.v[k][i] * s.v[k][j];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int i = tx + 16 * p;
+      if (i == k) {  // finalise row k of U and of D
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = ty + 16 * q;
+          if (j == k) a[p][q] = ukk;
+          else if (j > k) a[p][q] = uj[q];
+          d[p][q] = dk[q];
+        }
+      } else if (i > k) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = ty + 16 * q;
+          if (j >= i) a[p][q] = fma(-ui[p], uj[q], a[p][q]);
+          d[p][q] = fma(-ui[p], dk[q], d[p][q]);
+        }
+      }
     }
-    __syncthreads();
   }
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = tx + 16 * p, j = ty + 16 * q;
+      if (i <= j) s.v[i][j] = a[p][q];
+      D.v[i][j] = d[p][q];
+    }
+  __syncthreads();
   return true;
 }
 
@@ -164,21 +215,6 @@ __device__ void apply_inv_tile(const SqTile<T>& D, SqTile<T>& B, int nb) {
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj) B.v[tx + 16 * ii][ty + 16 * jj] = acc[ii][jj];
   __syncthreads();
-}
-
-// In place: B <- U^{-T} B, U upper nb x nb, B nb x ncols (both in shared memory).
-template <typename T>
-__device__ void trsm_tile_upperT(const SqTile<T>& U, SqTile<T>& B, int nb, int ncols) {
-  for (int i = 0; i < nb; ++i) {
-    if (threadIdx.x < ncols) B.v[i][threadIdx.x] /= U.v[i][i];
-    __syncthreads();
-    const int m = nb - i - 1;
-    for (int e = threadIdx.x; e < m * ncols; e += NT) {
-      const int l = i + 1 + e / ncols, j = e % ncols;
-      B.v[l][j] -= U.v[i][l] * B.v[i][j];
-    }
-    __syncthreads();
-  }
 }
 
 }  // namespace spand

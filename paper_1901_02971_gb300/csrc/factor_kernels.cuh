@@ -84,18 +84,12 @@ __global__ void __launch_bounds__(NT) k_potrf_diag(const RowDesc<T>* __restrict_
   const int nb = min(TB, d.n - k0);
   T* P = d.R + k0 + (size_t)k0 * d.ld;
   load_tile(s, P, d.ld, nb, nb);
-  for (int e = threadIdx.x; e < TB * TB; e += NT) {
-    const int i = e & (TB - 1), j = e >> 6;
-    Id.v[i][j] = (i == j) ? T(1) : T(0);
-  }
   __syncthreads();
-  const bool ok = potrf_tile_upper(s, nb);
-  if (!ok) {
+  if (!potrf_inv_tile(s, Id, nb)) {
     if (threadIdx.x == 0) atomicCAS(info, 0, (int)blockIdx.x + 1);
     return;
   }
   store_tile(s, P, d.ld, nb, nb);
-  trsm_tile_upperT(s, Id, nb, nb);
   store_tile(Id, d.dinv + (size_t)k * TB * TB, TB, TB, TB);
 }
 

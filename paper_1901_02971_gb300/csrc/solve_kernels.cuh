@@ -190,7 +190,7 @@ enum ApplyKind : int32_t {
 };
 
 template <typename TF>
-struct ApplyPhase {
+struct __align__(8) ApplyPhase {
   int32_t kind, n;             // n = items, or scatter targets
   const ElimOp<TF>* elim;
   const SqOp<TF>* sq;
@@ -201,6 +201,7 @@ struct ApplyPhase {
   const int64_t* tidx;
   int64_t nassign;
 };
+static_assert(sizeof(ApplyPhase<float>) % 8 == 0 && sizeof(ApplyPhase<double>) % 8 == 0, "phase table copy");
 
 constexpr unsigned kBarrierSpins = 1u << 24;  // with ~40 ns sleeps: well over a second
 
@@ -213,15 +214,22 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 // Grid-wide barrier on a monotonically increasing arrival counter (reset to 0
 // before the launch): barrier b completes when the counter reaches
 // (b + 1) * gridDim.x.  All CTAs are co-resident (cooperative launch).  The
-// wait is bounded: on timeout *err is set and false is returned to every
-// thread of the CTA, which then leaves the kernel.
-__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, int* err) {
-  __shared__ int ok;
+// CTA's writes are ordered before its arrival by bar.sync + a release fence,
+// and the waiter's acquire load + fence order the next phase's reads after
+// every arrival.  The wait is bounded: on timeout *err is set and false is
+// returned to every thread of the CTA, which then leaves the kernel.
+__device__ __forceinline__ void grid_arrive(unsigned* count) {
   __syncthreads();
   if (threadIdx.x == 0) {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(count), "r"(1u) : "memory");
+  }
+}
+
+__device__ __forceinline__ bool grid_wait(const unsigned* count, unsigned target, int* err) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
     ok = 1;
-    __threadfence();
-    atomicAdd(count, 1u);
     unsigned spins = 0;
     while (ld_acquire_u32(count) < target) {
       if (++spins > kBarrierSpins) {
@@ -229,12 +237,58 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, i
         ok = 0;
         break;
       }
-      __nanosleep(40);
+      if (spins > 64) __nanosleep(32);
     }
-    __threadfence();
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
   }
   __syncthreads();
   return ok != 0;
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// Warm the caches for this CTA's first item of phase P (read-only data only:
+// the item, its op, its slot list, and the lines of the factor block it
+// streams).  Runs between arriving at a grid barrier and waiting on it.
+template <typename TF>
+__device__ __forceinline__ void prefetch_first_item(const ApplyPhase<TF>& P) {
+  if (P.kind == PH_SCATTER || (int)blockIdx.x >= P.n) return;
+  const ApplyItem it = P.items[blockIdx.x];
+  const TF* A;
+  size_t ld;
+  int rows, lo, cols;     // row-block items: 32 rows from `lo`, `cols` columns; column items: `cols` from `lo`
+  bool rowblock;
+  const int32_t* sl;
+  int nsl;
+  if (P.kind == PH_FY || P.kind == PH_BA || P.kind == PH_FU || P.kind == PH_BX) {
+    const ElimOp<TF> o = P.elim[it.op];
+    sl = P.slots + o.slot;
+    ld = (size_t)o.ns;
+    rows = o.ns;
+    if (P.kind == PH_FY) { A = o.Y; rowblock = true; lo = it.first; cols = min(o.ns, it.first + RB); nsl = cols; }
+    else if (P.kind == PH_BA) { A = o.R + (size_t)o.ns * o.ns; rowblock = true; lo = it.first; cols = o.m; sl += o.ns; nsl = o.m; }
+    else if (P.kind == PH_FU) { A = o.R + (size_t)o.ns * o.ns; rowblock = false; lo = it.first; cols = min(o.m - it.first, AP_COLS); nsl = 0; }
+    else { A = o.Y; rowblock = false; lo = it.first; cols = min(o.ns - it.first, AP_COLS); nsl = cols + it.first; }
+  } else {
+    const SqOp<TF> o = P.sq[it.op];
+    sl = P.slots + o.slot;
+    ld = (size_t)o.np;
+    rows = o.np;
+    if (P.kind == PH_SY) { A = o.Y; rowblock = true; lo = it.first; cols = min(o.np, it.first + RB); nsl = cols; }
+    else if (P.kind == PH_SZ) { A = o.Q; rowblock = true; lo = it.first; cols = o.Q ? o.r : 0; nsl = o.r; }
+    else if (P.kind == PH_SC) { A = o.Q; rowblock = false; lo = it.first; cols = o.Q ? min(o.r - it.first, AP_COLS) : 0; nsl = 0; }
+    else { A = o.Y; rowblock = false; lo = it.first; cols = min(o.np - it.first, AP_COLS); nsl = o.np; }
+  }
+  for (int k = threadIdx.x * 32; k < nsl; k += AT * 32) prefetch_l2(sl + k);
+  if (!A || cols <= 0) return;
+  if (rowblock) {
+    for (int k = threadIdx.x; k < cols; k += AT) prefetch_l2(A + lo + (size_t)k * ld);
+  } else {  // columns lo .. lo+cols-1, contiguous: one line per 128 bytes
+    const char* b = reinterpret_cast<const char*>(A + (size_t)lo * ld);
+    const size_t bytes = (size_t)cols * ld * sizeof(TF);
+    for (size_t off = (size_t)threadIdx.x * 128; off < bytes; off += (size_t)AT * 128) prefetch_l2(b + off);
+  }
+  (void)rows;
 }
 
 template <typename TF>
@@ -243,10 +297,19 @@ __global__ void __launch_bounds__(AT) k_apply(const ApplyPhase<TF>* __restrict__
   typedef TF ACC;  // inner sums in the factor's precision
   extern __shared__ __align__(16) unsigned char apply_smem[];
   ACC* vs = reinterpret_cast<ACC*>(apply_smem);
+  // the phase table, copied once (its loads are off the per-phase critical path)
+  ApplyPhase<TF>* ptab = reinterpret_cast<ApplyPhase<TF>*>(apply_smem + SCH * sizeof(ACC));
   __shared__ ACC part[AT / 32][RB + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  {
+    const int words = nph * (int)(sizeof(ApplyPhase<TF>) / 8);
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(phases);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(ptab);
+    for (int w = threadIdx.x; w < words; w += AT) dst[w] = src[w];
+    __syncthreads();
+  }
   for (int p = 0; p < nph; ++p) {
-    const ApplyPhase<TF> P = phases[p];
+    const ApplyPhase<TF>& P = ptab[p];
     if (P.kind == PH_SCATTER) {
       for (int64_t t = blockIdx.x * (int64_t)AT + threadIdx.x; t < P.n; t += (int64_t)gridDim.x * AT) {
         if (t < P.nassign) {
@@ -327,7 +390,11 @@ __global__ void __launch_bounds__(AT) k_apply(const ApplyPhase<TF>* __restrict__
         }
       }
     }
-    if (p + 1 < nph && !grid_barrier(bar, (unsigned)(p + 1) * gridDim.x, err)) return;
+    if (p + 1 < nph) {
+      grid_arrive(bar);
+      prefetch_first_item(ptab[p + 1]);
+      if (!grid_wait(bar, (unsigned)(p + 1) * gridDim.x, err)) return;
+    }
   }
 }
 

@@ -89,6 +89,46 @@ class DevArena {
   ~DevArena() { release(); }
 };
 
+// Pinned host staging for descriptor uploads: cudaMemcpyAsync from pinned
+// memory returns at once, so the host keeps building the next launches while
+// the copies wait for their turn in the stream.  reset() may only be called
+// once the stream has executed every copy taken from the arena.
+class PinnedStage {
+  struct Chunk {
+    char* p;
+    size_t cap, used;
+  };
+  std::vector<Chunk> chunks_;
+  size_t cur_ = 0;
+
+ public:
+  void* take(size_t bytes) {
+    bytes = align256(std::max<size_t>(bytes, 1));
+    while (cur_ < chunks_.size()) {
+      Chunk& c = chunks_[cur_];
+      if (c.used + bytes <= c.cap) {
+        void* p = c.p + c.used;
+        c.used += bytes;
+        return p;
+      }
+      ++cur_;
+    }
+    size_t cap = std::max<size_t>(bytes, size_t(16) << 20);
+    char* p = nullptr;
+    CK(cudaMallocHost(&p, cap));
+    chunks_.push_back({p, cap, bytes});
+    cur_ = chunks_.size() - 1;
+    return p;
+  }
+  void reset() {
+    for (auto& c : chunks_) c.used = 0;
+    cur_ = 0;
+  }
+  ~PinnedStage() {
+    for (auto& c : chunks_) cudaFreeHost(c.p);
+  }
+};
+
 // Grow-only contiguous device buffer.
 struct DevBuf {
   void* p = nullptr;
@@ -289,6 +329,7 @@ struct spand_handle_s {
   int device = -1;
   bool consts_ready = false;
   DevArena persist, descs;
+  PinnedStage stage;  // host side of every descriptor upload of a factorization
   DevBuf scratch[2];
   DevBuf d_vals, d_asm_row, d_asm_off, d_prow, d_pcol, d_pval, d_pval_src, d_perm;
   DevBuf d_vec, d_tmp, d_save, d_bin, d_bout;
@@ -399,7 +440,9 @@ template <typename T>
 static void* upload(spand_handle h, const Packer& pk, cudaStream_t s) {
   if (pk.buf.empty()) return nullptr;
   void* d = h->descs.alloc(pk.buf.size());
-  CK(cudaMemcpyAsync(d, pk.buf.data(), pk.buf.size(), cudaMemcpyHostToDevice, s));
+  void* src = h->stage.take(pk.buf.size());
+  std::memcpy(src, pk.buf.data(), pk.buf.size());
+  CK(cudaMemcpyAsync(d, src, pk.buf.size(), cudaMemcpyHostToDevice, s));
   return d;
 }
 
@@ -549,10 +592,18 @@ static void set_identity(spand_handle h, const std::vector<RowDesc<T>>& rows, cu
   h->prof.launches += 1;
 }
 
+// Phase boundaries of every step (5 events per step, read once at the end of
+// the factorization, so that no step waits for its own timing).
 struct StepTimer {
-  cudaEvent_t ev[5];
-  StepTimer() { for (auto& e : ev) CK(cudaEventCreate(&e)); }
-  ~StepTimer() { for (auto& e : ev) cudaEventDestroy(e); }
+  std::vector<cudaEvent_t> ev;
+  explicit StepTimer(int nsteps) : ev(5 * (size_t)(nsteps + 1), nullptr) {
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+  }
+  cudaEvent_t at(int t, int k) const { return ev[5 * (size_t)t + k]; }
+  ~StepTimer() {
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+  }
 };
 
 // The apply program: the phases of every step in execution order (forward
@@ -607,13 +658,15 @@ static void build_apply_program(spand_handle h, const std::vector<ApplyStep<TF>>
   h->aprog = nullptr;
   if (!ph.empty()) {
     void* d = h->persist.alloc(ph.size() * sizeof(ApplyPhase<TF>));
-    CK(cudaMemcpyAsync(d, ph.data(), ph.size() * sizeof(ApplyPhase<TF>), cudaMemcpyHostToDevice, s));
+    void* src = h->stage.take(ph.size() * sizeof(ApplyPhase<TF>));
+    std::memcpy(src, ph.data(), ph.size() * sizeof(ApplyPhase<TF>));
+    CK(cudaMemcpyAsync(d, src, ph.size() * sizeof(ApplyPhase<TF>), cudaMemcpyHostToDevice, s));
     h->aprog = d;
   }
   h->d_bar.ensure(2 * sizeof(unsigned));
   CK(cudaMemsetAsync(h->d_bar.p, 0, 2 * sizeof(unsigned), s));
   const void* fn = (const void*)k_apply<TF>;
-  h->apply_smem = (size_t)SCH * sizeof(TF);
+  h->apply_smem = (size_t)SCH * sizeof(TF) + ph.size() * sizeof(ApplyPhase<TF>);
   ensure_smem(fn, h->apply_smem);
   int dev = 0, nsm = 0, coop = 0, per_sm = 0;
   CK(cudaGetDevice(&dev));
@@ -643,12 +696,25 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
   stt.factor_flops = 0;
   stt.fail_step = 0;
   stt.fail_cluster = -1;
-  StepTimer tm;
-  // info flag + cur_size scratch
-  // non-positive pivot flags: [0] elimination pivots, [1] scaling pivots
-  // (checked once per step, at the step's synchronisation point)
-  int* d_info = (int*)h->descs.alloc(2 * sizeof(int));
-  CK(cudaMemsetAsync(d_info, 0, 2 * sizeof(int), s));
+  StepTimer tm(L);
+  h->stage.reset();  // the previous factorization ended with a stream synchronisation
+  // non-positive pivot flags per step: [2t] elimination pivots, [2t+1]
+  // scaling pivots; read at the next host synchronisation (the rank readback
+  // of a sparsifying step, or the end of the factorization)
+  int* d_info = (int*)h->descs.alloc(2 * (size_t)(L + 1) * sizeof(int));
+  CK(cudaMemsetAsync(d_info, 0, 2 * (size_t)(L + 1) * sizeof(int), s));
+  std::vector<std::vector<int>> elim_cls(L + 1), scale_cls(L + 1);  // cluster of each pivot-batch entry
+  auto check_pivots = [&](int upto) {  // after a stream synchronisation
+    std::vector<int> info(2 * (size_t)(L + 1), 0);
+    CK(cudaMemcpy(info.data(), d_info, info.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int u = 1; u <= upto; ++u)
+      if (info[2 * u] || info[2 * u + 1]) {
+        stt.fail_step = u;
+        stt.fail_cluster = info[2 * u] ? elim_cls[u][info[2 * u] - 1] : scale_cls[u][info[2 * u + 1] - 1];
+        throw Fail{SPAND_ERR_NOT_SPD, std::string(info[2 * u] ? "pivot" : "interface") +
+                                          " block not positive definite at step " + std::to_string(u)};
+      }
+  };
 
   const int nc0 = (int)tr.cluster_ptr.size() - 1;
   std::vector<int32_t> sz(nc0);
@@ -658,7 +724,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
     slots[i].resize(sz[i]);
     std::iota(slots[i].begin(), slots[i].end(), tr.cluster_ptr[i]);
   }
-  CK(cudaEventRecord(tm.ev[0], s));
+  CK(cudaEventRecord(tm.at(0, 0), s));
   Layout<T> lay = make_layout<T>(h, 1, sz, s);
   {  // assemble A into the step-1 rows
     Packer pk;
@@ -673,13 +739,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       h->prof.launches += 1;
     }
   }
-  CK(cudaEventRecord(tm.ev[1], s));
-  {
-    float ms = 0;
-    CK(cudaEventSynchronize(tm.ev[1]));
-    CK(cudaEventElapsedTime(&ms, tm.ev[0], tm.ev[1]));
-    h->phase_ms[3] += ms;
-  }
+  CK(cudaEventRecord(tm.at(0, 1), s));
 
   int32_t* d_cur = nullptr;
   for (int t = 1; t <= L; ++t) {
@@ -689,11 +749,10 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
     if (t == L)
       for (int i = 0; i < n; ++i)
         if (st.elim[i]) stt.size_top += sz[i];
-    CK(cudaEventRecord(tm.ev[0], s));
+    CK(cudaEventRecord(tm.at(t, 0), s));
     // ------------------------------------------------ eliminate (Sec. 2.4)
     std::vector<int> seps, rems;
     for (int i = 0; i < n; ++i) (st.elim[i] ? seps : rems).push_back(i);
-    std::vector<int> elim_cl, scale_cl;  // cluster of each pivot-batch entry
     std::vector<T*> ysep(n, nullptr);
     {
       std::vector<RowDesc<T>> diag, ident;
@@ -713,8 +772,8 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         stt.factor_flops += ns * ns * ns / 3 + ns * ns * m + ns * m * m;
       }
       set_identity<T>(h, ident, s);
-      potrf_batch<T>(h, diag, d_info, s);
-      elim_cl = diag_cl;
+      potrf_batch<T>(h, diag, d_info + 2 * t, s);
+      elim_cls[t] = diag_cl;
       trsm_batch<T>(h, tr_tasks, s);
       // pull-form Schur update of every pair of neighbours
       std::vector<SchurBlock<T>> blocks;
@@ -786,7 +845,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         h->prof.end(pid, s, fl, by, 1);
       }
     }
-    CK(cudaEventRecord(tm.ev[1], s));
+    CK(cudaEventRecord(tm.at(t, 1), s));
     // ------------------------------------------------ apply ops of the elimination
     ApplyStep<T> ap;
     std::vector<int32_t> aslots;
@@ -797,56 +856,70 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
     std::vector<ApplyItem> it_fy, it_fu, it_ba, it_bx;
     int64_t tmp_off = 0;
     size_t sm_ns = 0, sm_m = 0;
-    for (int sidx : seps) {
-      if (sz[sidx] <= 0) continue;
-      ElimOp<T> o;
-      o.R = lay.row[sidx];
-      o.Y = ysep[sidx];
-      o.ns = sz[sidx];
-      o.m = lay.W[sidx] - sz[sidx];
-      o.slot = (int64_t)aslots.size();
-      o.ty = tmp_off;
-      o.tu = tmp_off + o.ns;
-      o.ta = tmp_off + o.ns + o.m;
-      const int32_t op = (int32_t)eops.size();
-      aslots.insert(aslots.end(), slots[sidx].begin(), slots[sidx].end());
-      for (int32_t i = 0; i < o.ns; ++i) {  // x_s = y_s
-        tslot.push_back(slots[sidx][i]);
-        tidx.push_back(o.ty + i);
-        tptr.push_back((int64_t)tidx.size());
-      }
-      int64_t j = 0;
-      for (int32_t e = lay.nptr[sidx]; e < lay.nptr[sidx + 1]; ++e) {
-        const int32_t q = lay.nidx[e];
-        for (int32_t k = 0; k < sz[q]; ++k, ++j) {
-          aslots.push_back(slots[q][k]);
-          tgt.push_back({slots[q][k], o.tu + j});
+    int64_t nassign = 0;
+    bool elim_ops_built = false;
+    // built after the sparsification launches (its host time then overlaps them)
+    auto build_elim_ops = [&]() {
+      for (int sidx : seps) {
+        if (sz[sidx] <= 0) continue;
+        ElimOp<T> o;
+        o.R = lay.row[sidx];
+        o.Y = ysep[sidx];
+        o.ns = sz[sidx];
+        o.m = lay.W[sidx] - sz[sidx];
+        o.slot = (int64_t)aslots.size();
+        o.ty = tmp_off;
+        o.tu = tmp_off + o.ns;
+        o.ta = tmp_off + o.ns + o.m;
+        const int32_t op = (int32_t)eops.size();
+        aslots.insert(aslots.end(), slots[sidx].begin(), slots[sidx].end());
+        for (int32_t i = 0; i < o.ns; ++i) {  // x_s = y_s
+          tslot.push_back(slots[sidx][i]);
+          tidx.push_back(o.ty + i);
+          tptr.push_back((int64_t)tidx.size());
         }
+        int64_t j = 0;
+        for (int32_t e = lay.nptr[sidx]; e < lay.nptr[sidx + 1]; ++e) {
+          const int32_t q = lay.nidx[e];
+          for (int32_t k = 0; k < sz[q]; ++k, ++j) {
+            aslots.push_back(slots[q][k]);
+            tgt.push_back({slots[q][k], o.tu + j});
+          }
+        }
+        for (int32_t r0 = 0; r0 < o.ns; r0 += RB) {
+          it_fy.push_back({op, r0});
+          it_ba.push_back({op, r0});
+        }
+        for (int32_t c0 = 0; c0 < o.m; c0 += AP_COLS) it_fu.push_back({op, c0});
+        for (int32_t c0 = 0; c0 < o.ns; c0 += AP_COLS) it_bx.push_back({op, c0});
+        tmp_off += 2 * (int64_t)o.ns + o.m;
+        eops.push_back(o);
+        stt.mem_f += (int64_t)o.ns * (o.ns + 1) / 2 + (int64_t)o.ns * o.m;
+        sm_ns = std::max(sm_ns, (size_t)o.ns * sizeof(double));
+        sm_m = std::max(sm_m, (size_t)o.m * sizeof(double));
       }
-      for (int32_t r0 = 0; r0 < o.ns; r0 += RB) {
-        it_fy.push_back({op, r0});
-        it_ba.push_back({op, r0});
+      h->tmp_len = std::max(h->tmp_len, tmp_off);
+      nassign = (int64_t)tslot.size();
+      // group the subtractions by target slot: a stable counting sort, so each
+      // target's sources stay in op order (the fixed summation order)
+      std::vector<int64_t> head((size_t)h->n + 1, 0);
+      for (const auto& e : tgt) ++head[(size_t)e.first + 1];
+      for (int64_t v = 0; v < h->n; ++v) head[v + 1] += head[v];
+      std::vector<int64_t> byslot(tgt.size());
+      for (size_t i = 0; i < tgt.size(); ++i) byslot[head[tgt[i].first]++] = tgt[i].second;
+      // head[v] is now the end of slot v's run
+      tidx.reserve(tidx.size() + tgt.size());
+      int64_t b = 0;
+      for (int64_t v = 0; v < h->n; ++v) {
+        const int64_t e = head[v];
+        if (e == b) continue;
+        tslot.push_back((int32_t)v);
+        for (int64_t k = b; k < e; ++k) tidx.push_back(byslot[k]);
+        tptr.push_back((int64_t)tidx.size());
+        b = e;
       }
-      for (int32_t c0 = 0; c0 < o.m; c0 += AP_COLS) it_fu.push_back({op, c0});
-      for (int32_t c0 = 0; c0 < o.ns; c0 += AP_COLS) it_bx.push_back({op, c0});
-      tmp_off += 2 * (int64_t)o.ns + o.m;
-      eops.push_back(o);
-      stt.mem_f += (int64_t)o.ns * (o.ns + 1) / 2 + (int64_t)o.ns * o.m;
-      sm_ns = std::max(sm_ns, (size_t)o.ns * sizeof(double));
-      sm_m = std::max(sm_m, (size_t)o.m * sizeof(double));
-    }
-    h->tmp_len = std::max(h->tmp_len, tmp_off);
-    const int64_t nassign = (int64_t)tslot.size();
-    std::stable_sort(tgt.begin(), tgt.end(),
-                     [](const std::pair<int32_t, int64_t>& a, const std::pair<int32_t, int64_t>& b) { return a.first < b.first; });
-    for (size_t i = 0; i < tgt.size(); ++i) {
-      if (i == 0 || tgt[i].first != tgt[i - 1].first) {
-        if (i) tptr.push_back((int64_t)tidx.size());
-        tslot.push_back(tgt[i].first);
-      }
-      tidx.push_back(tgt[i].second);
-    }
-    if (!tgt.empty()) tptr.push_back((int64_t)tidx.size());
+      elim_ops_built = true;
+    };
 
     // ------------------------------------------------ scale + sparsify
     std::vector<int32_t> sz_after = sz;
@@ -913,17 +986,21 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         sm_np = std::max(sm_np, (size_t)sz[p] * sizeof(double));
       }
       set_identity<T>(h, ident, s);
-      potrf_batch<T>(h, diag, d_info + 1, s);
-      scale_cl = diag_cl;
+      potrf_batch<T>(h, diag, d_info + 2 * t + 1, s);
+      scale_cls[t] = diag_cl;
       trsm_batch<T>(h, up, s);   // upper blocks U_p^{-T} A_pq and the inverses Y_p
       copy_batch<T>(h, m_up, s);
       trsm_batch<T>(h, lo, s);
       copy_batch<T>(h, m_lo, s);
       set_identity<T>(h, idr, s);
-      CK(cudaEventRecord(tm.ev[2], s));
+      CK(cudaEventRecord(tm.at(t, 2), s));
       // ---- sparsify, colour by colour (Sec. 2.6.1)
       d_cur = (int32_t*)h->descs.alloc((size_t)n * sizeof(int32_t));
-      CK(cudaMemcpyAsync(d_cur, sz.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      {
+        int32_t* src = (int32_t*)h->stage.take((size_t)n * sizeof(int32_t));
+        std::copy(sz.begin(), sz.end(), src);
+        CK(cudaMemcpyAsync(d_cur, src, (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      }
       std::vector<CpqrTask<T>> tasks;
       std::vector<CpqrNbr<T>> nbrs;
       std::vector<int> tclass;  // cluster size of each task
@@ -1058,9 +1135,14 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         }
         h->prof.launches += (int64_t)groups.size();
         h->prof.end(cpqr_pid, s, 0.0, 0.0, (int64_t)groups.size());
-        CK(cudaMemcpyAsync(sz_after.data(), d_cur, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        build_elim_ops();  // host work overlapped with the sparsification kernels
+        int32_t* hcur = (int32_t*)h->stage.take((size_t)n * sizeof(int32_t));
+        CK(cudaMemcpyAsync(hcur, d_cur, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        std::copy(hcur, hcur + n, sz_after.begin());
+        h->stage.reset();  // every copy issued so far has executed
+        check_pivots(t);
       }
-      CK(cudaStreamSynchronize(s));
       for (int sidx : seps) sz_after[sidx] = 0;
       // compact Q_pc (|p| x r) into the factor
       std::vector<CopyTask<T>> qcopy;
@@ -1085,9 +1167,10 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       for (auto& so : sqops) sm_r = std::max(sm_r, (size_t)std::max(so.r, 1) * sizeof(double));
       copy_batch<T>(h, qcopy, s);
     } else {
-      CK(cudaEventRecord(tm.ev[2], s));
+      CK(cudaEventRecord(tm.at(t, 2), s));
     }
-    CK(cudaEventRecord(tm.ev[3], s));
+    CK(cudaEventRecord(tm.at(t, 3), s));
+    if (!elim_ops_built) build_elim_ops();
     // slots, save areas, temporaries and work items of the scaling +
     // coarse-basis ops (step-t slot lists)
     std::vector<ApplyItem> it_sy, it_sc, it_sz, it_sx;
@@ -1123,7 +1206,9 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       void* d = nullptr;
       if (!pk.buf.empty()) {
         d = h->persist.alloc(pk.buf.size());
-        CK(cudaMemcpyAsync(d, pk.buf.data(), pk.buf.size(), cudaMemcpyHostToDevice, s));
+        void* src = h->stage.take(pk.buf.size());
+        std::memcpy(src, pk.buf.data(), pk.buf.size());
+        CK(cudaMemcpyAsync(d, src, pk.buf.size(), cudaMemcpyHostToDevice, s));
       }
       ap.n_elim = (int)eops.size();
       ap.n_sq = (int)sqops.size();
@@ -1207,26 +1292,20 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       sz = nsz;
       slots = std::move(nslots);
     }
-    CK(cudaEventRecord(tm.ev[4], s));
-    CK(cudaEventSynchronize(tm.ev[4]));
-    h->prof.flush();
-    {
-      int info[2] = {0, 0};
-      CK(cudaMemcpy(info, d_info, 2 * sizeof(int), cudaMemcpyDeviceToHost));
-      if (info[0] || info[1]) {
-        stt.fail_step = t;
-        stt.fail_cluster = info[0] ? elim_cl[info[0] - 1] : scale_cl[info[1] - 1];
-        throw Fail{SPAND_ERR_NOT_SPD, std::string(info[0] ? "pivot" : "interface") +
-                                          " block not positive definite at step " + std::to_string(t)};
-      }
-    }
-    float ms[4];
-    for (int k = 0; k < 4; ++k) CK(cudaEventElapsedTime(&ms[k], tm.ev[k], tm.ev[k + 1]));
-    h->phase_ms[0] += ms[0];
-    h->phase_ms[1] += ms[1];
-    h->phase_ms[2] += ms[2];
-    h->phase_ms[3] += ms[3];
+    CK(cudaEventRecord(tm.at(t, 4), s));
     if (t < L) lay = std::move(nxt);
+  }
+  CK(cudaStreamSynchronize(s));
+  check_pivots(L);
+  {
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, tm.at(0, 0), tm.at(0, 1)));
+    h->phase_ms[3] += ms;
+    for (int t = 1; t <= L; ++t)
+      for (int k = 0; k < 4; ++k) {
+        CK(cudaEventElapsedTime(&ms, tm.at(t, k), tm.at(t, k + 1)));
+        h->phase_ms[k] += ms;
+      }
   }
   build_apply_program<T>(h, apply, s);
   if constexpr (std::is_same<T, double>::value) {
