@@ -212,7 +212,7 @@ static int cpqr_max_cluster() {
   int& c = cached[sizeof(T) == 8 ? 1 : 0];
   if (c) return c;
   if (kCpqrMaxCluster <= 8) return c = kCpqrMaxCluster;
-  const void* fn = (const void*)k_cpqr_cluster<T>;
+  const void* fn = (const void*)k_cpqr_cluster<T, true>;
   const size_t smem = kCpqrChunkBudget + 16 * 1024;
   ensure_smem(fn, smem);
   c = 8;
@@ -1004,6 +1004,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       std::vector<CpqrTask<T>> tasks;
       std::vector<CpqrNbr<T>> nbrs;
       std::vector<int> tclass;  // cluster size of each task
+      std::vector<int> tres;    // 1: the task's chunk lives in shared memory
       const int ncol = st.ncolours();
       size_t wbytes = 0;
       struct WOff { size_t nrm, v, tau, qc, gw; };
@@ -1036,21 +1037,26 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         tk.m_max = mm;
         // smallest cluster whose per-CTA chunk fits in shared memory, and at
         // most ~2 columns per thread
+        const size_t Lp = (size_t)cq_ld<T>(sz[p]);
         int C = max_cluster;
         for (int c = 1; c <= max_cluster; c *= 2)
-          if ((size_t)sz[p] * ((mm + c - 1) / c) * sizeof(T) <= CB) { C = c; break; }
+          if (Lp * ((mm + c - 1) / c) * sizeof(T) <= CB) { C = c; break; }
         while (C < max_cluster && (mm + C - 1) / C > 2 * CQ_NT) C *= 2;
-        const bool resident = (size_t)sz[p] * ((mm + C - 1) / C) * sizeof(T) <= CB;
+        if ((mm + C - 1) / C > CQ_CPT * CQ_NT)
+          throw Fail{SPAND_ERR_INVALID_ARG, "interface coupling too wide for the sparsification kernel (" +
+                                                std::to_string(mm) + " columns)"};
+        const bool resident = Lp * ((mm + C - 1) / C) * sizeof(T) <= CB;
         WOff w;
         w.nrm = 0;
         w.v = wbytes; wbytes += align256((size_t)sz[p] * sz[p] * sizeof(T));
         w.tau = wbytes; wbytes += align256((size_t)sz[p] * sizeof(T));
         w.qc = wbytes; wbytes += align256((size_t)sz[p] * sz[p] * sizeof(T));
         w.gw = wbytes;
-        if (!resident) wbytes += align256((size_t)C * sz[p] * ((mm + C - 1) / C) * sizeof(T));
+        if (!resident) wbytes += align256((size_t)C * Lp * ((mm + C - 1) / C) * sizeof(T));
         woff.push_back(w);
         tasks.push_back(tk);
         tclass.push_back(C);
+        tres.push_back(resident ? 1 : 0);
         cp_cluster.push_back(p);
       }
       if (!tasks.empty()) {
@@ -1063,27 +1069,25 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
           cp_qc.push_back(tasks[i].Qc);
         }
         // launch groups: (colour, cluster size)
-        struct Group { int colour, C; std::vector<int32_t> ids; size_t smem = 0; size_t chunk = 0; };
+        struct Group { int colour, C, res; std::vector<int32_t> ids; size_t smem = 0; };
         std::vector<Group> groups;
         for (int c = 0; c < std::max(ncol, 1); ++c)
-          for (int C = 1; C <= kCpqrMaxCluster; C *= 2) {
-            Group g;
-            g.colour = c;
-            g.C = C;
-            for (size_t i = 0; i < tasks.size(); ++i)
-              if (st.colour[tasks[i].p] == c && tclass[i] == C) {
-                g.ids.push_back((int32_t)i);
-                const int np_ = tasks[i].np, mm = tasks[i].m_max;
-                const size_t chunk = (size_t)np_ * ((mm + C - 1) / C) * sizeof(T);
-                const size_t fixed = ((sizeof(CqShared<T>) + 15) & ~size_t(15)) +
-                                     (((size_t)(tasks[i].nend - tasks[i].nbeg + 1) * sizeof(int) + 15) & ~size_t(15)) +
-                                     (((size_t)np_ * sizeof(T) + 15) & ~size_t(15)) +
-                                     (((size_t)std::max((mm + C - 1) / C, 1) * sizeof(T) + 15) & ~size_t(15));
-                g.smem = std::max(g.smem, fixed);
-                if (chunk <= CB) g.chunk = std::max(g.chunk, chunk);
-              }
-            if (!g.ids.empty()) groups.push_back(std::move(g));
-          }
+          for (int res = 1; res >= 0; --res)
+            for (int C = 1; C <= kCpqrMaxCluster; C *= 2) {
+              Group g;
+              g.colour = c;
+              g.C = C;
+              g.res = res;
+              for (size_t i = 0; i < tasks.size(); ++i)
+                if (st.colour[tasks[i].p] == c && tclass[i] == C && tres[i] == res) {
+                  g.ids.push_back((int32_t)i);
+                  const int np_ = tasks[i].np, mm = tasks[i].m_max;
+                  size_t need = cq_fixed_smem<T>(tasks[i].nend - tasks[i].nbeg, np_);
+                  if (res) need += (size_t)cq_ld<T>(np_) * ((mm + C - 1) / C) * sizeof(T);
+                  g.smem = std::max(g.smem, need);
+                }
+              if (!g.ids.empty()) groups.push_back(std::move(g));
+            }
         std::vector<int32_t> list;
         std::vector<size_t> gbeg;
         for (auto& g : groups) {
@@ -1104,8 +1108,8 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
             cudaStream_t as = h->aux[(g - gi) % kAuxStreams];
             CK(cudaStreamWaitEvent(as, h->ev_fork, 0));
             const Group& G = groups[g];
-            const size_t smem = G.smem + G.chunk;
-            const void* fn = (const void*)k_cpqr_cluster<T>;
+            const size_t smem = G.smem;
+            const void* fn = G.res ? (const void*)k_cpqr_cluster<T, true> : (const void*)k_cpqr_cluster<T, false>;
             ensure_smem(fn, smem);
             if (G.C > 8) ensure_nonportable_cluster(fn);
             cudaLaunchConfig_t cfg = {};
@@ -1124,8 +1128,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
             const int32_t* a1 = at<const int32_t>(d, ol) + gbeg[g];
             const CpqrNbr<T>* a2 = at<const CpqrNbr<T>>(d, on);
             T a4 = (T)eps;
-            int32_t a5 = (int32_t)G.chunk;
-            void* args[] = {(void*)&a0, (void*)&a1, (void*)&a2, (void*)&d_cur, (void*)&a4, (void*)&a5};
+            void* args[] = {(void*)&a0, (void*)&a1, (void*)&a2, (void*)&d_cur, (void*)&a4};
             CK(cudaLaunchKernelExC(&cfg, fn, args));
             CK(cudaEventRecord(h->ev_join[(g - gi) % kAuxStreams], as));
           }
