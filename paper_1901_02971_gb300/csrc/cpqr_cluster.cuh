@@ -46,7 +46,7 @@ struct CpqrTask {
   T* Rp;              // p's block row (leading dimension ldp)
   T* gwork;           // global chunk storage when it does not fit in shared memory: C * L * cols_per
   T* V;               // np x np capacity, column k = v_k (v_k[k] = 1, rows above k unused)
-  T* tau;             // np
+  T* tau;             // np (unused: every CTA keeps the taus in shared memory)
   T* Qc;              // np x np capacity; first r columns = Q_pc on exit
   int32_t p, np, ldp, nbeg, nend, m_max;
 };
@@ -77,17 +77,45 @@ __host__ __device__ inline int cq_ld(int np) {
 
 template <typename T>
 struct CqShared {     // fixed part of the dynamic shared memory
-  T cand_v[CQ_MAXC * CQ_NW];  // warp pivot candidates of the whole cluster (pushed by their owners)
-  int cand_j[CQ_MAXC * CQ_NW];
-  T tau;                      // reflector of the current step (pushed by the pivot's owner)
+  // warp pivot candidates of the whole cluster (pushed by their owners),
+  // double-buffered by step parity: with one barrier per step, a fast warp
+  // pushes step k+1 while a slow one may still read step k
+  T cand_v[2][CQ_MAXC * CQ_NW];
+  int cand_j[2][CQ_MAXC * CQ_NW];
 };
 
-// Fixed shared memory before the chunk: CqShared, the neighbour column starts
-// (nnb + 1 ints) and the broadcast reflector (L elements), each 16-byte aligned.
+__host__ __device__ inline size_t cq_al16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// Fixed shared memory before the chunk, each part 16-byte aligned: CqShared,
+// the neighbour descriptors (nnb), their column starts (nnb + 1 ints), the
+// pivot column copy (L elements) and the tau of every reflector (np).
 template <typename T>
 __host__ __device__ inline size_t cq_fixed_smem(int nnb, int np) {
-  return ((sizeof(CqShared<T>) + 15) & ~size_t(15)) + (((size_t)(nnb + 1) * sizeof(int) + 15) & ~size_t(15)) +
-         (((size_t)cq_ld<T>(np) * sizeof(T) + 15) & ~size_t(15));
+  return cq_al16(sizeof(CqShared<T>)) + cq_al16((size_t)nnb * sizeof(CpqrNbr<T>)) +
+         cq_al16((size_t)(nnb + 1) * sizeof(int)) + cq_al16((size_t)cq_ld<T>(np) * sizeof(T)) +
+         cq_al16((size_t)(np > 0 ? np : 1) * sizeof(T));
+}
+
+// Warp-wide (largest value, lowest index on ties); every lane gets the result.
+// Values are squared norms (>= 0) or -1 for absent/retired columns.
+__device__ __forceinline__ void cq_warp_argmax(float& v, int& j) {
+  // for floats >= 0 the signed-integer order of the bit patterns is the float
+  // order, and every negative float is a negative integer
+  const int best = __reduce_max_sync(0xffffffffu, __float_as_int(v));
+  const int jj = __reduce_min_sync(0xffffffffu, __float_as_int(v) == best ? j : INT_MAX);
+  v = __int_as_float(best);
+  j = jj;
+}
+__device__ __forceinline__ void cq_warp_argmax(double& v, int& j) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oj = __shfl_xor_sync(0xffffffffu, j, o);
+    if (ov > v || (ov == v && oj < j)) {
+      v = ov;
+      j = oj;
+    }
+  }
 }
 
 // one barrier for the whole cluster (a plain block barrier when C == 1)
@@ -96,17 +124,56 @@ __device__ __forceinline__ void cq_sync(cg::cluster_group& cl, int C) {
   else cl.sync();
 }
 
+// Q_pc e_c = H_0 ... H_c e_c (H_k e_c = e_c for k > c) for the columns c of
+// this warp (one warp per column over the whole cluster), the column held in
+// registers: lane l owns rows l + 32 q, q < QR (np <= 32 QR).
+template <typename T, int QR>
+__device__ __forceinline__ void cq_form_q(const CpqrTask<T>& d, const T* Vsrc, const T* tau_s, int r, int np,
+                                          int rank, int C) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c = rank * CQ_NW + warp; c < r; c += C * CQ_NW) {
+    T col[QR];
+#pragma unroll
+    for (int q = 0; q < QR; ++q) col[q] = (lane + 32 * q == c) ? T(1) : T(0);
+    for (int k = c; k >= 0; --k) {
+      const T tk = tau_s[k];
+      if (tk == T(0)) continue;
+      const T* v = Vsrc + (size_t)k * np;
+      T vr[QR];
+      T w = 0;
+#pragma unroll
+      for (int q = 0; q < QR; ++q) {
+        const int i = lane + 32 * q;
+        vr[q] = (i >= k && i < np) ? v[i] : T(0);
+        w = fma(vr[q], col[q], w);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+      w *= tk;
+#pragma unroll
+      for (int q = 0; q < QR; ++q) col[q] = fma(-w, vr[q], col[q]);
+    }
+    T* out = d.Qc + (size_t)c * np;
+#pragma unroll
+    for (int q = 0; q < QR; ++q) {
+      const int i = lane + 32 * q;
+      if (i < np) out[i] = col[q];
+    }
+  }
+}
+
 // Per reflector step k:
 //   1. every warp reduces its threads' best live columns (largest squared
 //      trailing norm, lowest index on ties) and pushes the result into slot
-//      (rank, warp) of every CTA; barrier;
+//      (rank, warp) of set k mod 2 of every CTA; barrier;
 //   2. every thread reduces the C * 8 candidates: pivot j*, |R_kk| = sqrt(norm)
 //      (norms are recomputed exactly each step); the truncation rule is
-//      checked here, uniformly;
-//   3. the CTA owning j* forms the reflector (beta = -sign(alpha) |R_kk|,
-//      tau = (beta - alpha) / beta, v = x / (alpha - beta)), pushes v and tau
-//      into every CTA and retires the column (R_kk = beta, zeros below);
-//      barrier;
+//      checked here, uniformly.  The owner of the previous pivot retires that
+//      column now (R = beta, zeros below), every CTA having read it;
+//   3. every thread derives the reflector from the raw pivot column p (read in
+//      place when C == 1, else copied from the owner's shared memory into a
+//      local buffer + block barrier): beta = -sign(p_k) |R_kk|,
+//      tau = (beta - p_k) / beta, v = [1; p_{k+1:} / (p_k - beta)];
 //   4. every thread applies H_k to its live columns and recomputes their
 //      trailing norms.
 template <typename T, bool RES>
@@ -126,23 +193,29 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
   const int nnb = d.nend - d.nbeg;
   extern __shared__ __align__(16) unsigned char smraw[];
   CqShared<T>& sh = *reinterpret_cast<CqShared<T>*>(smraw);
-  size_t off = (sizeof(CqShared<T>) + 15) & ~size_t(15);
+  size_t off = cq_al16(sizeof(CqShared<T>));
+  CpqrNbr<T>* nbr = reinterpret_cast<CpqrNbr<T>*>(smraw + off);
+  off += cq_al16((size_t)nnb * sizeof(CpqrNbr<T>));
   int* cstart = reinterpret_cast<int*>(smraw + off);
-  off += ((size_t)(nnb + 1) * sizeof(int) + 15) & ~size_t(15);
-  T* vbuf = reinterpret_cast<T*>(smraw + off);
-  off += ((size_t)L * sizeof(T) + 15) & ~size_t(15);
+  off += cq_al16((size_t)(nnb + 1) * sizeof(int));
+  T* pbuf = reinterpret_cast<T*>(smraw + off);
+  off += cq_al16((size_t)L * sizeof(T));
+  T* tau_s = reinterpret_cast<T*>(smraw + off);
+  off += cq_al16((size_t)(np > 0 ? np : 1) * sizeof(T));
   T* schunk = reinterpret_cast<T*>(smraw + off);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  if (tid == 0) {
-    int m = 0;
-    for (int e = 0; e < nnb; ++e) {
-      cstart[e] = m;
-      m += cur_size[nbrs[d.nbeg + e].q];
-    }
-    cstart[nnb] = m;
+  // neighbour descriptors and their current sizes (cur_size of neighbours of
+  // earlier colours already holds their ranks), loaded in parallel
+  for (int e = tid; e < nnb; e += CQ_NT) {
+    nbr[e] = nbrs[d.nbeg + e];
+    cstart[e + 1] = cur_size[nbr[e].q];
   }
-  for (int i = tid; i < L; i += CQ_NT) vbuf[i] = T(0);
+  __syncthreads();
+  if (tid == 0) {
+    cstart[0] = 0;
+    for (int e = 0; e < nnb; ++e) cstart[e + 1] += cstart[e];
+  }
   __syncthreads();
   const int m = cstart[nnb];
   if (m == 0) {  // every neighbour reduced to nothing: p is kept as it is
@@ -170,15 +243,27 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
     return lo;
   };
 
-  // ---- gather my columns of A_pn (one warp per column, coalesced), zero the
-  // padding rows of the last vector
-  for (int jl = warp; jl < nc; jl += CQ_NW) {
-    const int j = j0 + jl;
-    const int e = owner_nbr(j);
-    const CpqrNbr<T> nb = nbrs[d.nbeg + e];
-    const T* src = d.Rp + (size_t)(nb.off_pq + (j - cstart[e])) * d.ldp;
-    T* dst = chunk + (size_t)jl * L;
-    for (int i = lane; i < ng * VW; i += 32) dst[i] = i < np ? src[i] : T(0);
+  // ---- gather my columns of A_pn, zero the padding rows of the last vector:
+  // each warp moves 8 columns at a time (lanes over rows, coalesced), with all
+  // 8 loads issued before the stores
+  constexpr int GU = 8;
+  for (int jb = warp * GU; jb < nc; jb += CQ_NW * GU) {
+    const T* src[GU];
+#pragma unroll
+    for (int u = 0; u < GU; ++u) {
+      const int jl = min(jb + u, nc - 1);
+      const int j = j0 + jl;
+      const int e = owner_nbr(j);
+      src[u] = d.Rp + (size_t)(nbr[e].off_pq + (j - cstart[e])) * d.ldp;
+    }
+    for (int i = lane; i < ng * VW; i += 32) {
+      T v[GU];
+#pragma unroll
+      for (int u = 0; u < GU; ++u) v[u] = (i < np && jb + u < nc) ? src[u][i] : T(0);
+#pragma unroll
+      for (int u = 0; u < GU; ++u)
+        if (jb + u < nc) chunk[(size_t)(jb + u) * L + i] = v[u];
+    }
   }
   __syncthreads();
   // thread t owns local columns t, t + CQ_NT, ...; squared norms (-1: retired or absent)
@@ -202,6 +287,15 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
   const int kmax = min(np, m);
   int r = kmax;
   T r00 = T(0);
+  int pj = -1, pk = 0;  // previous pivot column and its step (retired one step later)
+  T pbeta = T(0);
+  auto retire = [&]() {  // R_{pk,pj} = beta, zeros below, in the owner CTA
+    if (pj >= j0 && pj < j0 + nc) {
+      T* col = chunk + (size_t)(pj - j0) * L;
+      for (int i = pk + tid; i < ng * VW; i += CQ_NT) col[i] = (i == pk) ? pbeta : T(0);
+    }
+    pj = -1;
+  };
   for (int k = 0; k < kmax; ++k) {
     // 1. warp candidates -> every CTA
     T bv = T(-1);
@@ -212,133 +306,130 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
         bv = nrm[c];
         bj = j0 + tid + c * CQ_NT;
       }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-      if (ov > bv || (ov == bv && oj < bj)) {
-        bv = ov;
-        bj = oj;
-      }
-    }
+    cq_warp_argmax(bv, bj);
     if (lane < C) {  // lane q pushes this warp's candidate into CTA q
       CqShared<T>* o = C == 1 ? &sh : cluster.map_shared_rank(&sh, lane);
-      o->cand_v[rank * CQ_NW + warp] = bv;
-      o->cand_j[rank * CQ_NW + warp] = bj;
+      o->cand_v[k & 1][rank * CQ_NW + warp] = bv;
+      o->cand_j[k & 1][rank * CQ_NW + warp] = bj;
     }
     cq_sync(cluster, C);
     // 2. pivot and |R_kk| (identical in every thread of the cluster)
     T gv = T(-1);
     int gj = INT_MAX;
     for (int q = lane; q < C * CQ_NW; q += 32) {
-      const T v = sh.cand_v[q];
-      const int j = sh.cand_j[q];
+      const T v = sh.cand_v[k & 1][q];
+      const int j = sh.cand_j[k & 1][q];
       if (v > gv || (v == gv && j < gj)) {
         gv = v;
         gj = j;
       }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const T ov = __shfl_xor_sync(0xffffffffu, gv, o);
-      const int oj = __shfl_xor_sync(0xffffffffu, gj, o);
-      if (ov > gv || (ov == gv && oj < gj)) {
-        gv = ov;
-        gj = oj;
-      }
-    }
+    cq_warp_argmax(gv, gj);
     if (gj == INT_MAX) gj = 0;  // unreachable: k < kmax <= m leaves a live column
+    retire();                   // every CTA finished reading the previous pivot before this barrier
     const T rkk = sqrt(gv > T(0) ? gv : T(0));
     if (k == 0) r00 = rkk;
     if (r00 == T(0) || rkk < eps * r00) {
       r = k;
       break;
     }
-    const int owner = min(C - 1, gj / cols_per);
 #pragma unroll
     for (int c = 0; c < CQ_CPT; ++c)
-      if (j0 + tid + c * CQ_NT == gj) nrm[c] = T(-1);  // the pivot column retires
-    // 3. the owner forms the reflector, pushes it, retires the pivot column
-    if (rank == owner) {
-      T* col = chunk + (size_t)(gj - j0) * L;
-      const T alpha = col[k];
-      T beta, tau, scal;
-      if (rkk == T(0)) {
-        beta = T(0);
-        tau = T(0);
-        scal = T(0);
-      } else {
-        beta = alpha >= T(0) ? -rkk : rkk;
-        tau = (beta - alpha) / beta;
-        scal = T(1) / (alpha - beta);
+      if (j0 + tid + c * CQ_NT == gj) nrm[c] = T(-1);  // the pivot column leaves the live set
+    // 3. the raw pivot column and the reflector
+    const int owner = min(C - 1, gj / cols_per);
+    const int i0 = (k / VW) * VW;
+    const T* pcol;
+    if (C == 1) {
+      pcol = chunk + (size_t)(gj - j0) * L;
+    } else {
+      const size_t po = (size_t)(gj - owner * cols_per) * L;
+      if (RES) {
+        const T* src = cluster.map_shared_rank(schunk, owner) + po;
+        for (int i = i0 + tid; i < ng * VW; i += CQ_NT) pbuf[i] = src[i];
+      } else {  // the owner's chunk in global memory, written by another CTA: read through L2
+        const T* src = d.gwork + (size_t)owner * L * cols_per + po;
+        for (int i = i0 + tid; i < ng * VW; i += CQ_NT) pbuf[i] = __ldcg(src + i);
       }
-      const int i0 = (k / VW) * VW;
-      for (int i = i0 + tid; i < ng * VW; i += CQ_NT) {
-        const T x = col[i];
-        const T v = i < k ? T(0) : (i == k ? T(1) : x * scal);
-        if (C == 1) {
-          vbuf[i] = v;
-        } else {
-          for (int q = 0; q < C; ++q) cluster.map_shared_rank(vbuf, q)[i] = v;
-        }
-        if (i >= k && i < np) d.V[i + (size_t)k * np] = v;
-        if (i >= k) col[i] = (i == k) ? beta : T(0);
-      }
-      if (tid < C) {
-        CqShared<T>* o = C == 1 ? &sh : cluster.map_shared_rank(&sh, tid);
-        o->tau = tau;
-      }
-      if (tid == 0) d.tau[k] = tau;
+      __syncthreads();
+      pcol = pbuf;
     }
-    cq_sync(cluster, C);
-    const T tau = sh.tau;
-    // 4. apply H_k to my live columns, recompute their trailing norms
+    const T alpha = pcol[k];
+    T beta, tau, scal;
+    if (rkk == T(0)) {
+      beta = T(0);
+      tau = T(0);
+      scal = T(0);
+    } else {
+      beta = alpha >= T(0) ? -rkk : rkk;
+      tau = (beta - alpha) / beta;
+      scal = T(1) / (alpha - beta);
+    }
+    if (tid == 0) tau_s[k] = tau;
+    if (rank == owner)  // v_k for the formation of Q_pc
+      for (int i = k + tid; i < np; i += CQ_NT) d.V[i + (size_t)k * np] = (i == k) ? T(1) : pcol[i] * scal;
+    pj = gj;
+    pk = k;
+    pbeta = beta;
+    // 4. apply H_k = I - tau v v^T to my live columns, recompute their trailing norms:
+    //    w = tau (x_k + scal p_{k+1:}^T x_{k+1:}),  x_k -= w,  x_{k+1:} -= (w scal) p_{k+1:}
     const int gs = k / VW;
-    const V* __restrict__ vv = reinterpret_cast<const V*>(vbuf);
+    const int rb = gs * VW;
+    const V* __restrict__ pv = reinterpret_cast<const V*>(pcol);
 #pragma unroll
     for (int c = 0; c < CQ_CPT; ++c) {
       if (nrm[c] < T(0)) continue;
-      V* __restrict__ cv = reinterpret_cast<V*>(chunk + (size_t)(tid + c * CQ_NT) * L);
+      T* colp = chunk + (size_t)(tid + c * CQ_NT) * L;
+      V* __restrict__ cv = reinterpret_cast<V*>(colp);
       T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-#pragma unroll 2
-      for (int g = gs; g < ng; ++g) {
-        const V x = cv[g], v = vv[g];
-        a0 = fma(x.x, v.x, a0);
-        a1 = fma(x.y, v.y, a1);
+      {  // first vector: only rows > k
+        const V x = cv[gs], p = pv[gs];
+        if (rb > k) a0 = x.x * p.x;
+        if (rb + 1 > k) a1 = x.y * p.y;
         if constexpr (VW == 4) {
-          a2 = fma(x.z, v.z, a2);
-          a3 = fma(x.w, v.w, a3);
+          if (rb + 2 > k) a2 = x.z * p.z;
+          if (rb + 3 > k) a3 = x.w * p.w;
         }
       }
-      const T w = ((a0 + a1) + (a2 + a3)) * tau;
-      T q0 = 0, q1 = 0, q2 = 0, q3 = 0;
-      {  // first vector: rows <= k do not enter the trailing norm
-        V x = cv[gs];
-        const V v = vv[gs];
-        const int rb = gs * VW;
-        x.x = fma(-w, v.x, x.x);
-        x.y = fma(-w, v.y, x.y);
-        if (rb > k) q0 = x.x * x.x;
-        if (rb + 1 > k) q1 = x.y * x.y;
+#pragma unroll 2
+      for (int g = gs + 1; g < ng; ++g) {
+        const V x = cv[g], p = pv[g];
+        a0 = fma(x.x, p.x, a0);
+        a1 = fma(x.y, p.y, a1);
         if constexpr (VW == 4) {
-          x.z = fma(-w, v.z, x.z);
-          x.w = fma(-w, v.w, x.w);
-          if (rb + 2 > k) q2 = x.z * x.z;
-          if (rb + 3 > k) q3 = x.w * x.w;
+          a2 = fma(x.z, p.z, a2);
+          a3 = fma(x.w, p.w, a3);
+        }
+      }
+      const T w = tau * fma(scal, (a0 + a1) + (a2 + a3), colp[k]);
+      const T ws = w * scal;
+      T q0 = 0, q1 = 0, q2 = 0, q3 = 0;
+      {  // first vector: row k takes -w, rows > k take -ws p and enter the norm
+        V x = cv[gs];
+        const V p = pv[gs];
+        if (rb == k) x.x -= w;
+        else if (rb > k) { x.x = fma(-ws, p.x, x.x); q0 = x.x * x.x; }
+        if (rb + 1 == k) x.y -= w;
+        else if (rb + 1 > k) { x.y = fma(-ws, p.y, x.y); q1 = x.y * x.y; }
+        if constexpr (VW == 4) {
+          if (rb + 2 == k) x.z -= w;
+          else if (rb + 2 > k) { x.z = fma(-ws, p.z, x.z); q2 = x.z * x.z; }
+          if (rb + 3 == k) x.w -= w;
+          else if (rb + 3 > k) { x.w = fma(-ws, p.w, x.w); q3 = x.w * x.w; }
         }
         cv[gs] = x;
       }
 #pragma unroll 2
       for (int g = gs + 1; g < ng; ++g) {
         V x = cv[g];
-        const V v = vv[g];
-        x.x = fma(-w, v.x, x.x);
-        x.y = fma(-w, v.y, x.y);
+        const V p = pv[g];
+        x.x = fma(-ws, p.x, x.x);
+        x.y = fma(-ws, p.y, x.y);
         q0 = fma(x.x, x.x, q0);
         q1 = fma(x.y, x.y, q1);
         if constexpr (VW == 4) {
-          x.z = fma(-w, v.z, x.z);
-          x.w = fma(-w, v.w, x.w);
+          x.z = fma(-ws, p.z, x.z);
+          x.w = fma(-ws, p.w, x.w);
           q2 = fma(x.z, x.z, q2);
           q3 = fma(x.w, x.w, q3);
         }
@@ -347,6 +438,8 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
       nrm[c] = (q0 + q1) + (q2 + q3);
     }
   }
+  __syncthreads();  // every thread is done with the last pivot column
+  retire();         // the last pivot when the loop ran to kmax
   __syncthreads();
   // Rows 0..r-1 of every column now hold W_cn in the original column order
   // (the pivot found at step r, if any, was not touched).
@@ -354,8 +447,7 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
   for (int jl = warp; jl < nc; jl += CQ_NW) {
     const int j = j0 + jl;
     const int e = owner_nbr(j);
-    const CpqrNbr<T> nb = nbrs[d.nbeg + e];
-    T* dst = d.Rp + (size_t)(nb.off_pq + (j - cstart[e])) * d.ldp;
+    T* dst = d.Rp + (size_t)(nbr[e].off_pq + (j - cstart[e])) * d.ldp;
     const T* src = chunk + (size_t)jl * L;
     for (int i = lane; i < r; i += 32) dst[i] = src[i];
   }
@@ -363,7 +455,7 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
   for (int jl = tid; jl < nc; jl += CQ_NT) {
     const int j = j0 + jl;
     const int e = owner_nbr(j);
-    const CpqrNbr<T> nb = nbrs[d.nbeg + e];
+    const CpqrNbr<T> nb = nbr[e];
     const int cc = j - cstart[e];
     const T* src = chunk + (size_t)jl * L;
     for (int i = 0; i < r; ++i) nb.Rq[cc + (size_t)(nb.off_qp + i) * nb.ldq] = src[i];
@@ -373,7 +465,7 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
       const int i = (int)(x % r), j = (int)(x / r);
       d.Rp[i + (size_t)j * d.ldp] = (i == j) ? T(1) : T(0);
     }
-  if (C > 1) cluster.sync();  // every V column and tau is visible cluster-wide
+  if (C > 1) cluster.sync();  // every V column is visible cluster-wide
   else __syncthreads();
   // ---- Q_pc e_c = H_0 ... H_c e_c (H_k e_c = e_c for k > c), one warp per
   // column, the column held in registers (lane l owns rows l, l+32, ...).  The
@@ -389,58 +481,37 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
     __syncthreads();
     Vsrc = Vs;
   }
-  constexpr int QR = 16;  // rows per lane held in registers
-  if (np > 32 * QR) {     // tall interfaces: the column lives in global memory
+  if (np > 32 * 16) {  // tall interfaces: the column lives in global memory
     for (int c = rank * CQ_NW + warp; c < r; c += C * CQ_NW) {
       T* col = d.Qc + (size_t)c * np;
       for (int i = lane; i < np; i += 32) col[i] = (i == c) ? T(1) : T(0);
       __syncwarp();
       for (int k = c; k >= 0; --k) {
-        const T tk = __ldcg(d.tau + k);
+        const T tk = tau_s[k];
         if (tk == T(0)) continue;
         const T* v = Vsrc + (size_t)k * np;
         T w = 0;
-        for (int i = k + lane; i < np; i += 32) w += v[i] * col[i];
+        for (int i = k + lane; i < np; i += 32) w += __ldcg(v + i) * col[i];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
         w *= tk;
-        for (int i = k + lane; i < np; i += 32) col[i] -= w * v[i];
+        for (int i = k + lane; i < np; i += 32) col[i] -= w * __ldcg(v + i);
         __syncwarp();
       }
     }
-  }
-  for (int c = rank * CQ_NW + warp; np <= 32 * QR && c < r; c += C * CQ_NW) {
-    T col[QR];
-#pragma unroll
-    for (int q = 0; q < QR; ++q) col[q] = (lane + 32 * q == c) ? T(1) : T(0);
-    for (int k = c; k >= 0; --k) {
-      const T tk = __ldcg(d.tau + k);
-      if (tk == T(0)) continue;
-      const T* v = Vsrc + (size_t)k * np;
-      T w = 0;
-#pragma unroll
-      for (int q = 0; q < QR; ++q) {
-        const int i = lane + 32 * q;
-        if (i >= k && i < np) w += v[i] * col[q];
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-      w *= tk;
-#pragma unroll
-      for (int q = 0; q < QR; ++q) {
-        const int i = lane + 32 * q;
-        if (i >= k && i < np) col[q] -= w * v[i];
-      }
-    }
-    T* out = d.Qc + (size_t)c * np;
-#pragma unroll
-    for (int q = 0; q < QR; ++q) {
-      const int i = lane + 32 * q;
-      if (i < np) out[i] = col[q];
-    }
+  } else if (np > 32 * 8) {
+    cq_form_q<T, 16>(d, Vsrc, tau_s, r, np, rank, C);
+  } else if (np > 32 * 4) {
+    cq_form_q<T, 8>(d, Vsrc, tau_s, r, np, rank, C);
+  } else if (np > 32 * 2) {
+    cq_form_q<T, 4>(d, Vsrc, tau_s, r, np, rank, C);
+  } else if (np > 32) {
+    cq_form_q<T, 2>(d, Vsrc, tau_s, r, np, rank, C);
+  } else {
+    cq_form_q<T, 1>(d, Vsrc, tau_s, r, np, rank, C);
   }
   if (rank == 0 && tid == 0) cur_size[d.p] = r;
-  if (C > 1) cluster.sync();  // no CTA leaves while others may still write into its shared memory
+  if (C > 1) cluster.sync();  // no CTA leaves while others may still read its shared memory
 }
 
 }  // namespace spand
