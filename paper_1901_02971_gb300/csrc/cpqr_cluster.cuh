@@ -88,12 +88,13 @@ __host__ __device__ inline size_t cq_al16(size_t b) { return (b + 15) & ~size_t(
 
 // Fixed shared memory before the chunk, each part 16-byte aligned: CqShared,
 // the neighbour descriptors (nnb), their column starts (nnb + 1 ints), the
-// pivot column copy (L elements) and the tau of every reflector (np).
+// pivot column copy (L elements), the tau of every reflector (np) and, per
+// local column, its neighbour and its column in p's block row (2 cols_per ints).
 template <typename T>
-__host__ __device__ inline size_t cq_fixed_smem(int nnb, int np) {
+__host__ __device__ inline size_t cq_fixed_smem(int nnb, int np, int cols_per) {
   return cq_al16(sizeof(CqShared<T>)) + cq_al16((size_t)nnb * sizeof(CpqrNbr<T>)) +
          cq_al16((size_t)(nnb + 1) * sizeof(int)) + cq_al16((size_t)cq_ld<T>(np) * sizeof(T)) +
-         cq_al16((size_t)(np > 0 ? np : 1) * sizeof(T));
+         cq_al16((size_t)(np > 0 ? np : 1) * sizeof(T)) + cq_al16((size_t)2 * (cols_per > 0 ? cols_per : 1) * sizeof(int));
 }
 
 // Warp-wide (largest value, lowest index on ties); every lane gets the result.
@@ -130,34 +131,55 @@ __device__ __forceinline__ void cq_sync(cg::cluster_group& cl, int C) {
 template <typename T, int QR>
 __device__ __forceinline__ void cq_form_q(const CpqrTask<T>& d, const T* Vsrc, const T* tau_s, int r, int np,
                                           int rank, int C) {
+  // two columns per warp, their reflector chains interleaved (independent
+  // shuffle reductions); c1 > c0, so H_k for c0 < k <= c1 touches c1 only
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int c = rank * CQ_NW + warp; c < r; c += C * CQ_NW) {
-    T col[QR];
+  const int nwarps = C * CQ_NW, w0 = rank * CQ_NW + warp;
+  for (int c0 = w0; c0 < r; c0 += 2 * nwarps) {
+    const int c1 = c0 + nwarps;  // may be >= r (then only c0 is formed)
+    const bool two = c1 < r;
+    T a[QR], b[QR];
 #pragma unroll
-    for (int q = 0; q < QR; ++q) col[q] = (lane + 32 * q == c) ? T(1) : T(0);
-    for (int k = c; k >= 0; --k) {
+    for (int q = 0; q < QR; ++q) {
+      a[q] = (lane + 32 * q == c0) ? T(1) : T(0);
+      b[q] = (lane + 32 * q == c1) ? T(1) : T(0);
+    }
+    for (int k = two ? c1 : c0; k >= 0; --k) {
       const T tk = tau_s[k];
       if (tk == T(0)) continue;
+      const bool doa = k <= c0;
       const T* v = Vsrc + (size_t)k * np;
       T vr[QR];
-      T w = 0;
+      T wa = 0, wb = 0;
 #pragma unroll
       for (int q = 0; q < QR; ++q) {
         const int i = lane + 32 * q;
         vr[q] = (i >= k && i < np) ? v[i] : T(0);
-        w = fma(vr[q], col[q], w);
+        wa = fma(vr[q], a[q], wa);
+        wb = fma(vr[q], b[q], wb);
       }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-      w *= tk;
+      for (int o = 16; o > 0; o >>= 1) {
+        wa += __shfl_xor_sync(0xffffffffu, wa, o);
+        wb += __shfl_xor_sync(0xffffffffu, wb, o);
+      }
+      wa = doa ? wa * tk : T(0);
+      wb *= tk;
 #pragma unroll
-      for (int q = 0; q < QR; ++q) col[q] = fma(-w, vr[q], col[q]);
+      for (int q = 0; q < QR; ++q) {
+        a[q] = fma(-wa, vr[q], a[q]);
+        b[q] = fma(-wb, vr[q], b[q]);
+      }
     }
-    T* out = d.Qc + (size_t)c * np;
+    T* oa = d.Qc + (size_t)c0 * np;
+    T* ob = d.Qc + (size_t)c1 * np;
 #pragma unroll
     for (int q = 0; q < QR; ++q) {
       const int i = lane + 32 * q;
-      if (i < np) out[i] = col[q];
+      if (i < np) {
+        oa[i] = a[q];
+        if (two) ob[i] = b[q];
+      }
     }
   }
 }
@@ -202,6 +224,9 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
   off += cq_al16((size_t)L * sizeof(T));
   T* tau_s = reinterpret_cast<T*>(smraw + off);
   off += cq_al16((size_t)(np > 0 ? np : 1) * sizeof(T));
+  int* tcol = reinterpret_cast<int*>(smraw + off);  // tcol[jl]: neighbour e, tcol[cpm + jl]: column in p's row
+  const int cpm = d.m_max > 0 ? (d.m_max + (int)cluster.num_blocks() - 1) / (int)cluster.num_blocks() : 1;
+  off += cq_al16((size_t)2 * cpm * sizeof(int));
   T* schunk = reinterpret_cast<T*>(smraw + off);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -243,6 +268,14 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
     return lo;
   };
 
+  // per local column: its neighbour and its column in p's block row
+  for (int jl = tid; jl < nc; jl += CQ_NT) {
+    const int j = j0 + jl;
+    const int e = owner_nbr(j);
+    tcol[jl] = e;
+    tcol[cpm + jl] = nbr[e].off_pq + (j - cstart[e]);
+  }
+  __syncthreads();
   // ---- gather my columns of A_pn, zero the padding rows of the last vector:
   // each warp moves 8 columns at a time (lanes over rows, coalesced), with all
   // 8 loads issued before the stores
@@ -250,12 +283,7 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
   for (int jb = warp * GU; jb < nc; jb += CQ_NW * GU) {
     const T* src[GU];
 #pragma unroll
-    for (int u = 0; u < GU; ++u) {
-      const int jl = min(jb + u, nc - 1);
-      const int j = j0 + jl;
-      const int e = owner_nbr(j);
-      src[u] = d.Rp + (size_t)(nbr[e].off_pq + (j - cstart[e])) * d.ldp;
-    }
+    for (int u = 0; u < GU; ++u) src[u] = d.Rp + (size_t)tcol[cpm + min(jb + u, nc - 1)] * d.ldp;
     for (int i = lane; i < ng * VW; i += 32) {
       T v[GU];
 #pragma unroll
@@ -445,26 +473,23 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
   // (the pivot found at step r, if any, was not touched).
   // ---- write back W_cn into p's row (one warp per column, coalesced) ...
   for (int jl = warp; jl < nc; jl += CQ_NW) {
-    const int j = j0 + jl;
-    const int e = owner_nbr(j);
-    T* dst = d.Rp + (size_t)(nbr[e].off_pq + (j - cstart[e])) * d.ldp;
+    T* dst = d.Rp + (size_t)tcol[cpm + jl] * d.ldp;
     const T* src = chunk + (size_t)jl * L;
     for (int i = lane; i < r; i += 32) dst[i] = src[i];
   }
   // ... and its transpose into the neighbours' rows (one thread per column)
   for (int jl = tid; jl < nc; jl += CQ_NT) {
-    const int j = j0 + jl;
-    const int e = owner_nbr(j);
+    const int e = tcol[jl];
     const CpqrNbr<T> nb = nbr[e];
-    const int cc = j - cstart[e];
+    const int cc = j0 + jl - cstart[e];
     const T* src = chunk + (size_t)jl * L;
     for (int i = 0; i < r; ++i) nb.Rq[cc + (size_t)(nb.off_qp + i) * nb.ldq] = src[i];
   }
-  if (rank == 0)
-    for (int64_t x = tid; x < (int64_t)r * r; x += CQ_NT) {
-      const int i = (int)(x % r), j = (int)(x / r);
-      d.Rp[i + (size_t)j * d.ldp] = (i == j) ? T(1) : T(0);
-    }
+  // A_cc = I: column j by warp j of the cluster, lanes over rows
+  for (int j = rank * CQ_NW + warp; j < r; j += C * CQ_NW) {
+    T* dst = d.Rp + (size_t)j * d.ldp;
+    for (int i = lane; i < r; i += 32) dst[i] = (i == j) ? T(1) : T(0);
+  }
   if (C > 1) cluster.sync();  // every V column is visible cluster-wide
   else __syncthreads();
   // ---- Q_pc e_c = H_0 ... H_c e_c (H_k e_c = e_c for k > c), one warp per
@@ -473,11 +498,17 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
   // chunk's space (free again after the write-back).
   const T* Vsrc = d.V;
   if (RES && (size_t)np * r <= (size_t)L * cols_per) {
+    // V was written by other CTAs: read through L2; 8 columns per warp in flight
     T* Vs = schunk;
-    for (int64_t x = tid; x < (int64_t)np * r; x += CQ_NT) {
-      const int i = (int)(x % np), k = (int)(x / np);
-      Vs[x] = i >= k ? __ldcg(d.V + i + (size_t)k * np) : T(0);  // written by other CTAs: read through L2
-    }
+    for (int kb = warp * 8; kb < r; kb += CQ_NW * 8)
+      for (int i = lane; i < np; i += 32) {
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = (kb + u < r && i >= kb + u) ? __ldcg(d.V + i + (size_t)(kb + u) * np) : T(0);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (kb + u < r) Vs[i + (size_t)(kb + u) * np] = v[u];
+      }
     __syncthreads();
     Vsrc = Vs;
   }

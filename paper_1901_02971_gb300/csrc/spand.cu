@@ -1082,7 +1082,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
                 if (st.colour[tasks[i].p] == c && tclass[i] == C && tres[i] == res) {
                   g.ids.push_back((int32_t)i);
                   const int np_ = tasks[i].np, mm = tasks[i].m_max;
-                  size_t need = cq_fixed_smem<T>(tasks[i].nend - tasks[i].nbeg, np_);
+                  size_t need = cq_fixed_smem<T>(tasks[i].nend - tasks[i].nbeg, np_, (mm + C - 1) / C);
                   if (res) need += (size_t)cq_ld<T>(np_) * ((mm + C - 1) / C) * sizeof(T);
                   g.smem = std::max(g.smem, need);
                 }
