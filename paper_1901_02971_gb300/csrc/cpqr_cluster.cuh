@@ -15,11 +15,14 @@
 // shared memory when it fits, otherwise in global scratch.  One thread owns a
 // column (CQ_CPT at most) and streams it with 16-byte vector loads; the stride L
 // is chosen so that the 8 threads of a quarter-warp hit distinct bank groups.
-// Columns are never swapped: the pivot column is retired in place, so after r
-// steps the top r rows of every column are W_cn in the original column order.
-// Per reflector step the CTAs exchange warp pivot candidates and the
-// Householder vector through distributed shared memory, with two cluster
-// barriers and no spin-waits.
+// Columns are never swapped and a pivot column is never written again: its
+// entries below the diagonal keep the raw values p from which the Householder
+// vector is derived (v = [1; p / (p_k - beta)]), so the reflectors need no
+// storage of their own; the write-back emits R_kk = beta and zeros below for
+// retired columns.  Per reflector step the CTAs exchange warp pivot
+// candidates through distributed shared memory and pull the pivot column from
+// its owner: one cluster barrier per step (one block barrier when C == 1), no
+// spin-waits.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -30,10 +33,10 @@ namespace spand {
 
 namespace cg = cooperative_groups;
 
-constexpr int CQ_NT = 256;          // threads per CTA
-constexpr int CQ_NW = CQ_NT / 32;   // warps per CTA
+constexpr int CQ_MAXNT = 512;              // threads per CTA: 256 or 512 (chosen per launch)
+constexpr int CQ_MAXW = CQ_MAXNT / 32;
 constexpr int CQ_MAXC = 16;         // largest cluster
-constexpr int CQ_CPT = 4;           // columns per thread at most (the host sizes clusters for it)
+constexpr int CQ_CPT = 4;           // columns per thread group at most (the host sizes clusters for it)
 
 template <typename T>
 struct CpqrNbr {      // neighbour q of p (Sec. 2.6.1: A_pn spans all of them)
@@ -77,24 +80,29 @@ __host__ __device__ inline int cq_ld(int np) {
 
 template <typename T>
 struct CqShared {     // fixed part of the dynamic shared memory
-  // warp pivot candidates of the whole cluster (pushed by their owners),
-  // double-buffered by step parity: with one barrier per step, a fast warp
-  // pushes step k+1 while a slow one may still read step k
-  T cand_v[2][CQ_MAXC * CQ_NW];
-  int cand_j[2][CQ_MAXC * CQ_NW];
+  // pivot candidates, double-buffered by step parity (a fast warp or CTA
+  // writes step k+1 while a slow one may still read step k): with C == 1 one
+  // slot per warp; with C > 1 the warps' slots feed a CTA-level reduction and
+  // slot q of cta_v/cta_j holds the best of CTA q (pushed by it)
+  T cand_v[2][CQ_MAXW];
+  int cand_j[2][CQ_MAXW];
+  T cta_v[2][CQ_MAXC];
+  int cta_j[2][CQ_MAXC];
 };
 
 __host__ __device__ inline size_t cq_al16(size_t b) { return (b + 15) & ~size_t(15); }
 
 // Fixed shared memory before the chunk, each part 16-byte aligned: CqShared,
 // the neighbour descriptors (nnb), their column starts (nnb + 1 ints), the
-// pivot column copy (L elements), the tau of every reflector (np) and, per
-// local column, its neighbour and its column in p's block row (2 cols_per ints).
+// pivot column copy (L elements), per reflector its pivot column, beta, tau
+// and scale (np each), and per local column its neighbour, its column in p's
+// block row and the step at which it became the pivot (3 cols_per ints).
 template <typename T>
 __host__ __device__ inline size_t cq_fixed_smem(int nnb, int np, int cols_per) {
+  const size_t npp = (size_t)(np > 0 ? np : 1), cp = (size_t)(cols_per > 0 ? cols_per : 1);
   return cq_al16(sizeof(CqShared<T>)) + cq_al16((size_t)nnb * sizeof(CpqrNbr<T>)) +
          cq_al16((size_t)(nnb + 1) * sizeof(int)) + cq_al16((size_t)cq_ld<T>(np) * sizeof(T)) +
-         cq_al16((size_t)(np > 0 ? np : 1) * sizeof(T)) + cq_al16((size_t)2 * (cols_per > 0 ? cols_per : 1) * sizeof(int));
+         3 * cq_al16(npp * sizeof(T)) + cq_al16(npp * sizeof(int)) + cq_al16(3 * cp * sizeof(int));
 }
 
 // Warp-wide (largest value, lowest index on ties); every lane gets the result.
@@ -127,14 +135,17 @@ __device__ __forceinline__ void cq_sync(cg::cluster_group& cl, int C) {
 
 // Q_pc e_c = H_0 ... H_c e_c (H_k e_c = e_c for k > c) for the columns c of
 // this warp (one warp per column over the whole cluster), the column held in
-// registers: lane l owns rows l + 32 q, q < QR (np <= 32 QR).
-template <typename T, int QR>
-__device__ __forceinline__ void cq_form_q(const CpqrTask<T>& d, const T* Vsrc, const T* tau_s, int r, int np,
-                                          int rank, int C) {
+// registers: lane l owns rows l + 32 q, q < QR (np <= 32 QR).  Reflector k is
+// read either from a V array (column k, rows >= k) or, when DIRECT, from the
+// retired pivot column in the chunk: v_k = [1; p_{k+1:} scal_k].
+template <typename T, int QR, bool DIRECT>
+__device__ __forceinline__ void cq_form_q(const CpqrTask<T>& d, const T* V, const T* chunk, int L, int j0,
+                                          const int* piv_s, const T* scal_s, const T* tau_s, int r, int np, int rank,
+                                          int C) {
   // two columns per warp, their reflector chains interleaved (independent
   // shuffle reductions); c1 > c0, so H_k for c0 < k <= c1 touches c1 only
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nwarps = C * CQ_NW, w0 = rank * CQ_NW + warp;
+  const int nwc = (int)(blockDim.x >> 5), nwarps = C * nwc, w0 = rank * nwc + warp;
   for (int c0 = w0; c0 < r; c0 += 2 * nwarps) {
     const int c1 = c0 + nwarps;  // may be >= r (then only c0 is formed)
     const bool two = c1 < r;
@@ -148,13 +159,26 @@ __device__ __forceinline__ void cq_form_q(const CpqrTask<T>& d, const T* Vsrc, c
       const T tk = tau_s[k];
       if (tk == T(0)) continue;
       const bool doa = k <= c0;
-      const T* v = Vsrc + (size_t)k * np;
       T vr[QR];
+      if (DIRECT) {
+        const T* pc = chunk + (size_t)(piv_s[k] - j0) * L;
+        const T sc = scal_s[k];
+#pragma unroll
+        for (int q = 0; q < QR; ++q) {
+          const int i = lane + 32 * q;
+          vr[q] = (i > k && i < np) ? pc[i] * sc : (i == k ? T(1) : T(0));
+        }
+      } else {
+        const T* v = V + (size_t)k * np;
+#pragma unroll
+        for (int q = 0; q < QR; ++q) {
+          const int i = lane + 32 * q;
+          vr[q] = (i >= k && i < np) ? v[i] : T(0);
+        }
+      }
       T wa = 0, wb = 0;
 #pragma unroll
       for (int q = 0; q < QR; ++q) {
-        const int i = lane + 32 * q;
-        vr[q] = (i >= k && i < np) ? v[i] : T(0);
         wa = fma(vr[q], a[q], wa);
         wb = fma(vr[q], b[q], wb);
       }
@@ -184,22 +208,34 @@ __device__ __forceinline__ void cq_form_q(const CpqrTask<T>& d, const T* Vsrc, c
   }
 }
 
+template <typename T, bool DIRECT>
+__device__ __forceinline__ void cq_form_q_any(const CpqrTask<T>& d, const T* V, const T* chunk, int L, int j0,
+                                              const int* piv_s, const T* scal_s, const T* tau_s, int r, int np,
+                                              int rank, int C) {
+  if (np > 32 * 8) cq_form_q<T, 16, DIRECT>(d, V, chunk, L, j0, piv_s, scal_s, tau_s, r, np, rank, C);
+  else if (np > 32 * 4) cq_form_q<T, 8, DIRECT>(d, V, chunk, L, j0, piv_s, scal_s, tau_s, r, np, rank, C);
+  else if (np > 32 * 2) cq_form_q<T, 4, DIRECT>(d, V, chunk, L, j0, piv_s, scal_s, tau_s, r, np, rank, C);
+  else if (np > 32) cq_form_q<T, 2, DIRECT>(d, V, chunk, L, j0, piv_s, scal_s, tau_s, r, np, rank, C);
+  else cq_form_q<T, 1, DIRECT>(d, V, chunk, L, j0, piv_s, scal_s, tau_s, r, np, rank, C);
+}
+
 // Per reflector step k:
 //   1. every warp reduces its threads' best live columns (largest squared
 //      trailing norm, lowest index on ties) and pushes the result into slot
 //      (rank, warp) of set k mod 2 of every CTA; barrier;
 //   2. every thread reduces the C * 8 candidates: pivot j*, |R_kk| = sqrt(norm)
 //      (norms are recomputed exactly each step); the truncation rule is
-//      checked here, uniformly.  The owner of the previous pivot retires that
-//      column now (R = beta, zeros below), every CTA having read it;
+//      checked here, uniformly;
 //   3. every thread derives the reflector from the raw pivot column p (read in
 //      place when C == 1, else copied from the owner's shared memory into a
 //      local buffer + block barrier): beta = -sign(p_k) |R_kk|,
 //      tau = (beta - p_k) / beta, v = [1; p_{k+1:} / (p_k - beta)];
 //   4. every thread applies H_k to its live columns and recomputes their
 //      trailing norms.
-template <typename T, bool RES>
-__global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __restrict__ tasks,
+//
+// Column ownership: thread t owns the local columns t + c * NT, c < CQ_CPT.
+template <typename T, bool RES, int NT>
+__global__ void __launch_bounds__(NT) k_cpqr_cluster(const CpqrTask<T>* __restrict__ tasks,
                                                        const int32_t* __restrict__ list,
                                                        const CpqrNbr<T>* __restrict__ nbrs,
                                                        int32_t* __restrict__ cur_size, T eps) {
@@ -213,6 +249,8 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
   const int L = cq_ld<T>(np);
   const int ng = (np + VW - 1) / VW;  // vectors per column that hold rows < np
   const int nnb = d.nend - d.nbeg;
+  const int npp = np > 0 ? np : 1;
+  const int cpm = d.m_max > 0 ? (d.m_max + C - 1) / C : 1;  // host bound on the columns per CTA
   extern __shared__ __align__(16) unsigned char smraw[];
   CqShared<T>& sh = *reinterpret_cast<CqShared<T>*>(smraw);
   size_t off = cq_al16(sizeof(CqShared<T>));
@@ -223,16 +261,22 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
   T* pbuf = reinterpret_cast<T*>(smraw + off);
   off += cq_al16((size_t)L * sizeof(T));
   T* tau_s = reinterpret_cast<T*>(smraw + off);
-  off += cq_al16((size_t)(np > 0 ? np : 1) * sizeof(T));
-  int* tcol = reinterpret_cast<int*>(smraw + off);  // tcol[jl]: neighbour e, tcol[cpm + jl]: column in p's row
-  const int cpm = d.m_max > 0 ? (d.m_max + (int)cluster.num_blocks() - 1) / (int)cluster.num_blocks() : 1;
-  off += cq_al16((size_t)2 * cpm * sizeof(int));
+  off += cq_al16((size_t)npp * sizeof(T));
+  T* beta_s = reinterpret_cast<T*>(smraw + off);
+  off += cq_al16((size_t)npp * sizeof(T));
+  T* scal_s = reinterpret_cast<T*>(smraw + off);
+  off += cq_al16((size_t)npp * sizeof(T));
+  int* piv_s = reinterpret_cast<int*>(smraw + off);
+  off += cq_al16((size_t)npp * sizeof(int));
+  int* tcol = reinterpret_cast<int*>(smraw + off);  // [0, cpm): neighbour; [cpm, 2cpm): column in p's row;
+  off += cq_al16((size_t)3 * cpm * sizeof(int));    // [2cpm, 3cpm): step at which the column was the pivot (-1)
   T* schunk = reinterpret_cast<T*>(smraw + off);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = NT / 32;
 
   // neighbour descriptors and their current sizes (cur_size of neighbours of
   // earlier colours already holds their ranks), loaded in parallel
-  for (int e = tid; e < nnb; e += CQ_NT) {
+  for (int e = tid; e < nnb; e += NT) {
     nbr[e] = nbrs[d.nbeg + e];
     cstart[e + 1] = cur_size[nbr[e].q];
   }
@@ -245,7 +289,7 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
   const int m = cstart[nnb];
   if (m == 0) {  // every neighbour reduced to nothing: p is kept as it is
     if (rank == 0) {
-      for (int64_t x = tid; x < (int64_t)np * np; x += CQ_NT) {
+      for (int64_t x = tid; x < (int64_t)np * np; x += NT) {
         const int i = (int)(x % np), j = (int)(x / np);
         d.Qc[i + (size_t)j * np] = (i == j) ? T(1) : T(0);
       }
@@ -257,30 +301,27 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
   const int j0 = min(m, rank * cols_per);
   const int nc = min(m, j0 + cols_per) - j0;
   T* __restrict__ chunk = RES ? schunk : d.gwork + (size_t)rank * L * cols_per;
+  int* rstep = tcol + 2 * cpm;
 
-  // neighbour of a global column: largest e with cstart[e] <= j
-  auto owner_nbr = [&](int j) {
+  // per local column: its neighbour (binary search over the column starts) and
+  // its column in p's block row
+  for (int jl = tid; jl < nc; jl += NT) {
+    const int j = j0 + jl;
     int lo = 0, hi = nnb - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
       if (cstart[mid] <= j) lo = mid; else hi = mid - 1;
     }
-    return lo;
-  };
-
-  // per local column: its neighbour and its column in p's block row
-  for (int jl = tid; jl < nc; jl += CQ_NT) {
-    const int j = j0 + jl;
-    const int e = owner_nbr(j);
-    tcol[jl] = e;
-    tcol[cpm + jl] = nbr[e].off_pq + (j - cstart[e]);
+    tcol[jl] = lo;
+    tcol[cpm + jl] = nbr[lo].off_pq + (j - cstart[lo]);
+    rstep[jl] = -1;
   }
   __syncthreads();
   // ---- gather my columns of A_pn, zero the padding rows of the last vector:
   // each warp moves 8 columns at a time (lanes over rows, coalesced), with all
   // 8 loads issued before the stores
   constexpr int GU = 8;
-  for (int jb = warp * GU; jb < nc; jb += CQ_NW * GU) {
+  for (int jb = warp * GU; jb < nc; jb += NW * GU) {
     const T* src[GU];
 #pragma unroll
     for (int u = 0; u < GU; ++u) src[u] = d.Rp + (size_t)tcol[cpm + min(jb + u, nc - 1)] * d.ldp;
@@ -294,11 +335,11 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
     }
   }
   __syncthreads();
-  // thread t owns local columns t, t + CQ_NT, ...; squared norms (-1: retired or absent)
+  // squared norms of my columns (-1: retired or absent)
   T nrm[CQ_CPT];
 #pragma unroll
   for (int c = 0; c < CQ_CPT; ++c) {
-    const int jl = tid + c * CQ_NT;
+    const int jl = tid + c * NT;
     nrm[c] = T(-1);
     if (jl < nc) {
       const V* cv = reinterpret_cast<const V*>(chunk + (size_t)jl * L);
@@ -315,15 +356,6 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
   const int kmax = min(np, m);
   int r = kmax;
   T r00 = T(0);
-  int pj = -1, pk = 0;  // previous pivot column and its step (retired one step later)
-  T pbeta = T(0);
-  auto retire = [&]() {  // R_{pk,pj} = beta, zeros below, in the owner CTA
-    if (pj >= j0 && pj < j0 + nc) {
-      T* col = chunk + (size_t)(pj - j0) * L;
-      for (int i = pk + tid; i < ng * VW; i += CQ_NT) col[i] = (i == pk) ? pbeta : T(0);
-    }
-    pj = -1;
-  };
   for (int k = 0; k < kmax; ++k) {
     // 1. warp candidates -> every CTA
     T bv = T(-1);
@@ -332,29 +364,30 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
     for (int c = 0; c < CQ_CPT; ++c)
       if (nrm[c] > bv) {
         bv = nrm[c];
-        bj = j0 + tid + c * CQ_NT;
+        bj = j0 + tid + c * NT;
       }
     cq_warp_argmax(bv, bj);
-    if (lane < C) {  // lane q pushes this warp's candidate into CTA q
-      CqShared<T>* o = C == 1 ? &sh : cluster.map_shared_rank(&sh, lane);
-      o->cand_v[k & 1][rank * CQ_NW + warp] = bv;
-      o->cand_j[k & 1][rank * CQ_NW + warp] = bj;
+    if (lane == 0) {
+      sh.cand_v[k & 1][warp] = bv;
+      sh.cand_j[k & 1][warp] = bj;
     }
-    cq_sync(cluster, C);
+    __syncthreads();
     // 2. pivot and |R_kk| (identical in every thread of the cluster)
-    T gv = T(-1);
-    int gj = INT_MAX;
-    for (int q = lane; q < C * CQ_NW; q += 32) {
-      const T v = sh.cand_v[k & 1][q];
-      const int j = sh.cand_j[k & 1][q];
-      if (v > gv || (v == gv && j < gj)) {
-        gv = v;
-        gj = j;
-      }
-    }
+    T gv = lane < NW ? sh.cand_v[k & 1][lane] : T(-1);
+    int gj = lane < NW ? sh.cand_j[k & 1][lane] : INT_MAX;
     cq_warp_argmax(gv, gj);
+    if (C > 1) {  // one candidate per CTA crosses the cluster
+      if (warp == 0 && lane < C) {
+        CqShared<T>* o = cluster.map_shared_rank(&sh, lane);
+        o->cta_v[k & 1][rank] = gv;
+        o->cta_j[k & 1][rank] = gj;
+      }
+      cluster.sync();
+      gv = lane < C ? sh.cta_v[k & 1][lane] : T(-1);
+      gj = lane < C ? sh.cta_j[k & 1][lane] : INT_MAX;
+      cq_warp_argmax(gv, gj);
+    }
     if (gj == INT_MAX) gj = 0;  // unreachable: k < kmax <= m leaves a live column
-    retire();                   // every CTA finished reading the previous pivot before this barrier
     const T rkk = sqrt(gv > T(0) ? gv : T(0));
     if (k == 0) r00 = rkk;
     if (r00 == T(0) || rkk < eps * r00) {
@@ -363,21 +396,21 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
     }
 #pragma unroll
     for (int c = 0; c < CQ_CPT; ++c)
-      if (j0 + tid + c * CQ_NT == gj) nrm[c] = T(-1);  // the pivot column leaves the live set
-    // 3. the raw pivot column and the reflector
-    const int owner = min(C - 1, gj / cols_per);
-    const int i0 = (k / VW) * VW;
+      if (j0 + tid + c * NT == gj) nrm[c] = T(-1);  // the pivot column leaves the live set
+    // 3. the raw pivot column (never written again) and the reflector
     const T* pcol;
     if (C == 1) {
       pcol = chunk + (size_t)(gj - j0) * L;
     } else {
+      const int owner = min(C - 1, gj / cols_per);
+      const int i0 = (k / VW) * VW;
       const size_t po = (size_t)(gj - owner * cols_per) * L;
       if (RES) {
         const T* src = cluster.map_shared_rank(schunk, owner) + po;
-        for (int i = i0 + tid; i < ng * VW; i += CQ_NT) pbuf[i] = src[i];
+        for (int i = i0 + tid; i < ng * VW; i += NT) pbuf[i] = src[i];
       } else {  // the owner's chunk in global memory, written by another CTA: read through L2
         const T* src = d.gwork + (size_t)owner * L * cols_per + po;
-        for (int i = i0 + tid; i < ng * VW; i += CQ_NT) pbuf[i] = __ldcg(src + i);
+        for (int i = i0 + tid; i < ng * VW; i += NT) pbuf[i] = __ldcg(src + i);
       }
       __syncthreads();
       pcol = pbuf;
@@ -393,12 +426,13 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
       tau = (beta - alpha) / beta;
       scal = T(1) / (alpha - beta);
     }
-    if (tid == 0) tau_s[k] = tau;
-    if (rank == owner)  // v_k for the formation of Q_pc
-      for (int i = k + tid; i < np; i += CQ_NT) d.V[i + (size_t)k * np] = (i == k) ? T(1) : pcol[i] * scal;
-    pj = gj;
-    pk = k;
-    pbeta = beta;
+    if (tid == 0) {
+      tau_s[k] = tau;
+      beta_s[k] = beta;
+      scal_s[k] = scal;
+      piv_s[k] = gj;
+    }
+    if (gj >= j0 && gj < j0 + nc && tid == 0) rstep[gj - j0] = k;
     // 4. apply H_k = I - tau v v^T to my live columns, recompute their trailing norms:
     //    w = tau (x_k + scal p_{k+1:}^T x_{k+1:}),  x_k -= w,  x_{k+1:} -= (w scal) p_{k+1:}
     const int gs = k / VW;
@@ -407,9 +441,10 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
 #pragma unroll
     for (int c = 0; c < CQ_CPT; ++c) {
       if (nrm[c] < T(0)) continue;
-      T* colp = chunk + (size_t)(tid + c * CQ_NT) * L;
+      T* colp = chunk + (size_t)(tid + c * NT) * L;
       V* __restrict__ cv = reinterpret_cast<V*>(colp);
-      T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+      const T xk = colp[k];
+      T a0 = 0, a1 = 0, a2 = 0, a3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
       {  // first vector: only rows > k
         const V x = cv[gs], p = pv[gs];
         if (rb > k) a0 = x.x * p.x;
@@ -419,17 +454,31 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
           if (rb + 3 > k) a3 = x.w * p.w;
         }
       }
-#pragma unroll 2
-      for (int g = gs + 1; g < ng; ++g) {
-        const V x = cv[g], p = pv[g];
-        a0 = fma(x.x, p.x, a0);
-        a1 = fma(x.y, p.y, a1);
+      int g = gs + 1;
+      for (; g + 1 < ng; g += 2) {  // two vectors per trip, independent accumulators
+        const V x0 = cv[g], p0 = pv[g], x1 = cv[g + 1], p1 = pv[g + 1];
+        a0 = fma(x0.x, p0.x, a0);
+        a1 = fma(x0.y, p0.y, a1);
+        b0 = fma(x1.x, p1.x, b0);
+        b1 = fma(x1.y, p1.y, b1);
         if constexpr (VW == 4) {
-          a2 = fma(x.z, p.z, a2);
-          a3 = fma(x.w, p.w, a3);
+          a2 = fma(x0.z, p0.z, a2);
+          a3 = fma(x0.w, p0.w, a3);
+          b2 = fma(x1.z, p1.z, b2);
+          b3 = fma(x1.w, p1.w, b3);
         }
       }
-      const T w = tau * fma(scal, (a0 + a1) + (a2 + a3), colp[k]);
+      if (g < ng) {
+        const V x0 = cv[g], p0 = pv[g];
+        a0 = fma(x0.x, p0.x, a0);
+        a1 = fma(x0.y, p0.y, a1);
+        if constexpr (VW == 4) {
+          a2 = fma(x0.z, p0.z, a2);
+          a3 = fma(x0.w, p0.w, a3);
+        }
+      }
+      const T dot = ((a0 + b0) + (a1 + b1)) + ((a2 + b2) + (a3 + b3));
+      const T w = tau * fma(scal, dot, xk);
       const T ws = w * scal;
       T q0 = 0, q1 = 0, q2 = 0, q3 = 0;
       {  // first vector: row k takes -w, rows > k take -ws p and enter the norm
@@ -448,7 +497,7 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
         cv[gs] = x;
       }
 #pragma unroll 2
-      for (int g = gs + 1; g < ng; ++g) {
+      for (g = gs + 1; g < ng; ++g) {
         V x = cv[g];
         const V p = pv[g];
         x.x = fma(-ws, p.x, x.x);
@@ -466,61 +515,82 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
       nrm[c] = (q0 + q1) + (q2 + q3);
     }
   }
-  __syncthreads();  // every thread is done with the last pivot column
-  retire();         // the last pivot when the loop ran to kmax
   __syncthreads();
-  // Rows 0..r-1 of every column now hold W_cn in the original column order
-  // (the pivot found at step r, if any, was not touched).
+  // Rows 0..r-1 of every column hold W_cn in the original column order, except
+  // that a column retired at step s < r holds R_ss = beta_s at row s and zeros
+  // below it (its stored entries below s are the raw reflector source).
+  auto wval = [&](int jl, int i) -> T {
+    const int s = rstep[jl];
+    if (s < 0 || i < s) return chunk[(size_t)jl * L + i];
+    return i == s ? beta_s[s] : T(0);
+  };
   // ---- write back W_cn into p's row (one warp per column, coalesced) ...
-  for (int jl = warp; jl < nc; jl += CQ_NW) {
+  for (int jl = warp; jl < nc; jl += NW) {
     T* dst = d.Rp + (size_t)tcol[cpm + jl] * d.ldp;
-    const T* src = chunk + (size_t)jl * L;
-    for (int i = lane; i < r; i += 32) dst[i] = src[i];
+    for (int i = lane; i < r; i += 32) dst[i] = wval(jl, i);
   }
   // ... and its transpose into the neighbours' rows (one thread per column)
-  for (int jl = tid; jl < nc; jl += CQ_NT) {
+  for (int jl = tid; jl < nc; jl += NT) {
     const int e = tcol[jl];
     const CpqrNbr<T> nb = nbr[e];
     const int cc = j0 + jl - cstart[e];
-    const T* src = chunk + (size_t)jl * L;
-    for (int i = 0; i < r; ++i) nb.Rq[cc + (size_t)(nb.off_qp + i) * nb.ldq] = src[i];
+    for (int i = 0; i < r; ++i) nb.Rq[cc + (size_t)(nb.off_qp + i) * nb.ldq] = wval(jl, i);
   }
   // A_cc = I: column j by warp j of the cluster, lanes over rows
-  for (int j = rank * CQ_NW + warp; j < r; j += C * CQ_NW) {
+  for (int j = rank * NW + warp; j < r; j += C * NW) {
     T* dst = d.Rp + (size_t)j * d.ldp;
     for (int i = lane; i < r; i += 32) dst[i] = (i == j) ? T(1) : T(0);
   }
-  if (C > 1) cluster.sync();  // every V column is visible cluster-wide
-  else __syncthreads();
-  // ---- Q_pc e_c = H_0 ... H_c e_c (H_k e_c = e_c for k > c), one warp per
-  // column, the column held in registers (lane l owns rows l, l+32, ...).  The
-  // reflectors are read from a shared-memory copy of V when it fits in the
-  // chunk's space (free again after the write-back).
-  const T* Vsrc = d.V;
-  if (RES && (size_t)np * r <= (size_t)L * cols_per) {
-    // V was written by other CTAs: read through L2; 8 columns per warp in flight
-    T* Vs = schunk;
-    for (int kb = warp * 8; kb < r; kb += CQ_NW * 8)
-      for (int i = lane; i < np; i += 32) {
-        T v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = (kb + u < r && i >= kb + u) ? __ldcg(d.V + i + (size_t)(kb + u) * np) : T(0);
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (kb + u < r) Vs[i + (size_t)(kb + u) * np] = v[u];
-      }
+  // ---- Q_pc = H_0 ... H_{r-1} [I_r; 0]
+  if (C == 1) {
     __syncthreads();
-    Vsrc = Vs;
+    if (np <= 32 * 16) cq_form_q_any<T, true>(d, nullptr, chunk, L, j0, piv_s, scal_s, tau_s, r, np, 0, 1);
+  } else {
+    // the reflectors live in the owners' chunks: every CTA writes its own
+    // retired columns to V (column k = v_k, rows >= k), then each copies V
+    // into its chunk space when it fits
+    for (int k = warp; k < r; k += NW) {
+      const int jl = piv_s[k] - j0;
+      if (jl < 0 || jl >= nc) continue;
+      const T* pc = chunk + (size_t)jl * L;
+      const T sc = scal_s[k];
+      for (int i = k + lane; i < np; i += 32) d.V[i + (size_t)k * np] = i == k ? T(1) : pc[i] * sc;
+    }
+    cluster.sync();  // every V column is written; no CTA reads another's chunk any more
+    const T* Vsrc = d.V;
+    if (RES && (size_t)np * r <= (size_t)L * cols_per) {
+      T* Vs = schunk;
+      for (int kb = warp * 8; kb < r; kb += NW * 8)
+        for (int i = lane; i < np; i += 32) {
+          T v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[u] = (kb + u < r && i >= kb + u) ? __ldcg(d.V + i + (size_t)(kb + u) * np) : T(0);
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (kb + u < r) Vs[i + (size_t)(kb + u) * np] = v[u];
+        }
+      __syncthreads();
+      Vsrc = Vs;
+    }
+    if (np <= 32 * 16) cq_form_q_any<T, false>(d, Vsrc, nullptr, L, j0, piv_s, scal_s, tau_s, r, np, rank, C);
   }
-  if (np > 32 * 16) {  // tall interfaces: the column lives in global memory
-    for (int c = rank * CQ_NW + warp; c < r; c += C * CQ_NW) {
+  if (np > 32 * 16) {  // tall interfaces: V in global memory, the column of Q in global memory
+    if (C == 1) {
+      for (int k = warp; k < r; k += NW) {
+        const T* pc = chunk + (size_t)(piv_s[k] - j0) * L;
+        const T sc = scal_s[k];
+        for (int i = k + lane; i < np; i += 32) d.V[i + (size_t)k * np] = i == k ? T(1) : pc[i] * sc;
+      }
+      __syncthreads();
+    }
+    for (int c = rank * NW + warp; c < r; c += C * NW) {
       T* col = d.Qc + (size_t)c * np;
       for (int i = lane; i < np; i += 32) col[i] = (i == c) ? T(1) : T(0);
       __syncwarp();
       for (int k = c; k >= 0; --k) {
         const T tk = tau_s[k];
         if (tk == T(0)) continue;
-        const T* v = Vsrc + (size_t)k * np;
+        const T* v = d.V + (size_t)k * np;
         T w = 0;
         for (int i = k + lane; i < np; i += 32) w += __ldcg(v + i) * col[i];
 #pragma unroll
@@ -530,16 +600,6 @@ __global__ void __launch_bounds__(CQ_NT) k_cpqr_cluster(const CpqrTask<T>* __res
         __syncwarp();
       }
     }
-  } else if (np > 32 * 8) {
-    cq_form_q<T, 16>(d, Vsrc, tau_s, r, np, rank, C);
-  } else if (np > 32 * 4) {
-    cq_form_q<T, 8>(d, Vsrc, tau_s, r, np, rank, C);
-  } else if (np > 32 * 2) {
-    cq_form_q<T, 4>(d, Vsrc, tau_s, r, np, rank, C);
-  } else if (np > 32) {
-    cq_form_q<T, 2>(d, Vsrc, tau_s, r, np, rank, C);
-  } else {
-    cq_form_q<T, 1>(d, Vsrc, tau_s, r, np, rank, C);
   }
   if (rank == 0 && tid == 0) cur_size[d.p] = r;
   if (C > 1) cluster.sync();  // no CTA leaves while others may still read its shared memory

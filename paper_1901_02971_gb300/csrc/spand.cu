@@ -212,14 +212,14 @@ static int cpqr_max_cluster() {
   int& c = cached[sizeof(T) == 8 ? 1 : 0];
   if (c) return c;
   if (kCpqrMaxCluster <= 8) return c = kCpqrMaxCluster;
-  const void* fn = (const void*)k_cpqr_cluster<T, true>;
+  const void* fn = (const void*)k_cpqr_cluster<T, true, 256>;
   const size_t smem = kCpqrChunkBudget + 16 * 1024;
   ensure_smem(fn, smem);
   c = 8;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(16, 1, 1);
-    cfg.blockDim = dim3(CQ_NT, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -605,6 +605,14 @@ struct StepTimer {
       if (e) cudaEventDestroy(e);
   }
 };
+
+// The sparsification kernel for a launch group: chunk in shared memory or
+// not, 256 or 512 threads per CTA.
+template <typename T>
+static const void* cpqr_kernel(bool res, int nt) {
+  if (res) return nt == 512 ? (const void*)k_cpqr_cluster<T, true, 512> : (const void*)k_cpqr_cluster<T, true, 256>;
+  return nt == 512 ? (const void*)k_cpqr_cluster<T, false, 512> : (const void*)k_cpqr_cluster<T, false, 256>;
+}
 
 // The apply program: the phases of every step in execution order (forward
 // sweep leaves -> root, then the backward sweep root -> leaves), uploaded once
@@ -1041,8 +1049,8 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         int C = max_cluster;
         for (int c = 1; c <= max_cluster; c *= 2)
           if (Lp * ((mm + c - 1) / c) * sizeof(T) <= CB) { C = c; break; }
-        while (C < max_cluster && (mm + C - 1) / C > 2 * CQ_NT) C *= 2;
-        if ((mm + C - 1) / C > CQ_CPT * CQ_NT)
+        while (C < max_cluster && (mm + C - 1) / C > 2 * CQ_MAXNT) C *= 2;
+        if ((mm + C - 1) / C > CQ_CPT * CQ_MAXNT)
           throw Fail{SPAND_ERR_INVALID_ARG, "interface coupling too wide for the sparsification kernel (" +
                                                 std::to_string(mm) + " columns)"};
         const bool resident = Lp * ((mm + C - 1) / C) * sizeof(T) <= CB;
@@ -1069,7 +1077,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
           cp_qc.push_back(tasks[i].Qc);
         }
         // launch groups: (colour, cluster size)
-        struct Group { int colour, C, res; std::vector<int32_t> ids; size_t smem = 0; };
+        struct Group { int colour, C, res; std::vector<int32_t> ids; size_t smem = 0; int maxm = 0; };
         std::vector<Group> groups;
         for (int c = 0; c < std::max(ncol, 1); ++c)
           for (int res = 1; res >= 0; --res)
@@ -1085,6 +1093,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
                   size_t need = cq_fixed_smem<T>(tasks[i].nend - tasks[i].nbeg, np_, (mm + C - 1) / C);
                   if (res) need += (size_t)cq_ld<T>(np_) * ((mm + C - 1) / C) * sizeof(T);
                   g.smem = std::max(g.smem, need);
+                  g.maxm = std::max(g.maxm, mm);
                 }
               if (!g.ids.empty()) groups.push_back(std::move(g));
             }
@@ -1109,12 +1118,17 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
             CK(cudaStreamWaitEvent(as, h->ev_fork, 0));
             const Group& G = groups[g];
             const size_t smem = G.smem;
-            const void* fn = G.res ? (const void*)k_cpqr_cluster<T, true> : (const void*)k_cpqr_cluster<T, false>;
+            // 512 threads for one- and two-CTA interfaces (latency hiding);
+            // 256 for larger clusters (cheaper block barriers), unless the
+            // columns per CTA need 512
+            const int cpg = (G.maxm + G.C - 1) / G.C;
+            const int nt = (G.C <= 2 || cpg > CQ_CPT * 256) ? 512 : 256;
+            const void* fn = cpqr_kernel<T>(G.res != 0, nt);
             ensure_smem(fn, smem);
             if (G.C > 8) ensure_nonportable_cluster(fn);
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3((unsigned)(G.ids.size() * G.C), 1, 1);
-            cfg.blockDim = dim3(CQ_NT, 1, 1);
+            cfg.blockDim = dim3((unsigned)nt, 1, 1);
             cfg.dynamicSmemBytes = smem;
             cfg.stream = as;
             cudaLaunchAttribute attr[1];
