@@ -19,9 +19,9 @@
 // entries below the diagonal keep the raw values p from which the Householder
 // vector is derived (v = [1; p / (p_k - beta)]), so the reflectors need no
 // storage of their own; the write-back emits R_kk = beta and zeros below for
-// retired columns.  Per reflector step the CTAs exchange warp pivot
-// candidates through distributed shared memory and pull the pivot column from
-// its owner: one cluster barrier per step (one block barrier when C == 1), no
+// retired columns.  Per reflector step the CTAs of a cluster exchange their
+// pivot candidates, each with its column, through distributed shared memory:
+// one block barrier per step plus one cluster barrier when C > 1, no
 // spin-waits.
 #pragma once
 
@@ -94,15 +94,17 @@ __host__ __device__ inline size_t cq_al16(size_t b) { return (b + 15) & ~size_t(
 
 // Fixed shared memory before the chunk, each part 16-byte aligned: CqShared,
 // the neighbour descriptors (nnb), their column starts (nnb + 1 ints), the
-// pivot column copy (L elements), per reflector its pivot column, beta, tau
-// and scale (np each), and per local column its neighbour, its column in p's
-// block row and the step at which it became the pivot (3 cols_per ints).
+// candidate columns pushed by the cluster's CTAs (2 x C x L elements, none
+// when C == 1), per reflector its pivot column, beta, tau and scale (np
+// each), and per local column its neighbour, its column in p's block row and
+// the step at which it became the pivot (3 cols_per ints).
 template <typename T>
-__host__ __device__ inline size_t cq_fixed_smem(int nnb, int np, int cols_per) {
+__host__ __device__ inline size_t cq_fixed_smem(int nnb, int np, int cols_per, int C) {
   const size_t npp = (size_t)(np > 0 ? np : 1), cp = (size_t)(cols_per > 0 ? cols_per : 1);
+  const size_t cand = C > 1 ? (size_t)2 * C * cq_ld<T>(np) : 0;
   return cq_al16(sizeof(CqShared<T>)) + cq_al16((size_t)nnb * sizeof(CpqrNbr<T>)) +
-         cq_al16((size_t)(nnb + 1) * sizeof(int)) + cq_al16((size_t)cq_ld<T>(np) * sizeof(T)) +
-         3 * cq_al16(npp * sizeof(T)) + cq_al16(npp * sizeof(int)) + cq_al16(3 * cp * sizeof(int));
+         cq_al16((size_t)(nnb + 1) * sizeof(int)) + cq_al16(cand * sizeof(T)) + 3 * cq_al16(npp * sizeof(T)) +
+         cq_al16(npp * sizeof(int)) + cq_al16(3 * cp * sizeof(int));
 }
 
 // Warp-wide (largest value, lowest index on ties); every lane gets the result.
@@ -221,14 +223,16 @@ __device__ __forceinline__ void cq_form_q_any(const CpqrTask<T>& d, const T* V, 
 
 // Per reflector step k:
 //   1. every warp reduces its threads' best live columns (largest squared
-//      trailing norm, lowest index on ties) and pushes the result into slot
-//      (rank, warp) of set k mod 2 of every CTA; barrier;
-//   2. every thread reduces the C * 8 candidates: pivot j*, |R_kk| = sqrt(norm)
+//      trailing norm, lowest index on ties) into its slot of set k mod 2;
+//      block barrier; every warp reduces the slots to the CTA's candidate;
+//      with C > 1 each CTA pushes its candidate and that column's rows >= k
+//      into every CTA of the cluster; cluster barrier;
+//   2. every thread reduces the C candidates: pivot j*, |R_kk| = sqrt(norm)
 //      (norms are recomputed exactly each step); the truncation rule is
 //      checked here, uniformly;
 //   3. every thread derives the reflector from the raw pivot column p (read in
-//      place when C == 1, else copied from the owner's shared memory into a
-//      local buffer + block barrier): beta = -sign(p_k) |R_kk|,
+//      place when C == 1, else from the copy its owner pushed):
+//      beta = -sign(p_k) |R_kk|,
 //      tau = (beta - p_k) / beta, v = [1; p_{k+1:} / (p_k - beta)];
 //   4. every thread applies H_k to its live columns and recomputes their
 //      trailing norms.
@@ -258,8 +262,8 @@ __global__ void __launch_bounds__(NT) k_cpqr_cluster(const CpqrTask<T>* __restri
   off += cq_al16((size_t)nnb * sizeof(CpqrNbr<T>));
   int* cstart = reinterpret_cast<int*>(smraw + off);
   off += cq_al16((size_t)(nnb + 1) * sizeof(int));
-  T* pbuf = reinterpret_cast<T*>(smraw + off);
-  off += cq_al16((size_t)L * sizeof(T));
+  T* cbuf = reinterpret_cast<T*>(smraw + off);  // [parity][source CTA][L]: candidate columns
+  off += cq_al16((C > 1 ? (size_t)2 * C * L : 0) * sizeof(T));
   T* tau_s = reinterpret_cast<T*>(smraw + off);
   off += cq_al16((size_t)npp * sizeof(T));
   T* beta_s = reinterpret_cast<T*>(smraw + off);
@@ -376,7 +380,17 @@ __global__ void __launch_bounds__(NT) k_cpqr_cluster(const CpqrTask<T>* __restri
     T gv = lane < NW ? sh.cand_v[k & 1][lane] : T(-1);
     int gj = lane < NW ? sh.cand_j[k & 1][lane] : INT_MAX;
     cq_warp_argmax(gv, gj);
-    if (C > 1) {  // one candidate per CTA crosses the cluster
+    const int i0 = (k / VW) * VW;
+    if (C > 1) {
+      // one candidate per CTA crosses the cluster, with its column (rows
+      // >= i0), so that the winner's column is local after the barrier
+      if (gj != INT_MAX) {
+        const T* src = chunk + (size_t)(gj - j0) * L;
+        for (int i = i0 + tid; i < ng * VW; i += NT) {
+          const T v = src[i];
+          for (int q = 0; q < C; ++q) cluster.map_shared_rank(cbuf, q)[((size_t)(k & 1) * C + rank) * L + i] = v;
+        }
+      }
       if (warp == 0 && lane < C) {
         CqShared<T>* o = cluster.map_shared_rank(&sh, lane);
         o->cta_v[k & 1][rank] = gv;
@@ -398,23 +412,8 @@ __global__ void __launch_bounds__(NT) k_cpqr_cluster(const CpqrTask<T>* __restri
     for (int c = 0; c < CQ_CPT; ++c)
       if (j0 + tid + c * NT == gj) nrm[c] = T(-1);  // the pivot column leaves the live set
     // 3. the raw pivot column (never written again) and the reflector
-    const T* pcol;
-    if (C == 1) {
-      pcol = chunk + (size_t)(gj - j0) * L;
-    } else {
-      const int owner = min(C - 1, gj / cols_per);
-      const int i0 = (k / VW) * VW;
-      const size_t po = (size_t)(gj - owner * cols_per) * L;
-      if (RES) {
-        const T* src = cluster.map_shared_rank(schunk, owner) + po;
-        for (int i = i0 + tid; i < ng * VW; i += NT) pbuf[i] = src[i];
-      } else {  // the owner's chunk in global memory, written by another CTA: read through L2
-        const T* src = d.gwork + (size_t)owner * L * cols_per + po;
-        for (int i = i0 + tid; i < ng * VW; i += NT) pbuf[i] = __ldcg(src + i);
-      }
-      __syncthreads();
-      pcol = pbuf;
-    }
+    const T* pcol = C == 1 ? chunk + (size_t)(gj - j0) * L
+                           : cbuf + ((size_t)(k & 1) * C + min(C - 1, gj / cols_per)) * L;
     const T alpha = pcol[k];
     T beta, tau, scal;
     if (rkk == T(0)) {

@@ -41,7 +41,7 @@ struct Fail {
 
 static inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-constexpr size_t kCpqrChunkBudget = 192 * 1024;  // shared-memory chunk per CTA
+constexpr size_t kCpqrChunkBudget = 224 * 1024;  // shared memory per sparsification CTA (chunk included)
 constexpr int kCpqrMaxCluster = 8;              // thread-block cluster size (broadcasts to 16 CTAs cost 3.5x more)
 constexpr int kAuxStreams = 4;
 constexpr int kApplyCtasPerSm = 4;  // CTAs per SM of the cooperative apply
@@ -186,6 +186,16 @@ struct ApplyStep {
   const ApplyItem *sy = nullptr, *sc = nullptr, *sz = nullptr, *sx = nullptr;
 };
 
+// Streaming multiprocessors of the current device (cached per device).
+static int num_sms() {
+  static int cached[64] = {};
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return 1;
+  if (!cached[dev]) CK(cudaDeviceGetAttribute(&cached[dev], cudaDevAttrMultiProcessorCount, dev));
+  return cached[dev];
+}
+
 // Clusters of more than 8 CTAs need an explicit opt-in per kernel.
 static void ensure_nonportable_cluster(const void* fn) {
   static std::unordered_map<const void*, bool> done;
@@ -213,7 +223,7 @@ static int cpqr_max_cluster() {
   if (c) return c;
   if (kCpqrMaxCluster <= 8) return c = kCpqrMaxCluster;
   const void* fn = (const void*)k_cpqr_cluster<T, true, 256>;
-  const size_t smem = kCpqrChunkBudget + 16 * 1024;
+  const size_t smem = kCpqrChunkBudget;
   ensure_smem(fn, smem);
   c = 8;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
@@ -1046,14 +1056,20 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         // smallest cluster whose per-CTA chunk fits in shared memory, and at
         // most ~2 columns per thread
         const size_t Lp = (size_t)cq_ld<T>(sz[p]);
+        const int nnb_p = tk.nend - tk.nbeg;
+        // shared memory of a CTA with its chunk resident, for cluster size c
+        auto res_smem = [&](int c) {
+          const int cp = (mm + c - 1) / c;
+          return cq_fixed_smem<T>(nnb_p, sz[p], cp, c) + Lp * cp * sizeof(T);
+        };
         int C = max_cluster;
         for (int c = 1; c <= max_cluster; c *= 2)
-          if (Lp * ((mm + c - 1) / c) * sizeof(T) <= CB) { C = c; break; }
+          if (res_smem(c) <= CB) { C = c; break; }
         while (C < max_cluster && (mm + C - 1) / C > 2 * CQ_MAXNT) C *= 2;
         if ((mm + C - 1) / C > CQ_CPT * CQ_MAXNT)
           throw Fail{SPAND_ERR_INVALID_ARG, "interface coupling too wide for the sparsification kernel (" +
                                                 std::to_string(mm) + " columns)"};
-        const bool resident = Lp * ((mm + C - 1) / C) * sizeof(T) <= CB;
+        const bool resident = res_smem(C) <= CB;
         WOff w;
         w.nrm = 0;
         w.v = wbytes; wbytes += align256((size_t)sz[p] * sz[p] * sizeof(T));
@@ -1090,7 +1106,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
                 if (st.colour[tasks[i].p] == c && tclass[i] == C && tres[i] == res) {
                   g.ids.push_back((int32_t)i);
                   const int np_ = tasks[i].np, mm = tasks[i].m_max;
-                  size_t need = cq_fixed_smem<T>(tasks[i].nend - tasks[i].nbeg, np_, (mm + C - 1) / C);
+                  size_t need = cq_fixed_smem<T>(tasks[i].nend - tasks[i].nbeg, np_, (mm + C - 1) / C, C);
                   if (res) need += (size_t)cq_ld<T>(np_) * ((mm + C - 1) / C) * sizeof(T);
                   g.smem = std::max(g.smem, need);
                   g.maxm = std::max(g.maxm, mm);
@@ -1118,11 +1134,13 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
             CK(cudaStreamWaitEvent(as, h->ev_fork, 0));
             const Group& G = groups[g];
             const size_t smem = G.smem;
-            // 512 threads for one- and two-CTA interfaces (latency hiding);
-            // 256 for larger clusters (cheaper block barriers), unless the
-            // columns per CTA need 512
+            // 512 threads for one- and two-CTA interfaces (latency hiding)
+            // when the launch fits in one wave; 256 for larger clusters
+            // (cheaper block barriers) and for launches of more CTAs than
+            // SMs (several CTAs per SM), unless the columns per CTA need 512
             const int cpg = (G.maxm + G.C - 1) / G.C;
-            const int nt = (G.C <= 2 || cpg > CQ_CPT * 256) ? 512 : 256;
+            const bool one_wave = G.ids.size() * (size_t)G.C <= (size_t)num_sms();
+            const int nt = ((G.C <= 2 && one_wave) || cpg > CQ_CPT * 256) ? 512 : 256;
             const void* fn = cpqr_kernel<T>(G.res != 0, nt);
             ensure_smem(fn, smem);
             if (G.C > 8) ensure_nonportable_cluster(fn);
