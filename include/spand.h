@@ -47,7 +47,9 @@ enum {
   SPAND_ERR_NO_CONVERGENCE = 3,/* PCG reached maxit above tol */
   SPAND_ERR_CUDA = 4,          /* a CUDA runtime call failed */
   SPAND_ERR_OOM = 5,           /* device or host allocation failed */
-  SPAND_ERR_STATE = 6          /* call out of order (e.g. solve before factorize) */
+  SPAND_ERR_STATE = 6,         /* call out of order (e.g. solve before factorize) */
+  SPAND_ERR_TIMEOUT = 7        /* a bounded device-side wait gave up (the context
+                                  stays usable; the call's result is invalid) */
 };
 
 /* precision of the factorization (the PCG recurrences, its dot products
@@ -88,6 +90,30 @@ void spand_default_opts(spand_opts* opts);
  */
 int spand_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
                   const double* coords, int32_t dim, const spand_opts* opts, spand_handle* out);
+
+/* One problem of a batch (the arguments of spand_analyze). */
+typedef struct {
+  int64_t n;
+  const int64_t* rowptr;
+  const int32_t* colind;
+  const double* vals;
+  const double* coords;  /* NULL, or n*dim float64 row-major */
+  int32_t dim;
+} spand_problem;
+
+/*
+ * spand_analyze_batch -- spand_analyze of k independent problems (a batch of
+ * systems that share nothing, e.g. many small diffusion problems solved
+ * together), run on parallel host threads.
+ *   k     : number of problems, >= 0.
+ *   probs : k problem descriptions (host arrays, copied).
+ *   opts  : k option sets, one per problem (levels usually differ with size).
+ *   out   : k handles; on success every entry is a new handle, on any error
+ *           every entry is NULL and no handle is left allocated.
+ * Errors: those of spand_analyze; the message names the first failing
+ * problem (lowest index).
+ */
+int spand_analyze_batch(int32_t k, const spand_problem* probs, const spand_opts* opts, spand_handle* out);
 
 /*
  * spand_factorize -- numeric factorization on the current CUDA device

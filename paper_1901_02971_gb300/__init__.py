@@ -11,8 +11,8 @@ from __future__ import annotations
 from ._lib import (SPAND_FP32, SPAND_FP64, SpandError, default_opts, lib, spand_analyze, spand_apply,
                    spand_destroy, spand_factorize, spand_get_phase_times, spand_get_ranks, spand_get_stats,
                    spand_get_step, spand_get_tree, spand_solve)
-from .solver import Solver
+from .solver import Solver, factorize_all, solve_all
 
-__all__ = ["Solver", "SpandError", "SPAND_FP32", "SPAND_FP64", "default_opts", "lib", "spand_analyze",
+__all__ = ["Solver", "factorize_all", "solve_all", "SpandError", "SPAND_FP32", "SPAND_FP64", "default_opts", "lib", "spand_analyze",
            "spand_apply", "spand_destroy", "spand_factorize", "spand_get_phase_times", "spand_get_ranks",
            "spand_get_stats", "spand_get_step", "spand_get_tree", "spand_solve"]

@@ -24,11 +24,12 @@ SPAND_ERR_NO_CONVERGENCE = 3
 SPAND_ERR_CUDA = 4
 SPAND_ERR_OOM = 5
 SPAND_ERR_STATE = 6
+SPAND_ERR_TIMEOUT = 7
 SPAND_FP64 = 0
 SPAND_FP32 = 1
 
 # every function declared in include/spand.h
-EXPORTS = ["spand_default_opts", "spand_analyze", "spand_factorize", "spand_solve", "spand_apply",
+EXPORTS = ["spand_default_opts", "spand_analyze", "spand_analyze_batch", "spand_factorize", "spand_solve", "spand_apply",
            "spand_apply_noalloc", "spand_sampled_outer",
            "spand_get_tree", "spand_get_step", "spand_get_ranks", "spand_get_stats",
            "spand_get_phase_times", "spand_set_profiling", "spand_get_kernel_profile",
@@ -40,6 +41,11 @@ KERNEL_FAMILIES = ["potrf", "trsm", "schur", "cpqr", "copy", "apply", "pcg"]
 class Opts(C.Structure):
     _fields_ = [("levels", C.c_int32), ("eps", C.c_double), ("skip", C.c_int32),
                 ("precision", C.c_int32), ("maxit", C.c_int32), ("tol", C.c_double)]
+
+
+class Problem(C.Structure):
+    _fields_ = [("n", C.c_int64), ("rowptr", C.c_void_p), ("colind", C.c_void_p), ("vals", C.c_void_p),
+                ("coords", C.c_void_p), ("dim", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -71,6 +77,7 @@ def lib():
     L.spand_default_opts.argtypes = [C.POINTER(Opts)]
     L.spand_default_opts.restype = None
     L.spand_analyze.argtypes = [C.c_int64, P, P, P, P, C.c_int32, C.POINTER(Opts), C.POINTER(C.c_void_p)]
+    L.spand_analyze_batch.argtypes = [C.c_int32, C.POINTER(Problem), C.POINTER(Opts), C.POINTER(C.c_void_p)]
     L.spand_factorize.argtypes = [C.c_void_p, P, P]
     L.spand_solve.argtypes = [C.c_void_p, P, P, i32p, C.POINTER(C.c_double), P]
     L.spand_apply.argtypes = [C.c_void_p, P, P, P]
@@ -130,6 +137,32 @@ def spand_analyze(rowptr, colind, vals, coords=None, opts: Optional[Opts] = None
     h = C.c_void_p()
     _check(lib().spand_analyze(n, _ptr(rowptr), _ptr(colind), _ptr(vals), cptr, dim, C.byref(opts), C.byref(h)))
     return h.value
+
+
+def spand_analyze_batch(problems, opts_list) -> list:
+    """problems: list of (rowptr, colind, vals, coords-or-None); opts_list: one
+    Opts per problem.  Returns the list of handles (ints), analyzed on parallel
+    host threads inside the library."""
+    k = len(problems)
+    if len(opts_list) != k:
+        raise ValueError("one Opts per problem")
+    keep = []
+    P = (Problem * max(k, 1))()
+    for i, (rowptr, colind, vals, coords) in enumerate(problems):
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        colind = np.ascontiguousarray(colind, dtype=np.int32)
+        vals = np.ascontiguousarray(vals, dtype=np.float64)
+        dim = 0
+        if coords is not None:
+            coords = np.ascontiguousarray(coords, dtype=np.float64)
+            dim = coords.shape[1] if coords.ndim == 2 else 1
+        keep += [rowptr, colind, vals, coords]
+        P[i] = Problem(rowptr.size - 1, rowptr.ctypes.data, colind.ctypes.data, vals.ctypes.data,
+                       coords.ctypes.data if coords is not None else None, dim)
+    O = (Opts * max(k, 1))(*opts_list)
+    H = (C.c_void_p * max(k, 1))()
+    _check(lib().spand_analyze_batch(k, P, O, H))
+    return [H[i] for i in range(k)]
 
 
 def spand_factorize(h: int, vals_ptr: Optional[int] = None, stream: int = 0):

@@ -12,6 +12,8 @@
 #include <numeric>
 #include <stdexcept>
 #include <string>
+#include <mutex>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -186,42 +188,64 @@ struct ApplyStep {
   const ApplyItem *sy = nullptr, *sc = nullptr, *sz = nullptr, *sx = nullptr;
 };
 
-// Streaming multiprocessors of the current device (cached per device).
-static int num_sms() {
-  static int cached[64] = {};
+// Process-wide caches of device attributes and of the kernel attributes set so
+// far, keyed by device: handles on different host threads (or devices) share
+// them, so every access holds g_attr_mutex.
+static std::mutex g_attr_mutex;
+
+static int current_device() {
   int dev = 0;
   CK(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) return 1;
-  if (!cached[dev]) CK(cudaDeviceGetAttribute(&cached[dev], cudaDevAttrMultiProcessorCount, dev));
-  return cached[dev];
+  return dev;
+}
+
+// Streaming multiprocessors of the current device.
+static int num_sms() {
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lk(g_attr_mutex);
+  static std::unordered_map<int, int> cached;
+  auto it = cached.find(dev);
+  if (it != cached.end()) return it->second;
+  int n = 0;
+  CK(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+  cached[dev] = n;
+  return n;
 }
 
 // Clusters of more than 8 CTAs need an explicit opt-in per kernel.
 static void ensure_nonportable_cluster(const void* fn) {
-  static std::unordered_map<const void*, bool> done;
-  if (done.count(fn)) return;
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lk(g_attr_mutex);
+  static std::unordered_map<const void*, std::vector<int>> done;
+  auto& devs = done[fn];
+  if (std::find(devs.begin(), devs.end(), dev) != devs.end()) return;
   CK(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-  done[fn] = true;
+  devs.push_back(dev);
 }
 
-// Highest dynamic shared memory requested so far, per kernel.
+// Highest dynamic shared memory requested so far, per kernel and device.
 static void ensure_smem(const void* fn, size_t bytes) {
-  static std::unordered_map<const void*, size_t> done;
   if (bytes <= 48 * 1024) return;
-  auto it = done.find(fn);
-  if (it != done.end() && it->second >= bytes) return;
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lk(g_attr_mutex);
+  static std::unordered_map<const void*, std::unordered_map<int, size_t>> done;
+  size_t& have = done[fn][dev];
+  if (have >= bytes) return;
   CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  done[fn] = bytes;
+  have = bytes;
 }
+
+static std::mutex g_cluster_mutex;  // guards the cached cluster-size probe
 
 // Largest cluster size (16 or 8) at which the sparsification kernel can be
 // resident with a full shared-memory chunk on this device.
 template <typename T>
 static int cpqr_max_cluster() {
+  if constexpr (kCpqrMaxCluster <= 8) return kCpqrMaxCluster;
+  std::lock_guard<std::mutex> lk(g_cluster_mutex);
   static int cached[2] = {0, 0};
   int& c = cached[sizeof(T) == 8 ? 1 : 0];
   if (c) return c;
-  if (kCpqrMaxCluster <= 8) return c = kCpqrMaxCluster;
   const void* fn = (const void*)k_cpqr_cluster<T, true, 256>;
   const size_t smem = kCpqrChunkBudget;
   ensure_smem(fn, smem);
@@ -1389,7 +1413,7 @@ static void check_apply(spand_handle h) {
   CK(cudaMemcpy(&flag, (unsigned*)h->d_bar.p + 1, sizeof(int), cudaMemcpyDeviceToHost));
   if (flag) {
     CK(cudaMemset((unsigned*)h->d_bar.p + 1, 0, sizeof(int)));
-    throw Fail{SPAND_ERR_CUDA, "preconditioner apply: a grid barrier timed out"};
+    throw Fail{SPAND_ERR_TIMEOUT, "preconditioner apply: a grid barrier timed out"};
   }
 }
 
@@ -1458,6 +1482,7 @@ const char* spand_error_string(int code) {
     case SPAND_ERR_CUDA: return "CUDA error";
     case SPAND_ERR_OOM: return "out of memory";
     case SPAND_ERR_STATE: return "call out of order";
+    case SPAND_ERR_TIMEOUT: return "a bounded device-side wait timed out";
     default: return "unknown error code";
   }
 }
@@ -1981,5 +2006,47 @@ int spand_get_phase_times(spand_handle h, double* out6) {
 }
 
 void spand_destroy(spand_handle h) { delete h; }
+
+int spand_analyze_batch(int32_t k, const spand_problem* probs, const spand_opts* opts, spand_handle* out) {
+  g_err.clear();
+  if (k < 0) { g_err = "k must be >= 0"; return SPAND_ERR_INVALID_ARG; }
+  if (k == 0) return SPAND_OK;
+  if (!probs || !opts || !out) { g_err = "null argument"; return SPAND_ERR_INVALID_ARG; }
+  for (int32_t i = 0; i < k; ++i) out[i] = nullptr;
+  std::vector<int> rc(k, SPAND_OK);
+  std::vector<std::string> msg(k);
+  const int nth = (int)std::max(1u, std::min<unsigned>((unsigned)k, std::thread::hardware_concurrency()));
+  auto work = [&](int w) {  // problems w, w + nth, ... (analysis is host-only and handle-local)
+    for (int32_t i = w; i < k; i += nth) {
+      const spand_problem& p = probs[i];
+      rc[i] = spand_analyze(p.n, p.rowptr, p.colind, p.vals, p.coords, p.dim, &opts[i], &out[i]);
+      if (rc[i] != SPAND_OK) msg[i] = spand_last_error();
+    }
+  };
+  try {
+    std::vector<std::thread> pool;
+    for (int w = 1; w < nth; ++w) pool.emplace_back(work, w);
+    work(0);
+    for (auto& t : pool) t.join();
+  } catch (const std::exception& e) {  // thread creation failed
+    for (int32_t i = 0; i < k; ++i) {
+      delete out[i];
+      out[i] = nullptr;
+    }
+    g_err = std::string("analyze_batch: ") + e.what();
+    return SPAND_ERR_OOM;
+  }
+  for (int32_t i = 0; i < k; ++i)
+    if (rc[i] != SPAND_OK) {
+      const int code = rc[i];
+      g_err = "problem " + std::to_string(i) + ": " + msg[i];
+      for (int32_t j = 0; j < k; ++j) {
+        delete out[j];
+        out[j] = nullptr;
+      }
+      return code;
+    }
+  return SPAND_OK;
+}
 
 }  // extern "C"

@@ -173,6 +173,18 @@ def knn_laplacian(npts: int, k: int, seed: int, shift: float = 1e-4) -> Problem:
                    cols.astype(np.int32), vals, None, 3)
 
 
+def batch_diffusion_2d(i: int):
+    """Problem i (0..31) of the batch of independent 2D diffusion systems:
+    n_i = 128 + floor(384 i / 31) cells per side, log a ~ N(0, 1) per cell
+    (seed 4 + i), x* ~ N(0, 1) (seed 100 + i), b = A x*, and the level count
+    L_i = round(log2(N_i / 32)) + 1.  Returns (problem, x*, b, L_i)."""
+    n = 128 + (384 * i) // 31
+    p = diffusion_2d(n, 4 + i)
+    xs = rng(100 + i).standard_normal(p.n)
+    b = p.to_scipy() @ xs
+    return p, xs, b, int(round(np.log2(p.n / 32))) + 1
+
+
 def rhs(n: int, seed: int) -> np.ndarray:
     """b ~ N(0, 1), seeded."""
     return rng(seed).standard_normal(n)

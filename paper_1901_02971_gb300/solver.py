@@ -93,3 +93,54 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+    @classmethod
+    def batch(cls, problems, opts_list) -> list:
+        """Solvers for k independent problems, analyzed together
+        (spand_analyze_batch, parallel host threads).  problems: objects with
+        rowptr, colind, vals and coords (or None); opts_list: one dict of
+        Solver keyword arguments per problem."""
+        opts = []
+        for kw in opts_list:
+            prec = {"fp64": L.SPAND_FP64, "fp32": L.SPAND_FP32}[kw.get("precision", "fp64")]
+            opts.append(L.default_opts(levels=kw.get("levels", 8), eps=kw.get("eps", 1e-2), skip=kw.get("skip", 0),
+                                       precision=prec, maxit=kw.get("maxit", 500), tol=kw.get("tol", 1e-10)))
+        hs = L.spand_analyze_batch([(p.rowptr, p.colind, p.vals, p.coords) for p in problems], opts)
+        out = []
+        for p, o, h in zip(problems, opts, hs):
+            s = cls.__new__(cls)
+            s.opts, s.n, s.nnz, s.h = o, int(p.rowptr.size - 1), int(p.rowptr[-1]), h
+            out.append(s)
+        return out
+
+
+def _each_on_own_stream(solvers, fn):
+    """Runs fn(index, solver, stream) for every solver at once, one host thread
+    and one CUDA stream per solver (independent handles share nothing; the
+    library releases the GIL inside every call)."""
+    import concurrent.futures as cf
+    import torch
+    dev = torch.cuda.current_device()
+    streams = [torch.cuda.Stream() for _ in solvers]
+
+    def run(i):
+        torch.cuda.set_device(dev)
+        with torch.cuda.stream(streams[i]):
+            return fn(i, solvers[i], streams[i].cuda_stream)
+
+    with cf.ThreadPoolExecutor(max_workers=max(1, len(solvers))) as ex:
+        res = list(ex.map(run, range(len(solvers))))
+    for st in streams:
+        st.synchronize()
+    return res
+
+
+def factorize_all(solvers, vals_list=None):
+    """Factorizes independent solvers concurrently (one stream each)."""
+    _each_on_own_stream(solvers, lambda i, s, st: s.factorize(None if vals_list is None else vals_list[i], stream=st))
+    return solvers
+
+
+def solve_all(solvers, bs, xs=None):
+    """Solves independent systems concurrently; returns [(x, iters, relres)]."""
+    return _each_on_own_stream(solvers, lambda i, s, st: s.solve(bs[i], None if xs is None else xs[i], stream=st))

@@ -29,7 +29,7 @@ def test_every_symbol_exported(spand_lib):
 
 
 def test_error_strings(spand_lib):
-    for code in range(7):
+    for code in range(8):
         assert spand_lib.spand_error_string(code)
 
 
@@ -88,3 +88,47 @@ def test_solve_before_factorize_is_state_error(spand_lib):
             L.spand_get_ranks(h, 1)
     finally:
         L.spand_destroy(h)
+
+
+def _tree_arrays(h):
+    t = L.spand_get_tree(h)
+    return {k: np.asarray(v) for k, v in t.items()}
+
+
+def test_analyze_batch_matches_single(spand_lib):
+    """Batch analysis (parallel host threads) gives, problem by problem, the
+    same ordering, clusters and steps as spand_analyze."""
+    probs = [I.laplacian_2d(24), I.diffusion_2d(20, 3), I.laplacian_3d(10), I.knn_laplacian(400, 6, 2)]
+    levels = [5, 4, 4, 5]
+    opts = [L.default_opts(levels=lv) for lv in levels]
+    hs = L.spand_analyze_batch([(p.rowptr, p.colind, p.vals, p.coords) for p in probs], opts)
+    try:
+        for p, lv, h in zip(probs, levels, hs):
+            h1 = L.spand_analyze(p.rowptr, p.colind, p.vals, p.coords, L.default_opts(levels=lv))
+            try:
+                a, b = _tree_arrays(h), _tree_arrays(h1)
+                assert a.keys() == b.keys()
+                for k in a:
+                    assert np.array_equal(a[k], b[k]), k
+                for t in range(1, lv + 1):
+                    sa, sb = L.spand_get_step(h, t), L.spand_get_step(h1, t)
+                    for k in sa:
+                        assert np.array_equal(np.asarray(sa[k]), np.asarray(sb[k])), (t, k)
+            finally:
+                L.spand_destroy(h1)
+    finally:
+        for h in hs:
+            L.spand_destroy(h)
+
+
+def test_analyze_batch_error_names_problem(spand_lib):
+    good = I.laplacian_2d(12)
+    bad_colind = good.colind.copy()
+    bad_colind[1], bad_colind[2] = bad_colind[2], bad_colind[1]  # unsorted row
+    probs = [(good.rowptr, good.colind, good.vals, good.coords), (good.rowptr, bad_colind, good.vals, None),
+             (good.rowptr, good.colind, good.vals, None)]
+    with pytest.raises(L.SpandError) as e:
+        L.spand_analyze_batch(probs, [L.default_opts(levels=3)] * 3)
+    assert e.value.code == L.SPAND_ERR_INVALID_ARG
+    assert "problem 1" in str(e.value)
+    assert L.spand_analyze_batch([], []) == []
