@@ -261,8 +261,8 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def run_form(precision, steps, warmup, timed_clocks=False):
-        s = Solver.from_problem(p, levels=levels, eps=EPS, precision=precision)
+    def run_form(precision, steps, warmup, timed_clocks=False, skip=0):
+        s = Solver.from_problem(p, levels=levels, eps=EPS, precision=precision, skip=skip)
         for _ in range(warmup):
             s.factorize(vals_d)
             s.solve(b_d, x_d)
@@ -308,6 +308,16 @@ def main():
     ph32 = s32.phase_times()
     prof32 = kernel_profile(s32)
     s64, t64, it64, rr64, _, _ = run_form("fp64", max(1, args.fp64_steps), 1)
+    # skip sweep of the mixed form (a performance knob: no scaling or
+    # sparsification for the first `skip` steps)
+    sweep = {"0": {"s_per_step": statistics.mean(t32), "iters": it32[-1], "size_top": s32.stats().size_top,
+                   "mem_f": s32.stats().mem_f}}
+    for sk in (2, 4):
+        ss, ts, its, _, _, _ = run_form("fp32", 2, 1, skip=sk)
+        sst = ss.stats()
+        sweep[str(sk)] = {"s_per_step": statistics.mean(ts), "iters": its[-1], "size_top": sst.size_top,
+                          "mem_f": sst.mem_f}
+        ss.close()
     st64 = s64.stats()
     ph64 = s64.phase_times()
     # accuracy of x of each form against each other (FP64 reference on the GPU)
@@ -352,6 +362,7 @@ def main():
             "speedup_mixed_vs_fp64": statistics.mean(t64) / v,
             "x_rel_diff_mixed_vs_fp64": float(np.linalg.norm(x32 - x64) / np.linalg.norm(x64)),
             "true_relres_host": relres_host,
+            "skip_sweep_mixed_fp32": sweep,
         },
         "e2e": {"value": ve, "unit": "s", "h2d_bytes_per_step": int(p.nnz * 8 + p.n * 8),
                 "d2h_bytes_per_step": int(p.n * 8)},

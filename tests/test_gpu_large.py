@@ -1,0 +1,65 @@
+"""Full-size runs of the two large workloads, checked through properties that
+hold at any size (the FP64 oracle would take hours here):
+
+* 3D diffusion -div(a grad u) on 128^3 cells, a = 10^u with u ~ U(-3, 3) per
+  8^3 block (six decades of contrast), geometric separators, L = 13;
+* graph Laplacian of the symmetrised 10-nearest-neighbour graph of 10^6
+  random points (plus 1e-4 I), no coordinates (BFS bisection), L = 12.
+
+Each must reach the requested relative residual, confirmed on the host with
+the input matrix, within an iteration budget far below unpreconditioned CG.
+"""
+import numpy as np
+import pytest
+
+from paper_1901_02971_gb300 import Solver
+from paper_1901_02971_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(p, coords, **kw):
+    import torch
+    s = Solver.from_problem(p, use_coords=coords, tol=1e-10, maxit=500, **kw)
+    try:
+        s.factorize()
+        b = I.rhs(p.n, 1)
+        x, it, rr = s.solve(torch.from_numpy(b).cuda())
+        xh = x.cpu().numpy()
+        st = s.stats()
+        true_rr = np.linalg.norm(b - p.to_scipy() @ xh) / np.linalg.norm(b)
+        return xh, it, rr, true_rr, st
+    finally:
+        s.close()
+
+
+@pytest.fixture(scope="module")
+def diffusion_128():
+    return I.diffusion_3d(128, 2)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_diffusion_128_converges(cuda_ok, diffusion_128, precision):
+    p = diffusion_128
+    assert p.n == 2_097_152 and p.nnz == 14_581_760
+    x, it, rr, true_rr, st = _run(p, True, levels=13, eps=1e-2, precision=precision)
+    assert rr <= 1e-10 and true_rr <= 1.5e-10, (it, rr, true_rr)
+    assert it <= 40, it
+    assert 0 < st.size_top < 4096
+
+
+def test_diffusion_128_eps_sweep_is_monotone(cuda_ok, diffusion_128):
+    """Smaller eps keeps more of the interfaces: more memory, fewer iterations."""
+    res = {e: _run(diffusion_128, True, levels=13, eps=e, precision="fp32") for e in (1e-1, 1e-3)}
+    for e, (x, it, rr, true_rr, st) in res.items():
+        assert rr <= 1e-10 and true_rr <= 1.5e-10, (e, it, true_rr)
+    assert res[1e-3][1] < res[1e-1][1]
+    assert res[1e-3][4].mem_f > res[1e-1][4].mem_f
+
+
+def test_knn_million_converges(cuda_ok):
+    p = I.knn_laplacian(1_000_000, 10, 3)
+    assert p.coords is None
+    x, it, rr, true_rr, st = _run(p, False, levels=12, eps=1e-2, precision="fp32")
+    assert rr <= 1e-10 and true_rr <= 1.5e-10, (it, rr, true_rr)
+    assert it <= 40, it
