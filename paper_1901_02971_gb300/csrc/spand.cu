@@ -12,6 +12,7 @@
 #include <numeric>
 #include <stdexcept>
 #include <string>
+#include <functional>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -784,6 +785,15 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
   CK(cudaEventRecord(tm.at(0, 1), s));
 
   int32_t* d_cur = nullptr;
+  std::function<void()> pending;  // the previous step's deferred apply-program build
+  auto run_pending = [&]() {
+    if (pending) {
+      auto f = std::move(pending);
+      pending = nullptr;
+      f();
+    }
+  };
+  std::vector<std::vector<int32_t>> slots_of_step;
   for (int t = 1; t <= L; ++t) {
     const StepStruct& st = tr.steps[t - 1];
     const int n = st.n;
@@ -1195,6 +1205,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         h->prof.launches += (int64_t)groups.size();
         h->prof.end(cpqr_pid, s, 0.0, 0.0, (int64_t)groups.size());
         build_elim_ops();  // host work overlapped with the sparsification kernels
+        run_pending();
         int32_t* hcur = (int32_t*)h->stage.take((size_t)n * sizeof(int32_t));
         CK(cudaMemcpyAsync(hcur, d_cur, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -1230,77 +1241,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
     }
     CK(cudaEventRecord(tm.at(t, 3), s));
     if (!elim_ops_built) build_elim_ops();
-    // slots, save areas, temporaries and work items of the scaling +
-    // coarse-basis ops (step-t slot lists)
-    std::vector<ApplyItem> it_sy, it_sc, it_sz, it_sx;
-    {
-      int64_t save = h->save_len;
-      for (size_t i = 0; i < sqops.size(); ++i) {
-        SqOp<T>& so = sqops[i];
-        const int p = sq_cluster[i];
-        so.slot = (int64_t)aslots.size();
-        aslots.insert(aslots.end(), slots[p].begin(), slots[p].end());
-        so.save = save;
-        save += so.np + so.r;
-        so.tz = tmp_off;
-        tmp_off += so.np;
-        const int32_t op = (int32_t)i;
-        for (int32_t r0 = 0; r0 < so.np; r0 += RB) {
-          it_sy.push_back({op, r0});
-          it_sz.push_back({op, r0});
-        }
-        for (int32_t c0 = 0; c0 < so.r; c0 += AP_COLS) it_sc.push_back({op, c0});
-        for (int32_t c0 = 0; c0 < so.np; c0 += AP_COLS) it_sx.push_back({op, c0});
-      }
-      h->save_len = save;
-      h->tmp_len = std::max(h->tmp_len, tmp_off);
-    }
     h->sizes_after[t - 1] = sz_after;
-    {  // upload the step's apply program
-      Packer pk;
-      size_t oe = pk.add(eops), os = pk.add(sqops), osl = pk.add(aslots);
-      size_t osy = pk.add(it_sy), osc = pk.add(it_sc), osz = pk.add(it_sz), osx = pk.add(it_sx);
-      size_t ots = pk.add(tslot), otp = pk.add(tptr), oti = pk.add(tidx);
-      size_t ofy = pk.add(it_fy), ofu = pk.add(it_fu), oba = pk.add(it_ba), obx = pk.add(it_bx);
-      void* d = nullptr;
-      if (!pk.buf.empty()) {
-        d = h->persist.alloc(pk.buf.size());
-        void* src = h->stage.take(pk.buf.size());
-        std::memcpy(src, pk.buf.data(), pk.buf.size());
-        CK(cudaMemcpyAsync(d, src, pk.buf.size(), cudaMemcpyHostToDevice, s));
-      }
-      ap.n_elim = (int)eops.size();
-      ap.n_sq = (int)sqops.size();
-      ap.elim = at<const ElimOp<T>>(d, oe);
-      ap.sq = at<const SqOp<T>>(d, os);
-      ap.n_sy = (int)it_sy.size();
-      ap.n_sc = (int)it_sc.size();
-      ap.n_sz = (int)it_sz.size();
-      ap.n_sx = (int)it_sx.size();
-      ap.sy = at<const ApplyItem>(d, osy);
-      ap.sc = at<const ApplyItem>(d, osc);
-      ap.sz = at<const ApplyItem>(d, osz);
-      ap.sx = at<const ApplyItem>(d, osx);
-      ap.slots = at<const int32_t>(d, osl);
-      ap.ntgt = (int64_t)tslot.size();
-      ap.nassign = nassign;
-      ap.tslot = at<const int32_t>(d, ots);
-      ap.tptr = at<const int64_t>(d, otp);
-      ap.tidx = at<const int64_t>(d, oti);
-      ap.n_fy = (int)it_fy.size();
-      ap.n_fu = (int)it_fu.size();
-      ap.n_ba = (int)it_ba.size();
-      ap.n_bx = (int)it_bx.size();
-      ap.fy = at<const ApplyItem>(d, ofy);
-      ap.fu = at<const ApplyItem>(d, ofu);
-      ap.ba = at<const ApplyItem>(d, oba);
-      ap.bx = at<const ApplyItem>(d, obx);
-      ap.sm_ns = sm_ns;
-      ap.sm_m = sm_m;
-      ap.sm_np = sm_np;
-      ap.sm_r = sm_r;
-      apply.push_back(ap);
-    }
     // ------------------------------------------------ merge (Sec. 2.7)
     Layout<T> nxt;
     if (t < L) {
@@ -1349,11 +1290,100 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       }
       copy_batch<T>(h, cps, s);
       sz = nsz;
+      slots_of_step = std::move(slots);
       slots = std::move(nslots);
+    } else {
+      slots_of_step = std::move(slots);
     }
     CK(cudaEventRecord(tm.at(t, 4), s));
+    run_pending();  // the previous step's program, if the GPU never waited for us
+    // The step's apply program (scaling + coarse-basis ops, upload) is built
+    // later, during the next step's sparsification kernels (run_pending), so
+    // that the rank-dependent GPU work (merge, next elimination) is issued
+    // first.  Steps are finalized in order.
+    {
+      std::vector<std::vector<int32_t>> prev_slots = std::move(slots_of_step);
+      pending = [h, s, &apply, prev_slots = std::move(prev_slots), ap = std::move(ap), eops = std::move(eops),
+                 sqops = std::move(sqops), sq_cluster = std::move(sq_cluster), aslots = std::move(aslots),
+                 tslot = std::move(tslot), tptr = std::move(tptr), tidx = std::move(tidx), it_fy = std::move(it_fy),
+                 it_fu = std::move(it_fu), it_ba = std::move(it_ba), it_bx = std::move(it_bx), nassign, sm_ns, sm_m,
+                 sm_np, sm_r, tmp_off]() mutable {
+      // slots, save areas, temporaries and work items of the scaling +
+      // coarse-basis ops (step-t slot lists)
+      std::vector<ApplyItem> it_sy, it_sc, it_sz, it_sx;
+      {
+        int64_t save = h->save_len;
+        for (size_t i = 0; i < sqops.size(); ++i) {
+          SqOp<T>& so = sqops[i];
+          const int p = sq_cluster[i];
+          so.slot = (int64_t)aslots.size();
+          aslots.insert(aslots.end(), prev_slots[p].begin(), prev_slots[p].end());
+          so.save = save;
+          save += so.np + so.r;
+          so.tz = tmp_off;
+          tmp_off += so.np;
+          const int32_t op = (int32_t)i;
+          for (int32_t r0 = 0; r0 < so.np; r0 += RB) {
+            it_sy.push_back({op, r0});
+            it_sz.push_back({op, r0});
+          }
+          for (int32_t c0 = 0; c0 < so.r; c0 += AP_COLS) it_sc.push_back({op, c0});
+          for (int32_t c0 = 0; c0 < so.np; c0 += AP_COLS) it_sx.push_back({op, c0});
+        }
+        h->save_len = save;
+        h->tmp_len = std::max(h->tmp_len, tmp_off);
+      }
+      {  // upload the step's apply program
+        Packer pk;
+        size_t oe = pk.add(eops), os = pk.add(sqops), osl = pk.add(aslots);
+        size_t osy = pk.add(it_sy), osc = pk.add(it_sc), osz = pk.add(it_sz), osx = pk.add(it_sx);
+        size_t ots = pk.add(tslot), otp = pk.add(tptr), oti = pk.add(tidx);
+        size_t ofy = pk.add(it_fy), ofu = pk.add(it_fu), oba = pk.add(it_ba), obx = pk.add(it_bx);
+        void* d = nullptr;
+        if (!pk.buf.empty()) {
+          d = h->persist.alloc(pk.buf.size());
+          void* src = h->stage.take(pk.buf.size());
+          std::memcpy(src, pk.buf.data(), pk.buf.size());
+          CK(cudaMemcpyAsync(d, src, pk.buf.size(), cudaMemcpyHostToDevice, s));
+        }
+        ap.n_elim = (int)eops.size();
+        ap.n_sq = (int)sqops.size();
+        ap.elim = at<const ElimOp<T>>(d, oe);
+        ap.sq = at<const SqOp<T>>(d, os);
+        ap.n_sy = (int)it_sy.size();
+        ap.n_sc = (int)it_sc.size();
+        ap.n_sz = (int)it_sz.size();
+        ap.n_sx = (int)it_sx.size();
+        ap.sy = at<const ApplyItem>(d, osy);
+        ap.sc = at<const ApplyItem>(d, osc);
+        ap.sz = at<const ApplyItem>(d, osz);
+        ap.sx = at<const ApplyItem>(d, osx);
+        ap.slots = at<const int32_t>(d, osl);
+        ap.ntgt = (int64_t)tslot.size();
+        ap.nassign = nassign;
+        ap.tslot = at<const int32_t>(d, ots);
+        ap.tptr = at<const int64_t>(d, otp);
+        ap.tidx = at<const int64_t>(d, oti);
+        ap.n_fy = (int)it_fy.size();
+        ap.n_fu = (int)it_fu.size();
+        ap.n_ba = (int)it_ba.size();
+        ap.n_bx = (int)it_bx.size();
+        ap.fy = at<const ApplyItem>(d, ofy);
+        ap.fu = at<const ApplyItem>(d, ofu);
+        ap.ba = at<const ApplyItem>(d, oba);
+        ap.bx = at<const ApplyItem>(d, obx);
+        ap.sm_ns = sm_ns;
+        ap.sm_m = sm_m;
+        ap.sm_np = sm_np;
+        ap.sm_r = sm_r;
+        apply.push_back(ap);
+      }
+      };
+    }
+
     if (t < L) lay = std::move(nxt);
   }
+  run_pending();
   CK(cudaStreamSynchronize(s));
   check_pivots(L);
   {
