@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -1917,7 +1918,9 @@ int spand_solve(spand_handle h, const double* b, double* x, int32_t* iters, doub
   h->phase_ms[4] = napply ? apply_ms / napply : 0.0;
   h->phase_ms[5] = it ? spmv_ms / it : 0.0;
   if (bnorm != 0.0 && !(rel <= tol)) {
-    g_err = "PCG stopped at maxit with relative residual " + std::to_string(rel);
+    char buf[64];
+    std::snprintf(buf, sizeof buf, "%.3e", rel);
+    g_err = std::string("PCG stopped at maxit with relative residual ") + buf;
     return SPAND_ERR_NO_CONVERGENCE;
   }
   return SPAND_OK;

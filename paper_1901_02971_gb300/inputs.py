@@ -138,6 +138,26 @@ def diffusion_2d(n: int, seed: int, sigma: float = 1.0) -> Problem:
     return _assemble((n, n), cell, f"diff2d_{n}_s{seed}")
 
 
+def high_contrast_field(shape, rho: float, seed: int, sigma: float = 1.0) -> np.ndarray:
+    """The quantized high-contrast coefficient field of the 2D experiments
+    (Sec. 4.1): uniform (0, 1) noise per cell, smoothed by a Gaussian of
+    standard deviation `sigma` cells (boundary: mirror reflection), then
+    rho where the smoothed value is >= 0.5 and 1/rho elsewhere."""
+    from scipy.ndimage import gaussian_filter
+    a_hat = gaussian_filter(rng(seed).random(shape), sigma=sigma, mode="reflect")
+    return np.where(a_hat >= 0.5, float(rho), 1.0 / float(rho))
+
+
+def high_contrast_2d(n: int, rho: float, seed: int) -> Problem:
+    """-div(a grad u) on n^2 cells with the quantized high-contrast field."""
+    return _assemble((n, n), high_contrast_field((n, n), rho, seed), f"hc2d_{n}_r{rho:g}_s{seed}")
+
+
+def high_contrast_3d(n: int, rho: float, seed: int) -> Problem:
+    """-div(a grad u) on n^3 cells with the quantized high-contrast field."""
+    return _assemble((n, n, n), high_contrast_field((n, n, n), rho, seed), f"hc3d_{n}_r{rho:g}_s{seed}")
+
+
 def knn_laplacian(npts: int, k: int, seed: int, shift: float = 1e-4) -> Problem:
     """Graph Laplacian of the symmetrised k-NN graph of uniform points in the
     unit cube, weights exp(-d^2/h^2) with h the mean k-th neighbour distance,

@@ -57,6 +57,10 @@ CASES = [
     ("diff3d_16_L6_e1e-2", lambda: I.diffusion_3d(16, 2, block=4), 6, 1e-2, 0, True),
     ("diff2d_48_L7_e1e-2_nogeo", lambda: I.diffusion_2d(48, 4), 7, 1e-2, 0, False),
     ("knn_4000_L7_e1e-2", lambda: I.knn_laplacian(4000, 10, 3), 7, 1e-2, 0, False),
+    # quantized high-contrast fields (Sec. 4.1 generator), contrast 1e6 and 1e4
+    ("hc2d_64_r1000_L8_e1e-2", lambda: I.high_contrast_2d(64, 1000, 1), 8, 1e-2, 0, True),
+    ("hc2d_48_r1000_L7_e1e-4", lambda: I.high_contrast_2d(48, 1000, 2), 7, 1e-4, 0, True),
+    ("hc3d_16_r100_L6_e1e-2", lambda: I.high_contrast_3d(16, 100, 3), 6, 1e-2, 0, True),
 ]
 
 
