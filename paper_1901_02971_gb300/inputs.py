@@ -54,8 +54,9 @@ def rng(seed: int) -> np.random.Generator:
 
 
 def _grid_coords(shape) -> np.ndarray:
-    """Integer coordinates (x fastest) of a 2D/3D grid, as float64."""
-    idx = np.indices(shape[::-1]).reshape(len(shape), -1)[::-1]
+    """Integer coordinates (x, y[, z]) of every cell of a grid given in numpy
+    order (z, y, x) / (y, x), cells numbered x fastest; float64."""
+    idx = np.indices(shape).reshape(len(shape), -1)[::-1]
     return np.ascontiguousarray(idx.T.astype(np.float64))
 
 
@@ -63,11 +64,13 @@ def _harm(a, b):
     return 2.0 * a * b / (a + b)
 
 
-def _assemble(shape, cell: np.ndarray, name: str) -> Problem:
+def _assemble(shape, cell: np.ndarray, name: str, axis_scale=None) -> Problem:
     """Variable-coefficient 5/7-point stencil on a grid with Dirichlet faces.
 
     ``cell`` has the grid shape in (z, y, x) / (y, x) order (numpy C order,
-    so that ``cell.ravel()`` follows the unknown numbering)."""
+    so that ``cell.ravel()`` follows the unknown numbering).  ``axis_scale``
+    (x, y[, z]) multiplies the face coefficients along each grid axis
+    (anisotropy); default 1."""
     dim = len(shape)
     n_tot = int(np.prod(shape))
     a = cell.reshape(-1).astype(np.float64)
@@ -83,7 +86,8 @@ def _assemble(shape, cell: np.ndarray, name: str) -> Problem:
         hi[nax] = slice(1, None)
         i0 = ids[tuple(lo)].ravel()
         i1 = ids[tuple(hi)].ravel()
-        f = _harm(a[i0], a[i1])
+        sc = 1.0 if axis_scale is None else float(axis_scale[ax])
+        f = sc * _harm(a[i0], a[i1])
         rows += [i0, i1]
         cols += [i1, i0]
         vals += [-f, -f]
@@ -96,7 +100,7 @@ def _assemble(shape, cell: np.ndarray, name: str) -> Problem:
         last[nax] = -1
         for sl in (first, last):
             ib = ids[tuple(sl)].ravel()
-            np.add.at(diag, ib, a[ib])
+            np.add.at(diag, ib, (1.0 if axis_scale is None else float(axis_scale[ax])) * a[ib])
     rows.append(np.arange(n_tot))
     cols.append(np.arange(n_tot))
     vals.append(diag)
@@ -156,6 +160,24 @@ def high_contrast_2d(n: int, rho: float, seed: int) -> Problem:
 def high_contrast_3d(n: int, rho: float, seed: int) -> Problem:
     """-div(a grad u) on n^3 cells with the quantized high-contrast field."""
     return _assemble((n, n, n), high_contrast_field((n, n, n), rho, seed), f"hc3d_{n}_r{rho:g}_s{seed}")
+
+
+def extruded_3d(nx: int, ny: int, nz: int, seed: int, aniso: float = 100.0) -> Problem:
+    """Thin extruded 3D problem (stand-in for the ice-sheet runs of Sec. 4):
+    7-point -div(a grad u) on nx x ny x nz cells, nz small, with a background
+    field varying over six decades in the plane, a = 10^(3 s(x, y)), s a
+    Gaussian-smoothed (sigma = 4 cells) uniform noise rescaled to [-1, 1] and
+    constant along z, and vertical faces `aniso` times stronger (thin
+    layers).  Coordinates are the (x, y) of every cell only, so that the
+    geometric separator partitions the plane and extrudes the partition in z.
+    """
+    from scipy.ndimage import gaussian_filter
+    s = gaussian_filter(rng(seed).random((ny, nx)), sigma=4.0, mode="reflect")
+    s = 2.0 * (s - s.min()) / max(s.max() - s.min(), 1e-300) - 1.0
+    cell = np.broadcast_to(10.0 ** (3.0 * s), (nz, ny, nx)).copy()
+    p = _assemble((nz, ny, nx), cell, f"extr_{nx}x{ny}x{nz}_s{seed}", axis_scale=(1.0, 1.0, aniso))
+    xy = _grid_coords((nz, ny, nx))[:, :2].copy()
+    return Problem(p.name, p.n, p.rowptr, p.colind, p.vals, xy, 2)
 
 
 def knn_laplacian(npts: int, k: int, seed: int, shift: float = 1e-4) -> Problem:

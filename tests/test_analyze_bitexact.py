@@ -38,6 +38,9 @@ CASES = [
     ("knn_3000_L7", lambda: I.knn_laplacian(3000, 10, 3), 7, False),
     ("lapl2d_1_L1", lambda: I.laplacian_2d(1), 1, True),
     ("lapl2d_2_L3", lambda: I.laplacian_2d(2), 3, True),
+    # extruded thin 3D mesh, partitioned with its (x, y) coordinates only
+    ("extr_24x20x4_L6", lambda: I.extruded_3d(24, 20, 4, 1), 6, True),
+    ("extr_33x17x3_L7", lambda: I.extruded_3d(33, 17, 3, 2), 7, True),
 ]
 
 
@@ -50,3 +53,20 @@ def test_analyze_bitexact(spand_lib, name, gen, levels, geo):
 def test_analyze_bitexact_3d_64(spand_lib):
     """The benchmark workload itself: 7-point Laplacian on 64^3, L = 10."""
     _compare(I.laplacian_3d(64), 10, True)
+
+
+def test_extruded_partition_keeps_columns_whole(spand_lib):
+    """With (x, y) coordinates the separators are vertical: every column of
+    cells (same x, y, all z) lies in one cluster."""
+    p = I.extruded_3d(40, 28, 5, 3)
+    h = L.spand_analyze(p.rowptr, p.colind, p.vals, p.coords, L.default_opts(levels=7))
+    try:
+        t = L.spand_get_tree(h)
+        cl = np.empty(p.n, dtype=np.int64)
+        ptr = np.asarray(t["cluster_ptr"])
+        for c in range(len(ptr) - 1):
+            cl[np.asarray(t["perm"])[ptr[c]:ptr[c + 1]]] = c
+        col = cl.reshape(5, 28 * 40)
+        assert np.all(col == col[0]), "a column is split between clusters"
+    finally:
+        L.spand_destroy(h)

@@ -61,6 +61,8 @@ CASES = [
     ("hc2d_64_r1000_L8_e1e-2", lambda: I.high_contrast_2d(64, 1000, 1), 8, 1e-2, 0, True),
     ("hc2d_48_r1000_L7_e1e-4", lambda: I.high_contrast_2d(48, 1000, 2), 7, 1e-4, 0, True),
     ("hc3d_16_r100_L6_e1e-2", lambda: I.high_contrast_3d(16, 100, 3), 6, 1e-2, 0, True),
+    # thin extruded mesh with a six-decade background field, xy partition
+    ("extr_32x24x4_L7_e1e-2", lambda: I.extruded_3d(32, 24, 4, 1), 7, 1e-2, 0, True),
 ]
 
 
