@@ -143,8 +143,10 @@ HBM_BOUND = {"copy", "apply", "pcg"}
 # counters were taken on: a changed kernel reports null until re-measured.
 # The capture and its command are summarised under profiles/ (DRAM traffic, 64^3).
 MEASURED_TRAFFIC = {
-    "cpqr": {"bytes_per_launch": 529.5e6 / 125, "src": "paper_1901_02971_gb300/csrc/cpqr_cluster.cuh",
-             "sha256": "b52a96fcf89b786ddaee2ab7e08eea104d6bd0c970c7190346b14bf6c0078fb7"},
+    "cpqr": {"bytes_per_launch": 531.8e6 / 155,
+             "src": ["paper_1901_02971_gb300/csrc/cpqr_cluster.cuh", "paper_1901_02971_gb300/csrc/cpqr_reg.cuh"],
+             "sha256": ["afed2487a6de0008bf48db37f059975772761f8fb2c6fa98c301f169ff23bc70",
+                        "e766394825e5569cca9f0d738cfed1b62fe8de88c7db8f6385d55f2d9d71e4d5"]},
     "apply": {"bytes_per_launch": (2067.7e6 + 27.9e6) / 2, "src": "paper_1901_02971_gb300/csrc/solve_kernels.cuh",
               "sha256": "24edc4406567191d811d97b17722572c1630b4225aa648ce84d1856b9ea2db56"},
 }
@@ -155,13 +157,16 @@ def measured_traffic(fam: str, grid: int):
     if t is None or grid != GRID:
         return None
     import hashlib
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), t["src"])
-    try:
-        with open(path, "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest() != t["sha256"]:
-                return None
-    except OSError:
-        return None
+    srcs = t["src"] if isinstance(t["src"], list) else [t["src"]]
+    sums = t["sha256"] if isinstance(t["sha256"], list) else [t["sha256"]]
+    for src, want in zip(srcs, sums):
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), src)
+        try:
+            with open(path, "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() != want:
+                    return None
+        except OSError:
+            return None
     return t["bytes_per_launch"]
 
 

@@ -221,6 +221,107 @@ __device__ __forceinline__ void cq_form_q_any(const CpqrTask<T>& d, const T* V, 
   else cq_form_q<T, 1, DIRECT>(d, V, chunk, L, j0, piv_s, scal_s, tau_s, r, np, rank, C);
 }
 
+// Epilogue shared by the sparsification kernels, entered after a block barrier
+// with the CTA's final columns in `chunk` (column-major, stride L): the write-back
+// of W_cn into p's and the neighbours' block rows, A_cc = I, the coarse basis
+// Q_pc, and the rank in cur_size[p].
+template <typename T, bool RES, int NT>
+__device__ __forceinline__ void cq_finish(const CpqrTask<T>& d, cg::cluster_group& cluster, int C, int rank,
+                                          T* chunk, T* schunk, int L, int np, int r, int nc, int j0,
+                                          int cols_per, int cpm, const int* tcol, const int* rstep,
+                                          const T* beta_s, const T* scal_s, const T* tau_s, const int* piv_s,
+                                          const CpqrNbr<T>* nbr, const int* cstart, int32_t* cur_size) {
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // Rows 0..r-1 of every column hold W_cn in the original column order, except
+  // that a column retired at step s < r holds R_ss = beta_s at row s and zeros
+  // below it (its stored entries below s are the raw reflector source).
+  auto wval = [&](int jl, int i) -> T {
+    const int s = rstep[jl];
+    if (s < 0 || i < s) return chunk[(size_t)jl * L + i];
+    return i == s ? beta_s[s] : T(0);
+  };
+  // ---- write back W_cn into p's row (one warp per column, coalesced) ...
+  for (int jl = warp; jl < nc; jl += NW) {
+    T* dst = d.Rp + (size_t)tcol[cpm + jl] * d.ldp;
+    for (int i = lane; i < r; i += 32) dst[i] = wval(jl, i);
+  }
+  // ... and its transpose into the neighbours' rows (one thread per column)
+  for (int jl = tid; jl < nc; jl += NT) {
+    const int e = tcol[jl];
+    const CpqrNbr<T> nb = nbr[e];
+    const int cc = j0 + jl - cstart[e];
+    for (int i = 0; i < r; ++i) nb.Rq[cc + (size_t)(nb.off_qp + i) * nb.ldq] = wval(jl, i);
+  }
+  // A_cc = I: column j by warp j of the cluster, lanes over rows
+  for (int j = rank * NW + warp; j < r; j += C * NW) {
+    T* dst = d.Rp + (size_t)j * d.ldp;
+    for (int i = lane; i < r; i += 32) dst[i] = (i == j) ? T(1) : T(0);
+  }
+  // ---- Q_pc = H_0 ... H_{r-1} [I_r; 0]
+  if (C == 1) {
+    __syncthreads();
+    if (np <= 32 * 16) cq_form_q_any<T, true>(d, nullptr, chunk, L, j0, piv_s, scal_s, tau_s, r, np, 0, 1);
+  } else {
+    // the reflectors live in the owners' chunks: every CTA writes its own
+    // retired columns to V (column k = v_k, rows >= k), then each copies V
+    // into its chunk space when it fits
+    for (int k = warp; k < r; k += NW) {
+      const int jl = piv_s[k] - j0;
+      if (jl < 0 || jl >= nc) continue;
+      const T* pc = chunk + (size_t)jl * L;
+      const T sc = scal_s[k];
+      for (int i = k + lane; i < np; i += 32) d.V[i + (size_t)k * np] = i == k ? T(1) : pc[i] * sc;
+    }
+    cluster.sync();  // every V column is written; no CTA reads another's chunk any more
+    const T* Vsrc = d.V;
+    if (RES && (size_t)np * r <= (size_t)L * cols_per) {
+      T* Vs = schunk;
+      for (int kb = warp * 8; kb < r; kb += NW * 8)
+        for (int i = lane; i < np; i += 32) {
+          T v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[u] = (kb + u < r && i >= kb + u) ? __ldcg(d.V + i + (size_t)(kb + u) * np) : T(0);
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (kb + u < r) Vs[i + (size_t)(kb + u) * np] = v[u];
+        }
+      __syncthreads();
+      Vsrc = Vs;
+    }
+    if (np <= 32 * 16) cq_form_q_any<T, false>(d, Vsrc, nullptr, L, j0, piv_s, scal_s, tau_s, r, np, rank, C);
+  }
+  if (np > 32 * 16) {  // tall interfaces: V in global memory, the column of Q in global memory
+    if (C == 1) {
+      for (int k = warp; k < r; k += NW) {
+        const T* pc = chunk + (size_t)(piv_s[k] - j0) * L;
+        const T sc = scal_s[k];
+        for (int i = k + lane; i < np; i += 32) d.V[i + (size_t)k * np] = i == k ? T(1) : pc[i] * sc;
+      }
+      __syncthreads();
+    }
+    for (int c = rank * NW + warp; c < r; c += C * NW) {
+      T* col = d.Qc + (size_t)c * np;
+      for (int i = lane; i < np; i += 32) col[i] = (i == c) ? T(1) : T(0);
+      __syncwarp();
+      for (int k = c; k >= 0; --k) {
+        const T tk = tau_s[k];
+        if (tk == T(0)) continue;
+        const T* v = d.V + (size_t)k * np;
+        T w = 0;
+        for (int i = k + lane; i < np; i += 32) w += __ldcg(v + i) * col[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        w *= tk;
+        for (int i = k + lane; i < np; i += 32) col[i] -= w * __ldcg(v + i);
+        __syncwarp();
+      }
+    }
+  }
+  if (rank == 0 && tid == 0) cur_size[d.p] = r;
+  if (C > 1) cluster.sync();  // no CTA leaves while others may still read its shared memory
+}
+
 // Per reflector step k:
 //   1. every warp reduces its threads' best live columns (largest squared
 //      trailing norm, lowest index on ties) into its slot of set k mod 2;
@@ -515,93 +616,8 @@ __global__ void __launch_bounds__(NT) k_cpqr_cluster(const CpqrTask<T>* __restri
     }
   }
   __syncthreads();
-  // Rows 0..r-1 of every column hold W_cn in the original column order, except
-  // that a column retired at step s < r holds R_ss = beta_s at row s and zeros
-  // below it (its stored entries below s are the raw reflector source).
-  auto wval = [&](int jl, int i) -> T {
-    const int s = rstep[jl];
-    if (s < 0 || i < s) return chunk[(size_t)jl * L + i];
-    return i == s ? beta_s[s] : T(0);
-  };
-  // ---- write back W_cn into p's row (one warp per column, coalesced) ...
-  for (int jl = warp; jl < nc; jl += NW) {
-    T* dst = d.Rp + (size_t)tcol[cpm + jl] * d.ldp;
-    for (int i = lane; i < r; i += 32) dst[i] = wval(jl, i);
-  }
-  // ... and its transpose into the neighbours' rows (one thread per column)
-  for (int jl = tid; jl < nc; jl += NT) {
-    const int e = tcol[jl];
-    const CpqrNbr<T> nb = nbr[e];
-    const int cc = j0 + jl - cstart[e];
-    for (int i = 0; i < r; ++i) nb.Rq[cc + (size_t)(nb.off_qp + i) * nb.ldq] = wval(jl, i);
-  }
-  // A_cc = I: column j by warp j of the cluster, lanes over rows
-  for (int j = rank * NW + warp; j < r; j += C * NW) {
-    T* dst = d.Rp + (size_t)j * d.ldp;
-    for (int i = lane; i < r; i += 32) dst[i] = (i == j) ? T(1) : T(0);
-  }
-  // ---- Q_pc = H_0 ... H_{r-1} [I_r; 0]
-  if (C == 1) {
-    __syncthreads();
-    if (np <= 32 * 16) cq_form_q_any<T, true>(d, nullptr, chunk, L, j0, piv_s, scal_s, tau_s, r, np, 0, 1);
-  } else {
-    // the reflectors live in the owners' chunks: every CTA writes its own
-    // retired columns to V (column k = v_k, rows >= k), then each copies V
-    // into its chunk space when it fits
-    for (int k = warp; k < r; k += NW) {
-      const int jl = piv_s[k] - j0;
-      if (jl < 0 || jl >= nc) continue;
-      const T* pc = chunk + (size_t)jl * L;
-      const T sc = scal_s[k];
-      for (int i = k + lane; i < np; i += 32) d.V[i + (size_t)k * np] = i == k ? T(1) : pc[i] * sc;
-    }
-    cluster.sync();  // every V column is written; no CTA reads another's chunk any more
-    const T* Vsrc = d.V;
-    if (RES && (size_t)np * r <= (size_t)L * cols_per) {
-      T* Vs = schunk;
-      for (int kb = warp * 8; kb < r; kb += NW * 8)
-        for (int i = lane; i < np; i += 32) {
-          T v[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) v[u] = (kb + u < r && i >= kb + u) ? __ldcg(d.V + i + (size_t)(kb + u) * np) : T(0);
-#pragma unroll
-          for (int u = 0; u < 8; ++u)
-            if (kb + u < r) Vs[i + (size_t)(kb + u) * np] = v[u];
-        }
-      __syncthreads();
-      Vsrc = Vs;
-    }
-    if (np <= 32 * 16) cq_form_q_any<T, false>(d, Vsrc, nullptr, L, j0, piv_s, scal_s, tau_s, r, np, rank, C);
-  }
-  if (np > 32 * 16) {  // tall interfaces: V in global memory, the column of Q in global memory
-    if (C == 1) {
-      for (int k = warp; k < r; k += NW) {
-        const T* pc = chunk + (size_t)(piv_s[k] - j0) * L;
-        const T sc = scal_s[k];
-        for (int i = k + lane; i < np; i += 32) d.V[i + (size_t)k * np] = i == k ? T(1) : pc[i] * sc;
-      }
-      __syncthreads();
-    }
-    for (int c = rank * NW + warp; c < r; c += C * NW) {
-      T* col = d.Qc + (size_t)c * np;
-      for (int i = lane; i < np; i += 32) col[i] = (i == c) ? T(1) : T(0);
-      __syncwarp();
-      for (int k = c; k >= 0; --k) {
-        const T tk = tau_s[k];
-        if (tk == T(0)) continue;
-        const T* v = d.V + (size_t)k * np;
-        T w = 0;
-        for (int i = k + lane; i < np; i += 32) w += __ldcg(v + i) * col[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-        w *= tk;
-        for (int i = k + lane; i < np; i += 32) col[i] -= w * __ldcg(v + i);
-        __syncwarp();
-      }
-    }
-  }
-  if (rank == 0 && tid == 0) cur_size[d.p] = r;
-  if (C > 1) cluster.sync();  // no CTA leaves while others may still read its shared memory
+  cq_finish<T, RES, NT>(d, cluster, C, rank, chunk, schunk, L, np, r, nc, j0, cols_per, cpm, tcol, rstep, beta_s,
+                        scal_s, tau_s, piv_s, nbr, cstart, cur_size);
 }
 
 }  // namespace spand

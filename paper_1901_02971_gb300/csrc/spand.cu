@@ -13,13 +13,17 @@
 #include <numeric>
 #include <stdexcept>
 #include <string>
+#include <climits>
 #include <functional>
+#include <map>
+#include <tuple>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
 #include <vector>
 
 #include "cpqr_cluster.cuh"
+#include "cpqr_reg.cuh"
 #include "factor_kernels.cuh"
 #include "solve_kernels.cuh"
 #include "spand_internal.h"
@@ -642,6 +646,74 @@ struct StepTimer {
   }
 };
 
+// Register-resident sparsification (FP32 factors): 512 threads per CTA, 64
+// rows per lane, lane groups of G = 1..8 lanes per column, so an interface
+// of np <= 512 rows and m columns takes ceil(m / (512 / G)) CTAs (<= 16).
+constexpr int kCqrThreads = 512;
+constexpr int kCqrRows = 64;
+constexpr int kCqrMaxCluster = 16;
+
+template <typename T>
+static const void* cpqr_reg_kernel(int G) {
+  if constexpr (sizeof(T) != 4) {
+    return nullptr;
+  } else {
+    switch (G) {
+      case 1: return (const void*)k_cpqr_reg<float, kCqrThreads, 1, kCqrRows>;
+      case 2: return (const void*)k_cpqr_reg<float, kCqrThreads, 2, kCqrRows>;
+      case 4: return (const void*)k_cpqr_reg<float, kCqrThreads, 4, kCqrRows>;
+      case 8: return (const void*)k_cpqr_reg<float, kCqrThreads, 8, kCqrRows>;
+      default: return nullptr;
+    }
+  }
+}
+
+template <typename T>
+static size_t cpqr_reg_smem(int G, int nnb, int np, int cols_per, int C) {
+  switch (G) {
+    case 1: return cqr_smem<T, kCqrThreads, 1, kCqrRows>(nnb, np, cols_per, C);
+    case 2: return cqr_smem<T, kCqrThreads, 2, kCqrRows>(nnb, np, cols_per, C);
+    case 4: return cqr_smem<T, kCqrThreads, 4, kCqrRows>(nnb, np, cols_per, C);
+    default: return cqr_smem<T, kCqrThreads, 8, kCqrRows>(nnb, np, cols_per, C);
+  }
+}
+
+static std::mutex g_cqr_mutex;  // guards the cached cluster capacities
+
+// How many clusters of C register-resident CTAs (lane groups of G) can be
+// resident at once on this device (0 when the shape cannot launch).
+template <typename T>
+static int cpqr_reg_capacity(int G, int C) {
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lk(g_cqr_mutex);
+  static std::map<std::tuple<int, int, int>, int> cached;
+  auto it = cached.find({dev, G, C});
+  if (it != cached.end()) return it->second;
+  const void* fn = cpqr_reg_kernel<T>(G);
+  int n = 0;
+  if (fn) {
+    const size_t smem = 227 * 1024;  // one CTA per SM either way (registers)
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
+        (C <= 8 || cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess)) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)C, 1, 1);
+      cfg.blockDim = dim3((unsigned)kCqrThreads, 1, 1);
+      cfg.dynamicSmemBytes = smem;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = (unsigned)C;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) n = 0;
+    }
+    cudaGetLastError();  // a refused query only means "not this shape"
+  }
+  cached[{dev, G, C}] = n;
+  return n;
+}
+
 // The sparsification kernel for a launch group: chunk in shared memory or
 // not, 256 or 512 threads per CTA.
 template <typename T>
@@ -1058,6 +1130,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       std::vector<CpqrNbr<T>> nbrs;
       std::vector<int> tclass;  // cluster size of each task
       std::vector<int> tres;    // 1: the task's chunk lives in shared memory
+      std::vector<int> treg;    // lane-group size of the register-resident kernel (0: chunked kernel)
       const int ncol = st.ncolours();
       size_t wbytes = 0;
       struct WOff { size_t nrm, v, tau, qc, gw; };
@@ -1116,7 +1189,44 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         tasks.push_back(tk);
         tclass.push_back(C);
         tres.push_back(resident ? 1 : 0);
+        treg.push_back(0);
         cp_cluster.push_back(p);
+      }
+      // Colours whose interfaces all fit in one wave of register-resident
+      // clusters run on that kernel (FP32 factors only): its reflector steps
+      // are cheaper, but its CTAs fill whole SMs, so a colour that would need
+      // a second wave keeps the chunked kernel.
+      if (sizeof(T) == 4 && !tasks.empty()) {
+        std::vector<int> rg(tasks.size(), 0), rc(tasks.size(), 0);
+        for (size_t i = 0; i < tasks.size(); ++i) {
+          int G = 1;
+          while (G * kCqrRows < tasks[i].np && G < 8) G *= 2;
+          const int C = (tasks[i].m_max + kCqrThreads / G - 1) / (kCqrThreads / G);
+          if (G * kCqrRows >= tasks[i].np && C >= 1 && C <= kCqrMaxCluster) rg[i] = G, rc[i] = C;
+        }
+        const int nc_ = std::max(ncol, 1);
+        std::vector<int> need(nc_, 0), cap(nc_, INT_MAX);
+        std::vector<char> ok(nc_, 1);
+        int capc[4][kCqrMaxCluster + 1];  // SMs of one wave, per (G, C), looked up once
+        for (auto& row : capc)
+          for (int& v : row) v = -1;
+        for (size_t i = 0; i < tasks.size(); ++i) {
+          const int c = st.colour[tasks[i].p];
+          if (!ok[c]) continue;
+          if (!rg[i]) { ok[c] = 0; continue; }
+          need[c] += rc[i];
+          int& cc = capc[rg[i] == 1 ? 0 : rg[i] == 2 ? 1 : rg[i] == 4 ? 2 : 3][rc[i]];
+          if (cc < 0) cc = cpqr_reg_capacity<T>(rg[i], rc[i]) * rc[i];
+          cap[c] = std::min(cap[c], cc);
+        }
+        for (size_t i = 0; i < tasks.size(); ++i) {
+          const int c = st.colour[tasks[i].p];
+          if (ok[c] && need[c] <= cap[c]) {
+            treg[i] = rg[i];
+            tclass[i] = rc[i];
+            tres[i] = 1;
+          }
+        }
       }
       if (!tasks.empty()) {
         char* wb = (char*)h->scratch[(t + 1) & 1].ensure(wbytes);
@@ -1128,26 +1238,35 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
           cp_qc.push_back(tasks[i].Qc);
         }
         // launch groups: (colour, cluster size)
-        struct Group { int colour, C, res; std::vector<int32_t> ids; size_t smem = 0; int maxm = 0; };
+        struct Group { int colour, C, res, G = 0; std::vector<int32_t> ids; size_t smem = 0; int maxm = 0; };
+        // one pass: tasks bucketed by (colour, kernel, lane group, cluster
+        // size, residency); within a colour the register-resident groups come
+        // first
+        std::map<std::tuple<int, int, int, int, int>, Group> buckets;
+        for (size_t i = 0; i < tasks.size(); ++i) {
+          const int c = st.colour[tasks[i].p], C = tclass[i], Gr = treg[i], res = tres[i];
+          Group& g = buckets[std::make_tuple(c, Gr ? 0 : 1, Gr, C, -res)];
+          if (g.ids.empty()) {
+            g.colour = c;
+            g.C = C;
+            g.res = res;
+            g.G = Gr;
+          }
+          g.ids.push_back((int32_t)i);
+          const int np_ = tasks[i].np, mm = tasks[i].m_max, nnb_ = tasks[i].nend - tasks[i].nbeg;
+          size_t need;
+          if (Gr) {
+            need = cpqr_reg_smem<T>(Gr, nnb_, np_, (mm + C - 1) / C, C);
+          } else {
+            need = cq_fixed_smem<T>(nnb_, np_, (mm + C - 1) / C, C);
+            if (res) need += (size_t)cq_ld<T>(np_) * ((mm + C - 1) / C) * sizeof(T);
+          }
+          g.smem = std::max(g.smem, need);
+          g.maxm = std::max(g.maxm, mm);
+        }
         std::vector<Group> groups;
-        for (int c = 0; c < std::max(ncol, 1); ++c)
-          for (int res = 1; res >= 0; --res)
-            for (int C = 1; C <= kCpqrMaxCluster; C *= 2) {
-              Group g;
-              g.colour = c;
-              g.C = C;
-              g.res = res;
-              for (size_t i = 0; i < tasks.size(); ++i)
-                if (st.colour[tasks[i].p] == c && tclass[i] == C && tres[i] == res) {
-                  g.ids.push_back((int32_t)i);
-                  const int np_ = tasks[i].np, mm = tasks[i].m_max;
-                  size_t need = cq_fixed_smem<T>(tasks[i].nend - tasks[i].nbeg, np_, (mm + C - 1) / C, C);
-                  if (res) need += (size_t)cq_ld<T>(np_) * ((mm + C - 1) / C) * sizeof(T);
-                  g.smem = std::max(g.smem, need);
-                  g.maxm = std::max(g.maxm, mm);
-                }
-              if (!g.ids.empty()) groups.push_back(std::move(g));
-            }
+        groups.reserve(buckets.size());
+        for (auto& kv : buckets) groups.push_back(std::move(kv.second));
         std::vector<int32_t> list;
         std::vector<size_t> gbeg;
         for (auto& g : groups) {
@@ -1175,8 +1294,12 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
             // SMs (several CTAs per SM), unless the columns per CTA need 512
             const int cpg = (G.maxm + G.C - 1) / G.C;
             const bool one_wave = G.ids.size() * (size_t)G.C <= (size_t)num_sms();
-            const int nt = ((G.C <= 2 && one_wave) || cpg > CQ_CPT * 256) ? 512 : 256;
+            int nt = ((G.C <= 2 && one_wave) || cpg > CQ_CPT * 256) ? 512 : 256;
             const void* fn = cpqr_kernel<T>(G.res != 0, nt);
+            if (G.G) {
+              nt = kCqrThreads;
+              fn = cpqr_reg_kernel<T>(G.G);
+            }
             ensure_smem(fn, smem);
             if (G.C > 8) ensure_nonportable_cluster(fn);
             cudaLaunchConfig_t cfg = {};
@@ -1212,6 +1335,11 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         CK(cudaStreamSynchronize(s));
         std::copy(hcur, hcur + n, sz_after.begin());
         h->stage.reset();  // every copy issued so far has executed
+        for (size_t i = 0; i < tasks.size(); ++i) {
+          const int rr = sz_after[tasks[i].p];
+          if (rr == -2) throw Fail{SPAND_ERR_TIMEOUT, "sparsification: a cluster exchange timed out"};
+          if (rr < 0) throw Fail{SPAND_ERR_STATE, "sparsification: launch shape refused by the kernel"};
+        }
         check_pivots(t);
       }
       for (int sidx : seps) sz_after[sidx] = 0;
