@@ -143,10 +143,10 @@ HBM_BOUND = {"copy", "apply", "pcg"}
 # counters were taken on: a changed kernel reports null until re-measured.
 # The capture and its command are summarised under profiles/ (DRAM traffic, 64^3).
 MEASURED_TRAFFIC = {
-    "cpqr": {"bytes_per_launch": 531.8e6 / 155,
+    "cpqr": {"bytes_per_launch": (564.8e6 + 11.0e6) / 212,
              "src": ["paper_1901_02971_gb300/csrc/cpqr_cluster.cuh", "paper_1901_02971_gb300/csrc/cpqr_reg.cuh"],
-             "sha256": ["afed2487a6de0008bf48db37f059975772761f8fb2c6fa98c301f169ff23bc70",
-                        "e766394825e5569cca9f0d738cfed1b62fe8de88c7db8f6385d55f2d9d71e4d5"]},
+             "sha256": ["df81cb4f3a486696ea2b0dca01faaa4bbbe9a536c9f9ac17555724540692795e",
+                        "2e82245239d77d096745e58d855d3fa1e2b7ed0c039d23a4e2551d5401927287"]},
     "apply": {"bytes_per_launch": (2067.7e6 + 27.9e6) / 2, "src": "paper_1901_02971_gb300/csrc/solve_kernels.cuh",
               "sha256": "24edc4406567191d811d97b17722572c1630b4225aa648ce84d1856b9ea2db56"},
 }

@@ -49,8 +49,8 @@ struct CpqrTask {
   T* Rp;              // p's block row (leading dimension ldp)
   T* gwork;           // global chunk storage when it does not fit in shared memory: C * L * cols_per
   T* V;               // np x np capacity, column k = v_k (v_k[k] = 1, rows above k unused)
-  T* tau;             // np (unused: every CTA keeps the taus in shared memory)
-  T* Qc;              // np x np capacity; first r columns = Q_pc on exit
+  T* tau;             // np: tau_k of the reflectors, for k_form_q
+  T* Qc;              // np x np capacity; first r columns = Q_pc after k_form_q
   int32_t p, np, ldp, nbeg, nend, m_max;
 };
 
@@ -223,12 +223,12 @@ __device__ __forceinline__ void cq_form_q_any(const CpqrTask<T>& d, const T* V, 
 
 // Epilogue shared by the sparsification kernels, entered after a block barrier
 // with the CTA's final columns in `chunk` (column-major, stride L): the write-back
-// of W_cn into p's and the neighbours' block rows, A_cc = I, the coarse basis
-// Q_pc, and the rank in cur_size[p].
-template <typename T, bool RES, int NT>
+// of W_cn into p's and the neighbours' block rows, A_cc = I, the reflectors
+// (V, tau) from which k_form_q forms Q_pc, and the rank in cur_size[p].
+template <typename T, int NT>
 __device__ __forceinline__ void cq_finish(const CpqrTask<T>& d, cg::cluster_group& cluster, int C, int rank,
-                                          T* chunk, T* schunk, int L, int np, int r, int nc, int j0,
-                                          int cols_per, int cpm, const int* tcol, const int* rstep,
+                                          const T* chunk, int L, int np, int r, int nc, int j0,
+                                          int cpm, const int* tcol, const int* rstep,
                                           const T* beta_s, const T* scal_s, const T* tau_s, const int* piv_s,
                                           const CpqrNbr<T>* nbr, const int* cstart, int32_t* cur_size) {
   constexpr int NW = NT / 32;
@@ -258,68 +258,19 @@ __device__ __forceinline__ void cq_finish(const CpqrTask<T>& d, cg::cluster_grou
     T* dst = d.Rp + (size_t)j * d.ldp;
     for (int i = lane; i < r; i += 32) dst[i] = (i == j) ? T(1) : T(0);
   }
-  // ---- Q_pc = H_0 ... H_{r-1} [I_r; 0]
-  if (C == 1) {
-    __syncthreads();
-    if (np <= 32 * 16) cq_form_q_any<T, true>(d, nullptr, chunk, L, j0, piv_s, scal_s, tau_s, r, np, 0, 1);
-  } else {
-    // the reflectors live in the owners' chunks: every CTA writes its own
-    // retired columns to V (column k = v_k, rows >= k), then each copies V
-    // into its chunk space when it fits
-    for (int k = warp; k < r; k += NW) {
-      const int jl = piv_s[k] - j0;
-      if (jl < 0 || jl >= nc) continue;
-      const T* pc = chunk + (size_t)jl * L;
-      const T sc = scal_s[k];
-      for (int i = k + lane; i < np; i += 32) d.V[i + (size_t)k * np] = i == k ? T(1) : pc[i] * sc;
-    }
-    cluster.sync();  // every V column is written; no CTA reads another's chunk any more
-    const T* Vsrc = d.V;
-    if (RES && (size_t)np * r <= (size_t)L * cols_per) {
-      T* Vs = schunk;
-      for (int kb = warp * 8; kb < r; kb += NW * 8)
-        for (int i = lane; i < np; i += 32) {
-          T v[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) v[u] = (kb + u < r && i >= kb + u) ? __ldcg(d.V + i + (size_t)(kb + u) * np) : T(0);
-#pragma unroll
-          for (int u = 0; u < 8; ++u)
-            if (kb + u < r) Vs[i + (size_t)(kb + u) * np] = v[u];
-        }
-      __syncthreads();
-      Vsrc = Vs;
-    }
-    if (np <= 32 * 16) cq_form_q_any<T, false>(d, Vsrc, nullptr, L, j0, piv_s, scal_s, tau_s, r, np, rank, C);
+  // ---- the reflectors, for k_form_q: v_k (rows >= k, v_k[k] = 1) into
+  // column k of V by the CTA that holds pivot column k, tau by rank 0
+  for (int k = warp; k < r; k += NW) {
+    const int jl = piv_s[k] - j0;
+    if (jl < 0 || jl >= nc) continue;
+    const T* pc = chunk + (size_t)jl * L;
+    const T sc = scal_s[k];
+    for (int i = k + lane; i < np; i += 32) d.V[i + (size_t)k * np] = i == k ? T(1) : pc[i] * sc;
   }
-  if (np > 32 * 16) {  // tall interfaces: V in global memory, the column of Q in global memory
-    if (C == 1) {
-      for (int k = warp; k < r; k += NW) {
-        const T* pc = chunk + (size_t)(piv_s[k] - j0) * L;
-        const T sc = scal_s[k];
-        for (int i = k + lane; i < np; i += 32) d.V[i + (size_t)k * np] = i == k ? T(1) : pc[i] * sc;
-      }
-      __syncthreads();
-    }
-    for (int c = rank * NW + warp; c < r; c += C * NW) {
-      T* col = d.Qc + (size_t)c * np;
-      for (int i = lane; i < np; i += 32) col[i] = (i == c) ? T(1) : T(0);
-      __syncwarp();
-      for (int k = c; k >= 0; --k) {
-        const T tk = tau_s[k];
-        if (tk == T(0)) continue;
-        const T* v = d.V + (size_t)k * np;
-        T w = 0;
-        for (int i = k + lane; i < np; i += 32) w += __ldcg(v + i) * col[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-        w *= tk;
-        for (int i = k + lane; i < np; i += 32) col[i] -= w * __ldcg(v + i);
-        __syncwarp();
-      }
-    }
-  }
+  if (rank == 0)
+    for (int k = tid; k < r; k += NT) d.tau[k] = tau_s[k];
   if (rank == 0 && tid == 0) cur_size[d.p] = r;
-  if (C > 1) cluster.sync();  // no CTA leaves while others may still read its shared memory
+  if (C > 1) cluster.sync();  // no CTA leaves while another may still address its shared memory
 }
 
 // Per reflector step k:
@@ -392,12 +343,9 @@ __global__ void __launch_bounds__(NT) k_cpqr_cluster(const CpqrTask<T>* __restri
   }
   __syncthreads();
   const int m = cstart[nnb];
-  if (m == 0) {  // every neighbour reduced to nothing: p is kept as it is
+  if (m == 0) {  // every neighbour reduced to nothing: p is kept as it is (Q_pc = I, all tau = 0)
     if (rank == 0) {
-      for (int64_t x = tid; x < (int64_t)np * np; x += NT) {
-        const int i = (int)(x % np), j = (int)(x / np);
-        d.Qc[i + (size_t)j * np] = (i == j) ? T(1) : T(0);
-      }
+      for (int k = tid; k < np; k += NT) d.tau[k] = T(0);
       if (tid == 0) cur_size[d.p] = np;
     }
     return;  // uniform across the cluster (m is the same for every CTA)
@@ -616,8 +564,61 @@ __global__ void __launch_bounds__(NT) k_cpqr_cluster(const CpqrTask<T>* __restri
     }
   }
   __syncthreads();
-  cq_finish<T, RES, NT>(d, cluster, C, rank, chunk, schunk, L, np, r, nc, j0, cols_per, cpm, tcol, rstep, beta_s,
-                        scal_s, tau_s, piv_s, nbr, cstart, cur_size);
+  cq_finish<T, NT>(d, cluster, C, rank, chunk, L, np, r, nc, j0, cpm, tcol, rstep, beta_s, scal_s, tau_s, piv_s,
+                   nbr, cstart, cur_size);
+}
+
+
+// Q_pc = H_0 ... H_{r-1} [I_r; 0] (Sec. 2.6.1) of interfaces whose QR kernel
+// has finished, from the reflectors it left in V and tau and the rank in
+// cur_size[p].  Launched per colour on a side stream, so that it overlaps the
+// next colour's QR; it is off the sparsification's critical path.  Block b of
+// an interface (nb blocks each) takes the column pairs (c, c + nb NW) with
+// c = b NW + warp (mod 2 nb NW), so every block meets chains of every length;
+// V is copied into shared memory when it fits (smem_elems elements).
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_form_q(const CpqrTask<T>* __restrict__ tasks,
+                                                 const int32_t* __restrict__ list,
+                                                 const int32_t* __restrict__ cur_size, int nb, int smem_elems) {
+  constexpr int NW = NT / 32;
+  const CpqrTask<T> d = tasks[list[blockIdx.x / nb]];
+  const int b = blockIdx.x % nb;
+  const int np = d.np, r = cur_size[d.p];
+  if (r <= 0 || b * NW >= r) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* tau_s = reinterpret_cast<T*>(smraw);
+  T* vs = tau_s + cq_al16((size_t)r * sizeof(T)) / sizeof(T);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int k = tid; k < r; k += NT) tau_s[k] = d.tau[k];
+  const T* Vsrc = d.V;
+  const size_t nv = (size_t)np * r;
+  if (np <= 32 * 16 && (size_t)(vs - tau_s) + nv <= (size_t)smem_elems) {
+    for (size_t e = tid; e < nv; e += NT) vs[e] = __ldcg(d.V + e);  // rows < k of column k are never read
+    Vsrc = vs;
+  }
+  __syncthreads();
+  if (np <= 32 * 16) {
+    cq_form_q_any<T, false>(d, Vsrc, nullptr, 0, 0, nullptr, nullptr, tau_s, r, np, b, nb);
+    return;
+  }
+  // tall interfaces: one warp per column, V and the column in global memory
+  for (int c = b * NW + warp; c < r; c += nb * NW) {
+    T* col = d.Qc + (size_t)c * np;
+    for (int i = lane; i < np; i += 32) col[i] = (i == c) ? T(1) : T(0);
+    __syncwarp();
+    for (int k = c; k >= 0; --k) {
+      const T tk = tau_s[k];
+      if (tk == T(0)) continue;
+      const T* v = d.V + (size_t)k * np;
+      T w = 0;
+      for (int i = k + lane; i < np; i += 32) w += __ldcg(v + i) * col[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+      w *= tk;
+      for (int i = k + lane; i < np; i += 32) col[i] -= w * __ldcg(v + i);
+      __syncwarp();
+    }
+  }
 }
 
 }  // namespace spand

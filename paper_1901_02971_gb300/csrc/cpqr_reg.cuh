@@ -27,7 +27,7 @@
 // A retired pivot column keeps the raw values from which its reflector is
 // derived; at the end every group stores its column into the shared chunk
 // (column-major, stride cq_ld(np)) and the chunked kernel's epilogue writes
-// W_cn, A_cc = I and Q_pc.
+// W_cn, A_cc = I and the reflectors (Q_pc is formed by k_form_q).
 #pragma once
 
 #include <type_traits>
@@ -213,12 +213,9 @@ __global__ void __launch_bounds__(NT, 1) k_cpqr_reg(const CpqrTask<T>* __restric
   }
   __syncthreads();
   const int m = cstart[nnb];
-  if (m == 0) {  // every neighbour reduced to nothing: p is kept as it is
+  if (m == 0) {  // every neighbour reduced to nothing: p is kept as it is (Q_pc = I, all tau = 0)
     if (rank == 0) {
-      for (int64_t x = tid; x < (int64_t)np * np; x += NT) {
-        const int i = (int)(x % np), j = (int)(x / np);
-        d.Qc[i + (size_t)j * np] = (i == j) ? T(1) : T(0);
-      }
+      for (int k = tid; k < np; k += NT) d.tau[k] = T(0);
       if (tid == 0) cur_size[d.p] = np;
     }
     return;
@@ -249,18 +246,14 @@ __global__ void __launch_bounds__(NT, 1) k_cpqr_reg(const CpqrTask<T>* __restric
   auto xbytes = [&](int k) -> unsigned {
     return (unsigned)C * (unsigned)(G * (cbe - k / (8 * G)) * 8 * (int)sizeof(T) + (int)sizeof(CqrRec<T>));
   };
-  if (C > 1) {
-    if (tid == 0) {
-      cqr_bar_init(&sh.bar[0]);
-      cqr_bar_init(&sh.bar[1]);
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-      cqr_bar_expect(&sh.bar[0], xbytes(0));
-      if (kmax > 1) cqr_bar_expect(&sh.bar[1], xbytes(1));
-    }
-    cluster.sync();  // every CTA's barriers are armed before anyone sends
-  } else {
-    __syncthreads();
+  if (C > 1 && tid == 0) {  // visible to the cluster at the barrier after the register load
+    cqr_bar_init(&sh.bar[0]);
+    cqr_bar_init(&sh.bar[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    cqr_bar_expect(&sh.bar[0], xbytes(0));
+    if (kmax > 1) cqr_bar_expect(&sh.bar[1], xbytes(1));
   }
+  __syncthreads();
   bool timed_out = false;
   // ---- gather my columns of A_pn into the staging chunk (8 columns per warp
   // pass, lanes over rows, all loads before the stores)
@@ -298,7 +291,11 @@ __global__ void __launch_bounds__(NT, 1) k_cpqr_reg(const CpqrTask<T>* __restric
     s = cqr_group_sum<G>(s, gmask);
     nrm = own ? s : T(-1);
   }
-  __syncthreads();  // the staging chunk becomes the pivot slots
+  // the staging chunk becomes the pivot slots, into which the other CTAs of
+  // the cluster store from step 0 on: no CTA sends before every CTA has
+  // loaded its columns and armed its barriers
+  if (C > 1) cluster.sync();
+  else __syncthreads();
 
   int r = kmax;
   T r00 = T(0);
@@ -493,8 +490,8 @@ __global__ void __launch_bounds__(NT, 1) k_cpqr_reg(const CpqrTask<T>* __restric
     }
   }
   __syncthreads();
-  cq_finish<T, true, NT>(d, cluster, C, rank, chunk, uni, L, np, r, nc, j0, cols_per, cpm, tcol, rstep, beta_s,
-                         scal_s, tau_s, piv_s, nbr, cstart, cur_size);
+  cq_finish<T, NT>(d, cluster, C, rank, chunk, L, np, r, nc, j0, cpm, tcol, rstep, beta_s, scal_s, tau_s, piv_s,
+                   nbr, cstart, cur_size);
   // after the epilogue's last cluster barrier, so that it follows rank 0's
   // store of the rank
   if (timed_out && threadIdx.x == 0) cur_size[d.p] = -2;

@@ -384,6 +384,8 @@ struct spand_handle_s {
   std::vector<std::vector<int32_t>> sizes_before, sizes_after;
   cudaStream_t aux[kAuxStreams] = {};
   cudaEvent_t ev_fork = nullptr, ev_join[kAuxStreams] = {};
+  cudaStream_t qs = nullptr;                         // Q_pc formation, one colour behind the QR kernels
+  cudaEvent_t ev_q = nullptr, ev_qdone = nullptr;
   KProf prof;
   // the preconditioner apply program (phases of every step, on the device);
   // one cooperative launch of k_apply runs it
@@ -395,6 +397,9 @@ struct spand_handle_s {
   ~spand_handle_s() {
     for (auto& a : aux)
       if (a) cudaStreamDestroy(a);
+    if (qs) cudaStreamDestroy(qs);
+    if (ev_q) cudaEventDestroy(ev_q);
+    if (ev_qdone) cudaEventDestroy(ev_qdone);
     if (ev_fork) cudaEventDestroy(ev_fork);
     for (auto& e : ev_join)
       if (e) cudaEventDestroy(e);
@@ -472,6 +477,9 @@ static Layout<T> make_layout(spand_handle h, int t, const std::vector<int32_t>& 
 static void ensure_streams(spand_handle h) {
   if (h->ev_fork) return;
   for (auto& a : h->aux) CK(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&h->qs, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&h->ev_q, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&h->ev_qdone, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
   for (auto& e : h->ev_join) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
 }
@@ -1279,6 +1287,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         ensure_streams(h);
         cpqr_pid = h->prof.begin(F_CPQR, s);
         size_t gi = 0;
+        int64_t nformq = 0;  // k_form_q launches (one per colour)
         while (gi < groups.size()) {  // one colour at a time; its groups run side by side
           size_t ge = gi;
           while (ge < groups.size() && groups[ge].colour == groups[gi].colour) ++ge;
@@ -1324,10 +1333,39 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
           }
           for (size_t g = gi; g < std::min(ge, gi + (size_t)kAuxStreams); ++g)
             CK(cudaStreamWaitEvent(s, h->ev_join[(g - gi) % kAuxStreams], 0));
+          // Q_pc of this colour's interfaces on the side stream, overlapping
+          // the next colour's QR (nothing in the factorization reads Q_pc
+          // before the compaction below)
+          {
+            constexpr int NTQ = 256, NWQ = NTQ / 32;
+            const size_t l0 = gbeg[gi], l1 = ge < groups.size() ? gbeg[ge] : list.size();
+            int kmx = 0;
+            size_t need = 0;
+            for (size_t li = l0; li < l1; ++li) {
+              const CpqrTask<T>& tk = tasks[list[li]];
+              const int km = std::min(tk.np, tk.m_max);
+              kmx = std::max(kmx, km);
+              need = std::max(need, align256((size_t)km * sizeof(T)) + (size_t)tk.np * km * sizeof(T));
+            }
+            const size_t qsm = std::min(need + 256, (size_t)227 * 1024);
+            const int nb = std::max(1, (kmx + 2 * NWQ - 1) / (2 * NWQ));
+            const void* fq = (const void*)k_form_q<T, NTQ>;
+            ensure_smem(fq, qsm);
+            CK(cudaEventRecord(h->ev_q, s));
+            CK(cudaStreamWaitEvent(h->qs, h->ev_q, 0));
+            const CpqrTask<T>* q0 = at<const CpqrTask<T>>(d, ot);
+            const int32_t* q1 = at<const int32_t>(d, ol) + l0;
+            const int q3 = nb, q4 = (int)(qsm / sizeof(T));
+            void* qargs[] = {(void*)&q0, (void*)&q1, (void*)&d_cur, (void*)&q3, (void*)&q4};
+            CK(cudaLaunchKernel(fq, dim3((unsigned)((l1 - l0) * nb)), dim3(NTQ), qargs, qsm, h->qs));
+            ++nformq;
+          }
           gi = ge;
         }
-        h->prof.launches += (int64_t)groups.size();
-        h->prof.end(cpqr_pid, s, 0.0, 0.0, (int64_t)groups.size());
+        CK(cudaEventRecord(h->ev_qdone, h->qs));
+        CK(cudaStreamWaitEvent(s, h->ev_qdone, 0));
+        h->prof.launches += (int64_t)groups.size() + nformq;
+        h->prof.end(cpqr_pid, s, 0.0, 0.0, (int64_t)groups.size() + nformq);
         build_elim_ops();  // host work overlapped with the sparsification kernels
         run_pending();
         int32_t* hcur = (int32_t*)h->stage.take((size_t)n * sizeof(int32_t));
