@@ -230,6 +230,9 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--grid", type=int, default=GRID, help="cube edge (small cases for profiling only)")
     ap.add_argument("--levels", type=int, default=LEVELS)
+    ap.add_argument("--form", default="fp32", choices=["fp32", "tf32", "bf16"],
+                    help="mixed form that is timed and reported as the headline (FP32 factor; Schur GEMMs on the "
+                         "SIMT pipes, or on the tensor cores with TF32 / BF16 operands)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -311,7 +314,7 @@ def main():
         s.set_profiling(False)
         return s.kernel_profile()
 
-    s32, t32, it32, rr32, clocks, launches32 = run_form("fp32", args.steps, args.warmup, timed_clocks=True)
+    s32, t32, it32, rr32, clocks, launches32 = run_form(args.form, args.steps, args.warmup, timed_clocks=True)
     st32 = s32.stats()
     ph32 = s32.phase_times()
     prof32 = kernel_profile(s32)
@@ -321,7 +324,7 @@ def main():
     sweep = {"0": {"s_per_step": statistics.mean(t32), "iters": it32[-1], "size_top": s32.stats().size_top,
                    "mem_f": s32.stats().mem_f}}
     for sk in (2, 4):
-        ss, ts, its, _, _, _ = run_form("fp32", 2, 1, skip=sk)
+        ss, ts, its, _, _, _ = run_form(args.form, 2, 1, skip=sk)
         sst = ss.stats()
         sweep[str(sk)] = {"s_per_step": statistics.mean(ts), "iters": its[-1], "size_top": sst.size_top,
                           "mem_f": sst.mem_f}
@@ -356,12 +359,15 @@ def main():
     out = {
         "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
+        "dtype": {"fp32": "f32", "tf32": "f32 (tf32 Schur operands)", "bf16": "f32 (bf16 Schur operands)"}[args.form],
+        "data": "synthetic",
         "config": {"workload": workload, "N": p.n, "nnz": p.nnz, "levels": levels, "eps": EPS,
-                   "factor": "fp32 (mixed), PCG fp64", "parallelism": f"replicas x{world}",
+                   "factor": {"fp32": "fp32 (mixed)", "tf32": "fp32, Schur GEMMs tf32 on tensor cores",
+                              "bf16": "fp32, Schur GEMMs bf16 on tensor cores"}[args.form] + ", PCG fp64",
+                   "parallelism": f"replicas x{world}",
                    "l2": "256 MB L2 flush between timed steps; factor data > 129 MB"},
         "forms": {
-            "mixed_fp32": {"s_per_step": v, "iters": it32[-1], "relres": rr32, "t_factor_ms_phases": list(ph32[:4]),
+            "mixed_" + args.form: {"s_per_step": v, "iters": it32[-1], "relres": rr32, "t_factor_ms_phases": list(ph32[:4]),
                            "apply_ms": ph32[4], "size_top": st32.size_top, "mem_f": st32.mem_f,
                            "factor_gflop": st32.factor_flops / 1e9},
             "plain_fp64": {"s_per_step": statistics.mean(t64), "iters": it64[-1], "relres": rr64,
@@ -370,7 +376,7 @@ def main():
             "speedup_mixed_vs_fp64": statistics.mean(t64) / v,
             "x_rel_diff_mixed_vs_fp64": float(np.linalg.norm(x32 - x64) / np.linalg.norm(x64)),
             "true_relres_host": relres_host,
-            "skip_sweep_mixed_fp32": sweep,
+            "skip_sweep_mixed_" + args.form: sweep,
         },
         "e2e": {"value": ve, "unit": "s", "h2d_bytes_per_step": int(p.nnz * 8 + p.n * 8),
                 "d2h_bytes_per_step": int(p.n * 8)},

@@ -56,8 +56,12 @@ enum {
  * and the SpMV always run in FP64) */
 enum {
   SPAND_FP64 = 0,  /* plain: every factor kernel in FP64 */
-  SPAND_FP32 = 1   /* mixed: factor blocks, Schur GEMMs, QR and the
+  SPAND_FP32 = 1,  /* mixed: factor blocks, Schur GEMMs, QR and the
                       preconditioner apply in FP32; scaling pivots in FP64 */
+  SPAND_TF32 = 2,  /* as SPAND_FP32, with the elimination's Schur GEMMs on the
+                      tensor cores: TF32 operands, FP32 accumulation */
+  SPAND_BF16 = 3   /* as SPAND_TF32 with BF16 operands (FP32 accumulation,
+                      factor stored in FP32) */
 };
 
 typedef struct spand_handle_s* spand_handle;
@@ -67,7 +71,7 @@ typedef struct {
   double eps;         /* sparsification tolerance, >= 0 (0 = exact ND Cholesky) */
   int32_t skip;       /* no scaling / sparsification for the first `skip`
                          elimination steps counted from the leaves (Sec. 4.4) */
-  int32_t precision;  /* SPAND_FP64 or SPAND_FP32 */
+  int32_t precision;  /* SPAND_FP64, SPAND_FP32, SPAND_TF32 or SPAND_BF16 */
   int32_t maxit;      /* PCG iteration cap (paper: 500) */
   double tol;         /* PCG relative residual target (paper: 1e-12) */
 } spand_opts;

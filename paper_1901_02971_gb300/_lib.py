@@ -27,6 +27,8 @@ SPAND_ERR_STATE = 6
 SPAND_ERR_TIMEOUT = 7
 SPAND_FP64 = 0
 SPAND_FP32 = 1
+SPAND_TF32 = 2
+SPAND_BF16 = 3
 
 # every function declared in include/spand.h
 EXPORTS = ["spand_default_opts", "spand_analyze", "spand_analyze_batch", "spand_factorize", "spand_solve", "spand_apply",

@@ -25,6 +25,7 @@
 #include "cpqr_cluster.cuh"
 #include "cpqr_reg.cuh"
 #include "factor_kernels.cuh"
+#include "schur_tc.cuh"
 #include "solve_kernels.cuh"
 #include "spand_internal.h"
 
@@ -823,14 +824,16 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
   StepTimer tm(L);
   h->stage.reset();  // the previous factorization ended with a stream synchronisation
   // non-positive pivot flags per step: [2t] elimination pivots, [2t+1]
-  // scaling pivots; read at the next host synchronisation (the rank readback
-  // of a sparsifying step, or the end of the factorization)
+  // scaling pivots ([0]: a tensor-core wait of the Schur update timed out);
+  // read at the next host synchronisation (the rank readback of a
+  // sparsifying step, or the end of the factorization)
   int* d_info = (int*)h->descs.alloc(2 * (size_t)(L + 1) * sizeof(int));
   CK(cudaMemsetAsync(d_info, 0, 2 * (size_t)(L + 1) * sizeof(int), s));
   std::vector<std::vector<int>> elim_cls(L + 1), scale_cls(L + 1);  // cluster of each pivot-batch entry
   auto check_pivots = [&](int upto) {  // after a stream synchronisation
     std::vector<int> info(2 * (size_t)(L + 1), 0);
     CK(cudaMemcpy(info.data(), d_info, info.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    if (info[0]) throw Fail{SPAND_ERR_TIMEOUT, "Schur update: a tensor-core completion wait timed out"};
     for (int u = 1; u <= upto; ++u)
       if (info[2 * u] || info[2 * u + 1]) {
         stt.fail_step = u;
@@ -953,12 +956,16 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       if (!blocks.empty()) {
         std::vector<SchurContrib<T>> flat;
         std::vector<SchurTile> tiles;
+        // tensor cores for the TF32 / BF16 forms: 128 x 64 tiles; FP32 and
+        // FP64 on the SIMT pipes: 64 x 64 tiles
+        const bool tc = sizeof(T) == 4 && (h->opts.precision == SPAND_TF32 || h->opts.precision == SPAND_BF16);
+        const int ti = tc ? TC_M : TB, tj = tc ? TC_N : TB;
         for (size_t b = 0; b < blocks.size(); ++b) {
           blocks[b].cbeg = (int32_t)flat.size();
           flat.insert(flat.end(), contr[b].begin(), contr[b].end());
           blocks[b].cend = (int32_t)flat.size();
-          for (int i0 = 0; i0 < blocks[b].rows; i0 += TB)
-            for (int j0 = 0; j0 < blocks[b].cols; j0 += TB) tiles.push_back({(int32_t)b, i0, j0});
+          for (int i0 = 0; i0 < blocks[b].rows; i0 += ti)
+            for (int j0 = 0; j0 < blocks[b].cols; j0 += tj) tiles.push_back({(int32_t)b, i0, j0});
         }
         Packer pk;
         size_t ob = pk.add(blocks), oc = pk.add(flat), ot = pk.add(tiles);
@@ -971,8 +978,21 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
           by += ((double)(bl.rows + bl.cols) * ksum + (bl.C2 ? 3.0 : 2.0) * bl.rows * bl.cols) * sizeof(T);
         }
         const int pid = h->prof.begin(F_SCHUR, s);
-        k_schur<T><<<(unsigned)tiles.size(), NT, 0, s>>>(at<const SchurTile>(d, ot), at<const SchurBlock<T>>(d, ob),
-                                                        at<const SchurContrib<T>>(d, oc));
+        if constexpr (sizeof(T) == 4) {
+          if (tc) {
+            const void* fn = h->opts.precision == SPAND_BF16 ? (const void*)k_schur_tc<true> : (const void*)k_schur_tc<false>;
+            ensure_smem(fn, TC_SMEM);
+            const SchurTile* a0 = at<const SchurTile>(d, ot);
+            const SchurBlock<float>* a1 = at<const SchurBlock<float>>(d, ob);
+            const SchurContrib<float>* a2 = at<const SchurContrib<float>>(d, oc);
+            int* a3 = d_info;  // [0]: a bounded tensor-core wait gave up
+            void* args[] = {(void*)&a0, (void*)&a1, (void*)&a2, (void*)&a3};
+            CK(cudaLaunchKernel(fn, dim3((unsigned)tiles.size()), dim3(TC_NT), args, TC_SMEM, s));
+          }
+        }
+        if (!tc)
+          k_schur<T><<<(unsigned)tiles.size(), NT, 0, s>>>(at<const SchurTile>(d, ot), at<const SchurBlock<T>>(d, ob),
+                                                          at<const SchurContrib<T>>(d, oc));
         CKLAUNCH();
         h->prof.launches += 1;
         h->prof.end(pid, s, fl, by, 1);
@@ -1696,7 +1716,8 @@ int spand_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const
   if (opts->levels < 1 || opts->levels > 30) throw Fail{SPAND_ERR_INVALID_ARG, "levels must be in [1, 30]"};
   if (!(opts->eps >= 0.0)) throw Fail{SPAND_ERR_INVALID_ARG, "eps must be >= 0"};
   if (opts->skip < 0) throw Fail{SPAND_ERR_INVALID_ARG, "skip must be >= 0"};
-  if (opts->precision != SPAND_FP64 && opts->precision != SPAND_FP32)
+  if (opts->precision != SPAND_FP64 && opts->precision != SPAND_FP32 && opts->precision != SPAND_TF32 &&
+      opts->precision != SPAND_BF16)
     throw Fail{SPAND_ERR_INVALID_ARG, "unknown precision"};
   if (opts->maxit < 1 || !(opts->tol > 0.0)) throw Fail{SPAND_ERR_INVALID_ARG, "maxit >= 1 and tol > 0 required"};
   if (n > INT32_MAX - 1) throw Fail{SPAND_ERR_INVALID_ARG, "n too large"};

@@ -17,16 +17,20 @@ def _addr(a):
     return a.data_ptr()
 
 
+PRECISIONS = {"fp64": L.SPAND_FP64, "fp32": L.SPAND_FP32, "tf32": L.SPAND_TF32, "bf16": L.SPAND_BF16}
+
+
 class Solver:
     """analyze -> factorize -> solve on one CSR matrix.
 
     Parameters follow ``spand_opts``: levels (L of Algorithm 3), eps, skip,
-    precision ("fp64" or "fp32"), maxit, tol.
+    precision ("fp64", "fp32", or "tf32" / "bf16": FP32 factors whose Schur
+    GEMMs run on the tensor cores with TF32 / BF16 operands), maxit, tol.
     """
 
     def __init__(self, rowptr, colind, vals, coords=None, levels: int = 8, eps: float = 1e-2, skip: int = 0,
                  precision: str = "fp64", maxit: int = 500, tol: float = 1e-10):
-        prec = {"fp64": L.SPAND_FP64, "fp32": L.SPAND_FP32}[precision]
+        prec = PRECISIONS[precision]
         self.opts = L.default_opts(levels=levels, eps=eps, skip=skip, precision=prec, maxit=maxit, tol=tol)
         self.n = int(np.asarray(rowptr).size - 1)
         self.nnz = int(np.asarray(rowptr)[-1])
@@ -102,7 +106,7 @@ class Solver:
         Solver keyword arguments per problem."""
         opts = []
         for kw in opts_list:
-            prec = {"fp64": L.SPAND_FP64, "fp32": L.SPAND_FP32}[kw.get("precision", "fp64")]
+            prec = PRECISIONS[kw.get("precision", "fp64")]
             opts.append(L.default_opts(levels=kw.get("levels", 8), eps=kw.get("eps", 1e-2), skip=kw.get("skip", 0),
                                        precision=prec, maxit=kw.get("maxit", 500), tol=kw.get("tol", 1e-10)))
         hs = L.spand_analyze_batch([(p.rowptr, p.colind, p.vals, p.coords) for p in problems], opts)
