@@ -230,7 +230,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--grid", type=int, default=GRID, help="cube edge (small cases for profiling only)")
     ap.add_argument("--levels", type=int, default=LEVELS)
-    ap.add_argument("--form", default="fp32", choices=["fp32", "tf32", "bf16"],
+    ap.add_argument("--form", default="tf32", choices=["fp32", "tf32", "bf16"],
                     help="mixed form that is timed and reported as the headline (FP32 factor; Schur GEMMs on the "
                          "SIMT pipes, or on the tensor cores with TF32 / BF16 operands)")
     args = ap.parse_args()

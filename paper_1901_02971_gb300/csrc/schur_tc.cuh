@@ -8,15 +8,18 @@
 // (the separator size of every contributor, concatenated) is cut into chunks
 // of 128 bytes per row (32 TF32 or 64 BF16 elements), staged in shared memory
 // in the 128-byte-swizzled K-major layout (8-row atoms of 1024 bytes, 16-byte
-// chunk c of row r stored at chunk c ^ (r mod 8)), so that a warp storing one
-// row writes 128 contiguous bytes without bank conflicts.  Two stages: while
-// the tensor core works on one, the threads store the next chunk, which they
-// loaded into registers (coalesced: lane = k) during the previous MMAs.  One
+// chunk c of row r stored at chunk c ^ (r mod 8)), so that the 8 lanes that
+// store one row's 128 bytes hit distinct bank groups.  Two stages: while the
+// tensor core works on one, the threads store the next chunk, which they
+// loaded into registers (16-byte vectors, consecutive lanes along K) during
+// the previous MMAs.  One
 // elected thread issues 4 MMAs (K = 32 bytes each) per chunk and commits them
 // to the stage's mbarrier; every wait on it is bounded.
 #pragma once
 
 #include <cuda_bf16.h>
+
+#include <type_traits>
 
 #include "factor_kernels.cuh"
 
@@ -38,11 +41,6 @@ __device__ __forceinline__ uint64_t tc_desc_sw128(unsigned saddr) {
   d |= (uint64_t)1 << 46;  // descriptor version of this architecture family
   d |= (uint64_t)2 << 61;  // 128-byte swizzle
   return d;
-}
-
-// byte offset of the 4-byte word at byte kb (multiple of 4) of tile row r
-__device__ __forceinline__ int tc_sw_off(int r, int kb) {
-  return (r >> 3) * 1024 + (r & 7) * 128 + ((((kb >> 4) ^ (r & 7))) << 4) + (kb & 15);
 }
 
 __device__ __forceinline__ bool tc_wait(unsigned bar, unsigned parity) {
@@ -91,40 +89,41 @@ __global__ void __launch_bounds__(TC_NT, 4) k_schur_tc(const SchurTile* __restri
   // the chunk sequence: contributors in order, K in steps of BK
   int ci = b.cbeg, k0 = 0;
   while (ci < b.cend && contribs[ci].ns <= 0) ++ci;
-  // prefetch registers: rows warp + 4 j of A (j < 32) and of B (j < 16), one
-  // 32-bit word per lane: an FP32 value (k = k0 + lane) or a BF16 pair
-  // (k = k0 + 2 lane, 2 lane + 1)
-  uint32_t ra[TC_M / 4], rb[TC_N / 4];
+  // prefetch registers, 16 bytes of X per lane (the block rows' leading
+  // dimensions are whole 16-byte vectors, and their padding rows are zero, so
+  // a vector that starts below ns may run into the padding).  TF32: A holds
+  // 128 rows x 8 vectors (thread: row e >> 3, vector e & 7 for e = tid + 128 j),
+  // B 64 rows x 8.  BF16: A 128 rows x 16 vectors (row e >> 4, vector e & 15),
+  // converted to 4 BF16 values (8 bytes) at load time, B 64 rows x 16.
+  constexpr int VPR = BF16 ? 16 : 8;             // 16-byte source vectors per row
+  constexpr int NA = TC_M * VPR / TC_NT, NB = TC_N * VPR / TC_NT;
+  typedef typename std::conditional<BF16, uint2, uint4>::type Reg;
+  Reg ra[NA], rb[NB];
   auto load = [&](int c, int kk) {
     const SchurContrib<float> s = contribs[c];
-#pragma unroll
-    for (int j = 0; j < TC_M / 4; ++j) {
-      const int row = warp + 4 * j;
-      const float* p = s.Xa + (size_t)(t.i0 + row) * s.lds;
-      if (BF16) {
-        const int k = kk + 2 * lane;
-        const float v0 = (row < mi && k < s.ns) ? p[k] : 0.f, v1 = (row < mi && k + 1 < s.ns) ? p[k + 1] : 0.f;
-        __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-        ra[j] = *reinterpret_cast<uint32_t*>(&h);
+    auto one = [&](const float* X, int r0, int nr, int e) -> Reg {
+      const int row = e / VPR, v = e % VPR, k = kk + 4 * v;
+      float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (row < nr && k < s.ns) f = *reinterpret_cast<const float4*>(X + (size_t)(r0 + row) * s.lds + k);
+      if constexpr (BF16) {
+        __nv_bfloat162 lo = __floats2bfloat162_rn(f.x, f.y), hi = __floats2bfloat162_rn(f.z, f.w);
+        return make_uint2(*reinterpret_cast<uint32_t*>(&lo), *reinterpret_cast<uint32_t*>(&hi));
       } else {
-        const int k = kk + lane;
-        ra[j] = __float_as_uint((row < mi && k < s.ns) ? p[k] : 0.f);
+        return make_uint4(__float_as_uint(f.x), __float_as_uint(f.y), __float_as_uint(f.z), __float_as_uint(f.w));
       }
-    }
+    };
 #pragma unroll
-    for (int j = 0; j < TC_N / 4; ++j) {
-      const int row = warp + 4 * j;
-      const float* p = s.Xb + (size_t)(t.j0 + row) * s.lds;
-      if (BF16) {
-        const int k = kk + 2 * lane;
-        const float v0 = (row < nj && k < s.ns) ? p[k] : 0.f, v1 = (row < nj && k + 1 < s.ns) ? p[k + 1] : 0.f;
-        __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-        rb[j] = *reinterpret_cast<uint32_t*>(&h);
-      } else {
-        const int k = kk + lane;
-        rb[j] = __float_as_uint((row < nj && k < s.ns) ? p[k] : 0.f);
-      }
-    }
+    for (int j = 0; j < NA; ++j) ra[j] = one(s.Xa, t.i0, mi, tid + TC_NT * j);
+#pragma unroll
+    for (int j = 0; j < NB; ++j) rb[j] = one(s.Xb, t.j0, nj, tid + TC_NT * j);
+  };
+  // store of one register vector: 16 bytes (TF32) or 8 bytes (BF16) of row
+  // `row` at byte 16 v (TF32) / 8 v (BF16) of the row's 128 bytes
+  auto put = [&](unsigned char* base, int e, const Reg& x) {
+    const int row = e / VPR, v = e % VPR;
+    const int kb = BF16 ? 8 * v : 16 * v;
+    *reinterpret_cast<Reg*>(base + (row >> 3) * 1024 + (row & 7) * 128 + ((((kb >> 4) ^ (row & 7))) << 4) +
+                            (kb & 15)) = x;
   };
   bool ok = true;
   int it = 0;
@@ -138,9 +137,9 @@ __global__ void __launch_bounds__(TC_NT, 4) k_schur_tc(const SchurTile* __restri
       const bool late = it >= 2 && !tc_wait(tc_smem_addr(&bar[st]), (unsigned)((it - 2) >> 1) & 1u);
       if (!late) {
 #pragma unroll
-        for (int j = 0; j < TC_M / 4; ++j) *reinterpret_cast<uint32_t*>(sA + tc_sw_off(warp + 4 * j, 4 * lane)) = ra[j];
+        for (int j = 0; j < NA; ++j) put(sA, tid + TC_NT * j, ra[j]);
 #pragma unroll
-        for (int j = 0; j < TC_N / 4; ++j) *reinterpret_cast<uint32_t*>(sB + tc_sw_off(warp + 4 * j, 4 * lane)) = rb[j];
+        for (int j = 0; j < NB; ++j) put(sB, tid + TC_NT * j, rb[j]);
       }
       // the next chunk into registers while the tensor core runs this one
       k0 += BK;

@@ -23,9 +23,9 @@ constexpr int AT = 256;  // threads per CTA of the apply kernels
 
 template <typename TF>
 struct ElimOp {
-  const TF* R;       // [U_s | X^T], ns x (ns + m), ld = ns
+  const TF* R;       // [U_s | X^T], ns x (ns + m), leading dimension ld >= ns
   const TF* Y;       // U_s^{-T} (lower, ns x ns, ld = ns)
-  int32_t ns, m;
+  int32_t ns, m, ld, pad;
   int64_t slot;      // ns slots of s, then m slots of the neighbour columns
   int64_t ty, tu, ta;  // temp offsets: y_s (ns), u = X_ns y_s (m), backward acc (ns)
 };
@@ -266,8 +266,8 @@ __device__ __forceinline__ void prefetch_first_item(const ApplyPhase<TF>& P) {
     ld = (size_t)o.ns;
     rows = o.ns;
     if (P.kind == PH_FY) { A = o.Y; rowblock = true; lo = it.first; cols = min(o.ns, it.first + RB); nsl = cols; }
-    else if (P.kind == PH_BA) { A = o.R + (size_t)o.ns * o.ns; rowblock = true; lo = it.first; cols = o.m; sl += o.ns; nsl = o.m; }
-    else if (P.kind == PH_FU) { A = o.R + (size_t)o.ns * o.ns; rowblock = false; lo = it.first; cols = min(o.m - it.first, AP_COLS); nsl = 0; }
+    else if (P.kind == PH_BA) { A = o.R + (size_t)o.ld * o.ns; ld = (size_t)o.ld; rowblock = true; lo = it.first; cols = o.m; sl += o.ns; nsl = o.m; }
+    else if (P.kind == PH_FU) { A = o.R + (size_t)o.ld * o.ns; ld = (size_t)o.ld; rowblock = false; lo = it.first; cols = min(o.m - it.first, AP_COLS); nsl = 0; }
     else { A = o.Y; rowblock = false; lo = it.first; cols = min(o.ns - it.first, AP_COLS); nsl = cols + it.first; }
   } else {
     const SqOp<TF> o = P.sq[it.op];
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(AT) k_apply(const ApplyPhase<TF>* __restrict__
         if (P.kind == PH_FY || P.kind == PH_BA || P.kind == PH_FU || P.kind == PH_BX) {
           const ElimOp<TF> o = P.elim[it.op];
           const int32_t* sl = P.slots + o.slot;
-          const TF* XT = o.R + (size_t)o.ns * o.ns;
+          const TF* XT = o.R + (size_t)o.ld * o.ns;
           if (P.kind == PH_FY) {
             const int K = min(o.ns, it.first + RB);
             const ACC v = rowblock_gemv<TF, ACC>(o.Y, (size_t)o.ns, it.first, o.ns, K,
@@ -334,12 +334,12 @@ __global__ void __launch_bounds__(AT) k_apply(const ApplyPhase<TF>* __restrict__
             const int i = it.first + lane;
             if (warp == 0 && i < o.ns) tmp[o.ty + i] = (double)v;
           } else if (P.kind == PH_BA) {
-            const ACC v = rowblock_gemv<TF, ACC>(XT, (size_t)o.ns, it.first, o.ns, o.m,
+            const ACC v = rowblock_gemv<TF, ACC>(XT, (size_t)o.ld, it.first, o.ns, o.m,
                                                  [&](int k) { return ldv(x + sl[o.ns + k]); }, vs, part);
             const int i = it.first + lane;
             if (warp == 0 && i < o.ns) tmp[o.ta + i] = ldv(x + sl[i]) - (double)v;
           } else if (P.kind == PH_FU) {
-            coldot_gemv<TF, ACC>(XT, (size_t)o.ns, o.ns, it.first, min(o.m, it.first + AP_COLS), false,
+            coldot_gemv<TF, ACC>(XT, (size_t)o.ld, o.ns, it.first, min(o.m, it.first + AP_COLS), false,
                                  [&](int i) { return ldv(tmp + o.ty + i); },
                                  [&](int j, ACC v) { tmp[o.tu + j] = (double)v; }, vs);
           } else {  // PH_BX

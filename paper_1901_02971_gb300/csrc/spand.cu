@@ -49,6 +49,11 @@ struct Fail {
 #define CKLAUNCH() CK(cudaGetLastError())
 
 static inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+// Leading dimension of a cluster's block row: its size rounded up to 4
+// elements, so that every block's columns start on a 16-byte boundary (vector
+// loads in the tensor-core Schur update); the padding rows stay zero.  Used by
+// the analysis (assembly offsets) and every layout.
+static inline int32_t row_ld(int32_t size) { return (std::max<int32_t>(size, 1) + 3) / 4 * 4; }
 
 constexpr size_t kCpqrChunkBudget = 224 * 1024;  // shared memory per sparsification CTA (chunk included)
 constexpr int kCpqrMaxCluster = 8;              // thread-block cluster size (broadcasts to 16 CTAs cost 3.5x more)
@@ -455,7 +460,7 @@ static Layout<T> make_layout(spand_handle h, int t, const std::vector<int32_t>& 
     }
     lay.nptr.push_back((int32_t)lay.nidx.size());
     lay.W[i] = w;
-    lay.ld[i] = std::max<int32_t>(sz[i], 1);
+    lay.ld[i] = row_ld(sz[i]);
   }
   size_t pers = 0, scr = 0;
   for (int i = 0; i < n; ++i) {
@@ -958,7 +963,10 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         std::vector<SchurTile> tiles;
         // tensor cores for the TF32 / BF16 forms: 128 x 64 tiles; FP32 and
         // FP64 on the SIMT pipes: 64 x 64 tiles
-        const bool tc = sizeof(T) == 4 && (h->opts.precision == SPAND_TF32 || h->opts.precision == SPAND_BF16);
+        bool tc = sizeof(T) == 4 && (h->opts.precision == SPAND_TF32 || h->opts.precision == SPAND_BF16);
+        for (size_t b = 0; tc && b < contr.size(); ++b)  // the kernel loads 16-byte vectors of X
+          for (const auto& c : contr[b])
+            if (c.lds % 4 != 0 || ((uintptr_t)c.Xa | (uintptr_t)c.Xb) % 16 != 0) tc = false;
         const int ti = tc ? TC_M : TB, tj = tc ? TC_N : TB;
         for (size_t b = 0; b < blocks.size(); ++b) {
           blocks[b].cbeg = (int32_t)flat.size();
@@ -1015,8 +1023,9 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
     auto build_elim_ops = [&]() {
       for (int sidx : seps) {
         if (sz[sidx] <= 0) continue;
-        ElimOp<T> o;
+        ElimOp<T> o{};
         o.R = lay.row[sidx];
+        o.ld = lay.ld[sidx];
         o.Y = ysep[sidx];
         o.ns = sz[sidx];
         o.m = lay.W[sidx] - sz[sidx];
@@ -1777,7 +1786,7 @@ int spand_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const
           if (it != l.end() && it->first == cj) col = it->second;
         }
         if (col < 0) continue;  // entry (n, s) of an eliminated s: held in s's row only
-        const int64_t ld = std::max<int32_t>(csz[ci], 1);
+        const int64_t ld = row_ld(csz[ci]);
         h->asm_row[e] = ci;
         h->asm_off[e] = loc[v] + (int64_t)(col + loc[w]) * ld;
       }
