@@ -134,6 +134,10 @@ def load_peaks() -> dict:
 # GB300 (1.25 TFLOP/s).
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 FP64_ALU_TFLOPS = 1.25
+# TF32 tensor peak: cuBLAS 8192^3 TF32 GEMM measured on this machine's GB300
+# (torch.matmul with TF32 allowed: 1032.7 TFLOP/s; the same probe gave BF16
+# 1945 TFLOP/s, in line with the measured bf16 figure, and FP32 SIMT 69.8).
+TF32_TENSOR_TFLOPS = 1032.7
 HBM_BOUND = {"copy", "apply", "pcg"}
 
 
@@ -143,12 +147,12 @@ HBM_BOUND = {"copy", "apply", "pcg"}
 # counters were taken on: a changed kernel reports null until re-measured.
 # The capture and its command are summarised under profiles/ (DRAM traffic, 64^3).
 MEASURED_TRAFFIC = {
-    "cpqr": {"bytes_per_launch": (564.8e6 + 11.0e6) / 212,
+    "cpqr": {"bytes_per_launch": (583.3e6 + 13.8e6) / 212,
              "src": ["paper_1901_02971_gb300/csrc/cpqr_cluster.cuh", "paper_1901_02971_gb300/csrc/cpqr_reg.cuh"],
              "sha256": ["df81cb4f3a486696ea2b0dca01faaa4bbbe9a536c9f9ac17555724540692795e",
                         "2e82245239d77d096745e58d855d3fa1e2b7ed0c039d23a4e2551d5401927287"]},
-    "apply": {"bytes_per_launch": (2067.7e6 + 27.9e6) / 2, "src": "paper_1901_02971_gb300/csrc/solve_kernels.cuh",
-              "sha256": "24edc4406567191d811d97b17722572c1630b4225aa648ce84d1856b9ea2db56"},
+    "apply": {"bytes_per_launch": (2070.9e6 + 27.7e6) / 2, "src": "paper_1901_02971_gb300/csrc/solve_kernels.cuh",
+              "sha256": "d0f0fe613eb473dc7d77d8c65ee86cd5bf0c489ba06b3025e26d980cc3300dda"},
 }
 
 
@@ -188,6 +192,29 @@ def make_roofline(prof: dict, peaks: dict, dtype_peak_tflops: float = FP32_ALU_T
             "frac": ach / dtype_peak_tflops, "traffic": traffic,
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz", "launches": f["launches"],
             "ms": f["ms"]}
+
+
+def phase_rooflines(prof: dict, peaks: dict, form: str) -> dict:
+    """Achieved rate and fraction of its bounding peak for every kernel family
+    of one profiled factor+solve: HBM families against the measured copy
+    bandwidth; the Schur family of the TF32 / BF16 forms against the tensor
+    peak of its operand type; the rest against the FP32 ALU peak."""
+    out = {}
+    for fam, f in prof.items():
+        sec = f["ms"] / 1e3
+        if sec <= 0:
+            continue
+        if fam in HBM_BOUND:
+            ach, pk, unit, bound, src = f["bytes"] / sec / 1e9, float(peaks["hbm_gbs"]), "GB/s", "hbm", peaks["_source"]
+        elif fam == "schur" and form in ("tf32", "bf16"):
+            ach, unit, bound = f["flops"] / sec / 1e12, "TFLOP/s", "tensor"
+            pk = TF32_TENSOR_TFLOPS if form == "tf32" else float(peaks["bf16_tflops"])
+            src = "measured cuBLAS tf32 probe" if form == "tf32" else peaks["_source"] + " bf16"
+        else:
+            ach, pk, unit, bound, src = f["flops"] / sec / 1e12, FP32_ALU_TFLOPS, "TFLOP/s", "alu", "derived fp32"
+        out[fam] = {"ms": round(f["ms"], 3), "bound": bound, "achieved": round(ach, 3), "peak": pk, "unit": unit,
+                    "frac": round(ach / pk, 5), "peak_source": src}
+    return out
 
 
 def dist_env():
@@ -384,6 +411,7 @@ def main():
         "roofline": roofline,
         "gpu_launches": int(round(launches32)),
         "kernel_families_ms": {k: round(v["ms"], 3) for k, v in prof32.items()},
+        "phase_rooflines": phase_rooflines(prof32, peaks, args.form),
         "peaks_source": peaks["_source"],
     }
     if cpu is not None:

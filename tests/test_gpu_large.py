@@ -63,3 +63,22 @@ def test_knn_million_converges(cuda_ok):
     x, it, rr, true_rr, st = _run(p, False, levels=12, eps=1e-2, precision="fp32")
     assert rr <= 1e-10 and true_rr <= 1.5e-10, (it, rr, true_rr)
     assert it <= 40, it
+
+
+@pytest.mark.parametrize("eps", [1e-2, 1e-3])
+def test_diffusion_128_tc_forms(cuda_ok, diffusion_128, eps):
+    """TF32 and BF16 Schur operands on the high-contrast 128^3 problem: TF32
+    converges like FP32; BF16 (relative rounding 2^-8, above eps^2 here)
+    either converges or stops with a reported NOT_SPD pivot, never silently
+    wrong."""
+    from paper_1901_02971_gb300 import SpandError
+    from paper_1901_02971_gb300 import _lib as L
+    x, it, rr, true_rr, st = _run(diffusion_128, True, levels=13, eps=eps, precision="tf32")
+    assert rr <= 1e-10 and true_rr <= 1.5e-10, (eps, it, true_rr)
+    assert it <= 40, it  # TF32 rounding (2^-11) exceeds eps^2 at eps = 1e-3: more iterations than FP32
+    try:
+        x, it, rr, true_rr, st = _run(diffusion_128, True, levels=13, eps=eps, precision="bf16")
+    except SpandError as e:
+        assert e.code == L.SPAND_ERR_NOT_SPD, e
+        return
+    assert rr <= 1e-10 and true_rr <= 1.5e-10, (eps, it, true_rr)
