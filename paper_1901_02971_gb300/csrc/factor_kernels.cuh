@@ -192,19 +192,32 @@ __global__ void __launch_bounds__(NT) k_schur(const SchurTile* __restrict__ tile
     tn_acc(acc, s.Xa + (size_t)t.i0 * s.lds, s.lds, mi, s.Xb + (size_t)t.j0 * s.lds, s.lds, nj, s.ns, sm);
   }
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  // C1 -= acc; the results of 32 tile rows at a time also go through a
+  // shared-memory tile, from which C2 = C1^T is written along C2's rows
+  // (coalesced) instead of with a stride of ld2 per lane
+  __shared__ T tt[32][TB + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int jj = 0; jj < 4; ++jj) {
-    const int c = ty + 16 * jj;
-    if (c >= nj) continue;
+  for (int h = 0; h < 2; ++h) {
 #pragma unroll
-    for (int ii = 0; ii < 4; ++ii) {
-      const int r = tx + 16 * ii;
-      if (r >= mi) continue;
-      const size_t o1 = (size_t)(t.i0 + r) + (size_t)(t.j0 + c) * b.ld1;
-      const T v = b.C1[o1] - acc[ii][jj];
-      b.C1[o1] = v;
-      if (b.C2) b.C2[(size_t)(t.j0 + c) + (size_t)(t.i0 + r) * b.ld2] = v;
+    for (int jj = 0; jj < 4; ++jj) {
+      const int c = ty + 16 * jj;
+#pragma unroll
+      for (int ii = 2 * h; ii < 2 * h + 2; ++ii) {
+        const int r = tx + 16 * ii;
+        if (r >= mi || c >= nj) continue;
+        const size_t o1 = (size_t)(t.i0 + r) + (size_t)(t.j0 + c) * b.ld1;
+        const T v = b.C1[o1] - acc[ii][jj];
+        b.C1[o1] = v;
+        tt[r - 32 * h][c] = v;
+      }
     }
+    if (!b.C2) continue;  // uniform over the CTA
+    __syncthreads();
+    for (int rr = warp; rr < 32 && 32 * h + rr < mi; rr += NT / 32)
+      for (int c = lane; c < nj; c += 32)
+        b.C2[(size_t)(t.j0 + c) + (size_t)(t.i0 + 32 * h + rr) * b.ld2] = tt[rr][c];
+    __syncthreads();
   }
 }
 

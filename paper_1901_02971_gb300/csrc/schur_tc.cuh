@@ -182,7 +182,10 @@ __global__ void __launch_bounds__(TC_NT, 4) k_schur_tc(const SchurTile* __restri
   if (__syncthreads_or(!ok)) {
     if (tid == 0) atomicExch(timeout_flag, 1);
   } else {
-    // C1 -= acc (and its transpose into C2): lane = tile row, 16 columns per load
+    // C1 -= acc, lane = tile row, 16 columns per TMEM load (coalesced along
+    // C1's rows); the results also go to a shared-memory tile (row stride 65
+    // floats) from which C2 = C1^T is written with lanes along C2's rows
+    float* T = reinterpret_cast<float*>(sm);  // the stages are free: every MMA has completed
     const int row = 32 * warp + lane;
 #pragma unroll
     for (int c0 = 0; c0 < TC_N; c0 += 16) {
@@ -207,14 +210,21 @@ __global__ void __launch_bounds__(TC_NT, 4) k_schur_tc(const SchurTile* __restri
           const size_t o1 = (size_t)(t.i0 + row) + (size_t)(t.j0 + col) * b.ld1;
           const float v = b.C1[o1] - __uint_as_float(r[j]);
           b.C1[o1] = v;
-          if (b.C2) b.C2[(size_t)(t.j0 + col) + (size_t)(t.i0 + row) * b.ld2] = v;
+          T[row * (TC_N + 1) + col] = v;
         }
       }
+    }
+    if (b.C2) {
+      __syncthreads();
+      for (int rr = warp; rr < mi; rr += TC_NT / 32)
+        for (int col = lane; col < nj; col += 32)
+          b.C2[(size_t)(t.j0 + col) + (size_t)(t.i0 + rr) * b.ld2] = T[rr * (TC_N + 1) + col];
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TC_N) : "memory");
 }
+
 
 }  // namespace spand

@@ -989,13 +989,14 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         if constexpr (sizeof(T) == 4) {
           if (tc) {
             const void* fn = h->opts.precision == SPAND_BF16 ? (const void*)k_schur_tc<true> : (const void*)k_schur_tc<false>;
-            ensure_smem(fn, TC_SMEM);
+            const size_t tsm = TC_SMEM;
+            ensure_smem(fn, tsm);
             const SchurTile* a0 = at<const SchurTile>(d, ot);
             const SchurBlock<float>* a1 = at<const SchurBlock<float>>(d, ob);
             const SchurContrib<float>* a2 = at<const SchurContrib<float>>(d, oc);
             int* a3 = d_info;  // [0]: a bounded tensor-core wait gave up
             void* args[] = {(void*)&a0, (void*)&a1, (void*)&a2, (void*)&a3};
-            CK(cudaLaunchKernel(fn, dim3((unsigned)tiles.size()), dim3(TC_NT), args, TC_SMEM, s));
+            CK(cudaLaunchKernel(fn, dim3((unsigned)tiles.size()), dim3(TC_NT), args, tsm, s));
           }
         }
         if (!tc)
