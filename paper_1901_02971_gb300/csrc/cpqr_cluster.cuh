@@ -136,13 +136,12 @@ __device__ __forceinline__ void cq_sync(cg::cluster_group& cl, int C) {
 }
 
 // Q_pc e_c = H_0 ... H_c e_c (H_k e_c = e_c for k > c) for the columns c of
-// this warp (one warp per column over the whole cluster), the column held in
+// this warp (warp w of block `rank` out of C blocks takes the column pairs
+// (c, c + C NW) with c = rank NW + w mod 2 C NW), the column held in
 // registers: lane l owns rows l + 32 q, q < QR (np <= 32 QR).  Reflector k is
-// read either from a V array (column k, rows >= k) or, when DIRECT, from the
-// retired pivot column in the chunk: v_k = [1; p_{k+1:} scal_k].
-template <typename T, int QR, bool DIRECT>
-__device__ __forceinline__ void cq_form_q(const CpqrTask<T>& d, const T* V, const T* chunk, int L, int j0,
-                                          const int* piv_s, const T* scal_s, const T* tau_s, int r, int np, int rank,
+// read from column k of V (rows >= k; v_k[k] = 1).
+template <typename T, int QR>
+__device__ __forceinline__ void cq_form_q(const CpqrTask<T>& d, const T* V, const T* tau_s, int r, int np, int rank,
                                           int C) {
   // two columns per warp, their reflector chains interleaved (independent
   // shuffle reductions); c1 > c0, so H_k for c0 < k <= c1 touches c1 only
@@ -162,21 +161,11 @@ __device__ __forceinline__ void cq_form_q(const CpqrTask<T>& d, const T* V, cons
       if (tk == T(0)) continue;
       const bool doa = k <= c0;
       T vr[QR];
-      if (DIRECT) {
-        const T* pc = chunk + (size_t)(piv_s[k] - j0) * L;
-        const T sc = scal_s[k];
+      const T* v = V + (size_t)k * np;
 #pragma unroll
-        for (int q = 0; q < QR; ++q) {
-          const int i = lane + 32 * q;
-          vr[q] = (i > k && i < np) ? pc[i] * sc : (i == k ? T(1) : T(0));
-        }
-      } else {
-        const T* v = V + (size_t)k * np;
-#pragma unroll
-        for (int q = 0; q < QR; ++q) {
-          const int i = lane + 32 * q;
-          vr[q] = (i >= k && i < np) ? v[i] : T(0);
-        }
+      for (int q = 0; q < QR; ++q) {
+        const int i = lane + 32 * q;
+        vr[q] = (i >= k && i < np) ? v[i] : T(0);
       }
       T wa = 0, wb = 0;
 #pragma unroll
@@ -210,15 +199,14 @@ __device__ __forceinline__ void cq_form_q(const CpqrTask<T>& d, const T* V, cons
   }
 }
 
-template <typename T, bool DIRECT>
-__device__ __forceinline__ void cq_form_q_any(const CpqrTask<T>& d, const T* V, const T* chunk, int L, int j0,
-                                              const int* piv_s, const T* scal_s, const T* tau_s, int r, int np,
+template <typename T>
+__device__ __forceinline__ void cq_form_q_any(const CpqrTask<T>& d, const T* V, const T* tau_s, int r, int np,
                                               int rank, int C) {
-  if (np > 32 * 8) cq_form_q<T, 16, DIRECT>(d, V, chunk, L, j0, piv_s, scal_s, tau_s, r, np, rank, C);
-  else if (np > 32 * 4) cq_form_q<T, 8, DIRECT>(d, V, chunk, L, j0, piv_s, scal_s, tau_s, r, np, rank, C);
-  else if (np > 32 * 2) cq_form_q<T, 4, DIRECT>(d, V, chunk, L, j0, piv_s, scal_s, tau_s, r, np, rank, C);
-  else if (np > 32) cq_form_q<T, 2, DIRECT>(d, V, chunk, L, j0, piv_s, scal_s, tau_s, r, np, rank, C);
-  else cq_form_q<T, 1, DIRECT>(d, V, chunk, L, j0, piv_s, scal_s, tau_s, r, np, rank, C);
+  if (np > 32 * 8) cq_form_q<T, 16>(d, V, tau_s, r, np, rank, C);
+  else if (np > 32 * 4) cq_form_q<T, 8>(d, V, tau_s, r, np, rank, C);
+  else if (np > 32 * 2) cq_form_q<T, 4>(d, V, tau_s, r, np, rank, C);
+  else if (np > 32) cq_form_q<T, 2>(d, V, tau_s, r, np, rank, C);
+  else cq_form_q<T, 1>(d, V, tau_s, r, np, rank, C);
 }
 
 // Epilogue shared by the sparsification kernels, entered after a block barrier
@@ -598,7 +586,7 @@ __global__ void __launch_bounds__(NT) k_form_q(const CpqrTask<T>* __restrict__ t
   }
   __syncthreads();
   if (np <= 32 * 16) {
-    cq_form_q_any<T, false>(d, Vsrc, nullptr, 0, 0, nullptr, nullptr, tau_s, r, np, b, nb);
+    cq_form_q_any<T>(d, Vsrc, tau_s, r, np, b, nb);
     return;
   }
   // tall interfaces: one warp per column, V and the column in global memory

@@ -1,0 +1,35 @@
+"""Host logic of bench.py (no GPU): the per-phase roofline table and the
+source-hash guard of the measured DRAM traffic."""
+import bench
+
+
+def _prof():
+    return {"schur": {"ms": 2.0, "flops": 40e9, "bytes": 1e9, "launches": 9},
+            "apply": {"ms": 4.0, "flops": 1e9, "bytes": 8e9, "launches": 8},
+            "cpqr": {"ms": 10.0, "flops": 20e9, "bytes": 6e8, "launches": 212}}
+
+
+def test_phase_rooflines_bounds_and_fractions():
+    peaks = {"hbm_gbs": 8000.0, "bf16_tflops": 2000.0, "_source": "test"}
+    r = bench.phase_rooflines(_prof(), peaks, "tf32")
+    assert r["apply"]["bound"] == "hbm" and abs(r["apply"]["achieved"] - 2000.0) < 1e-9
+    assert abs(r["apply"]["frac"] - 0.25) < 1e-9
+    assert r["schur"]["bound"] == "tensor" and r["schur"]["peak"] == bench.TF32_TENSOR_TFLOPS
+    assert abs(r["schur"]["achieved"] - 20.0) < 1e-9
+    assert r["cpqr"]["bound"] == "alu" and r["cpqr"]["peak"] == bench.FP32_ALU_TFLOPS
+    rb = bench.phase_rooflines(_prof(), peaks, "bf16")
+    assert rb["schur"]["peak"] == 2000.0 and abs(rb["schur"]["frac"] - 0.01) < 1e-9
+    rf = bench.phase_rooflines(_prof(), peaks, "fp32")
+    assert rf["schur"]["bound"] == "alu"  # SIMT Schur in the FP32 form
+
+
+def test_measured_traffic_tied_to_source_hash(tmp_path, monkeypatch):
+    src = tmp_path / "k.cuh"
+    src.write_text("kernel")
+    import hashlib
+    good = hashlib.sha256(b"kernel").hexdigest()
+    monkeypatch.setattr(bench, "MEASURED_TRAFFIC", {"x": {"bytes_per_launch": 5.0, "src": [str(src)], "sha256": [good]}})
+    assert bench.measured_traffic("x", bench.GRID) == 5.0
+    assert bench.measured_traffic("x", bench.GRID + 1) is None  # another workload size
+    src.write_text("kernel changed")
+    assert bench.measured_traffic("x", bench.GRID) is None
