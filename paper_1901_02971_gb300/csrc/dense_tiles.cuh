@@ -111,17 +111,23 @@ __device__ __forceinline__ void store_tile(const SqTile<T>& s, T* P, int ld, int
 
 // Upper Cholesky of the nb x nb diagonal tile s (A = U^T U, upper triangle
 // read and overwritten with U, lower triangle left as loaded) fused with the
-// inverse D = U^{-T} (lower, TB x TB, identity beyond nb).  Right-looking: at
-// step k the pivot row k of A and row k of D are published to shared memory,
-// then every thread updates the 4 x 4 elements it holds in registers
-// (rows tx + 16a, columns ty + 16b):
-//   U_kj = A_kj / sqrt(A_kk);  A_ij -= U_ki U_kj (k < i <= j);
-//   D_k. <- D_k. / U_kk;       D_i. -= U_ki D_k. (i > k)      (row ops of L^{-1}, L = U^T).
-// One block barrier per step (the row buffers alternate).  Returns false
-// (for every thread) if a pivot is not positive; nothing is stored then.
+// inverse D = U^{-T} (lower, TB x TB, identity beyond nb).  Right-looking,
+// two pivot rows per step: rows k and k + 1 of A and of D are published to
+// shared memory, every thread forms the 2 x 2 pivot block from them,
+//   U_kk = sqrt(A_kk), U_k. = A_k. / U_kk,
+//   U_{k+1,k+1} = sqrt(A_{k+1,k+1} - U_{k,k+1}^2),
+//   U_{k+1,.} = (A_{k+1,.} - U_{k,k+1} U_k.) / U_{k+1,k+1},
+//   D_k. <- D_k. / U_kk,  D_{k+1,.} <- (D_{k+1,.} - U_{k,k+1} D_k.) / U_{k+1,k+1},
+// and updates the 4 x 4 elements it holds in registers (rows tx + 16a,
+// columns ty + 16b) with the rank-2 terms:
+//   A_ij -= U_ki U_kj + U_{k+1,i} U_{k+1,j} (k + 1 < i <= j),
+//   D_i. -= U_ki D_k. + U_{k+1,i} D_{k+1,.} (i > k + 1)   (row ops of L^{-1}, L = U^T).
+// One block barrier per pair of rows (the row buffers alternate); 1 / U_kk
+// comes from one reciprocal square root.  Returns false (for every thread) if
+// a pivot is not positive; nothing is stored then.
 template <typename T>
 __device__ bool potrf_inv_tile(SqTile<T>& s, SqTile<T>& D, int nb) {
-  __shared__ T rowA[2][TB], rowD[2][TB];
+  __shared__ T rowA[2][2][TB], rowD[2][2][TB];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   T a[4][4], d[4][4];
 #pragma unroll
@@ -132,28 +138,40 @@ __device__ bool potrf_inv_tile(SqTile<T>& s, SqTile<T>& D, int nb) {
       a[p][q] = s.v[i][j];
       d[p][q] = (i == j) ? T(1) : T(0);
     }
-  for (int k = 0; k < nb; ++k) {
-    const int par = k & 1;
+  for (int k = 0; k < nb; k += 2) {
+    const int par = (k >> 1) & 1;
+    const bool two = k + 1 < nb;
+    const int k1 = two ? k + 1 : k;  // a single last row repeats row k (unused)
 #pragma unroll
-    for (int p = 0; p < 4; ++p)  // owners of row k publish it (compile-time register indices)
-      if (tx + 16 * p == k) {
+    for (int p = 0; p < 4; ++p) {  // owners of rows k, k + 1 publish them (compile-time register indices)
+      const int i = tx + 16 * p;
+      if (i == k || i == k1) {
+        const int w = i == k ? 0 : 1;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          rowA[par][ty + 16 * q] = a[p][q];
-          rowD[par][ty + 16 * q] = d[p][q];
+          rowA[par][w][ty + 16 * q] = a[p][q];
+          rowD[par][w][ty + 16 * q] = d[p][q];
         }
       }
+    }
     __syncthreads();
-    const T piv = rowA[par][k];
-    if (!(piv > T(0))) return false;  // uniform: every thread read the same pivot
-    const T ukk = sqrt(piv);
-    const T inv = T(1) / ukk;
-    T ui[4], uj[4], dk[4];
+    const T a00 = rowA[par][0][k];
+    if (!(a00 > T(0))) return false;  // uniform: every thread read the same pivot
+    const T r0 = rsqrt(a00), u00 = a00 * r0;
+    const T u01 = two ? rowA[par][0][k1] * r0 : T(0);
+    const T s11 = two ? rowA[par][1][k1] - u01 * u01 : T(1);
+    if (!(s11 > T(0))) return false;
+    const T r1 = rsqrt(s11), u11 = s11 * r1;
+    T u0i[4], u1i[4], u0j[4], u1j[4], d0[4], d1[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      ui[q] = rowA[par][tx + 16 * q] * inv;
-      uj[q] = rowA[par][ty + 16 * q] * inv;
-      dk[q] = rowD[par][ty + 16 * q] * inv;
+      const int ci = tx + 16 * q, cj = ty + 16 * q;
+      u0i[q] = rowA[par][0][ci] * r0;
+      u0j[q] = rowA[par][0][cj] * r0;
+      d0[q] = rowD[par][0][cj] * r0;
+      u1i[q] = two ? (rowA[par][1][ci] - u01 * u0i[q]) * r1 : T(0);
+      u1j[q] = two ? (rowA[par][1][cj] - u01 * u0j[q]) * r1 : T(0);
+      d1[q] = two ? (rowD[par][1][cj] - u01 * d0[q]) * r1 : T(0);
     }
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
@@ -162,16 +180,24 @@ __device__ bool potrf_inv_tile(SqTile<T>& s, SqTile<T>& D, int nb) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int j = ty + 16 * q;
-          if (j == k) a[p][q] = ukk;
-          else if (j > k) a[p][q] = uj[q];
-          d[p][q] = dk[q];
+          if (j == k) a[p][q] = u00;
+          else if (j > k) a[p][q] = u0j[q];
+          d[p][q] = d0[q];
         }
-      } else if (i > k) {
+      } else if (two && i == k1) {  // finalise row k + 1
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int j = ty + 16 * q;
-          if (j >= i) a[p][q] = fma(-ui[p], uj[q], a[p][q]);
-          d[p][q] = fma(-ui[p], dk[q], d[p][q]);
+          if (j == k1) a[p][q] = u11;
+          else if (j > k1) a[p][q] = u1j[q];
+          d[p][q] = d1[q];
+        }
+      } else if (i > k1) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = ty + 16 * q;
+          if (j >= i) a[p][q] = fma(-u1i[p], u1j[q], fma(-u0i[p], u0j[q], a[p][q]));
+          d[p][q] = fma(-u1i[p], d1[q], fma(-u0i[p], d0[q], d[p][q]));
         }
       }
     }
