@@ -21,9 +21,9 @@ constexpr int NT = 256;   // threads per CTA of the tile kernels
 constexpr int KC = 16;    // k-chunk staged in shared memory
 
 template <typename T>
-struct TileSmem {
-  T a[KC][TB + 1];
-  T b[KC][TB + 1];
+struct TileSmem {  // two K chunks (double buffer)
+  T a[2][KC][TB + 1];
+  T b[2][KC][TB + 1];
 };
 
 // acc[ii][jj] (row = tx + 16 ii, col = ty + 16 jj; tx = tid % 16, ty = tid / 16)
@@ -33,34 +33,50 @@ template <typename T>
 __device__ __forceinline__ void tn_acc(T (&acc)[4][4], const T* __restrict__ A, int lda, int mi,
                                        const T* __restrict__ B, int ldb, int nj, int K,
                                        TileSmem<T>& sm) {
+  // K in chunks of KC, double-buffered: chunk c + 1 is loaded into registers
+  // while chunk c is multiplied from shared memory; one block barrier per chunk
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  for (int k0 = 0; k0 < K; k0 += KC) {
+  T ra[4], rb[4];
+  auto load = [&](int k0) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const int e = tid + NT * r;
       const int kk = e & (KC - 1);
       const int ii = e >> 4;
       const int k = k0 + kk;
-      sm.a[kk][ii] = (k < K && ii < mi) ? A[k + (size_t)ii * lda] : T(0);
-      sm.b[kk][ii] = (k < K && ii < nj) ? B[k + (size_t)ii * ldb] : T(0);
+      ra[r] = (k < K && ii < mi) ? A[k + (size_t)ii * lda] : T(0);
+      rb[r] = (k < K && ii < nj) ? B[k + (size_t)ii * ldb] : T(0);
+    }
+  };
+  if (K <= 0) return;
+  load(0);
+  int buf = 0;
+  for (int k0 = 0; k0 < K; k0 += KC) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int e = tid + NT * r;
+      sm.a[buf][e & (KC - 1)][e >> 4] = ra[r];
+      sm.b[buf][e & (KC - 1)][e >> 4] = rb[r];
     }
     __syncthreads();
+    if (k0 + KC < K) load(k0 + KC);
 #pragma unroll
     for (int kk = 0; kk < KC; ++kk) {
       T av[4], bv[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        av[q] = sm.a[kk][tx + 16 * q];
-        bv[q] = sm.b[kk][ty + 16 * q];
+        av[q] = sm.a[buf][kk][tx + 16 * q];
+        bv[q] = sm.b[buf][kk][ty + 16 * q];
       }
 #pragma unroll
       for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) acc[ii][jj] = fma(av[ii], bv[jj], acc[ii][jj]);
     }
-    __syncthreads();
+    buf ^= 1;
   }
+  __syncthreads();  // the caller may reuse the buffers
 }
 
 template <typename T>

@@ -195,7 +195,9 @@ __global__ void __launch_bounds__(NT) k_schur(const SchurTile* __restrict__ tile
   // C1 -= acc; the results of 32 tile rows at a time also go through a
   // shared-memory tile, from which C2 = C1^T is written along C2's rows
   // (coalesced) instead of with a stride of ld2 per lane
-  __shared__ T tt[32][TB + 1];
+  // the GEMM buffers are free (tn_acc ends with a block barrier)
+  static_assert(sizeof(TileSmem<T>) >= sizeof(T) * 32 * (TB + 1), "staging tile fits in the GEMM buffers");
+  T (*tt)[TB + 1] = reinterpret_cast<T (*)[TB + 1]>(&sm);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
