@@ -56,8 +56,9 @@ enum {
  * and the SpMV always run in FP64) */
 enum {
   SPAND_FP64 = 0,  /* plain: every factor kernel in FP64 */
-  SPAND_FP32 = 1,  /* mixed: factor blocks, Schur GEMMs, QR and the
-                      preconditioner apply in FP32; scaling pivots in FP64 */
+  SPAND_FP32 = 1,  /* mixed: every factor kernel (pivot and scaling Cholesky,
+                      TRSM, Schur GEMMs, QR) and the preconditioner apply in
+                      FP32; vectors, SpMV and the PCG recurrences in FP64 */
   SPAND_TF32 = 2,  /* as SPAND_FP32, with the elimination's Schur GEMMs on the
                       tensor cores: TF32 operands, FP32 accumulation */
   SPAND_BF16 = 3   /* as SPAND_TF32 with BF16 operands (FP32 accumulation,
