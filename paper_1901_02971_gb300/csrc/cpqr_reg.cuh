@@ -13,16 +13,18 @@
 // cluster, so the work per step follows the trailing rows.
 //
 // Pivot column: before the step's block barrier the group holding the warp's
-// candidate writes its live chunks into the warp's pivot slot, lane-major
-// (lane g's slots contiguous, segment stride R + one 16-byte vector, so that
-// the lanes of a group read distinct bank groups and the groups of a warp
-// share them by broadcast).  With C > 1 the CTA's winning slot is pushed into
-// every CTA of the cluster through distributed shared memory before the
-// cluster barrier, as in the chunked kernel: one block barrier per step plus
-// one cluster barrier when C > 1, no spin-waits.  The reader masks the slot's
-// rows above k and puts alpha - beta at row k, so that with
-// v = scal [0; alpha - beta; p_{k+1:}] both the dot product and the update run
-// unmasked over the live chunks.
+// candidate derives the reflector it would define (alpha, beta and
+// gam = 1 / (beta (beta - alpha)), so that H_k = I - gam u u^T) and writes u
+// into the warp's pivot slot: its live chunks, lane-major (lane g's slots
+// contiguous, segment stride R + one 16-byte vector, so that the lanes of a
+// group read distinct bank groups and the groups of a warp share them by
+// broadcast), with zeros above row k and alpha - beta at row k; dot product
+// and update then run unmasked over the live chunks.  With C > 1 every CTA
+// stores its record and winning slot into each CTA of the cluster with
+// st.async, which counts the bytes on the receiver's mbarrier for that step
+// parity; one thread per CTA waits (bounded) for the C records and slots, and
+// a block barrier hands them and the verdict to the CTA: one block barrier
+// plus one mbarrier wait per step, no cluster barrier.
 //
 // A retired pivot column keeps the raw values from which its reflector is
 // derived; at the end every group stores its column into the shared chunk
