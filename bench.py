@@ -150,7 +150,7 @@ MEASURED_TRAFFIC = {
     "cpqr": {"bytes_per_launch": (583.4e6 + 13.8e6) / 212,
              "src": ["paper_1901_02971_gb300/csrc/cpqr_cluster.cuh", "paper_1901_02971_gb300/csrc/cpqr_reg.cuh"],
              "sha256": ["354ec7fda5fb9373049b5f2a1946c215d720f4dd2c38934a2327d32eada75f44",
-                        "285dc822c335d7abe423a1273b7c0978ae5a11af63684b99407306cc469972c6"]},
+                        "836df7b7d270b09faac01137e4b748a8b7b66bba747ef1eb9b66b4622ec27290"]},
     "apply": {"bytes_per_launch": (2070.9e6 + 27.7e6) / 2, "src": "paper_1901_02971_gb300/csrc/solve_kernels.cuh",
               "sha256": "d0f0fe613eb473dc7d77d8c65ee86cd5bf0c489ba06b3025e26d980cc3300dda"},
 }

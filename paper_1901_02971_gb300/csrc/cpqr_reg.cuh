@@ -23,7 +23,7 @@
 // stores its record and winning slot into each CTA of the cluster with
 // st.async, which counts the bytes on the receiver's mbarrier for that step
 // parity; one thread per CTA waits (bounded) for the C records and slots, and
-// a block barrier hands them and the verdict to the CTA: one block barrier
+// a block barrier hands them and the outcome to the CTA: one block barrier
 // plus one mbarrier wait per step, no cluster barrier.
 //
 // A retired pivot column keeps the raw values from which its reflector is
@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(NT, 1) k_cpqr_reg(const CpqrTask<T>* __restric
         for (int e = 0; e < (int)(sizeof(CqrRec<T>) / 16); ++e) cqr_st_async(cqr_mapa(la + 16 * e, lane), wv[e], rb);
       }
       // one thread waits (bounded) for the C records and slots of step k; the
-      // block barrier hands the data and the verdict to the CTA
+      // block barrier hands the data and the outcome to the CTA
       bool late = false;
       if (tid == 0) {
         late = !cqr_bar_wait(&sh.bar[par], (unsigned)(k >> 1) & 1u);

@@ -1,7 +1,7 @@
 """GPU path (through the C ABI) against the FP64 oracle on the same seeded
 inputs.
 
-Bars (spec tolerances):
+Bars:
   * x within a relative 1e-8 of the oracle's x, both at PCG relative residual
     1e-10;
   * PCG iteration count within +10% of the oracle's (rounded up);
