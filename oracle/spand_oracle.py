@@ -21,7 +21,10 @@ What it computes, step by step in the paper's order and notation:
                       (Sec. 2.6.1 and the truncation rule of Sec. 4), merge
                       (Sec. 2.7).  Dense algebra uses LAPACK through scipy
                       (Cholesky, triangular solves, geqp3 -- the routine the
-                      paper names for its low-rank step).
+                      paper names for its low-rank step).  ``variant`` selects
+                      the ablation variants of Sec. 4.3: "In" (interpolative
+                      transformations, Sec. 2.6.2, no block scaling) and "InS"
+                      (interpolative with block scaling) instead of "OrthS".
 * ``apply``        -- z = M M^T r with M the product of the elementary
                       transforms (Sec. 2.8): forward sweep leaf->root, backward
                       sweep root->leaf with transposes.
@@ -308,7 +311,8 @@ def analyze(n, rowptr, colind, coords, L) -> Tree:
 
 @dataclass
 class Factor:
-    ops: list = field(default_factory=list)   # ('E', s_slots, Ls, [(n_slots, Xt)]), ('S', p_slots, Lp), ('Q', p_slots, Q)
+    ops: list = field(default_factory=list)   # ('E', s_slots, Ls, [(n_slots, Xt)]), ('S', p_slots, Lp), ('Q', p_slots, Q),
+    #                                           ('T', c_slots, f_slots, T_cf)
     ranks: List[Dict[int, int]] = field(default_factory=list)  # per step: cluster -> r
     sizes_before: List[np.ndarray] = field(default_factory=list)  # per step: cluster sizes at step start
     sizes_after: List[np.ndarray] = field(default_factory=list)   # per step: sizes after sparsification (0 = eliminated)
@@ -342,10 +346,55 @@ def sparsify_interface(Apn: np.ndarray, eps: float):
     return Q, r, W[:r], W[r:]
 
 
+def sparsify_interface_interp(Anp: np.ndarray, App: np.ndarray, eps: float):
+    """Interpolative sparsification of one interface (Sec. 2.6.2).
+
+    Column-pivoted QR of A_np (neighbour rows x the dofs of p): A_np P = Q R,
+    r from the truncation rule; c = the first r pivoted dofs, f = the rest,
+    T_cf = R_11^{-1} R_12, so that A_nf = A_nc T_cf + Q_2 R_22 (the second
+    term, O(eps), is dropped).  With T_p = I - E_cf T_cf (block (c, f) =
+    -T_cf) the diagonal block becomes
+        C_ff = A_ff - A_fc T_cf - T_cf^T A_cf + T_cf^T A_cc T_cf,
+        C_cf = A_cf - A_cc T_cf,
+    and f, coupled to c only, is eliminated: L_f = chol(C_ff) (NotSPDError if
+    C_ff is not SPD: the breakdown the paper reports for these variants),
+    X_fc = L_f^{-1} C_fc, A_cc <- A_cc - X_fc^T X_fc.
+    Returns (c, f, T_cf, L_f, X_fc, A_cc_new, R22) with c, f local indices."""
+    m, p = Anp.shape
+    if p == 0 or m == 0:
+        return np.arange(p), np.zeros(0, np.int64), np.zeros((p, 0)), np.zeros((0, 0)), np.zeros((0, p)), \
+            App.copy(), np.zeros((0, 0))
+    _, R, P = sla.qr(Anp, pivoting=True, mode="economic")
+    r = truncation_rank(np.diag(R), eps)
+    c, f = P[:r], P[r:]
+    T = sla.solve_triangular(R[:r, :r], R[:r, r:], lower=False) if r else np.zeros((0, p - r))
+    R22 = R[r:, r:]
+    Acc, Acf, Aff = App[np.ix_(c, c)], App[np.ix_(c, f)], App[np.ix_(f, f)]
+    Cff = Aff - Acf.T @ T - T.T @ Acf + T.T @ Acc @ T
+    Ccf = Acf - Acc @ T
+    if f.size:
+        try:
+            Lf = np.linalg.cholesky(Cff)
+        except np.linalg.LinAlgError as e:
+            raise NotSPDError("interpolative sparsification: C_ff not SPD") from e
+        Xfc = sla.solve_triangular(Lf, Ccf.T, lower=True)
+        Acc = Acc - Xfc.T @ Xfc
+    else:
+        Lf, Xfc = np.zeros((0, 0)), np.zeros((0, r))
+    return c, f, T, Lf, Xfc, Acc, R22
+
+
+VARIANTS = ("OrthS", "InS", "In")
+
+
 def factorize(prob_rowptr, prob_colind, prob_vals, tree: Tree, eps: float, skip: int = 0,
-              trace: Optional[list] = None) -> Factor:
+              trace: Optional[list] = None, variant: str = "OrthS") -> Factor:
     """Algorithm 2.  ``trace`` (a list, tests only) receives (step, phase,
-    set of block keys) before and after each level's sparsification."""
+    set of block keys) before and after each level's sparsification.
+    ``variant``: "OrthS" (Algorithm 2), "InS" or "In" (Sec. 4.3 ablation:
+    interpolative transformations with / without the block scaling)."""
+    if variant not in VARIANTS:
+        raise ValueError(f"unknown variant {variant!r}")
     n, L = tree.n, tree.L
     rowptr = np.asarray(prob_rowptr, dtype=np.int64)
     colind = np.asarray(prob_colind, dtype=np.int64)
@@ -411,9 +460,9 @@ def factorize(prob_rowptr, prob_colind, prob_vals, tree: Tree, eps: float, skip:
                 raise RuntimeError("numeric pattern differs from the symbolic one")
         ranks = {}
         if skip < t < L:
-            # ---- scale every interface (Sec. 2.5)
+            # ---- scale every interface (Sec. 2.5); the In variant skips it
             Lp = {}
-            for p in rem:
+            for p in (rem if variant != "In" else []):
                 if size[p] == 0:
                     Lp[p] = np.zeros((0, 0))
                     continue
@@ -421,7 +470,7 @@ def factorize(prob_rowptr, prob_colind, prob_vals, tree: Tree, eps: float, skip:
                     Lp[p] = np.linalg.cholesky(blocks[(p, p)])
                 except np.linalg.LinAlgError as e:
                     raise NotSPDError(f"scaling step {t} cluster {p}") from e
-            for p in rem:
+            for p in (rem if variant != "In" else []):
                 for q in st.adjf[p]:
                     if p < q:
                         X = sla.solve_triangular(Lp[p], blocks[(p, q)], lower=True) if size[p] else blocks[(p, q)]
@@ -429,7 +478,7 @@ def factorize(prob_rowptr, prob_colind, prob_vals, tree: Tree, eps: float, skip:
                             X = sla.solve_triangular(Lp[q], X.T, lower=True).T
                         blocks[(p, q)] = X
                         blocks[(q, p)] = X.T.copy()
-            for p in rem:
+            for p in (rem if variant != "In" else []):
                 blocks[(p, p)] = np.eye(size[p])
                 F.ops.append(("S", slots[p], Lp[p]))
                 F.mem_f += int(size[p] * (size[p] + 1) // 2)
@@ -445,6 +494,23 @@ def factorize(prob_rowptr, prob_colind, prob_vals, tree: Tree, eps: float, skip:
                     if not nb:
                         continue
                     widths = [int(size[q]) for q in nb]
+                    if variant != "OrthS":
+                        Anp = np.vstack([blocks[(q, p)] for q in nb])
+                        cl, fl, T, Lf, Xfc, Acc, _ = sparsify_interface_interp(Anp, blocks[(p, p)], eps)
+                        r = int(cl.size)
+                        for q in nb:  # A_qc is a subset of A_qp; A_qf - A_qc T_cf is dropped
+                            blocks[(q, p)] = blocks[(q, p)][:, cl].copy()
+                            blocks[(p, q)] = blocks[(q, p)].T.copy()
+                        blocks[(p, p)] = Acc
+                        cs, fs = slots[p][cl], slots[p][fl]
+                        if fl.size:
+                            F.ops.append(("T", cs, fs, T))
+                            F.ops.append(("E", fs, Lf, [(cs, Xfc)]))
+                            F.mem_f += int(r * fl.size * 2 + fl.size * (fl.size + 1) // 2)
+                        ranks[p] = r
+                        size[p] = r
+                        slots[p] = cs
+                        continue
                     Apn = np.hstack([blocks[(p, q)] for q in nb]) if nb else np.zeros((size[p], 0))
                     Q, r, Wc, _ = sparsify_interface(Apn, eps)
                     off = 0
@@ -514,6 +580,9 @@ def apply(F: Factor, r: np.ndarray) -> np.ndarray:
             _, ps, Lp = op
             if ps.size:
                 v[ps] = sla.solve_triangular(Lp, v[ps], lower=True)
+        elif op[0] == "T":                 # v <- T_p^T v
+            _, cs, fs, T = op
+            v[fs] -= T.T @ v[cs]
         else:
             _, ps, Q = op
             v[ps] = Q.T @ v[ps]
@@ -529,6 +598,9 @@ def apply(F: Factor, r: np.ndarray) -> np.ndarray:
             _, ps, Lp = op
             if ps.size:
                 v[ps] = sla.solve_triangular(Lp, v[ps], lower=True, trans="T")
+        elif op[0] == "T":                 # v <- T_p v
+            _, cs, fs, T = op
+            v[cs] -= T @ v[fs]
         else:
             _, ps, Q = op
             v[ps] = Q @ v[ps]
@@ -589,11 +661,11 @@ class Result:
 
 
 def solve(prob, b, L: int, eps: float, skip: int = 0, tol: float = 1e-10, maxit: int = 500,
-          use_coords: bool = True) -> Result:
+          use_coords: bool = True, variant: str = "OrthS") -> Result:
     """analyze + factorize + PCG on the original ordering of b / x."""
     coords = prob.coords if use_coords else None
     tree = analyze(prob.n, prob.rowptr, prob.colind, coords, L)
-    F = factorize(prob.rowptr, prob.colind, prob.vals, tree, eps, skip)
+    F = factorize(prob.rowptr, prob.colind, prob.vals, tree, eps, skip, variant=variant)
     Ap = permuted_matrix(prob.rowptr, prob.colind, prob.vals, tree.perm)
     xp, it, rr = pcg(Ap, np.asarray(b)[tree.perm], lambda r: apply(F, r), tol, maxit)
     x = np.empty(prob.n)

@@ -1,0 +1,114 @@
+"""Pins of the oracle's interpolative variants In / InS (Sec. 2.6.2 and the
+ablation of Sec. 4.3), checked against dense linear algebra written out here
+and against what the paper states, not against the oracle's own formulas:
+
+* eps = 0: no entry is dropped, so M M^T = A^{-1} for every variant
+  (dense check on small 2D / 3D problems).
+* One interface: the discarded block satisfies ||A_nf - A_nc T_cf||_F =
+  ||R_22||_F (A_np P = Q R); the diagonal block after the transform and the
+  elimination of f equals an explicit dense computation (form T_p, transform,
+  drop the (n, f) coupling, eliminate f by a dense Schur complement); with a
+  scaled block (A_pp = I) C_ff = I + T_cf^T T_cf as in the paper's table.
+* Sec. 4.3: at a given eps the interpolative variant without scaling (In)
+  needs more PCG iterations than InS and OrthS; InS stays close to OrthS.
+* OrthS never breaks down (eps up to 0.9); In / InS either converge or stop
+  with NotSPDError (the paper's reported failure mode), nothing else.
+"""
+import numpy as np
+import pytest
+
+from oracle import spand_oracle as O
+from paper_1901_02971_gb300 import inputs as I
+
+
+@pytest.mark.parametrize("variant", ["InS", "In"])
+@pytest.mark.parametrize("gen,L", [(lambda: I.laplacian_2d(12), 5), (lambda: I.laplacian_3d(6), 4),
+                                   (lambda: I.diffusion_2d(12, 3), 5)])
+def test_interp_exact_at_eps0(variant, gen, L):
+    p = gen()
+    tree = O.analyze(p.n, p.rowptr, p.colind, p.coords, L)
+    F = O.factorize(p.rowptr, p.colind, p.vals, tree, 0.0, variant=variant)
+    A = O.permuted_matrix(p.rowptr, p.colind, p.vals, tree.perm).toarray()
+    MMt = O.dense_preconditioner(F, p.n)
+    assert np.linalg.norm(MMt @ A - np.eye(p.n)) <= 1e-10 * p.n
+
+
+def _interface(seed, p=12, m=30, decay=0.5):
+    rng = np.random.default_rng(seed)
+    U = np.linalg.qr(rng.standard_normal((m, m)))[0][:, :p]
+    V = np.linalg.qr(rng.standard_normal((p, p)))[0]
+    Anp = U @ np.diag(decay ** np.arange(p)) @ V.T  # numerical rank well below p
+    B = rng.standard_normal((p, p))
+    App = B @ B.T + p * np.eye(p)
+    return Anp, App
+
+
+@pytest.mark.parametrize("seed,eps", [(1, 1e-2), (2, 1e-1), (3, 0.3)])
+def test_interface_transform_and_elimination(seed, eps):
+    Anp, App = _interface(seed)
+    m, p = Anp.shape
+    c, f, T, Lf, Xfc, Acc, R22 = O.sparsify_interface_interp(Anp, App, eps)
+    assert sorted(np.concatenate([c, f]).tolist()) == list(range(p))
+    assert 0 < c.size < p
+    # the dropped block is Q_2 R_22
+    drop = Anp[:, f] - Anp[:, c] @ T
+    assert abs(np.linalg.norm(drop) - np.linalg.norm(R22)) <= 1e-10 * np.linalg.norm(Anp)
+    # dense: K = [[A_pp, A_pn], [A_np, A_nn]] in the order (c, f, n)
+    order = np.concatenate([c, f])
+    Ann = Anp @ np.linalg.solve(App, Anp.T) + np.eye(m)  # any SPD completion
+    K = np.block([[App[np.ix_(order, order)], Anp[:, order].T], [Anp[:, order], Ann]])
+    r, nf = c.size, f.size
+    Tp = np.eye(p + m)
+    Tp[:r, r:r + nf] = -T                                  # T_p: block (c, f) = -T_cf
+    K2 = Tp.T @ K @ Tp
+    assert np.linalg.norm(K2[p:, r:p] - drop) <= 1e-10 * np.linalg.norm(K)
+    K2[p:, r:p] = 0.0                                      # drop the (n, f) coupling
+    K2[r:p, p:] = 0.0
+    Cff = K2[r:p, r:p]
+    assert np.allclose(Lf @ Lf.T, Cff, rtol=1e-12, atol=1e-12 * np.linalg.norm(Cff))
+    keep = np.r_[0:r, p:p + m]
+    S = K2[np.ix_(keep, keep)] - K2[np.ix_(keep, np.arange(r, p))] @ np.linalg.solve(Cff, K2[np.ix_(np.arange(r, p), keep)])
+    assert np.allclose(S[:r, :r], Acc, rtol=1e-10, atol=1e-10 * np.linalg.norm(App))
+    assert np.allclose(S[:r, r:], Anp[:, c].T, rtol=1e-12, atol=1e-12)  # A_cn: a subset of A_pn
+
+
+def test_scaled_block_gives_identity_plus_TtT():
+    Anp, _ = _interface(4)
+    p = Anp.shape[1]
+    c, f, T, Lf, Xfc, Acc, _ = O.sparsify_interface_interp(Anp, np.eye(p), 1e-1)
+    assert f.size > 0
+    assert np.allclose(Lf @ Lf.T, np.eye(f.size) + T.T @ T, rtol=1e-12, atol=1e-12)
+    # C_cf = -T_cf, so A_cc = I - T (I + T^T T)^{-1} T^T
+    ref = np.eye(c.size) - T @ np.linalg.solve(np.eye(f.size) + T.T @ T, T.T)
+    assert np.allclose(Acc, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_interpolative_without_scaling_is_least_accurate():
+    p = I.laplacian_2d(32)
+    b = I.rhs(p.n, 0)
+    it = {v: O.solve(p, b, 6, 1e-1, variant=v).iters for v in O.VARIANTS}
+    assert it["In"] > it["InS"], it
+    assert it["In"] > it["OrthS"], it
+    assert it["InS"] <= it["OrthS"] + 2, it
+
+
+@pytest.mark.parametrize("gen,L", [(lambda: I.laplacian_2d(24), 6), (lambda: I.high_contrast_2d(24, 1000, 1), 6),
+                                   (lambda: I.laplacian_3d(8), 5)])
+def test_large_eps_orths_never_breaks(gen, L):
+    p = gen()
+    b = I.rhs(p.n, 1)
+    r = O.solve(p, b, L, 0.9, variant="OrthS")
+    assert r.relres <= 1e-10
+    for v in ("InS", "In"):
+        try:
+            r = O.solve(p, b, L, 0.9, variant=v)
+        except O.NotSPDError:
+            continue
+        assert r.relres <= 1e-10
+
+
+def test_unknown_variant_is_rejected():
+    p = I.laplacian_2d(4)
+    tree = O.analyze(p.n, p.rowptr, p.colind, p.coords, 2)
+    with pytest.raises(ValueError):
+        O.factorize(p.rowptr, p.colind, p.vals, tree, 1e-2, variant="Orth")
