@@ -24,7 +24,13 @@ What it computes, step by step in the paper's order and notation:
                       paper names for its low-rank step).  ``variant`` selects
                       the ablation variants of Sec. 4.3: "In" (interpolative
                       transformations, Sec. 2.6.2, no block scaling) and "InS"
-                      (interpolative with block scaling) instead of "OrthS".
+                      (interpolative with block scaling) instead of "OrthS";
+                      "OrthS-rand" keeps OrthS but finds the basis of each
+                      interface with a randomized range finder (the
+                      randomized alternative of Sec. 2.6.2 and the
+                      conclusion; method of Halko, Martinsson and Tropp,
+                      SIAM Review 2011, Algorithm 4.2 with a doubling
+                      sketch), see ``sparsify_interface_rand``.
 * ``apply``        -- z = M M^T r with M the product of the elementary
                       transforms (Sec. 2.8): forward sweep leaf->root, backward
                       sweep root->leaf with transposes.
@@ -384,17 +390,69 @@ def sparsify_interface_interp(Anp: np.ndarray, App: np.ndarray, eps: float):
     return c, f, T, Lf, Xfc, Acc, R22
 
 
-VARIANTS = ("OrthS", "InS", "In")
+RAND_OVERSAMPLE = 10   # sketch columns beyond the rank (HMT 2011, Sec. 4.2)
+RAND_ELL0 = 32         # first sketch width; doubled while the rank saturates it
+
+
+def sparsify_interface_rand(Apn: np.ndarray, eps: float, Omega: np.ndarray,
+                            oversample: int = RAND_OVERSAMPLE, ell0: int = RAND_ELL0):
+    """Orthogonal sparsification of one scaled interface with a randomized
+    range finder in place of the column-pivoted QR of A_pn.
+
+    Omega is an m x min(p, m) Gaussian test matrix (an input: the random
+    numbers are drawn outside).  With ell = min(ell0, min(p, m)) sketch
+    columns, Y = A_pn Omega[:, :ell] samples the range of A_pn and the
+    column-pivoted QR Y P = Q R orders an orthogonal basis Q (p x p) of it.
+    W = Q^T A_pn.  The rank follows the meaning of the truncation rule of
+    Sec. 4: in a column-pivoted QR |R_kk| is the largest column norm of the
+    part of A_pn outside the first k basis vectors, so here r = the first
+    k <= ell with  max_j ||W[k:, j]|| < eps max_j ||A_pn[:, j]||.  If no
+    k <= ell qualifies, or r > ell - oversample (the sketch may miss part of
+    the range), ell doubles, capped at min(p, m), where range(Y) = range(A_pn)
+    with probability one; at the cap r = ell if still no k qualifies, so
+    eps = 0 stays exact.  Then, as in Sec. 2.6.1, c = the first r columns of
+    Q, W_cn = W[:r] is kept and W_fn = W[r:] dropped.
+    Returns (Q, r, W_cn, W_fn, ell)."""
+    p, m = Apn.shape
+    if m == 0:
+        return np.eye(p), p, np.zeros((p, 0)), np.zeros((0, 0)), 0
+    if p == 0:
+        return np.eye(0), 0, np.zeros((0, m)), np.zeros((0, m)), 0
+    ell_max = min(p, m)
+    if Omega.shape != (m, ell_max):
+        raise ValueError("sketch must be m x min(p, m)")
+    a0 = np.sqrt((Apn * Apn).sum(axis=0)).max()
+    ell = min(ell0, ell_max)
+    while True:
+        Y = Apn @ Omega[:, :ell]
+        Q, _, _ = sla.qr(Y, pivoting=True, mode="full")
+        W = Q.T @ Apn
+        # res[k] = max_j ||W[k:, j]||, k = 0..ell
+        tail = np.cumsum((W * W)[::-1], axis=0)[::-1]
+        res = np.sqrt(np.vstack([tail, np.zeros((1, m))]).max(axis=1))[:ell + 1]
+        below = np.nonzero(res < eps * a0)[0]
+        r = int(below[0]) if below.size else ell
+        if ell == ell_max or (below.size and r <= ell - oversample):
+            break
+        ell = min(2 * ell, ell_max)
+    return Q, r, W[:r], W[r:], ell
+
+
+VARIANTS = ("OrthS", "InS", "In", "OrthS-rand")
 
 
 def factorize(prob_rowptr, prob_colind, prob_vals, tree: Tree, eps: float, skip: int = 0,
-              trace: Optional[list] = None, variant: str = "OrthS") -> Factor:
+              trace: Optional[list] = None, variant: str = "OrthS", sketch=None) -> Factor:
     """Algorithm 2.  ``trace`` (a list, tests only) receives (step, phase,
     set of block keys) before and after each level's sparsification.
     ``variant``: "OrthS" (Algorithm 2), "InS" or "In" (Sec. 4.3 ablation:
-    interpolative transformations with / without the block scaling)."""
+    interpolative transformations with / without the block scaling), or
+    "OrthS-rand" (OrthS with the randomized range finder); the latter needs
+    ``sketch(step, cluster, m, ell)`` returning an m x ell Gaussian matrix."""
     if variant not in VARIANTS:
         raise ValueError(f"unknown variant {variant!r}")
+    if variant == "OrthS-rand" and sketch is None:
+        raise ValueError("the randomized variant needs a sketch generator")
     n, L = tree.n, tree.L
     rowptr = np.asarray(prob_rowptr, dtype=np.int64)
     colind = np.asarray(prob_colind, dtype=np.int64)
@@ -494,7 +552,7 @@ def factorize(prob_rowptr, prob_colind, prob_vals, tree: Tree, eps: float, skip:
                     if not nb:
                         continue
                     widths = [int(size[q]) for q in nb]
-                    if variant != "OrthS":
+                    if variant in ("InS", "In"):
                         Anp = np.vstack([blocks[(q, p)] for q in nb])
                         cl, fl, T, Lf, Xfc, Acc, _ = sparsify_interface_interp(Anp, blocks[(p, p)], eps)
                         r = int(cl.size)
@@ -512,7 +570,12 @@ def factorize(prob_rowptr, prob_colind, prob_vals, tree: Tree, eps: float, skip:
                         slots[p] = cs
                         continue
                     Apn = np.hstack([blocks[(p, q)] for q in nb]) if nb else np.zeros((size[p], 0))
-                    Q, r, Wc, _ = sparsify_interface(Apn, eps)
+                    if variant == "OrthS-rand":
+                        m = Apn.shape[1]
+                        Om = sketch(t, p, m, min(int(size[p]), m))
+                        Q, r, Wc, _, _ = sparsify_interface_rand(Apn, eps, Om)
+                    else:
+                        Q, r, Wc, _ = sparsify_interface(Apn, eps)
                     off = 0
                     for q, w in zip(nb, widths):
                         blocks[(p, q)] = Wc[:, off:off + w].copy()
@@ -661,11 +724,11 @@ class Result:
 
 
 def solve(prob, b, L: int, eps: float, skip: int = 0, tol: float = 1e-10, maxit: int = 500,
-          use_coords: bool = True, variant: str = "OrthS") -> Result:
+          use_coords: bool = True, variant: str = "OrthS", sketch=None) -> Result:
     """analyze + factorize + PCG on the original ordering of b / x."""
     coords = prob.coords if use_coords else None
     tree = analyze(prob.n, prob.rowptr, prob.colind, coords, L)
-    F = factorize(prob.rowptr, prob.colind, prob.vals, tree, eps, skip, variant=variant)
+    F = factorize(prob.rowptr, prob.colind, prob.vals, tree, eps, skip, variant=variant, sketch=sketch)
     Ap = permuted_matrix(prob.rowptr, prob.colind, prob.vals, tree.perm)
     xp, it, rr = pcg(Ap, np.asarray(b)[tree.perm], lambda r: apply(F, r), tol, maxit)
     x = np.empty(prob.n)

@@ -227,6 +227,16 @@ def batch_diffusion_2d(i: int):
     return p, xs, b, int(round(np.log2(p.n / 32))) + 1
 
 
+def sketch_gaussian(seed: int, step: int, cluster: int, m: int, ell: int) -> np.ndarray:
+    """Gaussian test matrix (m x ell) with i.i.d. N(0, 1) entries for the
+    randomized compression of one interface: drawn column by column from
+    PCG64 seeded by the triple (seed, step, cluster), so that the first j
+    columns are the same for every ell >= j (a sketch can grow without
+    redrawing)."""
+    g = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, step, cluster])))
+    return g.standard_normal((ell, m)).T
+
+
 def rhs(n: int, seed: int) -> np.ndarray:
     """b ~ N(0, 1), seeded."""
     return rng(seed).standard_normal(n)

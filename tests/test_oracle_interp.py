@@ -86,7 +86,7 @@ def test_scaled_block_gives_identity_plus_TtT():
 def test_interpolative_without_scaling_is_least_accurate():
     p = I.laplacian_2d(32)
     b = I.rhs(p.n, 0)
-    it = {v: O.solve(p, b, 6, 1e-1, variant=v).iters for v in O.VARIANTS}
+    it = {v: O.solve(p, b, 6, 1e-1, variant=v).iters for v in ("OrthS", "InS", "In")}
     assert it["In"] > it["InS"], it
     assert it["In"] > it["OrthS"], it
     assert it["InS"] <= it["OrthS"] + 2, it

@@ -1,0 +1,116 @@
+"""Pins of the oracle's randomized sparsification ("OrthS-rand": OrthS with
+the column-pivoted QR of A_pn replaced by a randomized range finder, the
+randomized alternative the paper names in Sec. 2.6.2 and its conclusion),
+checked against dense linear algebra and library routines, not against the
+oracle's own formulas:
+
+* the sketch generator is seeded and nested (growing a sketch keeps its
+  first columns);
+* eps = 0: the sketch grows to min(p, m) columns, whose range is that of
+  A_pn, so M M^T = A^{-1} (dense check on small 2D / 3D problems);
+* an interface of exact rank k (below and above the first sketch width):
+  r = k, the sketch grows only when k saturates it, nothing of A_pn is lost;
+* decaying spectra: Q is orthogonal, the dropped block Q_f^T A_pn is at
+  least sigma_{r+1}(A_pn) (Eckart-Young) and at most sqrt(m) eps times the
+  largest column of A_pn (the column-norm meaning of the truncation rule of
+  Sec. 4), and r stays within a few of scipy's column-pivoted QR rank;
+* whole solver on 2D / 3D Laplacians: ranks within 15 % of OrthS's, PCG
+  iterations within OrthS's + 3, x equal to OrthS's x at the PCG tolerance,
+  and no breakdown at eps = 0.9 (the transform stays orthogonal).
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from oracle import spand_oracle as O
+from paper_1901_02971_gb300 import inputs as I
+
+
+def _sketch(seed=0):
+    return lambda t, p, m, ell: I.sketch_gaussian(seed, t, p, m, ell)
+
+
+def test_sketch_generator_is_seeded_and_nested():
+    a = I.sketch_gaussian(3, 2, 7, 50, 20)
+    assert a.shape == (50, 20)
+    assert np.array_equal(a[:, :8], I.sketch_gaussian(3, 2, 7, 50, 8))
+    assert np.array_equal(a, I.sketch_gaussian(3, 2, 7, 50, 20))
+    assert not np.array_equal(a, I.sketch_gaussian(3, 2, 8, 50, 20))
+    assert abs(a.mean()) < 0.1 and abs(a.std() - 1) < 0.1
+
+
+@pytest.mark.parametrize("gen,L", [(lambda: I.laplacian_2d(12), 5), (lambda: I.laplacian_3d(6), 4),
+                                   (lambda: I.diffusion_2d(12, 3), 5)])
+def test_rand_exact_at_eps0(gen, L):
+    p = gen()
+    tree = O.analyze(p.n, p.rowptr, p.colind, p.coords, L)
+    F = O.factorize(p.rowptr, p.colind, p.vals, tree, 0.0, variant="OrthS-rand", sketch=_sketch())
+    A = O.permuted_matrix(p.rowptr, p.colind, p.vals, tree.perm).toarray()
+    assert np.linalg.norm(O.dense_preconditioner(F, p.n) @ A - np.eye(p.n)) <= 1e-10 * p.n
+
+
+def _lowrank(seed, p, m, sig):
+    rng = np.random.default_rng(seed)
+    k = sig.size
+    U = np.linalg.qr(rng.standard_normal((p, k)))[0]
+    V = np.linalg.qr(rng.standard_normal((m, k)))[0]
+    return U @ np.diag(sig) @ V.T
+
+
+@pytest.mark.parametrize("k,ell", [(20, 32), (25, 64), (40, 64), (70, 80)])
+def test_exact_rank_interface(k, ell):
+    p, m = 80, 200
+    A = _lowrank(k, p, m, np.linspace(1.0, 0.5, k))
+    Q, r, Wc, Wf, ell_used = O.sparsify_interface_rand(A, 1e-8, I.sketch_gaussian(1, 1, k, m, p))
+    assert r == k
+    assert ell_used == ell  # 32; doubled to 64 once r > 32 - 10 oversampling columns; capped at min(p, m) = 80
+    assert np.linalg.norm(Q.T @ Q - np.eye(p)) <= 1e-13 * p
+    assert np.linalg.norm(A - Q[:, :r] @ Wc) <= 1e-12 * np.linalg.norm(A)
+    assert np.linalg.norm(Wf) <= 1e-12 * np.linalg.norm(A)
+
+
+@pytest.mark.parametrize("seed", range(3))
+@pytest.mark.parametrize("p,m,decay", [(80, 200, 0.8), (120, 400, 0.9), (60, 50, 0.7), (200, 600, 0.95)])
+@pytest.mark.parametrize("eps", [1e-1, 1e-2, 1e-4])
+def test_decaying_spectrum_interface(seed, p, m, decay, eps):
+    A = _lowrank(seed, p, m, decay ** np.arange(min(p, m)))
+    Q, r, Wc, _, _ = O.sparsify_interface_rand(A, eps, I.sketch_gaussian(seed, 1, 2, m, min(p, m)))
+    assert np.linalg.norm(Q.T @ Q - np.eye(p)) <= 1e-13 * p
+    assert np.allclose(Wc, Q[:, :r].T @ A, atol=1e-13)
+    drop = np.linalg.norm(Q[:, r:].T @ A, 2) if r < p else 0.0
+    sig = np.linalg.svd(A, compute_uv=False)
+    a0 = np.linalg.norm(A, axis=0).max()
+    assert drop <= np.sqrt(m) * eps * a0
+    if r < sig.size:
+        assert drop >= sig[r] * (1 - 1e-12)
+    _, R, _ = sla.qr(A, pivoting=True)
+    rc = O.truncation_rank(np.diag(R), eps)
+    assert rc - 2 <= r <= 1.1 * rc + 3, (r, rc)
+
+
+@pytest.mark.parametrize("gen,L", [(lambda: I.laplacian_2d(32), 6), (lambda: I.laplacian_3d(12), 5)])
+@pytest.mark.parametrize("eps", [1e-1, 1e-2])
+def test_solver_close_to_orths(gen, L, eps):
+    p = gen()
+    b = I.rhs(p.n, 2)
+    a = O.solve(p, b, L, eps)
+    r = O.solve(p, b, L, eps, variant="OrthS-rand", sketch=_sketch())
+    ra = sum(sum(d.values()) for d in a.factor.ranks)
+    rr = sum(sum(d.values()) for d in r.factor.ranks)
+    assert 0.97 * ra <= rr <= 1.15 * ra, (rr, ra)
+    assert r.iters <= a.iters + 3, (r.iters, a.iters)
+    assert r.relres <= 1e-10
+    assert np.linalg.norm(r.x - a.x) <= 1e-8 * np.linalg.norm(a.x)
+
+
+def test_rand_never_breaks_at_large_eps():
+    for p, L in [(I.laplacian_2d(24), 6), (I.high_contrast_2d(24, 1000, 1), 6), (I.laplacian_3d(8), 5)]:
+        r = O.solve(p, I.rhs(p.n, 1), L, 0.9, variant="OrthS-rand", sketch=_sketch(5))
+        assert r.relres <= 1e-10
+
+
+def test_rand_needs_a_sketch():
+    p = I.laplacian_2d(4)
+    tree = O.analyze(p.n, p.rowptr, p.colind, p.coords, 2)
+    with pytest.raises(ValueError):
+        O.factorize(p.rowptr, p.colind, p.vals, tree, 1e-2, variant="OrthS-rand")
