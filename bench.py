@@ -224,6 +224,17 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(vals, dist=None, device="cpu"):
+    """Element-wise maximum of per-rank timings over the process group (the
+    replicas' whole-job time is the slowest rank's); identity without one."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return [float(v) for v in vals]
+    import torch
+    tt = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return tt.tolist()
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -375,10 +386,7 @@ def main():
             e2e.append(time.perf_counter() - t0)
     v = statistics.mean(t32)
     ve = statistics.mean(e2e)
-    if dist is not None:
-        tt = torch.tensor([v, ve], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        v, ve = tt.tolist()
+    v, ve = max_over_ranks([v, ve], dist, "cuda")
     if rank != 0:
         return 0
     peaks = load_peaks()
