@@ -1863,8 +1863,21 @@ int spand_factorize(spand_handle h, const double* vals, void* cuda_stream) {
   h->tmp_len = 0;
   h->save_len = 0;
   int rc;
-  if (h->opts.precision == SPAND_FP64) rc = factorize_impl<double>(h, s);
-  else rc = factorize_impl<float>(h, s);
+  if (n == 0) {  // empty system: an empty factorization (apply and solve return at once)
+    h->sizes_before.assign(h->tree.L, {});
+    h->sizes_after.assign(h->tree.L, {});
+    for (double& v : h->phase_ms) v = 0;
+    h->st.size_top = 0;
+    h->st.mem_f = 0;
+    h->st.factor_flops = 0;
+    h->st.fail_step = 0;
+    h->st.fail_cluster = -1;
+    rc = SPAND_OK;
+  } else if (h->opts.precision == SPAND_FP64) {
+    rc = factorize_impl<double>(h, s);
+  } else {
+    rc = factorize_impl<float>(h, s);
+  }
   h->fprec = h->opts.precision;
   CK(cudaStreamSynchronize(s));
   h->st.t_factor_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -27,6 +27,11 @@ def _compare(p, levels, geo=True):
         L.spand_destroy(h)
 
 
+def _empty():
+    """The empty system (n = 0): no clusters, every step empty."""
+    return I.Problem("empty", 0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0), np.zeros((0, 2)), 2)
+
+
 CASES = [
     ("lapl2d_8_L3", lambda: I.laplacian_2d(8), 3, True),
     ("lapl2d_64_L8", lambda: I.laplacian_2d(64), 8, True),
@@ -36,6 +41,7 @@ CASES = [
     ("diff3d_12_L5", lambda: I.diffusion_3d(12, 2, block=3), 5, True),
     ("diff2d_30_L6_nogeo", lambda: I.diffusion_2d(30, 4), 6, False),
     ("knn_3000_L7", lambda: I.knn_laplacian(3000, 10, 3), 7, False),
+    ("empty_L3", lambda: _empty(), 3, True),
     ("lapl2d_1_L1", lambda: I.laplacian_2d(1), 1, True),
     ("lapl2d_2_L3", lambda: I.laplacian_2d(2), 3, True),
     # extruded thin 3D mesh, partitioned with its (x, y) coordinates only

@@ -175,6 +175,25 @@ def test_single_unknown_and_one_level(cuda_ok):
         s.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_empty_system(cuda_ok, precision):
+    """n = 0: analyze, factorize, solve and apply succeed and do nothing."""
+    import torch
+    p = I.Problem("empty", 0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0), np.zeros((0, 2)), 2)
+    s, x, it, rr = _run(p, np.zeros(0), 3, 1e-2, precision=precision)
+    try:
+        assert x.size == 0 and it == 0 and rr == 0.0
+        st = s.stats()
+        assert st.size_top == 0 and st.mem_f == 0
+        xd, it, rr = s.solve(torch.zeros(0, dtype=torch.float64, device="cuda"))
+        assert xd.numel() == 0 and it == 0
+        assert s.apply(torch.zeros(0, dtype=torch.float64, device="cuda")).numel() == 0
+        sb, sa = s.ranks(1)
+        assert len(sb) == 0 and len(sa) == 0
+    finally:
+        s.close()
+
+
 def test_more_levels_than_vertices(cuda_ok):
     """Empty separators / interiors (levels far beyond log2 N)."""
     p = I.laplacian_2d(3)
