@@ -13,6 +13,10 @@ and against what the paper states, not against the oracle's own formulas:
   needs more PCG iterations than InS and OrthS; InS stays close to OrthS.
 * OrthS never breaks down (eps up to 0.9); In / InS either converge or stop
   with NotSPDError (the paper's reported failure mode), nothing else.
+* The breakdown itself (Sec. 4.3): on a high-contrast 2D problem (rho =
+  1000, 64², two field seeds) at eps = 0.3, InS loses positive definiteness
+  at a later level (a scaling Cholesky fails), while every Cholesky of
+  OrthS succeeds on the same input (and PCG converges on the first seed).
 """
 import numpy as np
 import pytest
@@ -112,3 +116,15 @@ def test_unknown_variant_is_rejected():
     tree = O.analyze(p.n, p.rowptr, p.colind, p.coords, 2)
     with pytest.raises(ValueError):
         O.factorize(p.rowptr, p.colind, p.vals, tree, 1e-2, variant="Orth")
+
+
+@pytest.mark.parametrize("seed", [1, 3])
+def test_interpolative_breaks_down_where_orthogonal_does_not(seed):
+    p = I.high_contrast_2d(64, 1000, seed)
+    b = I.rhs(p.n, 1)
+    with pytest.raises(O.NotSPDError, match="scaling step"):
+        O.solve(p, b, 8, 0.3, variant="InS")
+    tree = O.analyze(p.n, p.rowptr, p.colind, p.coords, 8)
+    O.factorize(p.rowptr, p.colind, p.vals, tree, 0.3, variant="OrthS")  # every Cholesky succeeds
+    if seed == 1:  # with seed 3 FP64 PCG stalls at 2-5e-10 (measured at eps 1e-2, 0.1 and 0.3: its accuracy floor)
+        assert O.solve(p, b, 8, 0.3, variant="OrthS").relres <= 1e-10
