@@ -310,8 +310,8 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def run_form(precision, steps, warmup, timed_clocks=False, skip=0):
-        s = Solver.from_problem(p, levels=levels, eps=EPS, precision=precision, skip=skip)
+    def run_form(precision, steps, warmup, timed_clocks=False, skip=0, order="coloured"):
+        s = Solver.from_problem(p, levels=levels, eps=EPS, precision=precision, skip=skip, sparsify_order=order)
         for _ in range(warmup):
             s.factorize(vals_d)
             s.solve(b_d, x_d)
@@ -367,6 +367,16 @@ def main():
         sweep[str(sk)] = {"s_per_step": statistics.mean(ts), "iters": its[-1], "size_top": sst.size_top,
                           "mem_f": sst.mem_f}
         ss.close()
+    # the simultaneous sparsification order (an option: every interface of a
+    # level compressed from the same scaled matrix in one launch), same form
+    try:
+        ssim, tsim, itsim, rrsim, _, _ = run_form(args.form, 2, 1, order="simultaneous")
+        phs = ssim.phase_times()
+        sim = {"s_per_step": statistics.mean(tsim), "iters": itsim[-1], "relres": rrsim,
+               "t_factor_ms_phases": list(phs[:4]), "size_top": ssim.stats().size_top, "mem_f": ssim.stats().mem_f}
+        ssim.close()
+    except Exception as e:  # reported, never fatal to the headline line
+        sim = {"error": str(e)[:300]}
     st64 = s64.stats()
     ph64 = s64.phase_times()
     # accuracy of x of each form against each other (FP64 reference on the GPU)
@@ -412,6 +422,7 @@ def main():
             "x_rel_diff_mixed_vs_fp64": float(np.linalg.norm(x32 - x64) / np.linalg.norm(x64)),
             "true_relres_host": relres_host,
             "skip_sweep_mixed_" + args.form: sweep,
+            "mixed_" + args.form + "_simultaneous_order": sim,
         },
         "e2e": {"value": ve, "unit": "s", "h2d_bytes_per_step": int(p.nnz * 8 + p.n * 8),
                 "d2h_bytes_per_step": int(p.n * 8)},

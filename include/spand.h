@@ -65,6 +65,21 @@ enum {
                       factor stored in FP32) */
 };
 
+/* order of the sparsifications inside a level (Algorithm 2 applies S_p to
+ * every interface p of the level; Sec. 2.6.1) */
+enum {
+  SPAND_COLOURED = 0,     /* greedy distance-1 colouring of the interfaces;
+                             colours in sequence, each interface compressed
+                             from the matrix its earlier-coloured neighbours
+                             left (a sequential order of Algorithm 2) */
+  SPAND_SIMULTANEOUS = 1  /* every interface compressed from the same scaled
+                             matrix, then every coupling block transformed
+                             from both sides, A_pq <- Q_pc^T A_pq Q_qc (one
+                             launch per level; the kept matrix is a principal
+                             submatrix of an orthogonal similarity, so SPD);
+                             differs from the coloured order at O(eps) */
+};
+
 typedef struct spand_handle_s* spand_handle;
 
 typedef struct {
@@ -75,9 +90,11 @@ typedef struct {
   int32_t precision;  /* SPAND_FP64, SPAND_FP32, SPAND_TF32 or SPAND_BF16 */
   int32_t maxit;      /* PCG iteration cap (paper: 500) */
   double tol;         /* PCG relative residual target (paper: 1e-12) */
+  int32_t sparsify_order; /* SPAND_COLOURED or SPAND_SIMULTANEOUS */
 } spand_opts;
 
-/* Fills *opts with levels 8, eps 1e-2, skip 0, FP64, maxit 500, tol 1e-10. */
+/* Fills *opts with levels 8, eps 1e-2, skip 0, FP64, maxit 500, tol 1e-10,
+ * coloured sparsification order. */
 void spand_default_opts(spand_opts* opts);
 
 /*

@@ -59,6 +59,10 @@ Readings where the paper is silent (they are the same for the product path):
 * Order of sparsification inside a level: greedy distance-1 colouring of the
   cluster graph (after the level's fill) in cluster order; colours are
   processed in increasing order, clusters of one colour are independent.
+  Option ``order="simultaneous"`` (OrthS only): every interface of the level
+  takes its pivoted QR from the same scaled matrix, then every coupling
+  block becomes A_pq <- Q_pc^T A_pq Q_qc (the c-c principal submatrix of
+  the orthogonal similarity diag(Q_p)^T A diag(Q_p), hence SPD).
 * Truncation: r = longest prefix with |R_ii| >= eps |R_11|; r = 0 when R_11 = 0
   (p is exactly decoupled).  A cluster with no neighbours (A_pn has no columns)
   is left as it is: there is nothing to compress it against, and keeping it
@@ -442,7 +446,8 @@ VARIANTS = ("OrthS", "InS", "In", "OrthS-rand")
 
 
 def factorize(prob_rowptr, prob_colind, prob_vals, tree: Tree, eps: float, skip: int = 0,
-              trace: Optional[list] = None, variant: str = "OrthS", sketch=None) -> Factor:
+              trace: Optional[list] = None, variant: str = "OrthS", sketch=None,
+              order: str = "coloured") -> Factor:
     """Algorithm 2.  ``trace`` (a list, tests only) receives (step, phase,
     set of block keys) before and after each level's sparsification.
     ``variant``: "OrthS" (Algorithm 2), "InS" or "In" (Sec. 4.3 ablation:
@@ -453,6 +458,8 @@ def factorize(prob_rowptr, prob_colind, prob_vals, tree: Tree, eps: float, skip:
         raise ValueError(f"unknown variant {variant!r}")
     if variant == "OrthS-rand" and sketch is None:
         raise ValueError("the randomized variant needs a sketch generator")
+    if order not in ("coloured", "simultaneous") or (order == "simultaneous" and variant != "OrthS"):
+        raise ValueError(f"order {order!r} is not available for variant {variant!r}")
     n, L = tree.n, tree.L
     rowptr = np.asarray(prob_rowptr, dtype=np.int64)
     colind = np.asarray(prob_colind, dtype=np.int64)
@@ -544,6 +551,36 @@ def factorize(prob_rowptr, prob_colind, prob_vals, tree: Tree, eps: float, skip:
             if trace is not None:
                 trace.append((t, "pre", frozenset(blocks)))
             ncol = int(st.colour.max()) + 1 if rem else 0
+            if order == "simultaneous":
+                # all interfaces from the same scaled matrix, then the
+                # two-sided transform of every coupling block
+                Qs = {}
+                for p in rem:
+                    nb = st.adjf[p]
+                    if not nb:
+                        continue
+                    Apn = np.hstack([blocks[(p, q)] for q in nb])
+                    Q, r, _, _ = sparsify_interface(Apn, eps)
+                    Qs[p] = (Q, r)
+                for (a, b_) in list(blocks):
+                    if a != b_ and a < b_:
+                        Qa, ra = Qs[a]
+                        Qb, rb = Qs[b_]
+                        X = Qa[:, :ra].T @ blocks[(a, b_)] @ Qb[:, :rb]
+                        blocks[(a, b_)] = X
+                        blocks[(b_, a)] = X.T.copy()
+                for p in rem:
+                    if p not in Qs:
+                        continue
+                    Q, r = Qs[p]
+                    blocks[(p, p)] = np.eye(r)
+                    F.ops.append(("Q", slots[p], Q))
+                    pz = int(size[p])
+                    F.mem_f += int(r * pz - r * (r + 1) // 2 + r)
+                    ranks[p] = r
+                    size[p] = r
+                    slots[p] = slots[p][:r]
+                ncol = 0
             for c in range(ncol):
                 for p in rem:
                     if st.colour[p] != c:
@@ -724,11 +761,11 @@ class Result:
 
 
 def solve(prob, b, L: int, eps: float, skip: int = 0, tol: float = 1e-10, maxit: int = 500,
-          use_coords: bool = True, variant: str = "OrthS", sketch=None) -> Result:
+          use_coords: bool = True, variant: str = "OrthS", sketch=None, order: str = "coloured") -> Result:
     """analyze + factorize + PCG on the original ordering of b / x."""
     coords = prob.coords if use_coords else None
     tree = analyze(prob.n, prob.rowptr, prob.colind, coords, L)
-    F = factorize(prob.rowptr, prob.colind, prob.vals, tree, eps, skip, variant=variant, sketch=sketch)
+    F = factorize(prob.rowptr, prob.colind, prob.vals, tree, eps, skip, variant=variant, sketch=sketch, order=order)
     Ap = permuted_matrix(prob.rowptr, prob.colind, prob.vals, tree.perm)
     xp, it, rr = pcg(Ap, np.asarray(b)[tree.perm], lambda r: apply(F, r), tol, maxit)
     x = np.empty(prob.n)

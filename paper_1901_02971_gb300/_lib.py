@@ -29,6 +29,8 @@ SPAND_FP64 = 0
 SPAND_FP32 = 1
 SPAND_TF32 = 2
 SPAND_BF16 = 3
+SPAND_COLOURED = 0
+SPAND_SIMULTANEOUS = 1
 
 # every function declared in include/spand.h
 EXPORTS = ["spand_default_opts", "spand_analyze", "spand_analyze_batch", "spand_factorize", "spand_solve", "spand_apply",
@@ -42,7 +44,8 @@ KERNEL_FAMILIES = ["potrf", "trsm", "schur", "cpqr", "copy", "apply", "pcg"]
 
 class Opts(C.Structure):
     _fields_ = [("levels", C.c_int32), ("eps", C.c_double), ("skip", C.c_int32),
-                ("precision", C.c_int32), ("maxit", C.c_int32), ("tol", C.c_double)]
+                ("precision", C.c_int32), ("maxit", C.c_int32), ("tol", C.c_double),
+                ("sparsify_order", C.c_int32)]
 
 
 class Problem(C.Structure):

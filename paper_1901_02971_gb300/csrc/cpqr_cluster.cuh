@@ -51,8 +51,18 @@ struct CpqrTask {
   T* V;               // np x np capacity, column k = v_k (v_k[k] = 1, rows above k unused)
   T* tau;             // np: tau_k of the reflectors, for k_form_q
   T* Qc;              // np x np capacity; first r columns = Q_pc after k_form_q
+  int32_t* rank_out;  // where the rank goes; nullptr: the cur_size array the sizes are read from
   int32_t p, np, ldp, nbeg, nend, m_max;
+  int32_t nowb;       // 1: leave the blocks untouched (no W_cn write-back, simultaneous order)
 };
+
+// Destination of the rank of task d: a separate array when every interface of
+// a level is sparsified from the same matrix (the neighbours' sizes must not
+// change while the launch reads them), else the size array itself.
+template <typename T>
+__device__ __forceinline__ int32_t* cq_rank_dst(const CpqrTask<T>& d, int32_t* cur_size) {
+  return d.rank_out ? d.rank_out : cur_size;
+}
 
 template <typename T>
 struct CqVec;
@@ -212,7 +222,8 @@ __device__ __forceinline__ void cq_form_q_any(const CpqrTask<T>& d, const T* V, 
 // Epilogue shared by the sparsification kernels, entered after a block barrier
 // with the CTA's final columns in `chunk` (column-major, stride L): the write-back
 // of W_cn into p's and the neighbours' block rows, A_cc = I, the reflectors
-// (V, tau) from which k_form_q forms Q_pc, and the rank in cur_size[p].
+// (V, tau) from which k_form_q forms Q_pc, and the rank in cur_size[p] (or
+// the task's rank_out); with nowb the blocks are left as they are.
 template <typename T, int NT>
 __device__ __forceinline__ void cq_finish(const CpqrTask<T>& d, cg::cluster_group& cluster, int C, int rank,
                                           const T* chunk, int L, int np, int r, int nc, int j0,
@@ -230,12 +241,13 @@ __device__ __forceinline__ void cq_finish(const CpqrTask<T>& d, cg::cluster_grou
     return i == s ? beta_s[s] : T(0);
   };
   // ---- write back W_cn into p's row (one warp per column, coalesced) ...
-  for (int jl = warp; jl < nc; jl += NW) {
+  const int nwb = d.nowb ? 0 : nc;
+  for (int jl = warp; jl < nwb; jl += NW) {
     T* dst = d.Rp + (size_t)tcol[cpm + jl] * d.ldp;
     for (int i = lane; i < r; i += 32) dst[i] = wval(jl, i);
   }
   // ... and its transpose into the neighbours' rows (one thread per column)
-  for (int jl = tid; jl < nc; jl += NT) {
+  for (int jl = tid; jl < nwb; jl += NT) {
     const int e = tcol[jl];
     const CpqrNbr<T> nb = nbr[e];
     const int cc = j0 + jl - cstart[e];
@@ -257,7 +269,7 @@ __device__ __forceinline__ void cq_finish(const CpqrTask<T>& d, cg::cluster_grou
   }
   if (rank == 0)
     for (int k = tid; k < r; k += NT) d.tau[k] = tau_s[k];
-  if (rank == 0 && tid == 0) cur_size[d.p] = r;
+  if (rank == 0 && tid == 0) cq_rank_dst(d, cur_size)[d.p] = r;
   if (C > 1) cluster.sync();  // no CTA leaves while another may still address its shared memory
 }
 
@@ -334,7 +346,7 @@ __global__ void __launch_bounds__(NT) k_cpqr_cluster(const CpqrTask<T>* __restri
   if (m == 0) {  // every neighbour reduced to nothing: p is kept as it is (Q_pc = I, all tau = 0)
     if (rank == 0) {
       for (int k = tid; k < np; k += NT) d.tau[k] = T(0);
-      if (tid == 0) cur_size[d.p] = np;
+      if (tid == 0) cq_rank_dst(d, cur_size)[d.p] = np;
     }
     return;  // uniform across the cluster (m is the same for every CTA)
   }
@@ -559,7 +571,7 @@ __global__ void __launch_bounds__(NT) k_cpqr_cluster(const CpqrTask<T>* __restri
 
 // Q_pc = H_0 ... H_{r-1} [I_r; 0] (Sec. 2.6.1) of interfaces whose QR kernel
 // has finished, from the reflectors it left in V and tau and the rank in
-// cur_size[p].  Launched per colour on a side stream, so that it overlaps the
+// cur_size[p] (or in the task's rank_out).  Launched per colour on a side stream, so that it overlaps the
 // next colour's QR; it is off the sparsification's critical path.  Block b of
 // an interface (nb blocks each) takes the column pairs (c, c + nb NW) with
 // c = b NW + warp (mod 2 nb NW), so every block meets chains of every length;
@@ -571,7 +583,7 @@ __global__ void __launch_bounds__(NT) k_form_q(const CpqrTask<T>* __restrict__ t
   constexpr int NW = NT / 32;
   const CpqrTask<T> d = tasks[list[blockIdx.x / nb]];
   const int b = blockIdx.x % nb;
-  const int np = d.np, r = cur_size[d.p];
+  const int np = d.np, r = d.rank_out ? d.rank_out[d.p] : cur_size[d.p];
   if (r <= 0 || b * NW >= r) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* tau_s = reinterpret_cast<T*>(smraw);

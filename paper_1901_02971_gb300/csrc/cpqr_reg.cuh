@@ -218,13 +218,13 @@ __global__ void __launch_bounds__(NT, 1) k_cpqr_reg(const CpqrTask<T>* __restric
   if (m == 0) {  // every neighbour reduced to nothing: p is kept as it is (Q_pc = I, all tau = 0)
     if (rank == 0) {
       for (int k = tid; k < np; k += NT) d.tau[k] = T(0);
-      if (tid == 0) cur_size[d.p] = np;
+      if (tid == 0) cq_rank_dst(d, cur_size)[d.p] = np;
     }
     return;
   }
   const int cols_per = (m + C - 1) / C;
   if (cols_per > NGRP || np > G * R) {  // the host sizes the launch so that this never holds
-    if (rank == 0 && tid == 0) cur_size[d.p] = -1;
+    if (rank == 0 && tid == 0) cq_rank_dst(d, cur_size)[d.p] = -1;
     return;  // uniform across the cluster
   }
   const int j0 = min(m, rank * cols_per);
@@ -496,7 +496,7 @@ __global__ void __launch_bounds__(NT, 1) k_cpqr_reg(const CpqrTask<T>* __restric
                    nbr, cstart, cur_size);
   // after the epilogue's last cluster barrier, so that it follows rank 0's
   // store of the rank
-  if (timed_out && threadIdx.x == 0) cur_size[d.p] = -2;
+  if (timed_out && threadIdx.x == 0) cq_rank_dst(d, cur_size)[d.p] = -2;
 }
 
 }  // namespace spand

@@ -26,6 +26,7 @@
 #include "cpqr_reg.cuh"
 #include "factor_kernels.cuh"
 #include "schur_tc.cuh"
+#include "sparsify_sim.cuh"
 #include "solve_kernels.cuh"
 #include "spand_internal.h"
 
@@ -1164,6 +1165,16 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         std::copy(sz.begin(), sz.end(), src);
         CK(cudaMemcpyAsync(d_cur, src, (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
       }
+      // simultaneous order: all interfaces in one launch, compressed from the
+      // same matrix; ranks go to d_rank so that the sizes the kernels read
+      // (d_cur) stay those of the scaled matrix until the launch is over
+      const bool sim = h->opts.sparsify_order == SPAND_SIMULTANEOUS;
+      int32_t* d_rank = nullptr;
+      if (sim) {
+        d_rank = (int32_t*)h->descs.alloc((size_t)n * sizeof(int32_t));
+        CK(cudaMemcpyAsync(d_rank, d_cur, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+      }
+      auto colour_of = [&](int p) { return sim ? 0 : (int)st.colour[p]; };
       std::vector<CpqrTask<T>> tasks;
       std::vector<CpqrNbr<T>> nbrs;
       std::vector<int> tclass;  // cluster size of each task
@@ -1199,6 +1210,8 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         }
         tk.nend = (int32_t)nbrs.size();
         tk.m_max = mm;
+        tk.rank_out = d_rank;
+        tk.nowb = sim ? 1 : 0;
         // smallest cluster whose per-CTA chunk fits in shared memory, and at
         // most ~2 columns per thread
         const size_t Lp = (size_t)cq_ld<T>(sz[p]);
@@ -1242,14 +1255,14 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
           const int C = (tasks[i].m_max + kCqrThreads / G - 1) / (kCqrThreads / G);
           if (G * kCqrRows >= tasks[i].np && C >= 1 && C <= kCqrMaxCluster) rg[i] = G, rc[i] = C;
         }
-        const int nc_ = std::max(ncol, 1);
+        const int nc_ = sim ? 1 : std::max(ncol, 1);
         std::vector<int> need(nc_, 0), cap(nc_, INT_MAX);
         std::vector<char> ok(nc_, 1);
         int capc[4][kCqrMaxCluster + 1];  // SMs of one wave, per (G, C), looked up once
         for (auto& row : capc)
           for (int& v : row) v = -1;
         for (size_t i = 0; i < tasks.size(); ++i) {
-          const int c = st.colour[tasks[i].p];
+          const int c = colour_of(tasks[i].p);
           if (!ok[c]) continue;
           if (!rg[i]) { ok[c] = 0; continue; }
           need[c] += rc[i];
@@ -1258,13 +1271,29 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
           cap[c] = std::min(cap[c], cc);
         }
         for (size_t i = 0; i < tasks.size(); ++i) {
-          const int c = st.colour[tasks[i].p];
+          const int c = colour_of(tasks[i].p);
           if (ok[c] && need[c] <= cap[c]) {
             treg[i] = rg[i];
             tclass[i] = rc[i];
             tres[i] = 1;
           }
         }
+      }
+      // simultaneous order: the coupling blocks to transform afterwards, one
+      // per unordered pair of interfaces (p < q), each with workspace for
+      // Y = A_pq Q_qc (|p| x |q| bound)
+      struct SimEdge { int i, j; int32_t e; size_t y; };
+      std::vector<SimEdge> sedges;
+      if (sim) {
+        std::vector<int> tix(n, -1);
+        for (size_t i = 0; i < tasks.size(); ++i) tix[tasks[i].p] = (int)i;
+        for (size_t i = 0; i < tasks.size(); ++i)
+          for (int32_t e = tasks[i].nbeg; e < tasks[i].nend; ++e) {
+            const int q = nbrs[e].q, j = tix[q];
+            if (j < 0 || tasks[i].p >= q) continue;
+            sedges.push_back({(int)i, j, e, wbytes});
+            wbytes += align256((size_t)tasks[i].np * tasks[j].np * sizeof(T));
+          }
       }
       if (!tasks.empty()) {
         char* wb = (char*)h->scratch[(t + 1) & 1].ensure(wbytes);
@@ -1282,7 +1311,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         // first
         std::map<std::tuple<int, int, int, int, int>, Group> buckets;
         for (size_t i = 0; i < tasks.size(); ++i) {
-          const int c = st.colour[tasks[i].p], C = tclass[i], Gr = treg[i], res = tres[i];
+          const int c = colour_of(tasks[i].p), C = tclass[i], Gr = treg[i], res = tres[i];
           Group& g = buckets[std::make_tuple(c, Gr ? 0 : 1, Gr, C, -res)];
           if (g.ids.empty()) {
             g.colour = c;
@@ -1394,8 +1423,66 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         }
         CK(cudaEventRecord(h->ev_qdone, h->qs));
         CK(cudaStreamWaitEvent(s, h->ev_qdone, 0));
-        h->prof.launches += (int64_t)groups.size() + nformq;
-        h->prof.end(cpqr_pid, s, 0.0, 0.0, (int64_t)groups.size() + nformq);
+        int64_t nsim = 0;  // k_sim_gemm launches
+        if (!sedges.empty()) {  // A_pq <- Q_pc^T (A_pq Q_qc): all reads in the first launch, all writes in the second
+          std::vector<SimGemm<T>> g1, g2;
+          std::vector<int32_t> o1{0}, o2{0};
+          for (const SimEdge& se : sedges) {
+            const CpqrTask<T>& tp = tasks[se.i];
+            const CpqrTask<T>& tq = tasks[se.j];
+            const CpqrNbr<T>& nb = nbrs[se.e];
+            T* Y = (T*)(wb + se.y);
+            T* Apq = tp.Rp + (size_t)nb.off_pq * tp.ldp;
+            const int tm = (tp.np + SG_TM - 1) / SG_TM, tn = (tq.np + SG_TN - 1) / SG_TN;
+            SimGemm<T> a{};  // Y (|p| x r_q) = A_pq Q_qc
+            a.A = Apq;
+            a.lda = tp.ldp;
+            a.B = tq.Qc;
+            a.ldb = tq.np;
+            a.C = Y;
+            a.ldc = tp.np;
+            a.m = tp.np;
+            a.n = tq.np;
+            a.k = tq.np;
+            a.mi = -1;
+            a.ni = tq.p;
+            a.tiles_m = tm;
+            g1.push_back(a);
+            o1.push_back(o1.back() + tm * tn);
+            SimGemm<T> b{};  // X (r_p x r_q) = Q_pc^T Y into A_pq, X^T into A_qp
+            b.A = tp.Qc;
+            b.lda = tp.np;
+            b.transA = 1;
+            b.B = Y;
+            b.ldb = tp.np;
+            b.C = Apq;
+            b.ldc = tp.ldp;
+            b.C2 = nb.Rq + (size_t)nb.off_qp * nb.ldq;
+            b.ldc2 = nb.ldq;
+            b.m = tp.np;
+            b.n = tq.np;
+            b.k = tp.np;
+            b.mi = tp.p;
+            b.ni = tq.p;
+            b.tiles_m = tm;
+            g2.push_back(b);
+            o2.push_back(o2.back() + tm * tn);
+          }
+          Packer pk2;
+          const size_t a1 = pk2.add(g1), a2 = pk2.add(o1), a3 = pk2.add(g2), a4 = pk2.add(o2);
+          void* d2 = upload<T>(h, pk2, s);
+          const int nd = (int)sedges.size();
+          k_sim_gemm<T><<<(unsigned)o1.back(), SG_NT, 0, s>>>(at<const SimGemm<T>>(d2, a1),
+                                                              at<const int32_t>(d2, a2), nd, d_rank);
+          CKLAUNCH();
+          k_sim_gemm<T><<<(unsigned)o2.back(), SG_NT, 0, s>>>(at<const SimGemm<T>>(d2, a3),
+                                                              at<const int32_t>(d2, a4), nd, d_rank);
+          CKLAUNCH();
+          nsim = 2;
+        }
+        if (sim) CK(cudaMemcpyAsync(d_cur, d_rank, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        h->prof.launches += (int64_t)groups.size() + nformq + nsim;
+        h->prof.end(cpqr_pid, s, 0.0, 0.0, (int64_t)groups.size() + nformq + nsim);
         build_elim_ops();  // host work overlapped with the sparsification kernels
         run_pending();
         int32_t* hcur = (int32_t*)h->stage.take((size_t)n * sizeof(int32_t));
@@ -1409,6 +1496,13 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
           if (rr < 0) throw Fail{SPAND_ERR_STATE, "sparsification: launch shape refused by the kernel"};
         }
         check_pivots(t);
+        for (const SimEdge& se : sedges) {  // algorithmic work of the two-sided transforms
+          const double np_ = tasks[se.i].np, nq_ = tasks[se.j].np;
+          const double rp = sz_after[tasks[se.i].p], rq = sz_after[tasks[se.j].p];
+          const double fl = 2 * np_ * nq_ * rq + 2 * rp * np_ * rq;
+          stt.factor_flops += fl;
+          h->prof.add(cpqr_pid, fl, (np_ * nq_ + nq_ * rq + 2 * np_ * rq + np_ * rp + 2 * rp * rq) * sizeof(T));
+        }
       }
       for (int sidx : seps) sz_after[sidx] = 0;
       // compact Q_pc (|p| x r) into the factor
@@ -1698,6 +1792,7 @@ void spand_default_opts(spand_opts* o) {
   o->precision = SPAND_FP64;
   o->maxit = 500;
   o->tol = 1e-10;
+  o->sparsify_order = SPAND_COLOURED;
 }
 
 const char* spand_error_string(int code) {
@@ -1730,6 +1825,8 @@ int spand_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const
       opts->precision != SPAND_BF16)
     throw Fail{SPAND_ERR_INVALID_ARG, "unknown precision"};
   if (opts->maxit < 1 || !(opts->tol > 0.0)) throw Fail{SPAND_ERR_INVALID_ARG, "maxit >= 1 and tol > 0 required"};
+  if (opts->sparsify_order != SPAND_COLOURED && opts->sparsify_order != SPAND_SIMULTANEOUS)
+    throw Fail{SPAND_ERR_INVALID_ARG, "unknown sparsify_order"};
   if (n > INT32_MAX - 1) throw Fail{SPAND_ERR_INVALID_ARG, "n too large"};
   if (coords && (dim < 1 || dim > 8)) throw Fail{SPAND_ERR_INVALID_ARG, "dim must be in [1, 8]"};
   std::string err;

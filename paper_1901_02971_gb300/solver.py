@@ -18,6 +18,7 @@ def _addr(a):
 
 
 PRECISIONS = {"fp64": L.SPAND_FP64, "fp32": L.SPAND_FP32, "tf32": L.SPAND_TF32, "bf16": L.SPAND_BF16}
+ORDERS = {"coloured": L.SPAND_COLOURED, "simultaneous": L.SPAND_SIMULTANEOUS}
 
 
 class Solver:
@@ -25,13 +26,17 @@ class Solver:
 
     Parameters follow ``spand_opts``: levels (L of Algorithm 3), eps, skip,
     precision ("fp64", "fp32", or "tf32" / "bf16": FP32 factors whose Schur
-    GEMMs run on the tensor cores with TF32 / BF16 operands), maxit, tol.
+    GEMMs run on the tensor cores with TF32 / BF16 operands), maxit, tol,
+    sparsify_order ("coloured", or "simultaneous": every interface of a level
+    compressed from the same scaled matrix, one launch per level).
     """
 
     def __init__(self, rowptr, colind, vals, coords=None, levels: int = 8, eps: float = 1e-2, skip: int = 0,
-                 precision: str = "fp64", maxit: int = 500, tol: float = 1e-10):
+                 precision: str = "fp64", maxit: int = 500, tol: float = 1e-10, sparsify_order: str = "coloured"):
         prec = PRECISIONS[precision]
-        self.opts = L.default_opts(levels=levels, eps=eps, skip=skip, precision=prec, maxit=maxit, tol=tol)
+        order = ORDERS[sparsify_order]
+        self.opts = L.default_opts(levels=levels, eps=eps, skip=skip, precision=prec, maxit=maxit, tol=tol,
+                                   sparsify_order=order)
         self.n = int(np.asarray(rowptr).size - 1)
         self.nnz = int(np.asarray(rowptr)[-1])
         self.h = L.spand_analyze(rowptr, colind, vals, coords, self.opts)

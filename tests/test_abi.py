@@ -70,6 +70,21 @@ def test_malformed_csr_rejected(spand_lib):
     assert "levels" in L.lib().spand_last_error().decode()
 
 
+def test_sparsify_order_option(spand_lib):
+    assert L.default_opts().sparsify_order == L.SPAND_COLOURED
+    p = I.laplacian_2d(6)
+    for order, want in [(L.SPAND_COLOURED, L.SPAND_OK), (L.SPAND_SIMULTANEOUS, L.SPAND_OK), (2, L.SPAND_ERR_INVALID_ARG),
+                        (-1, L.SPAND_ERR_INVALID_ARG)]:
+        o = L.default_opts(levels=3, sparsify_order=order)
+        h = C.c_void_p()
+        rc = L.lib().spand_analyze(p.n, p.rowptr.ctypes.data, p.colind.ctypes.data, p.vals.ctypes.data, None, 0,
+                                   C.byref(o), C.byref(h))
+        if h.value:
+            L.spand_destroy(h.value)
+        assert rc == want, (order, rc)
+    assert "sparsify_order" in L.lib().spand_last_error().decode()
+
+
 def test_missing_diagonal_rejected(spand_lib):
     rowptr = np.array([0, 1, 2], np.int64)
     colind = np.array([1, 0], np.int32)
