@@ -224,6 +224,27 @@ def dist_env():
     return rank, world, local
 
 
+ORACLE_GOLDEN = os.path.join("tests", "golden", "oracle_lapl3d_64.json")
+
+
+def x_vs_oracle(xs_by_form: dict) -> dict:
+    """Relative error of x against the FP64 oracle's x on the benchmark
+    workload, on the 256 sampled entries (and ||x||) that the oracle's run
+    stored (written by tests/golden/make_oracle_lapl3d_64.py, which calls
+    only the oracle; same problem and right-hand side as this benchmark)."""
+    import numpy as np
+    with open(os.path.join(ROOT, ORACLE_GOLDEN)) as f:
+        g = json.load(f)
+    idx = np.asarray(g["sample_idx"], dtype=np.int64)
+    ref = np.asarray(g["sample_x"], dtype=np.float64)
+    out = {"samples": int(idx.size), "oracle_iters": int(g["iters"]), "source": ORACLE_GOLDEN}
+    for name, x in xs_by_form.items():
+        x = np.asarray(x, dtype=np.float64)
+        out[name] = {"sampled_rel_err": float(np.linalg.norm(x[idx] - ref) / np.linalg.norm(ref)),
+                     "norm_rel_err": float(abs(np.linalg.norm(x) - g["x_norm"]) / g["x_norm"])}
+    return out
+
+
 def max_over_ranks(vals, dist=None, device="cpu"):
     """Element-wise maximum of per-rank timings over the process group (the
     replicas' whole-job time is the slowest rank's); identity without one."""
@@ -383,6 +404,12 @@ def main():
     x32 = s32.solve(b_d)[0].cpu().numpy()
     x64 = s64.solve(b_d)[0].cpu().numpy()
     relres_host = float(np.linalg.norm(b - p.to_scipy() @ x32) / np.linalg.norm(b))
+    vs_oracle = None
+    if workload == WORKLOAD:
+        try:
+            vs_oracle = x_vs_oracle({"mixed_" + args.form: x32, "plain_fp64": x64})
+        except (OSError, KeyError, ValueError) as e:
+            vs_oracle = {"error": str(e)[:200]}
     # end to end through the C ABI with host buffers
     x_h = np.empty(p.n)
     e2e = []
@@ -421,6 +448,7 @@ def main():
             "speedup_mixed_vs_fp64": statistics.mean(t64) / v,
             "x_rel_diff_mixed_vs_fp64": float(np.linalg.norm(x32 - x64) / np.linalg.norm(x64)),
             "true_relres_host": relres_host,
+            "x_vs_fp64_oracle": vs_oracle,
             "skip_sweep_mixed_" + args.form: sweep,
             "mixed_" + args.form + "_simultaneous_order": sim,
         },

@@ -1,5 +1,6 @@
-"""Host logic of bench.py (no GPU): the per-phase roofline table and the
-source-hash guard of the measured DRAM traffic."""
+"""Host logic of bench.py (no GPU): the per-phase roofline table, the
+source-hash guard of the measured DRAM traffic and the accuracy report
+against the oracle's stored samples."""
 import bench
 
 
@@ -33,3 +34,26 @@ def test_measured_traffic_tied_to_source_hash(tmp_path, monkeypatch):
     assert bench.measured_traffic("x", bench.GRID + 1) is None  # another workload size
     src.write_text("kernel changed")
     assert bench.measured_traffic("x", bench.GRID) is None
+
+
+def test_x_vs_oracle_against_stored_samples():
+    """The benchmark's accuracy report reads the oracle's stored samples: an
+    x that carries exactly those samples (and the stored norm) reports zero
+    sampled error; a perturbed one reports the perturbation."""
+    import json
+    import os
+
+    import numpy as np
+    g = json.load(open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                    bench.ORACLE_GOLDEN)))
+    n = 64 ** 3
+    idx = np.asarray(g["sample_idx"])
+    x = np.zeros(n)
+    x[idx] = g["sample_x"]
+    rest = np.setdiff1d(np.arange(n), idx)
+    # fill the other entries so that ||x|| equals the stored norm
+    x[rest[0]] = np.sqrt(g["x_norm"] ** 2 - np.sum(np.square(g["sample_x"])))
+    r = bench.x_vs_oracle({"a": x, "b": x * (1 + 1e-6)})
+    assert r["samples"] == 256 and r["oracle_iters"] == g["iters"]
+    assert r["a"]["sampled_rel_err"] == 0.0 and r["a"]["norm_rel_err"] < 1e-14
+    assert abs(r["b"]["sampled_rel_err"] - 1e-6) < 1e-12
