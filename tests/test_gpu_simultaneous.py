@@ -127,3 +127,24 @@ def test_simultaneous_large_eps_stays_spd(cuda_ok):
         assert rr <= 1e-10
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("name,gen,levels", [
+    ("single_unknown", lambda: I.laplacian_2d(1), 1),
+    ("more_levels_than_vertices", lambda: I.laplacian_2d(5), 7),
+    ("empty", lambda: I.Problem("empty", 0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0),
+                                np.zeros((0, 2)), 2), 3),
+])
+def test_simultaneous_degenerate_cases(cuda_ok, name, gen, levels):
+    p = gen()
+    b = I.rhs(p.n, 1)
+    s, x, it, rr = _run(p, b, levels, 1e-2)
+    try:
+        if p.n == 0:
+            assert x.size == 0 and it == 0
+            return
+        ref = O.solve(p, b, levels, 1e-2, order=SIM)
+        assert rr <= 1e-10
+        assert np.linalg.norm(x - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+    finally:
+        s.close()
