@@ -394,6 +394,66 @@ def sparsify_interface_interp(Anp: np.ndarray, App: np.ndarray, eps: float):
     return c, f, T, Lf, Xfc, Acc, R22
 
 
+# --------------------------------------------------------------------------
+# counter-based Gaussian sketch (the oracle's side of a generator that a GPU
+# form draws on the device): Philox4x64-10 (Salmon, Moraes, Dror and Shaw,
+# "Parallel random numbers: as easy as 1, 2, 3", SC 2011) and Box-Muller
+# --------------------------------------------------------------------------
+
+_PHILOX_M = (0xD2E7470EE14C6C93, 0xCA5A826395121157)  # round multipliers
+_PHILOX_W = (0x9E3779B97F4A7C15, 0xBB67AE8584CAA73B)  # key increments (Weyl)
+_M32 = np.uint64(0xFFFFFFFF)
+
+
+def _mulhilo64(a: np.ndarray, b: int):
+    """(high, low) 64-bit halves of the 128-bit products a * b (a uint64
+    array, b a 64-bit constant), from 32-bit partial products."""
+    a = a.astype(np.uint64)
+    s32 = np.uint64(32)
+    al, ah = a & _M32, a >> s32
+    bl, bh = np.uint64(b & 0xFFFFFFFF), np.uint64(b >> 32)
+    ll, lh, hl, hh = al * bl, al * bh, ah * bl, ah * bh
+    mid = (ll >> s32) + (lh & _M32) + (hl & _M32)
+    hi = hh + (lh >> s32) + (hl >> s32) + (mid >> s32)
+    lo = a * np.uint64(b)  # wraps modulo 2^64
+    return hi, lo
+
+
+def philox4x64_10(c0, c1, c2, c3, k0: int, k1: int):
+    """The Philox4x64 bijection with 10 rounds on counter words (uint64
+    arrays) under the key (k0, k1): per round, the products of M0 with x0 and
+    M1 with x2 give x <- (hi1 ^ x1 ^ k0, lo1, hi0 ^ x3 ^ k1, lo0); the key
+    advances by the Weyl constants between rounds."""
+    x = [np.asarray(c, dtype=np.uint64) for c in (c0, c1, c2, c3)]
+    mask = (1 << 64) - 1
+    for r in range(10):
+        if r:
+            k0, k1 = (k0 + _PHILOX_W[0]) & mask, (k1 + _PHILOX_W[1]) & mask
+        h0, l0 = _mulhilo64(x[0], _PHILOX_M[0])
+        h1, l1 = _mulhilo64(x[2], _PHILOX_M[1])
+        x = [h1 ^ x[1] ^ np.uint64(k0), l1, h0 ^ x[3] ^ np.uint64(k1), l0]
+    return x
+
+
+def sketch_philox(seed: int, step: int, cluster: int, m: int, ell: int) -> np.ndarray:
+    """Gaussian test matrix (m x ell) of the randomized compression, entry by
+    entry from a counter: key (seed, step * 2^32 + cluster), counter
+    (column j, row block i // 4, 0, 0); the four 64-bit words of a block give
+    four uniforms u = (w >> 11 + 1/2) 2^-53 in (0, 1), and Box-Muller turns
+    the pairs (u0, u1), (u2, u3) into rows 4b..4b+3:
+    sqrt(-2 ln u0) (cos 2 pi u1, sin 2 pi u1), likewise for (u2, u3).
+    Every entry depends only on (seed, step, cluster, i, j)."""
+    nb = (m + 3) // 4
+    jj, bb = np.meshgrid(np.arange(ell, dtype=np.uint64), np.arange(nb, dtype=np.uint64))
+    z = np.zeros_like(jj)
+    w = philox4x64_10(jj, bb, z, z, int(seed) & ((1 << 64) - 1), ((int(step) << 32) + int(cluster)) & ((1 << 64) - 1))
+    u = [((wi >> np.uint64(11)).astype(np.float64) + 0.5) * 2.0 ** -53 for wi in w]
+    r01, r23 = np.sqrt(-2.0 * np.log(u[0])), np.sqrt(-2.0 * np.log(u[2]))
+    rows = np.stack([r01 * np.cos(2 * np.pi * u[1]), r01 * np.sin(2 * np.pi * u[1]),
+                     r23 * np.cos(2 * np.pi * u[3]), r23 * np.sin(2 * np.pi * u[3])], axis=1)  # nb x 4 x ell
+    return rows.reshape(4 * nb, ell)[:m]
+
+
 RAND_OVERSAMPLE = 10   # sketch columns beyond the rank (HMT 2011, Sec. 4.2)
 RAND_ELL0 = 32         # first sketch width; doubled while the rank saturates it
 

@@ -16,7 +16,12 @@ oracle's own formulas:
   Sec. 4), and r stays within a few of scipy's column-pivoted QR rank;
 * whole solver on 2D / 3D Laplacians: ranks within 15 % of OrthS's, PCG
   iterations within OrthS's + 3, x equal to OrthS's x at the PCG tolerance,
-  and no breakdown at eps = 0.9 (the transform stays orthogonal).
+  and no breakdown at eps = 0.9 (the transform stays orthogonal);
+* the counter-based sketch (the oracle's Philox4x64-10 + Box-Muller, the
+  generator a GPU form would also implement): bit-identical to numpy's
+  independent Philox, entries addressed by (seed, step, cluster, row,
+  column), Gaussian by a Kolmogorov-Smirnov test, and the solver driven by
+  it behaves as with the PCG64 sketch.
 """
 import numpy as np
 import pytest
@@ -114,3 +119,45 @@ def test_rand_needs_a_sketch():
     tree = O.analyze(p.n, p.rowptr, p.colind, p.coords, 2)
     with pytest.raises(ValueError):
         O.factorize(p.rowptr, p.colind, p.vals, tree, 1e-2, variant="OrthS-rand")
+
+
+# ---------------------------------------------- counter-based sketch (Philox)
+
+def test_philox_matches_numpy_philox():
+    """The oracle's Philox4x64-10 against numpy's independent implementation
+    (numpy advances its counter before each block, so its block after
+    counter c - 1 is ours at c)."""
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        k = [int(v) for v in rng.integers(0, 2 ** 63, size=2, dtype=np.int64)]
+        c = [int(v) for v in rng.integers(1, 2 ** 63, size=4, dtype=np.int64)]
+        bg = np.random.Philox(key=np.array(k, dtype=np.uint64),
+                              counter=np.array([c[0] - 1] + c[1:], dtype=np.uint64))
+        want = [int(v) for v in bg.random_raw(4)]
+        got = O.philox4x64_10(*[np.array([v], np.uint64) for v in c], k[0], k[1])
+        assert [int(w[0]) for w in got] == want
+
+
+def test_philox_sketch_is_addressed_by_entry_and_gaussian():
+    import scipy.stats as st
+    a = O.sketch_philox(3, 2, 7, 50, 20)
+    assert np.array_equal(a[:, :8], O.sketch_philox(3, 2, 7, 50, 8))   # nested columns
+    assert np.array_equal(a[:29], O.sketch_philox(3, 2, 7, 29, 20))    # any m
+    assert not np.array_equal(a, O.sketch_philox(3, 2, 8, 50, 20))     # per cluster
+    assert not np.array_equal(a, O.sketch_philox(4, 2, 7, 50, 20))     # per seed
+    big = O.sketch_philox(5, 1, 1, 4000, 50).ravel()
+    assert abs(big.mean()) < 0.01 and abs(big.var() - 1) < 0.01
+    assert st.kstest(big, "norm").pvalue > 1e-3
+    # columns are uncorrelated
+    c = np.corrcoef(O.sketch_philox(6, 1, 1, 20000, 4).T)
+    assert np.abs(c - np.eye(4)).max() < 0.03
+
+
+@pytest.mark.parametrize("gen,L", [(lambda: I.laplacian_2d(32), 6), (lambda: I.laplacian_3d(12), 5)])
+def test_solver_with_philox_sketch(gen, L):
+    p = gen()
+    b = I.rhs(p.n, 2)
+    a = O.solve(p, b, L, 1e-2)
+    r = O.solve(p, b, L, 1e-2, variant="OrthS-rand", sketch=lambda t, c, m, ell: O.sketch_philox(0, t, c, m, ell))
+    assert r.iters <= a.iters + 3, (r.iters, a.iters)
+    assert np.linalg.norm(r.x - a.x) <= 1e-8 * np.linalg.norm(a.x)
