@@ -63,6 +63,13 @@ def oracle_sample_seconds(threads: int = 1) -> dict:
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def sample_phases(r: dict) -> dict:
+    """The oracle sample's own phase times and PCG count (unscaled): analysis
+    t_P, factorization t_F, PCG t_S (s), iterations n_CG."""
+    return {"t_p_s": round(r["t_p"], 4), "t_f_s": round(r["t_f"], 4), "t_s_s": round(r["t_s"], 4),
+            "n_cg": int(r["iters"])}
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -260,12 +267,13 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    times, iters = [], []
+    times, iters, last = [], [], None
     for i in range(args.warmup + args.steps):
         r = oracle_sample_seconds()
         if i >= args.warmup:
             times.append((r["t_f"] + r["t_s"]) * SAMPLE_SCALE)
             iters.append(r["iters"])
+            last = r
     v = statistics.mean(times)
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
@@ -273,7 +281,8 @@ def run_reference(args):
            "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (factor > 129 MB)"},
            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
                             "sample": f"FP64 oracle factor+PCG on the {SAMPLE_GRID}^3 cube (L={SAMPLE_LEVELS}), "
-                                      f"scaled x{SAMPLE_SCALE:.2f} by N log N to 64^3; iters {iters[0]}"},
+                                      f"scaled x{SAMPLE_SCALE:.2f} by N log N to 64^3; iters {iters[0]}",
+                            "sample_phases": sample_phases(last)},
            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0
@@ -466,12 +475,14 @@ def main():
         out["cpu_baseline"] = {"value": cv, "unit": "s", "cores": 1, "kind": "oracle",
                                "sample": f"FP64 oracle factor+PCG on the {SAMPLE_GRID}^3 cube (L={SAMPLE_LEVELS}, "
                                          f"{cpu['t_f'] + cpu['t_s']:.2f} s, {cpu['iters']} iters), scaled "
-                                         f"x{SAMPLE_SCALE:.2f} (N log N) to 64^3"}
+                                         f"x{SAMPLE_SCALE:.2f} (N log N) to 64^3",
+                               "sample_phases": sample_phases(cpu)}
         ca = (cpu_all["t_f"] + cpu_all["t_s"]) * SAMPLE_SCALE
         out["cpu_baseline_all_cores"] = {
             "value": ca, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"the same sample with the oracle's BLAS/LAPACK on all {os.cpu_count()} host cores "
-                      f"({cpu_all['t_f'] + cpu_all['t_s']:.2f} s), scaled x{SAMPLE_SCALE:.2f}"}
+                      f"({cpu_all['t_f'] + cpu_all['t_s']:.2f} s), scaled x{SAMPLE_SCALE:.2f}",
+            "sample_phases": sample_phases(cpu_all)}
     print(json.dumps(out))
     s32.close()
     s64.close()

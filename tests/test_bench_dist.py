@@ -69,3 +69,6 @@ def test_reference_arm_under_torchrun_prints_once():
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["higher_is_better"] is False
     assert d["value"] > 0 and d["e2e"]["value"] == d["value"]
     assert d["cpu_baseline"]["kind"] == "oracle"
+    ph = d["cpu_baseline"]["sample_phases"]
+    assert set(ph) == {"t_p_s", "t_f_s", "t_s_s", "n_cg"} and ph["n_cg"] >= 1
+    assert min(ph["t_p_s"], ph["t_f_s"], ph["t_s_s"]) > 0
