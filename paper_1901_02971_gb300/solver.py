@@ -113,7 +113,8 @@ class Solver:
         for kw in opts_list:
             prec = PRECISIONS[kw.get("precision", "fp64")]
             opts.append(L.default_opts(levels=kw.get("levels", 8), eps=kw.get("eps", 1e-2), skip=kw.get("skip", 0),
-                                       precision=prec, maxit=kw.get("maxit", 500), tol=kw.get("tol", 1e-10)))
+                                       precision=prec, maxit=kw.get("maxit", 500), tol=kw.get("tol", 1e-10),
+                                       sparsify_order=ORDERS[kw.get("sparsify_order", "coloured")]))
         hs = L.spand_analyze_batch([(p.rowptr, p.colind, p.vals, p.coords) for p in problems], opts)
         out = []
         for p, o, h in zip(problems, opts, hs):

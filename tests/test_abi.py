@@ -147,3 +147,24 @@ def test_analyze_batch_error_names_problem(spand_lib):
     assert e.value.code == L.SPAND_ERR_INVALID_ARG
     assert "problem 1" in str(e.value)
     assert L.spand_analyze_batch([], []) == []
+
+
+def test_batch_and_solver_pass_the_sparsify_order(spand_lib):
+    """The Python layer forwards the order to spand_opts (analysis only)."""
+    from paper_1901_02971_gb300 import Solver
+    ps = [I.laplacian_2d(8), I.laplacian_2d(9)]
+    ss = Solver.batch(ps, [{"levels": 3, "sparsify_order": "simultaneous"}, {"levels": 3}])
+    try:
+        assert ss[0].opts.sparsify_order == L.SPAND_SIMULTANEOUS
+        assert ss[1].opts.sparsify_order == L.SPAND_COLOURED
+    finally:
+        for s in ss:
+            s.close()
+    s = Solver.from_problem(ps[0], levels=3, sparsify_order="simultaneous")
+    try:
+        assert s.opts.sparsify_order == L.SPAND_SIMULTANEOUS
+    finally:
+        s.close()
+    with pytest.raises(KeyError):
+        Solver.from_problem(ps[0], levels=3, sparsify_order="random")
+
