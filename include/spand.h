@@ -189,6 +189,24 @@ int spand_apply(spand_handle h, const double* r_dev, double* z_dev, void* cuda_s
 int spand_apply_noalloc(spand_handle h, const double* r_dev, double* z_dev, void* cuda_stream);
 
 /*
+ * spand_sketch_gaussian -- the Gaussian test matrix of the randomized
+ * compression of one interface (Sec. 2.6.2 names randomized methods for the
+ * low-rank step): entry (i, j) of the m x ell matrix is a pure function of
+ * (seed, step, cluster, i, j), drawn by Philox4x64-10 (Salmon et al., SC
+ * 2011) under the key (seed, step * 2^32 + cluster) at the counter
+ * (j, i / 4, 0, 0), with Box-Muller turning the block's four words into rows
+ * 4 (i / 4) .. 4 (i / 4) + 3.  Column j is the same for every ell > j and
+ * row i for every m > i.  No handle needed.
+ *   out_dev     : device float64[m * ell], column-major (leading dimension m);
+ *                 owned by the caller.
+ *   cuda_stream : stream of the launch (asynchronous).
+ * Errors: SPAND_ERR_INVALID_ARG for a negative step, cluster, m or ell, or a
+ * null out_dev with m * ell > 0; SPAND_ERR_CUDA if the launch fails.
+ */
+int spand_sketch_gaussian(uint64_t seed, int32_t step, int32_t cluster, int32_t m, int32_t ell, double* out_dev,
+                          void* cuda_stream);
+
+/*
  * spand_sampled_outer -- out[e] = -lam[i] * x[j] for every stored entry e =
  * (i, j) of A, in the CSR order given to spand_analyze.  With x = A^{-1} b and
  * lam = A^{-1} (dL/dx) (the adjoint solve, same factorization since A is

@@ -34,7 +34,7 @@ SPAND_SIMULTANEOUS = 1
 
 # every function declared in include/spand.h
 EXPORTS = ["spand_default_opts", "spand_analyze", "spand_analyze_batch", "spand_factorize", "spand_solve", "spand_apply",
-           "spand_apply_noalloc", "spand_sampled_outer",
+           "spand_apply_noalloc", "spand_sampled_outer", "spand_sketch_gaussian",
            "spand_get_tree", "spand_get_step", "spand_get_ranks", "spand_get_stats",
            "spand_get_phase_times", "spand_set_profiling", "spand_get_kernel_profile",
            "spand_reset_kernel_profile", "spand_get_launch_count", "spand_destroy", "spand_error_string",
@@ -88,6 +88,7 @@ def lib():
     L.spand_apply.argtypes = [C.c_void_p, P, P, P]
     L.spand_apply_noalloc.argtypes = [C.c_void_p, P, P, P]
     L.spand_sampled_outer.argtypes = [C.c_void_p, P, P, P, P]
+    L.spand_sketch_gaussian.argtypes = [C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, P]
     L.spand_get_tree.argtypes = [C.c_void_p, P, P, P, i32p, i32p]
     L.spand_get_step.argtypes = [C.c_void_p, C.c_int32] + [P] * 10
     L.spand_get_ranks.argtypes = [C.c_void_p, C.c_int32, P, P]
@@ -200,6 +201,12 @@ def spand_apply_noalloc(h: int, r_ptr: int, z_ptr: int, stream: int = 0):
 def spand_sampled_outer(h: int, lam_ptr: int, x_ptr: int, out_ptr: int, stream: int = 0):
     """out[e] = -lam[i] x[j] on A's stored pattern (device pointers)."""
     _check(lib().spand_sampled_outer(h, lam_ptr, x_ptr, out_ptr, stream or None))
+
+
+def spand_sketch_gaussian(seed: int, step: int, cluster: int, m: int, ell: int, out_ptr: int, stream: int = 0):
+    """Gaussian test matrix (m x ell, column-major, device float64) of the
+    randomized compression, drawn on the device from its counter."""
+    _check(lib().spand_sketch_gaussian(seed, step, cluster, m, ell, out_ptr, stream or None))
 
 
 def spand_get_tree(h: int) -> dict:

@@ -27,6 +27,7 @@
 #include "factor_kernels.cuh"
 #include "schur_tc.cuh"
 #include "sparsify_sim.cuh"
+#include "sketch.cuh"
 #include "solve_kernels.cuh"
 #include "spand_internal.h"
 
@@ -2260,6 +2261,23 @@ int spand_get_launch_count(spand_handle h, int64_t* launches) {
   if (!h || !launches) { g_err = "null argument"; return SPAND_ERR_INVALID_ARG; }
   *launches = h->prof.launches;
   return SPAND_OK;
+}
+
+int spand_sketch_gaussian(uint64_t seed, int32_t step, int32_t cluster, int32_t m, int32_t ell, double* out_dev,
+                          void* cuda_stream) {
+  API_BEGIN
+  g_err.clear();
+  if (m < 0 || ell < 0 || step < 0 || cluster < 0)
+    throw Fail{SPAND_ERR_INVALID_ARG, "step, cluster, m and ell must be >= 0"};
+  if ((int64_t)m * ell == 0) return SPAND_OK;
+  if (!out_dev) throw Fail{SPAND_ERR_INVALID_ARG, "out_dev is NULL"};
+  const uint64_t k1 = ((uint64_t)(uint32_t)step << 32) + (uint64_t)(uint32_t)cluster;
+  const int64_t blocks = ((int64_t)(m + 3) / 4 * ell + 255) / 256;
+  k_sketch_philox<<<(unsigned)std::min<int64_t>(blocks, 8192), 256, 0, (cudaStream_t)cuda_stream>>>(seed, k1, m, ell,
+                                                                                                   out_dev);
+  CKLAUNCH();
+  return SPAND_OK;
+  API_END
 }
 
 int spand_sampled_outer(spand_handle h, const double* lam_dev, const double* x_dev, double* out_dev,

@@ -168,3 +168,15 @@ def test_batch_and_solver_pass_the_sparsify_order(spand_lib):
     with pytest.raises(KeyError):
         Solver.from_problem(ps[0], levels=3, sparsify_order="random")
 
+
+
+def test_sketch_argument_checks(spand_lib):
+    """Host-side checks of spand_sketch_gaussian (no launch happens)."""
+    f = spand_lib.spand_sketch_gaussian
+    assert f(1, 0, 0, -1, 4, None, None) == L.SPAND_ERR_INVALID_ARG
+    assert f(1, 0, 0, 4, -1, None, None) == L.SPAND_ERR_INVALID_ARG
+    assert f(1, -1, 0, 4, 4, None, None) == L.SPAND_ERR_INVALID_ARG
+    assert f(1, 0, -1, 4, 4, None, None) == L.SPAND_ERR_INVALID_ARG
+    assert f(1, 0, 0, 4, 4, None, None) == L.SPAND_ERR_INVALID_ARG   # null output
+    assert f(1, 0, 0, 0, 4, None, None) == L.SPAND_OK                # empty: nothing to do
+    assert f(1, 0, 0, 4, 0, None, None) == L.SPAND_OK
