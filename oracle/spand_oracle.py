@@ -173,8 +173,12 @@ def bfs_distance(U: np.ndarray, rowptr, colind, n: int) -> np.ndarray:
 # Algorithm 3: ordering and clustering
 # --------------------------------------------------------------------------
 
-def ordering_clustering(n, rowptr, colind, coords: Optional[np.ndarray], L: int):
-    """Returns C = (S, Lb, Rb) per vertex, heap-indexed (Algorithm 3)."""
+def ordering_clustering(n, rowptr, colind, coords: Optional[np.ndarray], L: int, separator=None):
+    """Returns C = (S, Lb, Rb) per vertex, heap-indexed (Algorithm 3).
+
+    ``separator(level, k, U) -> (left, mid, right)`` replaces the
+    vertex-separator routine (Algorithm 3 works with any); by default the
+    geometric bisection, or the BFS bisection without coordinates."""
     S = np.ones(n, dtype=np.int64)          # (1,1) for everyone
     Lb = np.full(n, NONE, dtype=np.int64)   # none
     Rb = np.full(n, NONE, dtype=np.int64)
@@ -184,11 +188,14 @@ def ordering_clustering(n, rowptr, colind, coords: Optional[np.ndarray], L: int)
             I = np.flatnonzero(S == h)
             B = np.flatnonzero((Lb == h) | (Rb == h))
             U = np.union1d(I, B)
-            if coords is not None:
-                x = coords[U]
+            if separator is not None:
+                left, mid, right = (np.asarray(a, dtype=np.int64) for a in separator(lvl, k, U))
             else:
-                x = bfs_distance(U, rowptr, colind, n) if U.size >= 2 else np.zeros((U.size, 1))
-            left, mid, right = bisect(U, x, rowptr, colind, n)
+                if coords is not None:
+                    x = coords[U]
+                else:
+                    x = bfs_distance(U, rowptr, colind, n) if U.size >= 2 else np.zeros((U.size, 1))
+                left, mid, right = bisect(U, x, rowptr, colind, n)
             inB = np.zeros(n, dtype=bool)
             inB[B] = True
             inI = np.zeros(n, dtype=bool)
@@ -238,10 +245,10 @@ class Tree:
     steps: List[Step]
 
 
-def analyze(n, rowptr, colind, coords, L) -> Tree:
+def analyze(n, rowptr, colind, coords, L, separator=None) -> Tree:
     rowptr = np.asarray(rowptr, dtype=np.int64)
     colind = np.asarray(colind, dtype=np.int64)
-    S, Lb, Rb = ordering_clustering(n, rowptr, colind, coords, L)
+    S, Lb, Rb = ordering_clustering(n, rowptr, colind, coords, L, separator)
     # clusters = vertices with the same C[v]; order (step, S, L, R), ids ascending
     step_of = L + 1 - np.array([level_of(h) for h in range(0, 1 << L)], dtype=np.int64)
     tv = step_of[S]

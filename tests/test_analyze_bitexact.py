@@ -32,7 +32,19 @@ def _empty():
     return I.Problem("empty", 0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0), np.zeros((0, 2)), 2)
 
 
+def _path_plus_isolated():
+    """1 - 0 - 2 and an isolated vertex 3 (the BFS tie-break and unreached-
+    vertex case of the oracle pins)."""
+    rowptr = np.array([0, 3, 5, 7, 8], np.int64)
+    colind = np.array([0, 1, 2, 0, 1, 0, 2, 3], np.int32)
+    vals = np.array([3.0, -1, -1, -1, 2, -1, 2, 1])
+    return I.Problem("path_iso", 4, rowptr, colind, vals, None, 1)
+
+
 CASES = [
+    ("bfs_path_iso_L2", lambda: _path_plus_isolated(), 2, False),
+    ("bfs_path_iso_L3", lambda: _path_plus_isolated(), 3, False),
+    ("bfs_grid_4x3_L2", lambda: I._assemble((3, 4), np.ones((3, 4)), "grid_4x3"), 2, False),
     ("lapl2d_8_L3", lambda: I.laplacian_2d(8), 3, True),
     ("lapl2d_64_L8", lambda: I.laplacian_2d(64), 8, True),
     ("lapl2d_37_L6", lambda: I.laplacian_2d(37), 6, True),

@@ -277,3 +277,154 @@ def test_pcg_true_residual_restart():
     assert it == 1 and rr < 1e-12
     _, it, rr = O.pcg(A, b, lambda r: 0.25 * r, tol=1e-10)
     assert rr <= 1e-10
+
+
+# ------------------------------------------------ colouring (order of Sec. 2.6.1)
+
+def test_colouring_8x8_matches_hand_derivation():
+    """Step 1 of the 8x8, L = 3 case (cluster order of the hand-derived
+    ordering above): after the leaves are eliminated the remaining clusters
+    c4 = (2,4,5), c5 = (3,6,7), c6 = (1,2,3), c7 = (1,4,6), c8 = (1,5,7) are
+    coupled by the original edges c4-c6, c5-c6, c6-c7, c6-c8 and by the fill
+    of the four leaves (leaf 4: c4-c7, leaf 5: c4-c8, leaf 6: c5-c7,
+    leaf 7: c5-c8).  Greedy colouring in cluster order on that graph:
+    c4 0, c5 0, c6 1, c7 2, c8 2.  (On the graph before the fill, c7 and c8
+    would take colour 0 and share it with their fill neighbours c4, c5.)"""
+    p = I.laplacian_2d(8)
+    tree = O.analyze(p.n, p.rowptr, p.colind, p.coords, 3)
+    st = tree.steps[0]
+    assert st.adjf[4:] == [[6, 7, 8], [6, 7, 8], [4, 5, 7, 8], [4, 5, 6], [4, 5, 6]]
+    assert st.colour.tolist() == [-1, -1, -1, -1, 0, 0, 1, 2, 2]
+    # step 2: one remaining cluster (the merged root pieces), no neighbours
+    assert tree.steps[1].colour.tolist() == [-1, -1, 0]
+    assert tree.steps[2].colour.tolist() == [-1]
+
+
+@pytest.mark.parametrize("gen,L,geo", [
+    (lambda: I.laplacian_2d(37), 6, True),
+    (lambda: I.laplacian_3d(12), 6, True),
+    (lambda: I.diffusion_2d(24, 3), 6, False),
+    (lambda: I.knn_laplacian(800, 8, 5), 6, False),
+])
+def test_colouring_is_proper_and_greedy(gen, L, geo):
+    """Every colour class is independent in the graph after the step's fill
+    (so its interfaces touch disjoint blocks and run in one launch), the
+    fill graph contains every coupling the eliminations create (Sec. 2.4),
+    and each cluster takes the smallest colour that none of its earlier
+    neighbours holds."""
+    p = gen()
+    tree = O.analyze(p.n, p.rowptr, p.colind, p.coords if geo else None, L)
+    for st in tree.steps:
+        nt = st.keys.shape[0]
+        rem = [i for i in range(nt) if not st.elim[i]]
+        for i in rem:
+            assert st.colour[i] >= 0
+            for j in st.adjf[i]:
+                assert not st.elim[j] and st.colour[j] != st.colour[i]
+                assert i in st.adjf[j]
+        for s in range(nt):  # neighbours of an eliminated separator become coupled
+            if st.elim[s]:
+                assert st.colour[s] == -1
+                nb = [q for q in st.adj[s] if not st.elim[q]]
+                for a in nb:
+                    assert set(nb) - {a} <= set(st.adjf[a])
+        for i in rem:
+            used = {int(st.colour[j]) for j in st.adjf[i] if j < i}
+            assert int(st.colour[i]) not in used
+            assert all(c in used for c in range(int(st.colour[i])))
+
+
+# ------------------------------------------------ BFS bisection (reading C3)
+
+def _csr(n, edges):
+    rows = {v: {v} for v in range(n)}
+    for a, b in edges:
+        rows[a].add(b)
+        rows[b].add(a)
+    rowptr = np.zeros(n + 1, np.int64)
+    colind = []
+    for v in range(n):
+        c = sorted(rows[v])
+        colind += c
+        rowptr[v + 1] = rowptr[v] + len(c)
+    return rowptr, np.array(colind, np.int64)
+
+
+def test_bfs_tie_break_and_unreached_vertices():
+    """Graph 1 - 0 - 2 plus an isolated vertex 3.  BFS from 0 reaches 1 and 2
+    at distance 1: the farthest-vertex tie goes to the smallest id, 1.  BFS
+    from 1: d = (1, 0, 2) for 0, 1, 2; vertex 3 is unreached and takes the
+    largest finite distance + 1 = 3.  Bisection on d: sorted (1, 0, 2, 3),
+    threshold d = 1 (position 1), P1 = {0, 1}; 0 touches 2 in P2, so
+    left = {1}, separator = {0}, right = {2, 3}.  (Ties to the largest id
+    would start from 2 and give d = (1, 2, 0, 3).)"""
+    rowptr, colind = _csr(4, [(0, 1), (0, 2)])
+    U = np.arange(4)
+    d = O.bfs_distance(U, rowptr, colind, 4)
+    assert d[:, 0].tolist() == [1.0, 0.0, 2.0, 3.0]
+    left, mid, right = O.bisect(U, d, rowptr, colind, 4)
+    assert left.tolist() == [1] and mid.tolist() == [0] and right.tolist() == [2, 3]
+
+
+def test_bfs_bisection_4x3_grid_matches_hand_derivation():
+    p = I._assemble((3, 4), np.ones((3, 4)), "grid_4x3")
+    S, Lb, Rb = O.ordering_clustering(p.n, p.rowptr, p.colind, None, 2)
+    with open(os.path.join(GOLDEN, "bfs_4x3_L2.txt")) as f:
+        rows = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+    want = np.zeros((12, 3), np.int64)
+    for r in rows:
+        y = int(r[0])
+        for x, lab in enumerate(r[1:]):
+            want[x + 4 * y] = [int(v) for v in lab.split(",")]
+    assert np.array_equal(np.stack([S, Lb, Rb], axis=1), want)
+
+
+# ------------------------------------------------ the cluster trees of Sec. 2.3
+
+def test_cluster_trees_of_the_ordering_figure():
+    """The ordering-and-clustering figure of Sec. 2.3 on a fine grid of its
+    square [-1, 1]^2, with the figure's separators as the vertex-separator
+    routine: root = the vertical strip |x| <= 0.075; level 2 = horizontal
+    strips at y in [0.10, 0.25] (left half) and [-0.30, -0.15] (right half);
+    level 3 = horizontal strips at y in [-0.70, -0.55] (both bottom
+    quarters) and [0.50, 0.65] (left top), and the vertical strip
+    x in [0.50, 0.65] (right top).  Algorithm 3's labels, clusters of equal
+    labels and the label-coarsening merge must give the figure's trees:
+    root 9 -> 5 -> 1, its five clusters made of 3, 1, 1, 1, 3 pieces from
+    bottom to top; left level-2 separator one cluster throughout; right
+    level-2 separator 3 -> 1 (cut by the right-top vertical strip); every
+    level-3 separator a single cluster."""
+    m = 80
+    c = -1 + (2.0 / m) * (np.arange(m) + 0.5)
+    p = I._assemble((m, m), np.ones((m, m)), "figure")
+    X, Y = c[p.coords[:, 0].astype(int)], c[p.coords[:, 1].astype(int)]
+    strips = {(1, 1): (X, -0.075, 0.075), (2, 1): (Y, 0.10, 0.25), (2, 2): (Y, -0.30, -0.15),
+              (3, 1): (Y, -0.70, -0.55), (3, 2): (Y, 0.50, 0.65), (3, 3): (Y, -0.70, -0.55),
+              (3, 4): (X, 0.50, 0.65)}
+
+    def sep(lvl, k, U):
+        v, lo, hi = strips[(lvl, k)]
+        v = v[U]
+        return U[v < lo], U[(v >= lo) & (v <= hi)], U[v > hi]
+
+    tree = O.analyze(p.n, p.rowptr, p.colind, None, 4, separator=sep)
+
+    def counts(S):
+        return [int(np.sum(st.keys[:, 0] == S)) for st in tree.steps if np.any(st.keys[:, 0] == S)]
+
+    assert counts(1) == [9, 5, 1, 1]
+    assert counts(2) == [1, 1, 1] and counts(3) == [3, 1, 1]
+    assert all(counts(S) == [1, 1] for S in (4, 5, 6, 7))
+    # the five step-2 root clusters, bottom to top, and how many step-1
+    # clusters each merged
+    st2 = tree.steps[1]
+    ids = [i for i in range(st2.keys.shape[0]) if st2.keys[i, 0] == 1]
+
+    def ymean(i):
+        vs = np.concatenate([tree.perm[tree.cluster_ptr[ch]:tree.cluster_ptr[ch + 1]] for ch in st2.children[i]])
+        return Y[vs].mean()
+
+    ids.sort(key=ymean)
+    assert [len(st2.children[i]) for i in ids] == [3, 1, 1, 1, 3]
+    right2 = [i for i in range(st2.keys.shape[0]) if st2.keys[i, 0] == 3]
+    assert [len(st2.children[i]) for i in right2] == [3]
