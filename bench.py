@@ -28,46 +28,81 @@ sys.path.insert(0, ROOT)
 GRID, LEVELS, EPS, SEED = 64, 10, 1e-2, 1
 WORKLOAD = "lapl3d_64^3_7pt_L10_eps1e-2"
 METRIC = "factor+PCG s to rel-res 1e-10 (3D), mixed/batched vs FP64; % roofline"
-# bounded oracle sample: the same family at 32^3 (L = 7 keeps the 8^3 leaves),
-# scaled to the 64^3 unit by the N log N factorization cost ratio (Sec. 3.3)
-SAMPLE_GRID, SAMPLE_LEVELS = 32, 7
+# wall-clock budget of the reference arm (full-size oracle steps)
+REF_BUDGET_S = 300.0
 
 
-def _nlogn(n):
-    return n * math.log2(n)
+def workload_config(n, nnz, levels=LEVELS, grid=GRID, world=1) -> dict:
+    """The `config` of both arms' lines: the workload only (no precision or
+    implementation keys), so that the two lines name the same problem."""
+    return {"workload": WORKLOAD if (grid, levels) == (GRID, LEVELS) else f"lapl3d_{grid}^3_7pt_L{levels}_eps1e-2",
+            "N": int(n), "nnz": int(nnz), "levels": int(levels), "eps": EPS, "tol": 1e-10, "b_seed": SEED,
+            "parallelism": f"replicas x{world}",
+            "l2": "256 MB L2 flush between timed GPU steps; factor data > 129 MB"}
 
 
-SAMPLE_SCALE = _nlogn(GRID ** 3) / _nlogn(SAMPLE_GRID ** 3)
+_ORACLE_RUN = r"""
+import json, os, sys, time
+sys.path.insert(0, %(root)r)
+from paper_1901_02971_gb300 import inputs as I
+from oracle import spand_oracle as O
+p = I.laplacian_3d(%(grid)d); b = I.rhs(p.n, %(seed)d)
+t0 = time.perf_counter(); tr = O.analyze(p.n, p.rowptr, p.colind, p.coords, %(levels)d); t_p = time.perf_counter() - t0
+print(json.dumps(dict(kind="analysis", t_p=t_p, n=p.n, nnz=p.nnz)), flush=True)
+A = O.permuted_matrix(p.rowptr, p.colind, p.vals, tr.perm)
+start = time.perf_counter(); last = 0.0
+for i in range(%(steps)d):
+    if i > 0 and time.perf_counter() - start + last > %(budget)r:
+        break
+    t1 = time.perf_counter()
+    F = O.factorize(p.rowptr, p.colind, p.vals, tr, %(eps)r)
+    t2 = time.perf_counter()
+    x, it, rr = O.pcg(A, b[tr.perm], lambda r: O.apply(F, r))
+    t3 = time.perf_counter()
+    last = t3 - t1
+    print(json.dumps(dict(kind="step", t_f=t2 - t1, t_s=t3 - t2, iters=it, relres=rr,
+                          size_top=F.size_top, mem_f=F.mem_f)), flush=True)
+"""
 
 
-def oracle_sample_seconds(threads: int = 1) -> dict:
-    """Runs the FP64 oracle once on the bounded sample in a fresh process
-    (spawned before any CUDA work) whose BLAS/LAPACK calls use `threads`
-    threads; returns its wall time."""
-    code = (
-        "import os,sys,time,json;sys.path.insert(0,%r)\n"
-        "from paper_1901_02971_gb300 import inputs as I\n"
-        "from oracle import spand_oracle as O\n"
-        "p=I.laplacian_3d(%d);b=I.rhs(p.n,%d)\n"
-        "t0=time.perf_counter();tr=O.analyze(p.n,p.rowptr,p.colind,p.coords,%d);t1=time.perf_counter()\n"
-        "F=O.factorize(p.rowptr,p.colind,p.vals,tr,%r);t2=time.perf_counter()\n"
-        "A=O.permuted_matrix(p.rowptr,p.colind,p.vals,tr.perm)\n"
-        "x,it,rr=O.pcg(A,b[tr.perm],lambda r:O.apply(F,r));t3=time.perf_counter()\n"
-        "print(json.dumps(dict(t_p=t1-t0,t_f=t2-t1,t_s=t3-t2,iters=it,relres=rr)))\n"
-    ) % (ROOT, SAMPLE_GRID, SEED, SAMPLE_LEVELS, EPS)
+def oracle_runs(steps: int = 1, budget_s: float = 1e30, threads: int = 1, grid: int = GRID,
+                levels: int = LEVELS) -> dict:
+    """Times the FP64 oracle on the whole workload in a fresh process
+    (started before any CUDA work in this one; its BLAS/LAPACK limited to
+    `threads` threads): the analysis once, then up to `steps` full
+    factorizations + PCG solves, stopping early when the next one would run
+    past `budget_s` (at least one always runs).  Returns t_P and the list of
+    per-step t_F, t_S, n_CG."""
+    code = _ORACLE_RUN % dict(root=ROOT, grid=grid, seed=SEED, levels=levels, steps=max(1, steps),
+                              budget=float(budget_s), eps=EPS)
     t = str(int(threads))
     env = dict(os.environ, OPENBLAS_NUM_THREADS=t, OMP_NUM_THREADS=t, MKL_NUM_THREADS=t)
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=7200)
     if r.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+        raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
+    recs = [json.loads(ln) for ln in r.stdout.splitlines() if ln.startswith("{")]
+    ana = [x for x in recs if x["kind"] == "analysis"][0]
+    return {"t_p": ana["t_p"], "steps": [x for x in recs if x["kind"] == "step"]}
 
 
-def sample_phases(r: dict) -> dict:
-    """The oracle sample's own phase times and PCG count (unscaled): analysis
-    t_P, factorization t_F, PCG t_S (s), iterations n_CG."""
-    return {"t_p_s": round(r["t_p"], 4), "t_f_s": round(r["t_f"], 4), "t_s_s": round(r["t_s"], 4),
-            "n_cg": int(r["iters"])}
+def oracle_phases(run: dict) -> dict:
+    """t_P, and the mean t_F, t_S (s) and the n_CG of the oracle's steps."""
+    st = run["steps"]
+    return {"t_p_s": round(run["t_p"], 3), "t_f_s": round(statistics.mean(x["t_f"] for x in st), 3),
+            "t_s_s": round(statistics.mean(x["t_s"] for x in st), 3), "n_cg": int(st[-1]["iters"]),
+            "relres": st[-1]["relres"], "size_top": int(st[-1]["size_top"]), "mem_f": int(st[-1]["mem_f"])}
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part", "hardware")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 class Clocks:
@@ -264,28 +299,165 @@ def max_over_ranks(vals, dist=None, device="cpu"):
 
 
 def run_reference(args):
+    """The oracle arm: the FP64 CPU oracle, as it stands, on the same workload
+    and metric.  The analysis runs once (t_P is not part of the metric); then
+    full-size factorizations + PCG solves are timed one after another, as
+    many of the requested steps as fit in REF_BUDGET_S of wall time (a step
+    takes tens of seconds on one host core).  The oracle has nothing to warm
+    up (no compilation or caches carried between runs), so no untimed step
+    runs; `steps` and `warmup` state what was actually done."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    times, iters, last = [], [], None
-    for i in range(args.warmup + args.steps):
-        r = oracle_sample_seconds()
-        if i >= args.warmup:
-            times.append((r["t_f"] + r["t_s"]) * SAMPLE_SCALE)
-            iters.append(r["iters"])
-            last = r
+    run = oracle_runs(steps=args.steps, budget_s=args.ref_budget, grid=args.grid, levels=args.levels)
+    st = run["steps"]
+    times = [x["t_f"] + x["t_s"] for x in st]
     v = statistics.mean(times)
+    ph = oracle_phases(run)
+    import numpy as np  # noqa: F401  (the oracle's dependency; the reference arm needs no GPU)
+    from paper_1901_02971_gb300 import inputs as I
+    p = I.laplacian_3d(args.grid)
+    sample = (f"the whole workload: FP64 oracle factorization + PCG on the {args.grid}^3 cube (L={args.levels}), "
+              f"{len(st)} full-size runs one after another on 1 host core ({cpu_model()}); analysis once "
+              f"(t_P {run['t_p']:.1f} s, not in the metric); {len(st)} of the {args.steps} requested steps fit "
+              f"in the {args.ref_budget:.0f} s budget")
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (factor > 129 MB)"},
-           "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
-                            "sample": f"FP64 oracle factor+PCG on the {SAMPLE_GRID}^3 cube (L={SAMPLE_LEVELS}), "
-                                      f"scaled x{SAMPLE_SCALE:.2f} by N log N to 64^3; iters {iters[0]}",
-                            "sample_phases": sample_phases(last)},
+           "steps": len(st), "warmup": 0, "steps_requested": args.steps, "warmup_requested": args.warmup,
+           "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": workload_config(p.n, p.nnz, levels=args.levels, grid=args.grid, world=args.gpus),
+           "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample,
+                            "phases": ph, "step_times_s": [round(t, 3) for t in times]},
            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0
+
+
+def extra_configs(peaks: dict, budget_s: float = 240.0) -> dict:
+    """The other workloads of the benchmark family, one factorization + PCG
+    each (after one untimed warm-up factorization that allocates the
+    device memory), with the paper's metrics: t_F, t_S, n_CG, size_Top,
+    mem_F, and the per-phase rooflines of a profiled run.
+      * 3D diffusion, a = 10^U(-3,3) per 8^3 block, 128^3 cells, L = 13,
+        eps 1e-1 / 1e-2 / 1e-3, FP64 / FP32 / BF16 factors;
+      * graph Laplacian of the 10-NN graph of 10^6 random points (+1e-4 I),
+        no coordinates, L = 12, eps 1e-2, FP32 factor;
+      * the batch of 32 independent 2D diffusion problems (128^2 .. 512^2,
+        log-normal a), analyzed together and factorized / solved
+        concurrently (one stream each), FP32 factors, with the backward pass
+        (adjoint solves and dL/dA) of loss = sum ||x_i - y_i||^2.
+    Stops adding workloads once `budget_s` of wall time is spent."""
+    import numpy as np
+    import torch
+
+    from paper_1901_02971_gb300 import Solver, SpandError, factorize_all, solve_all
+    from paper_1901_02971_gb300 import inputs as I
+    t_start = time.perf_counter()
+    out = {}
+
+    def one(p, coords, tag, **kw):
+        s = Solver.from_problem(p, use_coords=coords, tol=1e-10, maxit=500, **kw)
+        try:
+            b = torch.from_numpy(I.rhs(p.n, SEED)).cuda()
+            s.factorize()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.factorize()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            x, it, rr = s.solve(b, check=False)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            st = s.stats()
+            s.reset_kernel_profile()
+            s.set_profiling(True)
+            s.factorize()
+            s.solve(b, check=False)
+            torch.cuda.synchronize()
+            s.set_profiling(False)
+            form = kw.get("precision", "fp64")
+            pr = phase_rooflines(s.kernel_profile(), peaks, form)
+            return {"t_f_s": t1 - t0, "t_s_s": t2 - t1, "n_cg": it, "relres": rr, "size_top": st.size_top,
+                    "mem_f": st.mem_f, "t_p_s": st.t_analyze_s, "phase_rooflines": pr}
+        except SpandError as e:
+            return {"error": str(e)[:200]}
+        finally:
+            s.close()
+
+    def left():
+        return budget_s - (time.perf_counter() - t_start)
+
+    try:
+        p = I.diffusion_3d(128, 2)
+        c3 = {}
+        for eps in (1e-1, 1e-2, 1e-3):
+            for form in ("fp64", "fp32", "bf16"):
+                if left() <= 0:
+                    break
+                c3[f"eps{eps:g}_{form}"] = one(p, True, "diff3d_128", levels=13, eps=eps, precision=form)
+        out["diff3d_128^3_L13"] = {"N": p.n, "nnz": p.nnz, "runs": c3}
+        del p
+    except Exception as e:  # reported, never fatal to the headline line
+        out["diff3d_128^3_L13"] = {"error": str(e)[:300]}
+    try:
+        if left() > 0:
+            t0 = time.perf_counter()
+            p = I.knn_laplacian(1_000_000, 10, 3)
+            gen = time.perf_counter() - t0
+            r = one(p, False, "knn", levels=12, eps=1e-2, precision="fp32")
+            r["generation_s"] = gen
+            out["knn_1e6_k10_L12"] = dict(N=p.n, nnz=p.nnz, **r)
+            del p
+    except Exception as e:
+        out["knn_1e6_k10_L12"] = {"error": str(e)[:300]}
+    try:
+        if left() > 0:
+            from paper_1901_02971_gb300.autograd import spand_solve
+            items = [I.batch_diffusion_2d(i) for i in range(32)]
+            probs = [it[0] for it in items]
+            opts = [dict(levels=it[3], eps=1e-2, precision="fp32", tol=1e-10) for it in items]
+            t0 = time.perf_counter()
+            solvers = Solver.batch(probs, opts)
+            t_p = time.perf_counter() - t0
+            try:
+                bs = [torch.from_numpy(it[2]).cuda() for it in items]
+                factorize_all(solvers)
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                factorize_all(solvers)
+                torch.cuda.synchronize()
+                t2 = time.perf_counter()
+                res = solve_all(solvers, bs)
+                torch.cuda.synchronize()
+                t3 = time.perf_counter()
+                # backward of loss = sum ||x_i - y_i||^2 (adjoint solves + dL/dA), values unchanged
+                vals = [torch.from_numpy(p.vals).cuda().requires_grad_(True) for p in probs]
+                bv = [b.clone().requires_grad_(True) for b in bs]
+                for s, v in zip(solvers, vals):
+                    s._vals_version, s._vals_stamp = v, v._version
+                ys = [torch.from_numpy(it[1] + 0.01 * I.rhs(p.n, 200 + i)).cuda()
+                      for i, (it, p) in enumerate(zip(items, probs))]
+                torch.cuda.synchronize()
+                t4 = time.perf_counter()
+                loss = sum(((spand_solve(v, b, s) - y) ** 2).sum() for v, b, s, y in zip(vals, bv, solvers, ys))
+                loss.backward()
+                torch.cuda.synchronize()
+                t5 = time.perf_counter()
+                its = [r[1] for r in res]
+                out["batch32_diff2d"] = {"N_total": int(sum(p.n for p in probs)), "t_p_s": t_p, "t_f_s": t2 - t1,
+                                         "t_s_s": t3 - t2, "n_cg_max": int(max(its)), "n_cg_mean": float(np.mean(its)),
+                                         "relres_max": float(max(r[2] for r in res)),
+                                         "forward_backward_s": t5 - t4,
+                                         "note": "concurrent factorizations / solves, one CUDA stream per problem; "
+                                                 "forward+backward re-solves every problem then runs its adjoint "
+                                                 "solve and the sampled dL/dA kernel"}
+            finally:
+                for s in solvers:
+                    s.close()
+    except Exception as e:
+        out["batch32_diff2d"] = {"error": str(e)[:300]}
+    out["wall_s"] = time.perf_counter() - t_start
+    return out
 
 
 def main():
@@ -295,6 +467,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra-configs", action="store_true",
+                    help="skip the 128^3 diffusion, 10^6-point kNN and 32-problem batch workloads")
+    ap.add_argument("--ref-budget", type=float, default=REF_BUDGET_S,
+                    help="wall-clock budget (s) of the reference arm's full-size oracle steps")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--grid", type=int, default=GRID, help="cube edge (small cases for profiling only)")
     ap.add_argument("--levels", type=int, default=LEVELS)
@@ -305,10 +481,9 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     rank, world, local = dist_env()
-    cpu = cpu_all = None
+    cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and (args.grid, args.levels) == (GRID, LEVELS):
-        cpu = oracle_sample_seconds()  # before any CUDA work in this process
-        cpu_all = oracle_sample_seconds(os.cpu_count() or 1)
+        cpu = oracle_runs(steps=1)  # the whole workload, once, 1 thread; before any CUDA work here
     import numpy as np
     import torch
 
@@ -437,16 +612,22 @@ def main():
         return 0
     peaks = load_peaks()
     roofline = make_roofline(prof32, peaks, grid=args.grid)
+    extras = None
+    if rank == 0 and not args.no_extra_configs and workload == WORKLOAD:
+        s32.close()
+        s64.close()
+        extras = extra_configs(peaks)
     out = {
         "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32", "tf32": "f32 (tf32 Schur operands)", "bf16": "f32 (bf16 Schur operands)"}[args.form],
+        "dtype": {"fp32": "f32 factor; f64 pivot Cholesky, PCG, SpMV",
+                  "tf32": "f32 factor (tf32 Schur operands); f64 pivot Cholesky, PCG, SpMV",
+                  "bf16": "f32 factor (bf16 Schur operands); f64 pivot Cholesky, PCG, SpMV"}[args.form],
         "data": "synthetic",
-        "config": {"workload": workload, "N": p.n, "nnz": p.nnz, "levels": levels, "eps": EPS,
-                   "factor": {"fp32": "fp32 (mixed)", "tf32": "fp32, Schur GEMMs tf32 on tensor cores",
-                              "bf16": "fp32, Schur GEMMs bf16 on tensor cores"}[args.form] + ", PCG fp64",
-                   "parallelism": f"replicas x{world}",
-                   "l2": "256 MB L2 flush between timed steps; factor data > 129 MB"},
+        "config": workload_config(p.n, p.nnz, levels=levels, grid=args.grid, world=world),
+        "factor": {"fp32": "fp32 storage, fp32 solves/GEMMs/QR", "tf32": "fp32 storage, Schur GEMMs tf32 on tensor cores",
+                   "bf16": "fp32 storage, Schur GEMMs bf16 on tensor cores"}[args.form] +
+                  "; pivot and scaling Cholesky fp64; PCG, dots and SpMV fp64",
         "forms": {
             "mixed_" + args.form: {"s_per_step": v, "iters": it32[-1], "relres": rr32, "t_factor_ms_phases": list(ph32[:4]),
                            "apply_ms": ph32[4], "size_top": st32.size_top, "mem_f": st32.mem_f,
@@ -470,19 +651,16 @@ def main():
         "phase_rooflines": phase_rooflines(prof32, peaks, args.form),
         "peaks_source": peaks["_source"],
     }
+    if extras is not None:
+        out["other_workloads"] = extras
     if cpu is not None:
-        cv = (cpu["t_f"] + cpu["t_s"]) * SAMPLE_SCALE
+        ph = oracle_phases(cpu)
+        cv = ph["t_f_s"] + ph["t_s_s"]
         out["cpu_baseline"] = {"value": cv, "unit": "s", "cores": 1, "kind": "oracle",
-                               "sample": f"FP64 oracle factor+PCG on the {SAMPLE_GRID}^3 cube (L={SAMPLE_LEVELS}, "
-                                         f"{cpu['t_f'] + cpu['t_s']:.2f} s, {cpu['iters']} iters), scaled "
-                                         f"x{SAMPLE_SCALE:.2f} (N log N) to 64^3",
-                               "sample_phases": sample_phases(cpu)}
-        ca = (cpu_all["t_f"] + cpu_all["t_s"]) * SAMPLE_SCALE
-        out["cpu_baseline_all_cores"] = {
-            "value": ca, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"the same sample with the oracle's BLAS/LAPACK on all {os.cpu_count()} host cores "
-                      f"({cpu_all['t_f'] + cpu_all['t_s']:.2f} s), scaled x{SAMPLE_SCALE:.2f}",
-            "sample_phases": sample_phases(cpu_all)}
+                               "sample": f"the whole workload, once: FP64 oracle factorization + PCG on the 64^3 "
+                                         f"cube (L={LEVELS}) on 1 host core ({cpu_model()}), {ph['n_cg']} "
+                                         f"iterations; analysis t_P {ph['t_p_s']:.1f} s not in the metric",
+                               "phases": ph}
     print(json.dumps(out))
     s32.close()
     s64.close()

@@ -53,12 +53,17 @@ enum {
 };
 
 /* precision of the factorization (the PCG recurrences, its dot products
- * and the SpMV always run in FP64) */
+ * and the SpMV always run in FP64, and so does the Cholesky of every pivot
+ * block: the eliminated separators of Sec. 2.4 and the scaled interfaces of
+ * Sec. 2.5) */
 enum {
   SPAND_FP64 = 0,  /* plain: every factor kernel in FP64 */
-  SPAND_FP32 = 1,  /* mixed: every factor kernel (pivot and scaling Cholesky,
-                      TRSM, Schur GEMMs, QR) and the preconditioner apply in
-                      FP32; vectors, SpMV and the PCG recurrences in FP64 */
+  SPAND_FP32 = 1,  /* mixed: factor stored in FP32; pivot and scaling Cholesky
+                      in FP64 (on an FP64 copy of each pivot block, U and the
+                      inverses of its diagonal tiles rounded to FP32);
+                      triangular solves, Schur GEMMs, QR and the
+                      preconditioner apply in FP32; vectors, SpMV and the PCG
+                      recurrences in FP64 */
   SPAND_TF32 = 2,  /* as SPAND_FP32, with the elimination's Schur GEMMs on the
                       tensor cores: TF32 operands, FP32 accumulation */
   SPAND_BF16 = 3   /* as SPAND_TF32 with BF16 operands (FP32 accumulation,
@@ -300,6 +305,23 @@ int spand_get_kernel_profile(spand_handle h, int32_t family, double* out4);
 int spand_reset_kernel_profile(spand_handle h);
 /* Kernels launched by this handle since it was created (always counted). */
 int spand_get_launch_count(spand_handle h, int64_t* launches);
+
+/*
+ * spand_set_apply_wait -- failure-path knob (not part of the method).  The
+ * preconditioner apply is one cooperative kernel whose phases are separated
+ * by grid barriers; every barrier wait is bounded, and a wait that runs out
+ * makes the CTA record the timeout and leave the kernel, so that the call
+ * returns SPAND_ERR_TIMEOUT and the context stays usable.  For later
+ * spand_apply / spand_apply_noalloc / spand_solve calls on h:
+ *   polls       : polls per barrier wait before giving up (0 = the default,
+ *                 2^24 polls with short sleeps, well over a second).
+ *   unreachable : nonzero makes every barrier wait for one arrival more than
+ *                 the grid has (a count nothing reaches), so every wait runs
+ *                 out after `polls` polls and the call returns
+ *                 SPAND_ERR_TIMEOUT without having computed z; 0 restores
+ *                 normal barriers.
+ */
+int spand_set_apply_wait(spand_handle h, uint32_t polls, int32_t unreachable);
 
 void spand_destroy(spand_handle h);
 

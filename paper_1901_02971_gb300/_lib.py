@@ -37,7 +37,8 @@ EXPORTS = ["spand_default_opts", "spand_analyze", "spand_analyze_batch", "spand_
            "spand_apply_noalloc", "spand_sampled_outer", "spand_sketch_gaussian",
            "spand_get_tree", "spand_get_step", "spand_get_ranks", "spand_get_stats",
            "spand_get_phase_times", "spand_set_profiling", "spand_get_kernel_profile",
-           "spand_reset_kernel_profile", "spand_get_launch_count", "spand_destroy", "spand_error_string",
+           "spand_reset_kernel_profile", "spand_get_launch_count", "spand_set_apply_wait", "spand_destroy",
+           "spand_error_string",
            "spand_last_error"]
 KERNEL_FAMILIES = ["potrf", "trsm", "schur", "cpqr", "copy", "apply", "pcg"]
 
@@ -98,6 +99,7 @@ def lib():
     L.spand_get_kernel_profile.argtypes = [C.c_void_p, C.c_int32, P]
     L.spand_reset_kernel_profile.argtypes = [C.c_void_p]
     L.spand_get_launch_count.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
+    L.spand_set_apply_wait.argtypes = [C.c_void_p, C.c_uint32, C.c_int32]
     L.spand_destroy.argtypes = [C.c_void_p]
     L.spand_destroy.restype = None
     L.spand_error_string.argtypes = [C.c_int]
@@ -280,6 +282,12 @@ def spand_get_launch_count(h: int) -> int:
     v = C.c_int64(0)
     _check(lib().spand_get_launch_count(h, C.byref(v)))
     return v.value
+
+
+def spand_set_apply_wait(h: int, polls: int = 0, unreachable: bool = False):
+    """Failure-path knob: bound the apply's grid-barrier waits by `polls`
+    polls (0 = default); `unreachable` makes every wait run out."""
+    _check(lib().spand_set_apply_wait(h, polls, 1 if unreachable else 0))
 
 
 def spand_destroy(h: int):

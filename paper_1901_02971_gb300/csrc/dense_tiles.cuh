@@ -29,7 +29,10 @@ struct TileSmem {  // two K chunks (double buffer)
 // acc[ii][jj] (row = tx + 16 ii, col = ty + 16 jj; tx = tid % 16, ty = tid / 16)
 // += sum_{k < K} A[k + row*lda] * B[k + col*ldb]     ("TN": C += A^T B)
 // Rows >= mi and columns >= nj read as zero.
-template <typename T>
+// UPPER: only the outputs on or above the diagonal of a diagonal tile are
+// needed (rows tx + 16 ii > columns ty + 16 jj whenever ii > jj: those
+// products are skipped and their accumulators stay zero).
+template <typename T, bool UPPER = false>
 __device__ __forceinline__ void tn_acc(T (&acc)[4][4], const T* __restrict__ A, int lda, int mi,
                                        const T* __restrict__ B, int ldb, int nj, int K,
                                        TileSmem<T>& sm) {
@@ -72,7 +75,8 @@ __device__ __forceinline__ void tn_acc(T (&acc)[4][4], const T* __restrict__ A, 
 #pragma unroll
       for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) acc[ii][jj] = fma(av[ii], bv[jj], acc[ii][jj]);
+        for (int jj = 0; jj < 4; ++jj)
+          if (!UPPER || ii <= jj) acc[ii][jj] = fma(av[ii], bv[jj], acc[ii][jj]);
     }
     buf ^= 1;
   }
@@ -209,11 +213,13 @@ __device__ bool potrf_inv_tile(SqTile<T>& s, SqTile<T>& D, int nb) {
           d[p][q] = d1[q];
         }
       } else if (i > k1) {
+        // U's upper triangle: column block q >= row block p; D's lower
+        // triangle: q <= p (the other blocks are zero in D and unused in U)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int j = ty + 16 * q;
-          if (j >= i) a[p][q] = fma(-u1i[p], u1j[q], fma(-u0i[p], u0j[q], a[p][q]));
-          d[p][q] = fma(-u1i[p], d1[q], fma(-u0i[p], d0[q], d[p][q]));
+          if (q >= p && j >= i) a[p][q] = fma(-u1i[p], u1j[q], fma(-u0i[p], u0j[q], a[p][q]));
+          if (q <= p) d[p][q] = fma(-u1i[p], d1[q], fma(-u0i[p], d0[q], d[p][q]));
         }
       }
     }
@@ -234,22 +240,29 @@ __device__ bool potrf_inv_tile(SqTile<T>& s, SqTile<T>& D, int nb) {
 // zero above the diagonal), i.e. B <- U^{-T} B as one small GEMM instead of a
 // serial substitution.  D, B in shared memory; each thread produces a 4x4
 // patch; starts and ends synchronised.
+// D is lower triangular: for l in the 16-row block lb, the rows tx + 16 ii
+// with ii < lb lie above l, where D is zero, so their products are skipped
+// (uniformly over the CTA).
 template <typename T>
 __device__ void apply_inv_tile(const SqTile<T>& D, SqTile<T>& B, int nb) {
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   T acc[4][4];
   zero_acc(acc);
-  for (int l = 0; l < nb; ++l) {
-    T dv[4], bv[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      dv[q] = D.v[tx + 16 * q][l];
-      bv[q] = B.v[l][ty + 16 * q];
+  for (int lb = 0; lb < 4; ++lb) {
+    const int le = min(nb, 16 * lb + 16);
+    for (int l = 16 * lb; l < le; ++l) {
+      T dv[4], bv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        dv[q] = D.v[tx + 16 * q][l];
+        bv[q] = B.v[l][ty + 16 * q];
+      }
+#pragma unroll
+      for (int ii = lb; ii < 4; ++ii)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) acc[ii][jj] = fma(dv[ii], bv[jj], acc[ii][jj]);
     }
-#pragma unroll
-    for (int ii = 0; ii < 4; ++ii)
-#pragma unroll
-      for (int jj = 0; jj < 4; ++jj) acc[ii][jj] = fma(dv[ii], bv[jj], acc[ii][jj]);
   }
   __syncthreads();
 #pragma unroll

@@ -10,12 +10,20 @@ namespace spand {
 
 // ---------------------------------------------------------------- descriptors
 
+// Tile bandwidth of a pivot block: U's tile (I, J), I <= J, can be nonzero
+// only if J - I <= bw (0 = dense).  A Cholesky factor keeps the envelope of
+// its matrix (no fill above the first nonzero of a column), so for a pivot
+// block that is still a piece of the sparse A (a leaf interior, eliminated
+// first, with its vertices in lexicographic order: a band of one grid layer)
+// the tiles outside the band hold exact zeros before and after the
+// factorization, and the kernels skip them: same result, far fewer flops.
 template <typename T>
 struct RowDesc {      // a cluster's block row or its diagonal block
   T* R;               // column-major, leading dimension ld
   int32_t n;          // rows (cluster size)
   int32_t ld;
   T* dinv;            // ceil(n/64) tiles of 64x64: inverses U_kk^{-T} of the diagonal tiles
+  int32_t bw, pad;    // tile bandwidth of U (0 = dense)
 };
 
 template <typename T>
@@ -23,7 +31,7 @@ struct TrsmTask {     // B <- U^{-T} B: U upper n x n, B n x nc (rows < i_start 
   const T* U;
   const T* dinv;      // inverses of U's diagonal 64x64 tiles (see RowDesc)
   T* B;
-  int32_t n, ldu, ldb, nc, i_start, pad;
+  int32_t n, ldu, ldb, nc, i_start, bw;  // bw: tile bandwidth of U (0 = dense)
 };
 
 template <typename T>
@@ -102,7 +110,7 @@ __global__ void __launch_bounds__(NT) k_potrf_trsm(const RowDesc<T>* __restrict_
   const RowDesc<T> d = rows[blockIdx.y];
   const int k0 = k * TB;
   const int j0 = k0 + TB * (1 + blockIdx.x);
-  if (j0 >= d.n) return;
+  if (j0 >= d.n || (d.bw > 0 && (int)blockIdx.x + 1 > d.bw)) return;  // past the end, or a zero tile
   const int nb = min(TB, d.n - k0), nc = min(TB, d.n - j0);
   load_tile(D, d.dinv + (size_t)k * TB * TB, TB, TB, TB);
   load_tile(B, d.R + k0 + (size_t)j0 * d.ld, d.ld, nb, nc);
@@ -125,11 +133,15 @@ __global__ void __launch_bounds__(NT) k_potrf_update(const RowDesc<T>* __restric
   int i = 0;
   while (lin >= m - i) { lin -= m - i; ++i; }
   const int j = i + lin;
+  if (d.bw > 0 && j + 1 > d.bw) return;  // U_kj is a zero tile: nothing to subtract
   const int i0 = (k + 1 + i) * TB, j0 = (k + 1 + j) * TB, k0 = k * TB;
   const int mi = min(TB, d.n - i0), nj = min(TB, d.n - j0), kb = min(TB, d.n - k0);
   T acc[4][4];
   zero_acc(acc);
-  tn_acc(acc, d.R + k0 + (size_t)i0 * d.ld, d.ld, mi, d.R + k0 + (size_t)j0 * d.ld, d.ld, nj, kb, sm);
+  if (i == j)  // diagonal tile: only its upper triangle is used
+    tn_acc<T, true>(acc, d.R + k0 + (size_t)i0 * d.ld, d.ld, mi, d.R + k0 + (size_t)j0 * d.ld, d.ld, nj, kb, sm);
+  else
+    tn_acc<T, false>(acc, d.R + k0 + (size_t)i0 * d.ld, d.ld, mi, d.R + k0 + (size_t)j0 * d.ld, d.ld, nj, kb, sm);
   sub_store(acc, d.R + i0 + (size_t)j0 * d.ld, d.ld, mi, nj);
 }
 
@@ -152,7 +164,9 @@ __global__ void __launch_bounds__(NT) k_trsm_cols(const TrsmTask<T>* __restrict_
     const int nb = min(TB, d.n - i0);
     T acc[4][4];
     zero_acc(acc);
-    if (i0 > is) tn_acc(acc, d.U + is + (size_t)i0 * d.ldu, d.ldu, nb, X + is, d.ldb, nc, i0 - is, sm);
+    // rows of U's column block i0 above the band are zero tiles
+    const int ls = d.bw > 0 ? max(is, i0 - d.bw * TB) : is;
+    if (i0 > ls) tn_acc(acc, d.U + ls + (size_t)i0 * d.ldu, d.ldu, nb, X + ls, d.ldb, nc, i0 - ls, sm);
     load_tile(U, d.dinv + (size_t)(i0 / TB) * TB * TB, TB, TB, TB);  // U_ii^{-T}
     load_tile(B, X + i0, d.ldb, nb, nc);
     __syncthreads();
@@ -248,6 +262,46 @@ __global__ void __launch_bounds__(NT) k_copy(const CopyTile* __restrict__ tiles,
     const int rr = t.r0 + tx, cc = t.c0 + c;
     if (rr < d.rows && cc < d.cols) d.dst[rr + (size_t)cc * d.ldd] = s[tx][c];
   }
+}
+
+// ---------------------------------------------------------------- FP64 pivots of FP32 factors
+//
+// In the mixed forms the factor is stored in FP32, but the Cholesky of every
+// pivot block (eliminated separators, Sec. 2.4, and scaled interfaces,
+// Sec. 2.5) runs in FP64: the block is widened into an FP64 copy, factored
+// there by the FP64 tile kernels above, and its upper factor U and the
+// inverses of U's diagonal tiles are rounded back to FP32 for the FP32 tile
+// solves and GEMMs that follow.
+
+struct PivotCopy {
+  float* R;           // FP32 diagonal block (leading dimension ld)
+  double* W;          // FP64 copy, n x n, leading dimension n
+  float* dinv;        // FP32 inverses of the diagonal 64x64 tiles
+  const double* wdinv;  // their FP64 counterparts
+  int32_t n, ld;
+};
+
+// W <- (double) R (every entry of the n x n block).
+__global__ void k_widen_pivot(const PivotCopy* __restrict__ cps) {
+  const PivotCopy c = cps[blockIdx.y];
+  const int64_t tot = (int64_t)c.n * c.n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % c.n), j = (int)(e / c.n);
+    c.W[e] = (double)c.R[i + (size_t)j * c.ld];
+  }
+}
+
+// R's upper triangle <- (float) U; dinv <- (float) wdinv (ceil(n/64) tiles).
+__global__ void k_narrow_pivot(const PivotCopy* __restrict__ cps) {
+  const PivotCopy c = cps[blockIdx.y];
+  const int64_t tot = (int64_t)c.n * c.n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % c.n), j = (int)(e / c.n);
+    if (i <= j) c.R[i + (size_t)j * c.ld] = (float)c.W[e];
+  }
+  const int64_t nd = (int64_t)((c.n + TB - 1) / TB) * TB * TB;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nd; e += (int64_t)gridDim.x * blockDim.x)
+    c.dinv[e] = (float)c.wdinv[e];
 }
 
 // Diagonal block <- identity (after scaling, Sec. 2.5: S_p A S_p^T has I on p).

@@ -175,8 +175,9 @@ __global__ void __launch_bounds__(TC_NT, 4) k_schur_tc(const SchurTile* __restri
       ++it;
       if (!more) break;
     }
-    // the last commit completes after every earlier MMA
-    if (ok && !tc_wait(tc_smem_addr(&bar[(it - 1) & 1]), (unsigned)((it - 1) >> 1) & 1u)) ok = false;
+    // the last commit completes after every earlier MMA; on a give-up too the
+    // MMAs already issued must finish (bounded wait) before TMEM is freed
+    if (it > 0 && !tc_wait(tc_smem_addr(&bar[(it - 1) & 1]), (unsigned)((it - 1) >> 1) & 1u)) ok = false;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   }
   if (__syncthreads_or(!ok)) {

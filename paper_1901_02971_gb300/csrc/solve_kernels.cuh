@@ -226,13 +226,13 @@ __device__ __forceinline__ void grid_arrive(unsigned* count) {
   }
 }
 
-__device__ __forceinline__ bool grid_wait(const unsigned* count, unsigned target, int* err) {
+__device__ __forceinline__ bool grid_wait(const unsigned* count, unsigned target, int* err, unsigned limit) {
   __shared__ int ok;
   if (threadIdx.x == 0) {
     ok = 1;
     unsigned spins = 0;
     while (ld_acquire_u32(count) < target) {
-      if (++spins > kBarrierSpins) {
+      if (++spins > limit) {
         atomicExch(err, 1);
         ok = 0;
         break;
@@ -291,9 +291,13 @@ __device__ __forceinline__ void prefetch_first_item(const ApplyPhase<TF>& P) {
   (void)rows;
 }
 
+// spin_limit bounds every barrier wait (kBarrierSpins by default); bias is
+// added to every barrier target (0 in normal use; a failure-path test sets 1,
+// a target no arrival count reaches, so that every wait runs out).
 template <typename TF>
 __global__ void __launch_bounds__(AT) k_apply(const ApplyPhase<TF>* __restrict__ phases, int nph, double* x,
-                                              double* tmp, double* save, unsigned* bar, int* err) {
+                                              double* tmp, double* save, unsigned* bar, int* err,
+                                              unsigned spin_limit, unsigned bias) {
   typedef TF ACC;  // inner sums in the factor's precision
   extern __shared__ __align__(16) unsigned char apply_smem[];
   ACC* vs = reinterpret_cast<ACC*>(apply_smem);
@@ -393,7 +397,7 @@ __global__ void __launch_bounds__(AT) k_apply(const ApplyPhase<TF>* __restrict__
     if (p + 1 < nph) {
       grid_arrive(bar);
       prefetch_first_item(ptab[p + 1]);
-      if (!grid_wait(bar, (unsigned)(p + 1) * gridDim.x, err)) return;
+      if (!grid_wait(bar, (unsigned)(p + 1) * gridDim.x + bias, err, spin_limit)) return;
     }
   }
 }

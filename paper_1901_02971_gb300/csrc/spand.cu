@@ -3,6 +3,7 @@
 #include "spand.h"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -369,6 +370,11 @@ struct spand_handle_s {
   // step-1 assembly: original nnz e -> (cluster row, offset in that row)
   std::vector<int32_t> asm_row;
   std::vector<int64_t> asm_off;
+  // envelope of the step-1 pivot blocks (pieces of A itself; other pivots
+  // are dense): per initial cluster, U's tile bandwidth (0 = dense), the
+  // Cholesky flops sum_j r_j^2 over U's row lengths r_j, and nnz(U)
+  std::vector<int32_t> env_bw;
+  std::vector<double> env_flops, env_nnz;
   // A in the cluster order (for the SpMV of PCG)
   std::vector<int64_t> prow;
   std::vector<int32_t> pcol;
@@ -381,6 +387,7 @@ struct spand_handle_s {
   DevBuf scratch[2];
   DevBuf d_vals, d_asm_row, d_asm_off, d_prow, d_pcol, d_pval, d_pval_src, d_perm;
   DevBuf d_vec, d_tmp, d_save, d_bin, d_bout;
+  DevBuf d_piv64;  // FP64 copies of the pivot blocks of FP32 factors (scratch)
   DevBuf d_rowptr, d_colind;  // original CSR pattern (gradient on A's pattern)
   int fprec = -1;
   bool factored = false;
@@ -402,6 +409,8 @@ struct spand_handle_s {
   int apply_grid = 0;
   size_t apply_smem = 0;
   DevBuf d_bar;  // [0] grid-barrier arrival counter, [1] barrier-timeout flag
+  unsigned apply_spin_limit = kBarrierSpins;  // polls per grid-barrier wait of the apply
+  unsigned apply_bias = 0;                    // 1: failure-path test, no barrier completes
   ~spand_handle_s() {
     for (auto& a : aux)
       if (a) cudaStreamDestroy(a);
@@ -507,7 +516,8 @@ static X* at(void* base, size_t off) { return reinterpret_cast<X*>((char*)base +
 
 // Tiled upper Cholesky of a batch of diagonal blocks (right-looking over 64x64 tiles).
 template <typename T>
-static void potrf_batch(spand_handle h, const std::vector<RowDesc<T>>& rows, int* d_info, cudaStream_t s) {
+static void potrf_batch(spand_handle h, const std::vector<RowDesc<T>>& rows, int* d_info, cudaStream_t s,
+                        const std::vector<double>* row_flops = nullptr) {
   if (rows.empty()) return;
   Packer pk;
   size_t o = pk.add(rows);
@@ -521,8 +531,9 @@ static void potrf_batch(spand_handle h, const std::vector<RowDesc<T>>& rows, int
   ensure_smem((const void*)k_potrf_trsm<T>, sm2);
   const int nb = (int)rows.size();
   double fl = 0, by = 0;
-  for (auto& r : rows) {
-    fl += (double)r.n * r.n * r.n / 3;
+  for (size_t i = 0; i < rows.size(); ++i) {
+    const RowDesc<T>& r = rows[i];
+    fl += row_flops ? (*row_flops)[i] : (double)r.n * r.n * r.n / 3;
     by += 2.0 * r.n * r.n * sizeof(T);
   }
   const int pid = h->prof.begin(F_POTRF, s);
@@ -543,8 +554,57 @@ static void potrf_batch(spand_handle h, const std::vector<RowDesc<T>>& rows, int
   h->prof.end(pid, s, fl, by, nl);
 }
 
+// Cholesky of a batch of pivot blocks in FP64 (Sec. 2.4, 2.5).  FP64 factors
+// are factored in place; FP32 factors (the mixed forms) are widened into an
+// FP64 scratch copy, factored there, and U and the inverses of its diagonal
+// tiles are rounded back to FP32 for the FP32 solves and GEMMs.
 template <typename T>
-static void trsm_batch(spand_handle h, const std::vector<TrsmTask<T>>& tasks, cudaStream_t s) {
+static void pivot_chol(spand_handle h, const std::vector<RowDesc<T>>& rows, int* d_info, cudaStream_t s,
+                       const std::vector<double>* row_flops = nullptr) {
+  if constexpr (std::is_same<T, double>::value) {
+    potrf_batch<double>(h, rows, d_info, s, row_flops);
+  } else {
+    if (rows.empty()) return;
+    size_t tot = 0;
+    for (auto& r : rows) tot += ((size_t)r.n * r.n + 31) / 32 * 32 + (size_t)((r.n + TB - 1) / TB) * TB * TB;
+    double* base = (double*)h->d_piv64.ensure(tot * sizeof(double));
+    std::vector<RowDesc<double>> r64;
+    std::vector<PivotCopy> cps;
+    r64.reserve(rows.size());
+    cps.reserve(rows.size());
+    size_t o = 0;
+    for (auto& r : rows) {
+      double* W = base + o;
+      o += ((size_t)r.n * r.n + 31) / 32 * 32;
+      double* D = base + o;
+      o += (size_t)((r.n + TB - 1) / TB) * TB * TB;
+      r64.push_back({W, r.n, r.n, D, r.bw, 0});
+      cps.push_back({r.R, W, r.dinv, D, r.n, r.ld});
+    }
+    Packer pk;
+    const size_t oc = pk.add(cps);
+    void* d = upload<T>(h, pk, s);
+    const PivotCopy* dc = at<const PivotCopy>(d, oc);
+    const size_t nb = cps.size();
+    for (size_t b0 = 0; b0 < nb; b0 += 65535) {
+      const unsigned cnt = (unsigned)std::min<size_t>(nb - b0, 65535);
+      k_widen_pivot<<<dim3(8, cnt), 256, 0, s>>>(dc + b0);
+      CKLAUNCH();
+      ++h->prof.launches;
+    }
+    potrf_batch<double>(h, r64, d_info, s, row_flops);
+    for (size_t b0 = 0; b0 < nb; b0 += 65535) {
+      const unsigned cnt = (unsigned)std::min<size_t>(nb - b0, 65535);
+      k_narrow_pivot<<<dim3(8, cnt), 256, 0, s>>>(dc + b0);
+      CKLAUNCH();
+      ++h->prof.launches;
+    }
+  }
+}
+
+template <typename T>
+static void trsm_batch(spand_handle h, const std::vector<TrsmTask<T>>& tasks, cudaStream_t s,
+                       const std::vector<double>* task_flops = nullptr) {
   if (tasks.empty()) return;
   Packer pk;
   size_t o = pk.add(tasks);
@@ -552,9 +612,10 @@ static void trsm_batch(spand_handle h, const std::vector<TrsmTask<T>>& tasks, cu
   const size_t sm = 2 * sizeof(SqTile<T>) + sizeof(TileSmem<T>);
   ensure_smem((const void*)k_trsm_cols<T>, sm);
   double fl = 0, by = 0;
-  for (auto& t : tasks) {
+  for (size_t i = 0; i < tasks.size(); ++i) {
+    const TrsmTask<T>& t = tasks[i];
     const double nn = t.n - (t.i_start / TB) * TB;
-    fl += nn * nn * t.nc;
+    fl += task_flops ? (*task_flops)[i] : nn * nn * t.nc;
     by += (nn * nn / 2 + 2.0 * nn * t.nc) * sizeof(T);
   }
   const int pid = h->prof.begin(F_TRSM, s);
@@ -565,9 +626,13 @@ static void trsm_batch(spand_handle h, const std::vector<TrsmTask<T>>& tasks, cu
 }
 
 // Panels of at most 64 columns [c0, c1) of a block row: B <- U^{-T} B.
+// fl (optional): receives each task's algorithmic flops, 2 nnz(U) per column
+// (nnzU: nonzeros of U's upper triangle, n (n + 1) / 2 when dense).
 template <typename T>
-static void add_panels(std::vector<TrsmTask<T>>& out, T* R, const T* dinv, int n, int ld, int c0, int c1) {
+static void add_panels(std::vector<TrsmTask<T>>& out, T* R, const T* dinv, int n, int ld, int c0, int c1,
+                       int bw = 0, std::vector<double>* fl = nullptr, double nnzU = -1) {
   if (n <= 0) return;
+  if (nnzU < 0) nnzU = (double)n * (n + 1) / 2;
   for (int c = c0; c < c1; c += TB) {
     TrsmTask<T> t;
     t.U = R;
@@ -578,14 +643,16 @@ static void add_panels(std::vector<TrsmTask<T>>& out, T* R, const T* dinv, int n
     t.ldb = ld;
     t.nc = std::min(c + TB, c1) - c;
     t.i_start = 0;
-    t.pad = 0;
+    t.bw = bw;
     out.push_back(t);
+    if (fl) fl->push_back(2.0 * nnzU * t.nc);
   }
 }
 
 // Y = U^{-T} (lower): the same solve on identity panels (Y must hold I).
 template <typename T>
-static void add_inverse(std::vector<TrsmTask<T>>& out, const T* U, const T* dinv, int n, int ldu, T* Y) {
+static void add_inverse(std::vector<TrsmTask<T>>& out, const T* U, const T* dinv, int n, int ldu, T* Y,
+                        int bw = 0, std::vector<double>* fl = nullptr) {
   for (int c = 0; c < n; c += TB) {
     TrsmTask<T> t;
     t.U = U;
@@ -596,8 +663,12 @@ static void add_inverse(std::vector<TrsmTask<T>>& out, const T* U, const T* dinv
     t.ldb = n;
     t.nc = std::min(c + TB, n) - c;
     t.i_start = c;
-    t.pad = 0;
+    t.bw = bw;
     out.push_back(t);
+    if (fl) {  // rows [c, n) of a lower-triangular panel: ~ (n - c)^2 per column
+      const double nn = n - c;
+      fl->push_back(nn * nn * t.nc);
+    }
   }
 }
 
@@ -900,24 +971,32 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
     {
       std::vector<RowDesc<T>> diag, ident;
       std::vector<int> diag_cl;
+      std::vector<double> diag_fl, tr_fl;
       std::vector<TrsmTask<T>> tr_tasks;
       for (int sidx : seps) {
         if (sz[sidx] <= 0) continue;
+        const double ns = sz[sidx], m = lay.W[sidx] - sz[sidx];
+        // step 1: the pivot is a piece of A, with the envelope found at analysis
+        const bool env = t == 1 && !h->env_bw.empty();
+        const int bw = env ? h->env_bw[sidx] : 0;
+        const double cfl = env ? h->env_flops[sidx] : ns * ns * ns / 3;
+        const double nnzU = env ? h->env_nnz[sidx] : ns * (ns + 1) / 2;
         T* dv = alloc_dinv<T>(h, sz[sidx]);
-        diag.push_back({lay.row[sidx], sz[sidx], lay.ld[sidx], dv});
+        diag.push_back({lay.row[sidx], sz[sidx], lay.ld[sidx], dv, bw, 0});
         diag_cl.push_back(sidx);
-        add_panels(tr_tasks, lay.row[sidx], (const T*)dv, sz[sidx], lay.ld[sidx], sz[sidx], lay.W[sidx]);
+        diag_fl.push_back(cfl);
+        add_panels(tr_tasks, lay.row[sidx], (const T*)dv, sz[sidx], lay.ld[sidx], sz[sidx], lay.W[sidx], bw, &tr_fl,
+                   nnzU);
         T* Y = (T*)h->persist.alloc((size_t)sz[sidx] * sz[sidx] * sizeof(T));
         ysep[sidx] = Y;
-        ident.push_back({Y, sz[sidx], sz[sidx], nullptr});
-        add_inverse(tr_tasks, (const T*)lay.row[sidx], (const T*)dv, sz[sidx], lay.ld[sidx], Y);
-        const double ns = sz[sidx], m = lay.W[sidx] - sz[sidx];
-        stt.factor_flops += ns * ns * ns / 3 + ns * ns * m + ns * m * m;
+        ident.push_back({Y, sz[sidx], sz[sidx], nullptr, 0, 0});
+        add_inverse(tr_tasks, (const T*)lay.row[sidx], (const T*)dv, sz[sidx], lay.ld[sidx], Y, bw, &tr_fl);
+        stt.factor_flops += cfl + 2 * nnzU * m + ns * m * m;
       }
       set_identity<T>(h, ident, s);
-      potrf_batch<T>(h, diag, d_info + 2 * t, s);
+      pivot_chol<T>(h, diag, d_info + 2 * t, s, &diag_fl);
       elim_cls[t] = diag_cl;
-      trsm_batch<T>(h, tr_tasks, s);
+      trsm_batch<T>(h, tr_tasks, s, &tr_fl);
       // pull-form Schur update of every pair of neighbours
       std::vector<SchurBlock<T>> blocks;
       std::vector<std::vector<SchurContrib<T>>> contr;
@@ -1151,7 +1230,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         sm_np = std::max(sm_np, (size_t)sz[p] * sizeof(double));
       }
       set_identity<T>(h, ident, s);
-      potrf_batch<T>(h, diag, d_info + 2 * t + 1, s);
+      pivot_chol<T>(h, diag, d_info + 2 * t + 1, s);
       scale_cls[t] = diag_cl;
       trsm_batch<T>(h, up, s);   // upper blocks U_p^{-T} A_pq and the inverses Y_p
       copy_batch<T>(h, m_up, s);
@@ -1714,7 +1793,9 @@ static void apply_prec(spand_handle h, double* x, double* tmp, double* save, cud
   CK(cudaMemsetAsync(bar, 0, sizeof(unsigned), s));
   const ApplyPhase<TF>* ph = (const ApplyPhase<TF>*)h->aprog;
   int nph = h->n_aprog;
-  void* args[] = {(void*)&ph, (void*)&nph, (void*)&x, (void*)&tmp, (void*)&save, (void*)&bar, (void*)&err};
+  unsigned lim = h->apply_spin_limit, bias = h->apply_bias;
+  void* args[] = {(void*)&ph, (void*)&nph, (void*)&x,   (void*)&tmp, (void*)&save,
+                  (void*)&bar, (void*)&err, (void*)&lim, (void*)&bias};
   CK(cudaLaunchCooperativeKernel((const void*)k_apply<TF>, dim3((unsigned)h->apply_grid), dim3(AT), args,
                                  h->apply_smem, s));
   CKLAUNCH();
@@ -1890,6 +1971,50 @@ int spand_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const
         h->asm_off[e] = loc[v] + (int64_t)(col + loc[w]) * ld;
       }
   }
+  // Envelope of every step-1 pivot block (the rows of A within one cluster
+  // eliminated first, in cluster order): f(i) = the first row holding a
+  // nonzero of column i.  U keeps that envelope, so tiles further than
+  // bw = max_i (i/64 - f(i)/64) above the diagonal stay zero; the row lengths
+  // r_j = #{i >= j : f(i) <= j} of U give the Cholesky flops sum_j r_j^2.
+  h->env_bw.assign(nc, 0);
+  h->env_flops.assign(nc, 0.0);
+  h->env_nnz.assign(nc, 0.0);
+  if (n > 0) {
+    std::vector<int32_t> f;
+    std::vector<int64_t> cnt;
+    for (int c = 0; c < nc; ++c) {
+      if (!s1.elim[c]) continue;
+      const int32_t b = tr.cluster_ptr[c], sz = tr.cluster_ptr[c + 1] - b;
+      f.resize(sz);
+      for (int32_t i = 0; i < sz; ++i) {
+        const int32_t v = tr.perm[b + i];
+        int32_t fi = i;
+        for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+          const int32_t w = colind[e];
+          if (cl[w] == c && loc[w] < fi) fi = loc[w];
+        }
+        f[i] = fi;
+      }
+      int32_t bw = 0;
+      double nnzU = 0;
+      cnt.assign((size_t)sz + 1, 0);
+      for (int32_t i = 0; i < sz; ++i) {
+        bw = std::max(bw, i / 64 - f[i] / 64);
+        nnzU += i - f[i] + 1;
+        ++cnt[f[i]];  // column i covers rows f(i) .. i
+        --cnt[i + 1];
+      }
+      double fl = 0, r = 0;
+      for (int32_t j = 0; j < sz; ++j) {
+        r += (double)cnt[j];
+        fl += r * r;
+      }
+      const int32_t ntile = (sz + 63) / 64;
+      h->env_bw[c] = (bw + 1 >= ntile) ? 0 : bw;  // 0: dense (no tile is structurally zero)
+      h->env_flops[c] = fl;
+      h->env_nnz[c] = nnzU;
+    }
+  }
   // A in cluster order
   h->prow.assign(n + 1, 0);
   h->pcol.resize(nnz);
@@ -1979,7 +2104,8 @@ int spand_factorize(spand_handle h, const double* vals, void* cuda_stream) {
   h->fprec = h->opts.precision;
   CK(cudaStreamSynchronize(s));
   h->st.t_factor_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  h->st.device_bytes = (int64_t)(h->persist.bytes_held + h->descs.bytes_held + h->scratch[0].cap + h->scratch[1].cap);
+  h->st.device_bytes = (int64_t)(h->persist.bytes_held + h->descs.bytes_held + h->scratch[0].cap + h->scratch[1].cap +
+                                   h->d_piv64.cap);
   const size_t esz = h->fprec == SPAND_FP64 ? 8 : 4;
   h->st.apply_bytes = 2.0 * (double)h->st.mem_f * esz;
   h->factored = rc == SPAND_OK;
@@ -2029,7 +2155,9 @@ namespace spand {
 constexpr int64_t kNoAllocMaxDoubles = int64_t(1) << 21;
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxDoubles];
 constexpr int kNoAllocMaxDevices = 64;
-static double* g_noalloc_addr[kNoAllocMaxDevices] = {};  // device address of the array, per device
+// device address of the array, per device (looked up once; threads that race
+// on the first call store the same value)
+static std::atomic<double*> g_noalloc_addr[kNoAllocMaxDevices];
 }  // namespace spand
 
 extern "C" {
@@ -2049,13 +2177,15 @@ int spand_apply_noalloc(spand_handle h, const double* r_dev, double* z_dev, void
   if (n == 0) return SPAND_OK;
   int dev = 0;
   CK(cudaGetDevice(&dev));
+  if (dev != h->device)
+    throw Fail{SPAND_ERR_INVALID_ARG, "spand_apply_noalloc: the current device is not the one the handle was "
+                                      "factorized on"};
   if (dev < 0 || dev >= kNoAllocMaxDevices) throw Fail{SPAND_ERR_INVALID_ARG, "device ordinal out of range"};
-  if (!g_noalloc_addr[dev]) {  // once per device, with that device current
-    double* p = nullptr;
-    CK(cudaGetSymbolAddress((void**)&p, g_noalloc_scratch));
-    g_noalloc_addr[dev] = p;
+  double* w = g_noalloc_addr[dev].load(std::memory_order_acquire);
+  if (!w) {  // once per device, with that device current
+    CK(cudaGetSymbolAddress((void**)&w, g_noalloc_scratch));
+    g_noalloc_addr[dev].store(w, std::memory_order_release);
   }
-  double* w = g_noalloc_addr[dev];
   double* tmp = w + n;
   double* save = tmp + h->tmp_len;
   cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -2235,6 +2365,13 @@ int spand_solve(spand_handle h, const double* b, double* x, int32_t* iters, doub
   API_END
 }
 
+int spand_set_apply_wait(spand_handle h, uint32_t polls, int32_t unreachable) {
+  if (!h) { g_err = "null handle"; return SPAND_ERR_INVALID_ARG; }
+  h->apply_spin_limit = polls ? polls : kBarrierSpins;
+  h->apply_bias = unreachable ? 1u : 0u;
+  return SPAND_OK;
+}
+
 int spand_set_profiling(spand_handle h, int32_t on) {
   if (!h) { g_err = "null handle"; return SPAND_ERR_INVALID_ARG; }
   h->prof.on = on != 0;
@@ -2271,6 +2408,7 @@ int spand_sketch_gaussian(uint64_t seed, int32_t step, int32_t cluster, int32_t 
     throw Fail{SPAND_ERR_INVALID_ARG, "step, cluster, m and ell must be >= 0"};
   if ((int64_t)m * ell == 0) return SPAND_OK;
   if (!out_dev) throw Fail{SPAND_ERR_INVALID_ARG, "out_dev is NULL"};
+  if (!is_device_ptr(out_dev)) throw Fail{SPAND_ERR_INVALID_ARG, "out_dev is not device memory"};
   const uint64_t k1 = ((uint64_t)(uint32_t)step << 32) + (uint64_t)(uint32_t)cluster;
   const int64_t blocks = ((int64_t)(m + 3) / 4 * ell + 255) / 256;
   k_sketch_philox<<<(unsigned)std::min<int64_t>(blocks, 8192), 256, 0, (cudaStream_t)cuda_stream>>>(seed, k1, m, ell,

@@ -178,5 +178,19 @@ def test_sketch_argument_checks(spand_lib):
     assert f(1, -1, 0, 4, 4, None, None) == L.SPAND_ERR_INVALID_ARG
     assert f(1, 0, -1, 4, 4, None, None) == L.SPAND_ERR_INVALID_ARG
     assert f(1, 0, 0, 4, 4, None, None) == L.SPAND_ERR_INVALID_ARG   # null output
+    host = np.zeros(16)
+    assert f(1, 0, 0, 4, 4, host.ctypes.data, None) == L.SPAND_ERR_INVALID_ARG  # not device memory
     assert f(1, 0, 0, 0, 4, None, None) == L.SPAND_OK                # empty: nothing to do
     assert f(1, 0, 0, 4, 0, None, None) == L.SPAND_OK
+
+
+def test_apply_wait_knob_argument_checks(spand_lib):
+    """The failure-path knob of the apply is a host-side setting."""
+    assert spand_lib.spand_set_apply_wait(None, 16, 1) == L.SPAND_ERR_INVALID_ARG
+    p = I.laplacian_2d(8)
+    h = L.spand_analyze(p.rowptr, p.colind, p.vals, p.coords, L.default_opts(levels=3))
+    try:
+        L.spand_set_apply_wait(h, 16, True)
+        L.spand_set_apply_wait(h, 0, False)
+    finally:
+        L.spand_destroy(h)

@@ -59,7 +59,8 @@ def test_max_over_ranks_without_group():
 def test_reference_arm_under_torchrun_prints_once():
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
-           os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0"]
+           os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2", "--steps", "2", "--warmup", "1",
+           "--grid", "12", "--levels", "5"]
     r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600,
                        env={**os.environ, "OMP_NUM_THREADS": "1"})
     assert r.returncode == 0, r.stderr[-2000:]
@@ -68,7 +69,11 @@ def test_reference_arm_under_torchrun_prints_once():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["higher_is_better"] is False
     assert d["value"] > 0 and d["e2e"]["value"] == d["value"]
-    assert d["cpu_baseline"]["kind"] == "oracle"
-    ph = d["cpu_baseline"]["sample_phases"]
-    assert set(ph) == {"t_p_s", "t_f_s", "t_s_s", "n_cg"} and ph["n_cg"] >= 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    ph = d["cpu_baseline"]["phases"]
+    assert {"t_p_s", "t_f_s", "t_s_s", "n_cg"} <= set(ph) and ph["n_cg"] >= 1
     assert min(ph["t_p_s"], ph["t_f_s"], ph["t_s_s"]) > 0
+    # every step is a full run of the workload; the line states how many ran
+    assert d["steps"] == len(d["cpu_baseline"]["step_times_s"]) == 2 and d["warmup"] == 0
+    assert d["steps_requested"] == 2 and d["warmup_requested"] == 1
+    assert d["config"]["N"] == 12 ** 3 and d["config"]["levels"] == 5

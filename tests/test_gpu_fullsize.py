@@ -7,7 +7,10 @@ which calls only the oracle).
 Checked at full size: PCG iterations within +10% of the oracle's, the true
 residual recomputed here on the host, x on 256 sampled positions and ||x||
 within a relative 1e-8, size_Top and the per-step size totals after
-sparsification within 2% (pivot near-ties may move a rank by one).
+sparsification within 2% (pivot near-ties may move a rank by one).  Every
+form (FP64, and the FP32 / TF32 / BF16 factors with FP64 pivots and PCG) is
+also compared on the whole of x with a full oracle run on the same workload,
+made in a spawned process (no CUDA state is shared with it).
 """
 import json
 import math
@@ -33,7 +36,48 @@ def problem():
     return p, b, g
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def _oracle_full_x():
+    """x of the FP64 oracle on the benchmark workload (runs in a child process)."""
+    import os
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    from oracle import spand_oracle as O
+    p = I.laplacian_3d(64)
+    res = O.solve(p, I.rhs(p.n, 1), 10, 1e-2)
+    return res.x, res.iters
+
+
+@pytest.fixture(scope="module")
+def oracle_x():
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(1) as pool:
+        return pool.apply(_oracle_full_x)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tf32", "bf16"])
+def test_benchmark_workload_full_x(cuda_ok, problem, oracle_x, precision):
+    """The whole solution vector of every form against the oracle's."""
+    import torch
+    p, b, g = problem
+    x_ref, it_ref = oracle_x
+    assert it_ref == g["iters"]
+    s = Solver.from_problem(p, levels=10, eps=1e-2, precision=precision)
+    try:
+        s.factorize(torch.from_numpy(p.vals).cuda())
+        xd, it, rr = s.solve(torch.from_numpy(b).cuda())
+        x = xd.cpu().numpy()
+        assert rr <= 1e-10
+        err = np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref)
+        assert err <= 1e-8, err
+        assert np.abs(x - x_ref).max() <= 1e-8 * np.abs(x_ref).max()
+        if precision == "fp64":
+            assert it <= math.ceil(1.1 * it_ref), (it, it_ref)
+        else:  # the lower-precision factor may only cost iterations
+            assert it <= it_ref + 3, (it, it_ref)
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tf32"])
 def test_benchmark_workload_matches_oracle(cuda_ok, problem, precision):
     import torch
     p, b, g = problem
