@@ -85,6 +85,18 @@ enum {
                              differs from the coloured order at O(eps) */
 };
 
+/* how each interface is compressed (Sec. 2.6) */
+enum {
+  SPAND_CPQR = 0,       /* column-pivoted QR of A_pn truncated at eps (Sec. 2.6.1, rule of Sec. 4) */
+  SPAND_RANDOMIZED = 1  /* randomized range finder (the randomized alternative of Sec. 2.6.2 and
+                           Sec. 5; Halko, Martinsson and Tropp 2011, Algorithm 4.2): Gaussian
+                           sketch Y = A_pn Omega (Philox4x64-10 counter, keyed by sketch_seed, the
+                           step and the cluster; 32 columns, doubled while the rank comes within
+                           10 of them), column-pivoted QR of Y for the basis, rank = the first k
+                           whose largest column of the remainder of A_pn falls below eps times its
+                           largest column; coloured order only */
+};
+
 typedef struct spand_handle_s* spand_handle;
 
 typedef struct {
@@ -96,10 +108,12 @@ typedef struct {
   int32_t maxit;      /* PCG iteration cap (paper: 500) */
   double tol;         /* PCG relative residual target (paper: 1e-12) */
   int32_t sparsify_order; /* SPAND_COLOURED or SPAND_SIMULTANEOUS */
+  int32_t compression;    /* SPAND_CPQR or SPAND_RANDOMIZED */
+  uint64_t sketch_seed;   /* seed of the Gaussian sketches (SPAND_RANDOMIZED) */
 } spand_opts;
 
 /* Fills *opts with levels 8, eps 1e-2, skip 0, FP64, maxit 500, tol 1e-10,
- * coloured sparsification order. */
+ * coloured sparsification order, column-pivoted QR compression, sketch seed 0. */
 void spand_default_opts(spand_opts* opts);
 
 /*
@@ -273,6 +287,10 @@ typedef struct {
   int32_t fail_step;      /* NOT_SPD: elimination step (1-based), else 0 */
   int32_t fail_cluster;   /* NOT_SPD: cluster index in that step, else -1 */
   int64_t device_bytes;   /* device memory held by the handle */
+  int32_t apply_ctas_per_sm; /* shape of the preconditioner apply's cooperative
+                                launch (CTAs per SM), chosen by the autotuner
+                                at the first apply or set by
+                                spand_set_apply_shape; 0 before the first apply */
 } spand_stats;
 
 int spand_get_stats(spand_handle h, spand_stats* st);
@@ -305,6 +323,17 @@ int spand_get_kernel_profile(spand_handle h, int32_t family, double* out4);
 int spand_reset_kernel_profile(spand_handle h);
 /* Kernels launched by this handle since it was created (always counted). */
 int spand_get_launch_count(spand_handle h, int64_t* launches);
+
+/*
+ * spand_set_apply_shape -- launch shape of the preconditioner apply (one
+ * cooperative kernel for z = M M^T r): ctas_per_sm in 1..4 fixes the number
+ * of CTAs per SM (capped by the kernel's occupancy); 0 (the default) lets the
+ * library's autotuner choose at the first apply or solve after the handle's
+ * first factorization, by timing every candidate on a scratch vector, and
+ * keep that choice for the handle.  The shape never changes the result:
+ * every item of an apply phase is computed by one CTA in a fixed order.
+ */
+int spand_set_apply_shape(spand_handle h, int32_t ctas_per_sm);
 
 /*
  * spand_set_apply_wait -- failure-path knob (not part of the method).  The

@@ -31,13 +31,16 @@ SPAND_TF32 = 2
 SPAND_BF16 = 3
 SPAND_COLOURED = 0
 SPAND_SIMULTANEOUS = 1
+SPAND_CPQR = 0
+SPAND_RANDOMIZED = 1
 
 # every function declared in include/spand.h
 EXPORTS = ["spand_default_opts", "spand_analyze", "spand_analyze_batch", "spand_factorize", "spand_solve", "spand_apply",
            "spand_apply_noalloc", "spand_sampled_outer", "spand_sketch_gaussian",
            "spand_get_tree", "spand_get_step", "spand_get_ranks", "spand_get_stats",
            "spand_get_phase_times", "spand_set_profiling", "spand_get_kernel_profile",
-           "spand_reset_kernel_profile", "spand_get_launch_count", "spand_set_apply_wait", "spand_destroy",
+           "spand_reset_kernel_profile", "spand_get_launch_count", "spand_set_apply_wait", "spand_set_apply_shape",
+           "spand_destroy",
            "spand_error_string",
            "spand_last_error"]
 KERNEL_FAMILIES = ["potrf", "trsm", "schur", "cpqr", "copy", "apply", "pcg"]
@@ -46,7 +49,7 @@ KERNEL_FAMILIES = ["potrf", "trsm", "schur", "cpqr", "copy", "apply", "pcg"]
 class Opts(C.Structure):
     _fields_ = [("levels", C.c_int32), ("eps", C.c_double), ("skip", C.c_int32),
                 ("precision", C.c_int32), ("maxit", C.c_int32), ("tol", C.c_double),
-                ("sparsify_order", C.c_int32)]
+                ("sparsify_order", C.c_int32), ("compression", C.c_int32), ("sketch_seed", C.c_uint64)]
 
 
 class Problem(C.Structure):
@@ -58,7 +61,8 @@ class Stats(C.Structure):
     _fields_ = [("t_analyze_s", C.c_double), ("t_factor_s", C.c_double), ("t_solve_s", C.c_double),
                 ("n_cg", C.c_int32), ("relres", C.c_double), ("size_top", C.c_int64),
                 ("mem_f", C.c_int64), ("factor_flops", C.c_double), ("apply_bytes", C.c_double),
-                ("fail_step", C.c_int32), ("fail_cluster", C.c_int32), ("device_bytes", C.c_int64)]
+                ("fail_step", C.c_int32), ("fail_cluster", C.c_int32), ("device_bytes", C.c_int64),
+                ("apply_ctas_per_sm", C.c_int32)]
 
 
 class SpandError(RuntimeError):
@@ -100,6 +104,7 @@ def lib():
     L.spand_reset_kernel_profile.argtypes = [C.c_void_p]
     L.spand_get_launch_count.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
     L.spand_set_apply_wait.argtypes = [C.c_void_p, C.c_uint32, C.c_int32]
+    L.spand_set_apply_shape.argtypes = [C.c_void_p, C.c_int32]
     L.spand_destroy.argtypes = [C.c_void_p]
     L.spand_destroy.restype = None
     L.spand_error_string.argtypes = [C.c_int]
@@ -288,6 +293,11 @@ def spand_set_apply_wait(h: int, polls: int = 0, unreachable: bool = False):
     """Failure-path knob: bound the apply's grid-barrier waits by `polls`
     polls (0 = default); `unreachable` makes every wait run out."""
     _check(lib().spand_set_apply_wait(h, polls, 1 if unreachable else 0))
+
+
+def spand_set_apply_shape(h: int, ctas_per_sm: int = 0):
+    """CTAs per SM of the preconditioner apply (1..4), or 0: autotuned."""
+    _check(lib().spand_set_apply_shape(h, ctas_per_sm))
 
 
 def spand_destroy(h: int):

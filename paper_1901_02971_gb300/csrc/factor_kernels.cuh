@@ -23,7 +23,8 @@ struct RowDesc {      // a cluster's block row or its diagonal block
   int32_t n;          // rows (cluster size)
   int32_t ld;
   T* dinv;            // ceil(n/64) tiles of 64x64: inverses U_kk^{-T} of the diagonal tiles
-  int32_t bw, pad;    // tile bandwidth of U (0 = dense)
+  int32_t bw;         // tile bandwidth of U in 64-tiles (0 = dense)
+  int32_t bw2;        // the same in 32-tiles (FP64 pivot factorization)
 };
 
 template <typename T>
@@ -47,6 +48,7 @@ struct SchurContrib { // one eliminated separator s adjacent to both a and b
   const T* Xa;        // X^T columns of a inside s's row: Xa[k + i*lds], k < ns
   const T* Xb;
   int32_t lds, ns;
+  int32_t owner, pad; // s (index in the step's cluster list; host bookkeeping)
 };
 
 struct SchurTile {
@@ -78,18 +80,24 @@ __global__ void k_assemble(const double* __restrict__ vals, const int32_t* __res
 
 // ---------------------------------------------------------------- tiled Cholesky
 
+// Tiled upper Cholesky of a batch of pivot blocks, B x B tiles (B = 64, or
+// 32 for the FP64 pivots, whose per-SM rate makes the dependent chain of
+// diagonal-tile factor -> tile solve -> trailing tile update the cost: a
+// smaller tile shortens every link of that chain).  dinv holds ceil(n/B)
+// tiles of B x B (the inverses U_kk^{-T} of phase 1); bw counts B-tiles.
+
 // Tile step k, phase 1: factor diagonal tile (k, k) of every block and store
-// the inverse of its factor, U_kk^{-T}, for the tile solves of phase 2 and of
-// k_trsm_cols.
-template <typename T>
-__global__ void __launch_bounds__(NT) k_potrf_diag(const RowDesc<T>* __restrict__ rows, int k, int* info) {
+// the inverse of its factor, U_kk^{-T}, for the tile solves of phase 2.
+template <typename T, int B = TB>
+__global__ void __launch_bounds__(TileGeom<B>::NTH) k_potrf_diag(const RowDesc<T>* __restrict__ rows, int k,
+                                                                 int* info) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  SqTile<T>& s = *reinterpret_cast<SqTile<T>*>(smraw);
-  SqTile<T>& Id = *reinterpret_cast<SqTile<T>*>(smraw + sizeof(SqTile<T>));
+  SqTileB<T, B>& s = *reinterpret_cast<SqTileB<T, B>*>(smraw);
+  SqTileB<T, B>& Id = *reinterpret_cast<SqTileB<T, B>*>(smraw + sizeof(SqTileB<T, B>));
   const RowDesc<T> d = rows[blockIdx.x];
-  const int k0 = k * TB;
+  const int k0 = k * B;
   if (k0 >= d.n) return;
-  const int nb = min(TB, d.n - k0);
+  const int nb = min(B, d.n - k0);
   T* P = d.R + k0 + (size_t)k0 * d.ld;
   load_tile(s, P, d.ld, nb, nb);
   __syncthreads();
@@ -98,33 +106,33 @@ __global__ void __launch_bounds__(NT) k_potrf_diag(const RowDesc<T>* __restrict_
     return;
   }
   store_tile(s, P, d.ld, nb, nb);
-  store_tile(Id, d.dinv + (size_t)k * TB * TB, TB, TB, TB);
+  store_tile(Id, d.dinv + (size_t)k * B * B, B, B, B);
 }
 
 // Tile step k, phase 2: U_kj = U_kk^{-T} A_kj for the tiles j > k of the diagonal block.
-template <typename T>
-__global__ void __launch_bounds__(NT) k_potrf_trsm(const RowDesc<T>* __restrict__ rows, int k) {
+template <typename T, int B = TB>
+__global__ void __launch_bounds__(TileGeom<B>::NTH) k_potrf_trsm(const RowDesc<T>* __restrict__ rows, int k) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  SqTile<T>& D = *reinterpret_cast<SqTile<T>*>(smraw);
-  SqTile<T>& B = *reinterpret_cast<SqTile<T>*>(smraw + sizeof(SqTile<T>));
+  SqTileB<T, B>& D = *reinterpret_cast<SqTileB<T, B>*>(smraw);
+  SqTileB<T, B>& Bt = *reinterpret_cast<SqTileB<T, B>*>(smraw + sizeof(SqTileB<T, B>));
   const RowDesc<T> d = rows[blockIdx.y];
-  const int k0 = k * TB;
-  const int j0 = k0 + TB * (1 + blockIdx.x);
+  const int k0 = k * B;
+  const int j0 = k0 + B * (1 + blockIdx.x);
   if (j0 >= d.n || (d.bw > 0 && (int)blockIdx.x + 1 > d.bw)) return;  // past the end, or a zero tile
-  const int nb = min(TB, d.n - k0), nc = min(TB, d.n - j0);
-  load_tile(D, d.dinv + (size_t)k * TB * TB, TB, TB, TB);
-  load_tile(B, d.R + k0 + (size_t)j0 * d.ld, d.ld, nb, nc);
+  const int nb = min(B, d.n - k0), nc = min(B, d.n - j0);
+  load_tile(D, d.dinv + (size_t)k * B * B, B, B, B);
+  load_tile(Bt, d.R + k0 + (size_t)j0 * d.ld, d.ld, nb, nc);
   __syncthreads();
-  apply_inv_tile(D, B, nb);
-  store_tile(B, d.R + k0 + (size_t)j0 * d.ld, d.ld, nb, nc);
+  apply_inv_tile(D, Bt, nb);
+  store_tile(Bt, d.R + k0 + (size_t)j0 * d.ld, d.ld, nb, nc);
 }
 
 // Tile step k, phase 3: A_ij -= U_ki^T U_kj for k < i <= j (upper trailing tiles).
-template <typename T>
-__global__ void __launch_bounds__(NT) k_potrf_update(const RowDesc<T>* __restrict__ rows, int k) {
-  __shared__ TileSmem<T> sm;
+template <typename T, int B = TB>
+__global__ void __launch_bounds__(TileGeom<B>::NTH) k_potrf_update(const RowDesc<T>* __restrict__ rows, int k) {
+  __shared__ TileSmemB<T, B> sm;
   const RowDesc<T> d = rows[blockIdx.y];
-  const int nt = (d.n + TB - 1) / TB;
+  const int nt = (d.n + B - 1) / B;
   const int m = nt - k - 1;  // trailing tiles per side
   if (m <= 0) return;
   int lin = blockIdx.x;
@@ -134,15 +142,33 @@ __global__ void __launch_bounds__(NT) k_potrf_update(const RowDesc<T>* __restric
   while (lin >= m - i) { lin -= m - i; ++i; }
   const int j = i + lin;
   if (d.bw > 0 && j + 1 > d.bw) return;  // U_kj is a zero tile: nothing to subtract
-  const int i0 = (k + 1 + i) * TB, j0 = (k + 1 + j) * TB, k0 = k * TB;
-  const int mi = min(TB, d.n - i0), nj = min(TB, d.n - j0), kb = min(TB, d.n - k0);
+  const int i0 = (k + 1 + i) * B, j0 = (k + 1 + j) * B, k0 = k * B;
+  const int mi = min(B, d.n - i0), nj = min(B, d.n - j0), kb = min(B, d.n - k0);
   T acc[4][4];
   zero_acc(acc);
   if (i == j)  // diagonal tile: only its upper triangle is used
     tn_acc<T, true>(acc, d.R + k0 + (size_t)i0 * d.ld, d.ld, mi, d.R + k0 + (size_t)j0 * d.ld, d.ld, nj, kb, sm);
   else
     tn_acc<T, false>(acc, d.R + k0 + (size_t)i0 * d.ld, d.ld, mi, d.R + k0 + (size_t)j0 * d.ld, d.ld, nj, kb, sm);
-  sub_store(acc, d.R + i0 + (size_t)j0 * d.ld, d.ld, mi, nj);
+  sub_store<B>(acc, d.R + i0 + (size_t)j0 * d.ld, d.ld, mi, nj);
+}
+
+// The inverses U_kk^{-T} of the 64 x 64 diagonal tiles of a factored pivot
+// block (for the block-row solves of k_trsm_cols), tile k = blockIdx.x of
+// block blockIdx.y, from U itself.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_inv_diag(const RowDesc<T>* __restrict__ rows) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  SqTile<T>& U = *reinterpret_cast<SqTile<T>*>(smraw);
+  SqTile<T>& D = *reinterpret_cast<SqTile<T>*>(smraw + sizeof(SqTile<T>));
+  const RowDesc<T> d = rows[blockIdx.y];
+  const int k0 = blockIdx.x * TB;
+  if (k0 >= d.n) return;
+  const int nb = min(TB, d.n - k0);
+  load_tile(U, d.R + k0 + (size_t)k0 * d.ld, d.ld, nb, nb);
+  __syncthreads();
+  inv_tile(U, D, nb);
+  store_tile(D, d.dinv + (size_t)blockIdx.x * TB * TB, TB, TB, TB);
 }
 
 // B <- U^{-T} B for one panel of at most 64 columns, left-looking over the
@@ -276,8 +302,6 @@ __global__ void __launch_bounds__(NT) k_copy(const CopyTile* __restrict__ tiles,
 struct PivotCopy {
   float* R;           // FP32 diagonal block (leading dimension ld)
   double* W;          // FP64 copy, n x n, leading dimension n
-  float* dinv;        // FP32 inverses of the diagonal 64x64 tiles
-  const double* wdinv;  // their FP64 counterparts
   int32_t n, ld;
 };
 
@@ -291,7 +315,7 @@ __global__ void k_widen_pivot(const PivotCopy* __restrict__ cps) {
   }
 }
 
-// R's upper triangle <- (float) U; dinv <- (float) wdinv (ceil(n/64) tiles).
+// R's upper triangle <- (float) U.
 __global__ void k_narrow_pivot(const PivotCopy* __restrict__ cps) {
   const PivotCopy c = cps[blockIdx.y];
   const int64_t tot = (int64_t)c.n * c.n;
@@ -299,9 +323,6 @@ __global__ void k_narrow_pivot(const PivotCopy* __restrict__ cps) {
     const int i = (int)(e % c.n), j = (int)(e / c.n);
     if (i <= j) c.R[i + (size_t)j * c.ld] = (float)c.W[e];
   }
-  const int64_t nd = (int64_t)((c.n + TB - 1) / TB) * TB * TB;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nd; e += (int64_t)gridDim.x * blockDim.x)
-    c.dinv[e] = (float)c.wdinv[e];
 }
 
 // Diagonal block <- identity (after scaling, Sec. 2.5: S_p A S_p^T has I on p).

@@ -36,6 +36,20 @@ __device__ __forceinline__ void philox4x64_10(uint64_t x[4], uint64_t k0, uint64
   }
 }
 
+// The four Gaussian entries of rows 4b .. 4b + 3 of column j.
+__device__ __forceinline__ void philox_gauss4(uint64_t k0, uint64_t k1, uint64_t j, uint64_t b, double z[4]) {
+  uint64_t x[4] = {j, b, 0ull, 0ull};
+  philox4x64_10(x, k0, k1);
+  double u[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) u[k] = ((double)(x[k] >> 11) + 0.5) * 0x1.0p-53;
+  const double ra = sqrt(-2.0 * log(u[0])), rb = sqrt(-2.0 * log(u[2]));
+  z[0] = ra * cospi(2.0 * u[1]);
+  z[1] = ra * sinpi(2.0 * u[1]);
+  z[2] = rb * cospi(2.0 * u[3]);
+  z[3] = rb * sinpi(2.0 * u[3]);
+}
+
 // out: m x ell, column-major (leading dimension m); one thread per 4-row block
 // of one column (grid-stride).
 __global__ void k_sketch_philox(uint64_t k0, uint64_t k1, int m, int ell, double* __restrict__ out) {
@@ -43,13 +57,8 @@ __global__ void k_sketch_philox(uint64_t k0, uint64_t k1, int m, int ell, double
   const int64_t total = (int64_t)nb * ell;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int j = (int)(t / nb), b = (int)(t % nb);
-    uint64_t x[4] = {(uint64_t)j, (uint64_t)b, 0ull, 0ull};
-    philox4x64_10(x, k0, k1);
-    double u[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) u[k] = ((double)(x[k] >> 11) + 0.5) * 0x1.0p-53;
-    const double ra = sqrt(-2.0 * log(u[0])), rb = sqrt(-2.0 * log(u[2]));
-    const double z[4] = {ra * cospi(2.0 * u[1]), ra * sinpi(2.0 * u[1]), rb * cospi(2.0 * u[3]), rb * sinpi(2.0 * u[3])};
+    double z[4];
+    philox_gauss4(k0, k1, (uint64_t)j, (uint64_t)b, z);
     double* col = out + (size_t)j * m;
 #pragma unroll
     for (int k = 0; k < 4; ++k)

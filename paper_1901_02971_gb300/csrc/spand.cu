@@ -27,6 +27,8 @@
 #include "cpqr_reg.cuh"
 #include "factor_kernels.cuh"
 #include "schur_tc.cuh"
+#include "schur_tma.cuh"
+#include "sparsify_rand.cuh"
 #include "sparsify_sim.cuh"
 #include "sketch.cuh"
 #include "solve_kernels.cuh"
@@ -61,7 +63,7 @@ static inline int32_t row_ld(int32_t size) { return (std::max<int32_t>(size, 1) 
 constexpr size_t kCpqrChunkBudget = 224 * 1024;  // shared memory per sparsification CTA (chunk included)
 constexpr int kCpqrMaxCluster = 8;              // thread-block cluster size (broadcasts to 16 CTAs cost 3.5x more)
 constexpr int kAuxStreams = 4;
-constexpr int kApplyCtasPerSm = 4;  // CTAs per SM of the cooperative apply
+constexpr int kApplyCtasPerSm = 4;  // the most CTAs per SM the apply autotuner tries
 
 // Chunked bump allocator over cudaMalloc; reset() keeps the chunks for reuse.
 class DevArena {
@@ -250,6 +252,41 @@ static void ensure_smem(const void* fn, size_t bytes) {
   have = bytes;
 }
 
+// cuTensorMapEncodeTiled of the driver, looked up once through the runtime
+// (no link against the driver library); nullptr if unavailable.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn tmap_encoder() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+// Tensor map over a column-major FP32 block row (ld floats between columns,
+// rows x cols), boxes of 32 rows x box_cols columns, 128-byte swizzle,
+// zeros outside.  False if the driver refuses it.
+static bool encode_row_map(CUtensorMap* m, const float* base, int rows, int cols, int ld, int box_cols) {
+  EncodeTiledFn enc = tmap_encoder();
+  if (!enc || rows <= 0 || cols <= 0) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+  const cuuint32_t box[2] = {32u, (cuuint32_t)box_cols};
+  const cuuint32_t estr[2] = {1u, 1u};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 static std::mutex g_cluster_mutex;  // guards the cached cluster-size probe
 
 // Largest cluster size (16 or 8) at which the sparsification kernel can be
@@ -373,7 +410,7 @@ struct spand_handle_s {
   // envelope of the step-1 pivot blocks (pieces of A itself; other pivots
   // are dense): per initial cluster, U's tile bandwidth (0 = dense), the
   // Cholesky flops sum_j r_j^2 over U's row lengths r_j, and nnz(U)
-  std::vector<int32_t> env_bw;
+  std::vector<int32_t> env_bw, env_bw32;  // in 64-tiles and in 32-tiles
   std::vector<double> env_flops, env_nnz;
   // A in the cluster order (for the SpMV of PCG)
   std::vector<int64_t> prow;
@@ -388,6 +425,7 @@ struct spand_handle_s {
   DevBuf d_vals, d_asm_row, d_asm_off, d_prow, d_pcol, d_pval, d_pval_src, d_perm;
   DevBuf d_vec, d_tmp, d_save, d_bin, d_bout;
   DevBuf d_piv64;  // FP64 copies of the pivot blocks of FP32 factors (scratch)
+  DevBuf d_rand;   // sketches, products and state of the randomized compression (scratch)
   DevBuf d_rowptr, d_colind;  // original CSR pattern (gradient on A's pattern)
   int fprec = -1;
   bool factored = false;
@@ -407,6 +445,8 @@ struct spand_handle_s {
   const void* aprog = nullptr;
   int n_aprog = 0;
   int apply_grid = 0;
+  int apply_per_sm_max = 1;  // occupancy limit of the apply kernel for this program
+  int apply_ctas = 0;        // CTAs per SM of the apply: 0 = not chosen yet (autotuned at the first apply)
   size_t apply_smem = 0;
   DevBuf d_bar;  // [0] grid-barrier arrival counter, [1] barrier-timeout flag
   unsigned apply_spin_limit = kBarrierSpins;  // polls per grid-barrier wait of the apply
@@ -514,8 +554,9 @@ static void* upload(spand_handle h, const Packer& pk, cudaStream_t s) {
 template <typename X>
 static X* at(void* base, size_t off) { return reinterpret_cast<X*>((char*)base + off); }
 
-// Tiled upper Cholesky of a batch of diagonal blocks (right-looking over 64x64 tiles).
-template <typename T>
+// Tiled upper Cholesky of a batch of diagonal blocks (right-looking over
+// B x B tiles; dinv and bw of the rows in B-tiles).
+template <typename T, int B = TB>
 static void potrf_batch(spand_handle h, const std::vector<RowDesc<T>>& rows, int* d_info, cudaStream_t s,
                         const std::vector<double>* row_flops = nullptr) {
   if (rows.empty()) return;
@@ -525,10 +566,11 @@ static void potrf_batch(spand_handle h, const std::vector<RowDesc<T>>& rows, int
   const RowDesc<T>* dr = at<const RowDesc<T>>(d, o);
   int nmax = 0;
   for (auto& r : rows) nmax = std::max(nmax, r.n);
-  const int nt = (nmax + TB - 1) / TB;
-  const size_t sm1 = 2 * sizeof(SqTile<T>), sm2 = 2 * sizeof(SqTile<T>);
-  ensure_smem((const void*)k_potrf_diag<T>, sm1);
-  ensure_smem((const void*)k_potrf_trsm<T>, sm2);
+  const int nt = (nmax + B - 1) / B;
+  const size_t sm1 = 2 * sizeof(SqTileB<T, B>), sm2 = 2 * sizeof(SqTileB<T, B>);
+  ensure_smem((const void*)k_potrf_diag<T, B>, sm1);
+  ensure_smem((const void*)k_potrf_trsm<T, B>, sm2);
+  constexpr int nth = TileGeom<B>::NTH;
   const int nb = (int)rows.size();
   double fl = 0, by = 0;
   for (size_t i = 0; i < rows.size(); ++i) {
@@ -540,13 +582,13 @@ static void potrf_batch(spand_handle h, const std::vector<RowDesc<T>>& rows, int
   int64_t nl = 0;
   for (int k = 0; k < nt; ++k) {
     nl += (nt - k - 1 > 0) ? 3 : 1;
-    k_potrf_diag<T><<<nb, NT, sm1, s>>>(dr, k, d_info);
+    k_potrf_diag<T, B><<<nb, nth, sm1, s>>>(dr, k, d_info);
     CKLAUNCH();
     const int m = nt - k - 1;
     if (m > 0) {
-      k_potrf_trsm<T><<<dim3(m, nb), NT, sm2, s>>>(dr, k);
+      k_potrf_trsm<T, B><<<dim3(m, nb), nth, sm2, s>>>(dr, k);
       CKLAUNCH();
-      k_potrf_update<T><<<dim3(m * (m + 1) / 2, nb), NT, 0, s>>>(dr, k);
+      k_potrf_update<T, B><<<dim3(m * (m + 1) / 2, nb), nth, 0, s>>>(dr, k);
       CKLAUNCH();
     }
   }
@@ -554,52 +596,81 @@ static void potrf_batch(spand_handle h, const std::vector<RowDesc<T>>& rows, int
   h->prof.end(pid, s, fl, by, nl);
 }
 
-// Cholesky of a batch of pivot blocks in FP64 (Sec. 2.4, 2.5).  FP64 factors
-// are factored in place; FP32 factors (the mixed forms) are widened into an
-// FP64 scratch copy, factored there, and U and the inverses of its diagonal
-// tiles are rounded back to FP32 for the FP32 solves and GEMMs.
+// U_kk^{-T} of every 64 x 64 diagonal tile of a batch of factored pivot
+// blocks (rows: R = U, dinv = destination), for the block-row solves.
+template <typename T>
+static void inv_diag_batch(spand_handle h, const std::vector<RowDesc<T>>& rows, cudaStream_t s) {
+  if (rows.empty()) return;
+  Packer pk;
+  size_t o = pk.add(rows);
+  void* d = upload<T>(h, pk, s);
+  int nmax = 0;
+  for (auto& r : rows) nmax = std::max(nmax, r.n);
+  const int nt = (nmax + TB - 1) / TB;
+  const size_t sm = 2 * sizeof(SqTile<T>);
+  ensure_smem((const void*)k_inv_diag<T>, sm);
+  const size_t nb = rows.size();
+  for (size_t b0 = 0; b0 < nb; b0 += 65535) {
+    const unsigned cnt = (unsigned)std::min<size_t>(nb - b0, 65535);
+    k_inv_diag<T><<<dim3(nt, cnt), NT, sm, s>>>(at<const RowDesc<T>>(d, o) + b0);
+    CKLAUNCH();
+    ++h->prof.launches;
+  }
+}
+
+// Cholesky of a batch of pivot blocks in FP64 (Sec. 2.4, 2.5), on 32 x 32
+// tiles: FP64 factors are factored in place; FP32 factors (the mixed forms)
+// are widened into an FP64 scratch copy, factored there, and U is rounded
+// back to FP32.  Then the inverses of U's 64 x 64 diagonal tiles (rows'
+// dinv, in the factor's precision) for the block-row solves.
 template <typename T>
 static void pivot_chol(spand_handle h, const std::vector<RowDesc<T>>& rows, int* d_info, cudaStream_t s,
                        const std::vector<double>* row_flops = nullptr) {
-  if constexpr (std::is_same<T, double>::value) {
-    potrf_batch<double>(h, rows, d_info, s, row_flops);
-  } else {
-    if (rows.empty()) return;
-    size_t tot = 0;
-    for (auto& r : rows) tot += ((size_t)r.n * r.n + 31) / 32 * 32 + (size_t)((r.n + TB - 1) / TB) * TB * TB;
-    double* base = (double*)h->d_piv64.ensure(tot * sizeof(double));
-    std::vector<RowDesc<double>> r64;
-    std::vector<PivotCopy> cps;
-    r64.reserve(rows.size());
-    cps.reserve(rows.size());
-    size_t o = 0;
-    for (auto& r : rows) {
-      double* W = base + o;
+  if (rows.empty()) return;
+  const bool wide = !std::is_same<T, double>::value;
+  size_t tot = 0;
+  for (auto& r : rows)
+    tot += (wide ? ((size_t)r.n * r.n + 31) / 32 * 32 : 0) + (size_t)((r.n + TB2 - 1) / TB2) * TB2 * TB2;
+  double* base = (double*)h->d_piv64.ensure(std::max<size_t>(tot, 1) * sizeof(double));
+  std::vector<RowDesc<double>> r64;
+  std::vector<PivotCopy> cps;
+  r64.reserve(rows.size());
+  size_t o = 0;
+  for (auto& r : rows) {
+    double* W = nullptr;
+    if (wide) {
+      W = base + o;
       o += ((size_t)r.n * r.n + 31) / 32 * 32;
-      double* D = base + o;
-      o += (size_t)((r.n + TB - 1) / TB) * TB * TB;
-      r64.push_back({W, r.n, r.n, D, r.bw, 0});
-      cps.push_back({r.R, W, r.dinv, D, r.n, r.ld});
+      cps.push_back({(float*)r.R, W, r.n, r.ld});
     }
+    double* D = base + o;
+    o += (size_t)((r.n + TB2 - 1) / TB2) * TB2 * TB2;
+    if (wide) r64.push_back({W, r.n, r.n, D, r.bw2, 0});
+    else r64.push_back({(double*)r.R, r.n, r.ld, D, r.bw2, 0});
+  }
+  const PivotCopy* dc = nullptr;
+  if (wide) {
     Packer pk;
     const size_t oc = pk.add(cps);
     void* d = upload<T>(h, pk, s);
-    const PivotCopy* dc = at<const PivotCopy>(d, oc);
-    const size_t nb = cps.size();
-    for (size_t b0 = 0; b0 < nb; b0 += 65535) {
-      const unsigned cnt = (unsigned)std::min<size_t>(nb - b0, 65535);
+    dc = at<const PivotCopy>(d, oc);
+    for (size_t b0 = 0; b0 < cps.size(); b0 += 65535) {
+      const unsigned cnt = (unsigned)std::min<size_t>(cps.size() - b0, 65535);
       k_widen_pivot<<<dim3(8, cnt), 256, 0, s>>>(dc + b0);
       CKLAUNCH();
       ++h->prof.launches;
     }
-    potrf_batch<double>(h, r64, d_info, s, row_flops);
-    for (size_t b0 = 0; b0 < nb; b0 += 65535) {
-      const unsigned cnt = (unsigned)std::min<size_t>(nb - b0, 65535);
+  }
+  potrf_batch<double, TB2>(h, r64, d_info, s, row_flops);
+  if (wide) {
+    for (size_t b0 = 0; b0 < cps.size(); b0 += 65535) {
+      const unsigned cnt = (unsigned)std::min<size_t>(cps.size() - b0, 65535);
       k_narrow_pivot<<<dim3(8, cnt), 256, 0, s>>>(dc + b0);
       CKLAUNCH();
       ++h->prof.launches;
     }
   }
+  inv_diag_batch<T>(h, rows, s);
 }
 
 template <typename T>
@@ -809,6 +880,237 @@ static const void* cpqr_kernel(bool res, int nt) {
   return nt == 512 ? (const void*)k_cpqr_cluster<T, false, 512> : (const void*)k_cpqr_cluster<T, false, 256>;
 }
 
+// Randomized compression (SPAND_RANDOMIZED) of the interfaces of one step,
+// colour by colour (the kernels and the method are described in
+// sparsify_rand.cuh).  The column-pivoted QR of each sketch runs on the
+// chunked QR kernel as a task of its own (the sketch Y as its coupling
+// block, no write-back); between rounds the host reads which interfaces
+// still need a wider sketch.  Returns each task's final sketch width.
+template <typename T>
+static std::vector<int> sparsify_randomized(spand_handle h, int t, const std::vector<CpqrTask<T>>& tasks,
+                                            const std::vector<int>& tcolour, int ncol,
+                                            const std::vector<CpqrNbr<T>>& nbrs, int32_t* d_cur, double eps,
+                                            cudaStream_t s) {
+  const size_t ntk = tasks.size();
+  std::vector<int> ell_final(ntk, 0);
+  if (ntk == 0) return ell_final;
+  struct Off { size_t om, y, w, tcol, res, gw; };
+  std::vector<Off> off(ntk);
+  size_t bytes = 0;
+  for (size_t i = 0; i < ntk; ++i) {
+    const size_t np = (size_t)std::max(tasks[i].np, 1), mm = (size_t)std::max(tasks[i].m_max, 1);
+    const size_t Lp = (size_t)cq_ld<T>((int)np), cap = std::min(np, mm);
+    off[i].om = bytes; bytes += align256(mm * np * sizeof(T));
+    off[i].y = bytes; bytes += align256(np * np * sizeof(T));
+    off[i].w = bytes; bytes += align256(np * mm * sizeof(T));
+    off[i].tcol = bytes; bytes += align256(mm * sizeof(int32_t));
+    off[i].res = bytes; bytes += align256((np + 2) * sizeof(unsigned long long));
+    off[i].gw = bytes; bytes += align256(Lp * (cap + 16) * sizeof(T));
+  }
+  char* base = (char*)h->d_rand.ensure(bytes);
+  Packer pkn;
+  const size_t onb = pkn.add(nbrs);
+  const CpqrNbr<T>* d_nbrs = at<const CpqrNbr<T>>(upload<T>(h, pkn, s), onb);
+  const size_t CB = kCpqrChunkBudget;
+  const int max_cluster = cpqr_max_cluster<T>();
+  const uint64_t seed = h->opts.sketch_seed;
+  int32_t* hbuf = nullptr;
+  for (int c = 0; c < std::max(ncol, 1); ++c) {
+    std::vector<int> ids;
+    for (size_t i = 0; i < ntk; ++i)
+      if (tcolour[i] == c) ids.push_back((int)i);
+    const int nc = (int)ids.size();
+    if (nc == 0) continue;
+    std::vector<RandTask<T>> rt(nc);
+    std::vector<CpqrTask<T>> vt(nc);
+    std::vector<CpqrNbr<T>> vn(nc);
+    int npmax = 1, mmax = 1;
+    for (int k = 0; k < nc; ++k) {
+      const CpqrTask<T>& tk = tasks[ids[k]];
+      const Off& o = off[ids[k]];
+      RandTask<T> r{};
+      r.Rp = tk.Rp;
+      r.Om = (T*)(base + o.om);
+      r.Y = (T*)(base + o.y);
+      r.W = (T*)(base + o.w);
+      r.Qc = tk.Qc;
+      r.tcol = (int32_t*)(base + o.tcol);
+      r.res = (unsigned long long*)(base + o.res);
+      r.p = tk.p;
+      r.np = tk.np;
+      r.ldp = tk.ldp;
+      r.nbeg = tk.nbeg;
+      r.nend = tk.nend;
+      r.m_max = tk.m_max;
+      rt[k] = r;
+      CpqrTask<T> v = tk;  // V, tau and Qc of the interface; the sketch is the coupling block
+      v.Rp = r.Y;
+      v.ldp = std::max(tk.np, 1);
+      v.gwork = (T*)(base + o.gw);
+      v.rank_out = nullptr;  // set after the upload (the rank array of the sketches)
+      v.p = k;
+      v.nbeg = k;
+      v.nend = k + 1;
+      v.m_max = std::min(tk.np, tk.m_max);
+      v.nowb = 1;
+      vt[k] = v;
+      CpqrNbr<T> nb{};
+      nb.Rq = r.Y;
+      nb.q = k;
+      nb.off_pq = 0;
+      nb.off_qp = 0;
+      nb.ldq = std::max(tk.np, 1);
+      vn[k] = nb;
+      npmax = std::max(npmax, tk.np);
+      mmax = std::max(mmax, tk.m_max);
+      if (tk.nend - tk.nbeg > 256)
+        throw Fail{SPAND_ERR_INVALID_ARG, "randomized compression: an interface with more than 256 neighbours"};
+    }
+    // device state: [vcur | vrank | active] ints, then the task arrays
+    const size_t ist = 0;
+    Packer pk;
+    const size_t ostate = pk.add(std::vector<int32_t>((size_t)3 * nc, 0));
+    (void)ist;
+    const size_t ort = pk.add(rt), ovn = pk.add(vn);
+    const size_t ovt = pk.add(vt);
+    void* dev = h->descs.alloc(pk.buf.size());
+    int32_t* d_vcur = at<int32_t>(dev, ostate);
+    int32_t* d_vrank = d_vcur + nc;
+    int32_t* d_active = d_vcur + 2 * nc;
+    for (int k = 0; k < nc; ++k) {
+      CpqrTask<T> v = vt[k];
+      v.rank_out = d_vrank;
+      std::memcpy(pk.buf.data() + ovt + k * sizeof(CpqrTask<T>), &v, sizeof(CpqrTask<T>));
+    }
+    {
+      void* src = h->stage.take(pk.buf.size());
+      std::memcpy(src, pk.buf.data(), pk.buf.size());
+      CK(cudaMemcpyAsync(dev, src, pk.buf.size(), cudaMemcpyHostToDevice, s));
+    }
+    RandTask<T>* d_rt = at<RandTask<T>>(dev, ort);
+    CpqrTask<T>* d_vt = at<CpqrTask<T>>(dev, ovt);
+    const CpqrNbr<T>* d_vn = at<const CpqrNbr<T>>(dev, ovn);
+    k_rand_init<T><<<nc, 256, 0, s>>>(d_rt, d_nbrs, d_cur, d_vcur);
+    CKLAUNCH();
+    std::vector<int> ub(nc), act(nc, 1), prev(nc, 0);
+    for (int k = 0; k < nc; ++k) ub[k] = std::min(RD_ELL0, std::max(0, std::min(rt[k].np, rt[k].m_max)));
+    int64_t nl = 1;
+    for (;;) {
+      std::vector<int32_t> alist;
+      int maxub = 1, maxnew = 1;
+      for (int k = 0; k < nc; ++k)
+        if (act[k]) {
+          alist.push_back(k);
+          maxub = std::max(maxub, ub[k]);
+          maxnew = std::max(maxnew, ub[k] - prev[k]);
+        }
+      if (alist.empty()) break;
+      k_rand_omega<T><<<dim3(16, nc), 256, 0, s>>>(d_rt, seed, t);
+      CKLAUNCH();
+      const int tiles = ((npmax + 31) / 32) * ((maxnew + 31) / 32);
+      k_rand_sketch<T><<<dim3(tiles, nc), 256, 0, s>>>(d_rt);
+      CKLAUNCH();
+      // the QR of every active sketch, grouped by launch shape
+      std::map<std::tuple<int, int, int>, std::vector<int32_t>> groups;  // (C, resident, threads) -> tasks
+      std::map<std::tuple<int, int, int>, size_t> gsmem;
+      for (int k : alist) {
+        const int np = std::max(rt[k].np, 1), cols = std::max(ub[k], 1);
+        const size_t Lp = (size_t)cq_ld<T>(np);
+        auto res_smem = [&](int cc) {
+          const int cp = (cols + cc - 1) / cc;
+          return cq_fixed_smem<T>(1, np, cp, cc) + Lp * cp * sizeof(T);
+        };
+        int C = max_cluster;
+        for (int cc = 1; cc <= max_cluster; cc *= 2)
+          if (res_smem(cc) <= CB) { C = cc; break; }
+        while (C < max_cluster && (cols + C - 1) / C > 2 * CQ_MAXNT) C *= 2;
+        const bool resident = res_smem(C) <= CB;
+        const int cp = (cols + C - 1) / C;
+        const int nth = cp > CQ_CPT * 256 ? 512 : 256;
+        const auto key = std::make_tuple(C, resident ? 1 : 0, nth);
+        groups[key].push_back(k);
+        const size_t need = resident ? res_smem(C) : cq_fixed_smem<T>(1, np, cp, C);
+        gsmem[key] = std::max(gsmem[key], need);
+      }
+      Packer pkl;
+      std::vector<size_t> lo;
+      for (auto& kv : groups) lo.push_back(pkl.add(kv.second));
+      const size_t oal = pkl.add(alist);
+      void* dl = upload<T>(h, pkl, s);
+      size_t gi = 0;
+      for (auto& kv : groups) {
+        const int C = std::get<0>(kv.first), res = std::get<1>(kv.first), nth = std::get<2>(kv.first);
+        const void* fn = cpqr_kernel<T>(res != 0, nth);
+        const size_t smem = gsmem[kv.first];
+        ensure_smem(fn, smem);
+        if (C > 8) ensure_nonportable_cluster(fn);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(kv.second.size() * C), 1, 1);
+        cfg.blockDim = dim3((unsigned)nth, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const CpqrTask<T>* a0 = d_vt;
+        const int32_t* a1 = at<const int32_t>(dl, lo[gi]);
+        const CpqrNbr<T>* a2 = d_vn;
+        T a4 = T(0);  // no truncation: the rank comes from step 5
+        void* args[] = {(void*)&a0, (void*)&a1, (void*)&a2, (void*)&d_vcur, (void*)&a4};
+        CK(cudaLaunchKernelExC(&cfg, fn, args));
+        ++gi;
+        ++nl;
+      }
+      {  // the bases Q = H_0 ... H_{ell-1} [I; 0]
+        constexpr int NTQ = 256, NWQ = NTQ / 32;
+        int kmx = 1;
+        size_t need = 0;
+        for (int k : alist) {
+          const int km = std::min(rt[k].np, ub[k]);
+          kmx = std::max(kmx, km);
+          need = std::max(need, align256((size_t)km * sizeof(T)) + (size_t)rt[k].np * km * sizeof(T));
+        }
+        const size_t qsm = std::min(need + 256, (size_t)227 * 1024);
+        const int nb = std::max(1, (kmx + 2 * NWQ - 1) / (2 * NWQ));
+        const void* fq = (const void*)k_form_q<T, NTQ>;
+        ensure_smem(fq, qsm);
+        const CpqrTask<T>* q0 = d_vt;
+        const int32_t* q1 = at<const int32_t>(dl, oal);
+        const int q3 = nb, q4 = (int)(qsm / sizeof(T));
+        void* qargs[] = {(void*)&q0, (void*)&q1, (void*)&d_vcur, (void*)&q3, (void*)&q4};
+        CK(cudaLaunchKernel(fq, dim3((unsigned)(alist.size() * nb)), dim3(NTQ), qargs, qsm, s));
+        ++nl;
+      }
+      k_rand_project<T><<<dim3((unsigned)((mmax + 31) / 32), nc), 256, 0, s>>>(d_rt);
+      CKLAUNCH();
+      k_rand_decide<T><<<(nc + 127) / 128, 128, 0, s>>>(d_rt, nc, eps, d_vcur, d_vt, d_active);
+      CKLAUNCH();
+      nl += 5;
+      // which sketches must grow, and to what width
+      if (!hbuf) hbuf = (int32_t*)h->stage.take((size_t)2 * ntk * sizeof(int32_t) + 256);
+      CK(cudaMemcpyAsync(hbuf, d_vcur, (size_t)nc * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(hbuf + nc, d_active, (size_t)nc * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int k : alist) {
+        ell_final[ids[k]] = ub[k];
+        act[k] = hbuf[nc + k];
+        if (act[k]) {
+          prev[k] = ub[k];
+          ub[k] = hbuf[k];
+        }
+      }
+    }
+    k_rand_writeback<T><<<nc, 256, 0, s>>>(d_rt, d_nbrs, d_cur);
+    CKLAUNCH();
+    h->prof.launches += nl + 1;
+  }
+  return ell_final;
+}
+
 // The apply program: the phases of every step in execution order (forward
 // sweep leaves -> root, then the backward sweep root -> leaves), uploaded once
 // per factorization, and the cooperative grid that runs it.
@@ -878,7 +1180,8 @@ static void build_apply_program(spand_handle h, const std::vector<ApplyStep<TF>>
   if (!coop) throw Fail{SPAND_ERR_CUDA, "device does not support cooperative launches (needed by the apply)"};
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_apply<TF>, AT, h->apply_smem));
   if (per_sm < 1) throw Fail{SPAND_ERR_CUDA, "apply kernel cannot be resident"};
-  h->apply_grid = nsm * std::min(per_sm, kApplyCtasPerSm);
+  h->apply_per_sm_max = std::min(per_sm, kApplyCtasPerSm);
+  h->apply_grid = nsm * (h->apply_ctas > 0 ? std::min(h->apply_ctas, h->apply_per_sm_max) : h->apply_per_sm_max);
 }
 
 template <typename T>
@@ -902,7 +1205,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
   StepTimer tm(L);
   h->stage.reset();  // the previous factorization ended with a stream synchronisation
   // non-positive pivot flags per step: [2t] elimination pivots, [2t+1]
-  // scaling pivots ([0]: a tensor-core wait of the Schur update timed out);
+  // scaling pivots ([0]: a bounded device wait gave up);
   // read at the next host synchronisation (the rank readback of a
   // sparsifying step, or the end of the factorization)
   int* d_info = (int*)h->descs.alloc(2 * (size_t)(L + 1) * sizeof(int));
@@ -911,7 +1214,9 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
   auto check_pivots = [&](int upto) {  // after a stream synchronisation
     std::vector<int> info(2 * (size_t)(L + 1), 0);
     CK(cudaMemcpy(info.data(), d_info, info.size() * sizeof(int), cudaMemcpyDeviceToHost));
-    if (info[0]) throw Fail{SPAND_ERR_TIMEOUT, "Schur update: a tensor-core completion wait timed out"};
+    if (info[0])
+      throw Fail{SPAND_ERR_TIMEOUT, "Schur update: a bounded tensor-core wait (MMA completion or operand "
+                                    "copy) timed out"};
     for (int u = 1; u <= upto; ++u)
       if (info[2 * u] || info[2 * u + 1]) {
         stt.fail_step = u;
@@ -978,11 +1283,11 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         const double ns = sz[sidx], m = lay.W[sidx] - sz[sidx];
         // step 1: the pivot is a piece of A, with the envelope found at analysis
         const bool env = t == 1 && !h->env_bw.empty();
-        const int bw = env ? h->env_bw[sidx] : 0;
+        const int bw = env ? h->env_bw[sidx] : 0, bw2 = env ? h->env_bw32[sidx] : 0;
         const double cfl = env ? h->env_flops[sidx] : ns * ns * ns / 3;
         const double nnzU = env ? h->env_nnz[sidx] : ns * (ns + 1) / 2;
         T* dv = alloc_dinv<T>(h, sz[sidx]);
-        diag.push_back({lay.row[sidx], sz[sidx], lay.ld[sidx], dv, bw, 0});
+        diag.push_back({lay.row[sidx], sz[sidx], lay.ld[sidx], dv, bw, bw2});
         diag_cl.push_back(sidx);
         diag_fl.push_back(cfl);
         add_panels(tr_tasks, lay.row[sidx], (const T*)dv, sz[sidx], lay.ld[sidx], sz[sidx], lay.W[sidx], bw, &tr_fl,
@@ -1035,6 +1340,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
             c.Xb = lay.row[sidx] + (size_t)lay.noff[eb] * lay.ld[sidx];
             c.lds = lay.ld[sidx];
             c.ns = sz[sidx];
+            c.owner = sidx;
             contr[id].push_back(c);
           }
         }
@@ -1048,6 +1354,22 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         for (size_t b = 0; tc && b < contr.size(); ++b)  // the kernel loads 16-byte vectors of X
           for (const auto& c : contr[b])
             if (c.lds % 4 != 0 || ((uintptr_t)c.Xa | (uintptr_t)c.Xb) % 16 != 0) tc = false;
+        // TF32: operands through the copy engine (one tensor map pair per
+        // separator row); BF16 converts in registers (k_schur_tc)
+        std::vector<CUtensorMap> tmaps;
+        std::vector<int32_t> tmap_of(n, -1);
+        bool tma = tc && h->opts.precision == SPAND_TF32 && tmap_encoder() != nullptr;
+        for (int sidx : seps) {
+          if (!tma) break;
+          if (sz[sidx] <= 0 || lay.nptr[sidx + 1] == lay.nptr[sidx]) continue;
+          tmap_of[sidx] = (int32_t)tmaps.size();
+          tmaps.resize(tmaps.size() + 2);
+          if (!encode_row_map(&tmaps[tmaps.size() - 2], (const float*)lay.row[sidx], sz[sidx], lay.W[sidx],
+                              lay.ld[sidx], TC_M) ||
+              !encode_row_map(&tmaps[tmaps.size() - 1], (const float*)lay.row[sidx], sz[sidx], lay.W[sidx],
+                              lay.ld[sidx], TC_N))
+            tma = false;
+        }
         const int ti = tc ? TC_M : TB, tj = tc ? TC_N : TB;
         for (size_t b = 0; b < blocks.size(); ++b) {
           blocks[b].cbeg = (int32_t)flat.size();
@@ -1056,8 +1378,29 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
           for (int i0 = 0; i0 < blocks[b].rows; i0 += ti)
             for (int j0 = 0; j0 < blocks[b].cols; j0 += tj) tiles.push_back({(int32_t)b, i0, j0});
         }
+        const CUtensorMap* dmaps = nullptr;
+        if (tma) {
+          Packer pkm;
+          const size_t om = pkm.add(tmaps);
+          dmaps = at<const CUtensorMap>(upload<T>(h, pkm, s), om);
+        }
+        std::vector<SchurContribTma> flat_tma;
+        if (tma) {
+          flat_tma.reserve(flat.size());
+          for (const SchurContrib<T>& c : flat) {
+            // the separator row is the one whose columns Xa, Xb point into
+            const int sidx = c.owner;
+            SchurContribTma m{};
+            m.map_a = dmaps + tmap_of[sidx];
+            m.map_b = dmaps + tmap_of[sidx] + 1;
+            m.col_a = (int32_t)((c.Xa - lay.row[sidx]) / lay.ld[sidx]);
+            m.col_b = (int32_t)((c.Xb - lay.row[sidx]) / lay.ld[sidx]);
+            m.ns = c.ns;
+            flat_tma.push_back(m);
+          }
+        }
         Packer pk;
-        size_t ob = pk.add(blocks), oc = pk.add(flat), ot = pk.add(tiles);
+        size_t ob = pk.add(blocks), oc = tma ? pk.add(flat_tma) : pk.add(flat), ot = pk.add(tiles);
         void* d = upload<T>(h, pk, s);
         double fl = 0, by = 0;
         for (auto& bl : blocks) {
@@ -1068,7 +1411,16 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         }
         const int pid = h->prof.begin(F_SCHUR, s);
         if constexpr (sizeof(T) == 4) {
-          if (tc) {
+          if (tma) {
+            const void* fn = (const void*)k_schur_tma;
+            ensure_smem(fn, TM_SMEM);
+            const SchurTile* a0 = at<const SchurTile>(d, ot);
+            const SchurBlock<float>* a1 = at<const SchurBlock<float>>(d, ob);
+            const SchurContribTma* a2 = at<const SchurContribTma>(d, oc);
+            int* a3 = d_info;  // [0]: a bounded wait gave up
+            void* args[] = {(void*)&a0, (void*)&a1, (void*)&a2, (void*)&a3};
+            CK(cudaLaunchKernel(fn, dim3((unsigned)tiles.size()), dim3(TC_NT), args, TM_SMEM, s));
+          } else if (tc) {
             const void* fn = h->opts.precision == SPAND_BF16 ? (const void*)k_schur_tc<true> : (const void*)k_schur_tc<false>;
             const size_t tsm = TC_SMEM;
             ensure_smem(fn, tsm);
@@ -1174,6 +1526,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
     size_t sm_np = 0, sm_r = 0;
     const bool sparsify = (skip < t) && (t < L);
     int cpqr_pid = -1;
+    std::vector<int> ell_fin;              // randomized compression: final sketch width per task
     std::vector<int> cp_cluster;           // sparsified clusters (task order)
     std::vector<T*> cp_qc;                 // their Q_pc scratch
     if (sparsify) {
@@ -1384,6 +1737,13 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
           tasks[i].gwork = (T*)(wb + woff[i].gw);
           cp_qc.push_back(tasks[i].Qc);
         }
+        if (h->opts.compression == SPAND_RANDOMIZED) {
+          cpqr_pid = h->prof.begin(F_CPQR, s);
+          std::vector<int> tcolr(tasks.size());
+          for (size_t i = 0; i < tasks.size(); ++i) tcolr[i] = colour_of(tasks[i].p);
+          ell_fin = sparsify_randomized<T>(h, t, tasks, tcolr, ncol, nbrs, d_cur, eps, s);
+          h->prof.end(cpqr_pid, s, 0.0, 0.0, 1);
+        } else {
         // launch groups: (colour, cluster size)
         struct Group { int colour, C, res, G = 0; std::vector<int32_t> ids; size_t smem = 0; int maxm = 0; };
         // one pass: tasks bucketed by (colour, kernel, lane group, cluster
@@ -1563,6 +1923,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         if (sim) CK(cudaMemcpyAsync(d_cur, d_rank, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
         h->prof.launches += (int64_t)groups.size() + nformq + nsim;
         h->prof.end(cpqr_pid, s, 0.0, 0.0, (int64_t)groups.size() + nformq + nsim);
+        }
         build_elim_ops();  // host work overlapped with the sparsification kernels
         run_pending();
         int32_t* hcur = (int32_t*)h->stage.take((size_t)n * sizeof(int32_t));
@@ -1599,7 +1960,11 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         so.Q = Q;
         so.r = r;
         const double np_ = sz[p], m = lay.W[p] - sz[p], rr = r;
-        const double qfl = 4 * np_ * m * rr - 2 * rr * rr * (np_ + m) + 4 * rr * rr * rr / 3;
+        // CPQR of A_pn to rank r; randomized: sketch and projection (2 np m ell
+        // each) and the QR of the np x ell sketch
+        const double el = i < ell_fin.size() ? ell_fin[i] : 0.0;
+        const double qfl = ell_fin.empty() ? 4 * np_ * m * rr - 2 * rr * rr * (np_ + m) + 4 * rr * rr * rr / 3
+                                           : 4 * np_ * m * el + 4 * np_ * el * el - 4 * el * el * el / 3;
         stt.factor_flops += qfl;
         // algorithmic bytes: A_pn read once, W written twice, Q_pc written
         h->prof.add(cpqr_pid, qfl, (np_ * m + 2 * rr * m + np_ * rr) * sizeof(T));
@@ -1824,6 +2189,45 @@ static void apply_any(spand_handle h, double* x, cudaStream_t s) {
   apply_any(h, x, (double*)h->d_tmp.p, (double*)h->d_save.p, s);
 }
 
+// Tile-shape autotuner of the apply (the grid of its cooperative launch):
+// the first apply after a handle's first factorization times 1 .. 4 CTAs per
+// SM (two applications each, on a scratch vector) and keeps the fastest for
+// the handle's later factorizations and solves.  Every item of a phase is
+// computed by one CTA in a fixed order whatever the grid, so the choice never
+// changes a bit of z.  More CTAs stream the large leaf phases faster; fewer
+// make the grid barriers of many small phases cheaper.
+static void apply_autotune(spand_handle h, double* scratch, cudaStream_t s) {
+  if (h->apply_ctas > 0 || !h->n_aprog) return;
+  int nsm = 0, dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaMemsetAsync(scratch, 0, (size_t)h->n * sizeof(double), s));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const bool prof = h->prof.on;
+  h->prof.on = false;
+  float best = 0.f;
+  int pick = h->apply_per_sm_max;
+  for (int c = 1; c <= h->apply_per_sm_max; ++c) {
+    h->apply_grid = nsm * c;
+    apply_any(h, scratch, s);  // warm-up
+    CK(cudaEventRecord(e0, s));
+    apply_any(h, scratch, s);
+    apply_any(h, scratch, s);
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (c == 1 || ms < best) best = ms, pick = c;
+  }
+  h->prof.on = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->apply_ctas = pick;
+  h->apply_grid = nsm * pick;
+}
+
 static void ensure_solve_buffers(spand_handle h) {
   const int64_t n = std::max<int64_t>(h->n, 1);
   h->d_vec.ensure((size_t)(7 * n + RED_BLOCKS + 16) * sizeof(double));
@@ -1875,6 +2279,8 @@ void spand_default_opts(spand_opts* o) {
   o->maxit = 500;
   o->tol = 1e-10;
   o->sparsify_order = SPAND_COLOURED;
+  o->compression = SPAND_CPQR;
+  o->sketch_seed = 0;
 }
 
 const char* spand_error_string(int code) {
@@ -1909,6 +2315,10 @@ int spand_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const
   if (opts->maxit < 1 || !(opts->tol > 0.0)) throw Fail{SPAND_ERR_INVALID_ARG, "maxit >= 1 and tol > 0 required"};
   if (opts->sparsify_order != SPAND_COLOURED && opts->sparsify_order != SPAND_SIMULTANEOUS)
     throw Fail{SPAND_ERR_INVALID_ARG, "unknown sparsify_order"};
+  if (opts->compression != SPAND_CPQR && opts->compression != SPAND_RANDOMIZED)
+    throw Fail{SPAND_ERR_INVALID_ARG, "unknown compression"};
+  if (opts->compression == SPAND_RANDOMIZED && opts->sparsify_order != SPAND_COLOURED)
+    throw Fail{SPAND_ERR_INVALID_ARG, "randomized compression runs in the coloured order only"};
   if (n > INT32_MAX - 1) throw Fail{SPAND_ERR_INVALID_ARG, "n too large"};
   if (coords && (dim < 1 || dim > 8)) throw Fail{SPAND_ERR_INVALID_ARG, "dim must be in [1, 8]"};
   std::string err;
@@ -1977,6 +2387,7 @@ int spand_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const
   // bw = max_i (i/64 - f(i)/64) above the diagonal stay zero; the row lengths
   // r_j = #{i >= j : f(i) <= j} of U give the Cholesky flops sum_j r_j^2.
   h->env_bw.assign(nc, 0);
+  h->env_bw32.assign(nc, 0);
   h->env_flops.assign(nc, 0.0);
   h->env_nnz.assign(nc, 0.0);
   if (n > 0) {
@@ -1995,11 +2406,12 @@ int spand_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const
         }
         f[i] = fi;
       }
-      int32_t bw = 0;
+      int32_t bw = 0, bw32 = 0;
       double nnzU = 0;
       cnt.assign((size_t)sz + 1, 0);
       for (int32_t i = 0; i < sz; ++i) {
         bw = std::max(bw, i / 64 - f[i] / 64);
+        bw32 = std::max(bw32, i / 32 - f[i] / 32);
         nnzU += i - f[i] + 1;
         ++cnt[f[i]];  // column i covers rows f(i) .. i
         --cnt[i + 1];
@@ -2009,8 +2421,9 @@ int spand_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const
         r += (double)cnt[j];
         fl += r * r;
       }
-      const int32_t ntile = (sz + 63) / 64;
+      const int32_t ntile = (sz + 63) / 64, ntile32 = (sz + 31) / 32;
       h->env_bw[c] = (bw + 1 >= ntile) ? 0 : bw;  // 0: dense (no tile is structurally zero)
+      h->env_bw32[c] = (bw32 + 1 >= ntile32) ? 0 : bw32;
       h->env_flops[c] = fl;
       h->env_nnz[c] = nnzU;
     }
@@ -2125,6 +2538,7 @@ int spand_apply(spand_handle h, const double* r_dev, double* z_dev, void* cuda_s
   const int64_t n = h->n;
   if (n == 0) return SPAND_OK;
   double* w = (double*)h->d_vec.p;
+  apply_autotune(h, w, s);
   const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
   k_permute<<<g, 256, 0, s>>>(n, (const int32_t*)h->d_perm.p, r_dev, w, 1);
   CKLAUNCH();
@@ -2219,6 +2633,7 @@ int spand_solve(spand_handle h, const double* b, double* x, int32_t* iters, doub
   }
   double* V = (double*)h->d_vec.p;
   double *bp = V, *xv = V + n, *r = V + 2 * n, *z = V + 3 * n, *p = V + 4 * n, *q = V + 5 * n, *io = V + 6 * n;
+  apply_autotune(h, z, s);
   double* part = V + 7 * n;
   double* sc = part + RED_BLOCKS;  // scalars
   const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
@@ -2372,6 +2787,17 @@ int spand_set_apply_wait(spand_handle h, uint32_t polls, int32_t unreachable) {
   return SPAND_OK;
 }
 
+int spand_set_apply_shape(spand_handle h, int32_t ctas_per_sm) {
+  if (!h) { g_err = "null handle"; return SPAND_ERR_INVALID_ARG; }
+  if (ctas_per_sm < 0 || ctas_per_sm > kApplyCtasPerSm) {
+    g_err = "ctas_per_sm must be in [0, 4]";
+    return SPAND_ERR_INVALID_ARG;
+  }
+  h->apply_ctas = ctas_per_sm;
+  if (h->apply_grid > 0 && ctas_per_sm > 0) h->apply_grid = num_sms() * std::min(ctas_per_sm, h->apply_per_sm_max);
+  return SPAND_OK;
+}
+
 int spand_set_profiling(spand_handle h, int32_t on) {
   if (!h) { g_err = "null handle"; return SPAND_ERR_INVALID_ARG; }
   h->prof.on = on != 0;
@@ -2491,6 +2917,7 @@ int spand_get_ranks(spand_handle h, int32_t t, int32_t* sizes_before, int32_t* s
 
 int spand_get_stats(spand_handle h, spand_stats* st) {
   if (!h || !st) { g_err = "null argument"; return SPAND_ERR_INVALID_ARG; }
+  h->st.apply_ctas_per_sm = h->apply_ctas;
   *st = h->st;
   return SPAND_OK;
 }

@@ -185,12 +185,36 @@ def test_sketch_argument_checks(spand_lib):
 
 
 def test_apply_wait_knob_argument_checks(spand_lib):
-    """The failure-path knob of the apply is a host-side setting."""
+    """The failure-path knob and the launch shape of the apply are host-side
+    settings."""
     assert spand_lib.spand_set_apply_wait(None, 16, 1) == L.SPAND_ERR_INVALID_ARG
+    assert spand_lib.spand_set_apply_shape(None, 2) == L.SPAND_ERR_INVALID_ARG
     p = I.laplacian_2d(8)
     h = L.spand_analyze(p.rowptr, p.colind, p.vals, p.coords, L.default_opts(levels=3))
     try:
         L.spand_set_apply_wait(h, 16, True)
         L.spand_set_apply_wait(h, 0, False)
+        assert spand_lib.spand_set_apply_shape(h, 5) == L.SPAND_ERR_INVALID_ARG
+        assert spand_lib.spand_set_apply_shape(h, -1) == L.SPAND_ERR_INVALID_ARG
+        L.spand_set_apply_shape(h, 3)
+        L.spand_set_apply_shape(h, 0)
     finally:
         L.spand_destroy(h)
+
+
+def test_compression_option(spand_lib):
+    """compression is SPAND_CPQR by default; SPAND_RANDOMIZED is accepted in
+    the coloured order only; unknown values are refused."""
+    assert L.default_opts().compression == L.SPAND_CPQR and L.default_opts().sketch_seed == 0
+    p = I.laplacian_2d(6)
+    for comp, order, want in [(L.SPAND_CPQR, L.SPAND_COLOURED, L.SPAND_OK),
+                              (L.SPAND_RANDOMIZED, L.SPAND_COLOURED, L.SPAND_OK),
+                              (L.SPAND_RANDOMIZED, L.SPAND_SIMULTANEOUS, L.SPAND_ERR_INVALID_ARG),
+                              (2, L.SPAND_COLOURED, L.SPAND_ERR_INVALID_ARG)]:
+        o = L.default_opts(levels=3, compression=comp, sparsify_order=order, sketch_seed=2 ** 63 + 5)
+        h = C.c_void_p()
+        rc = L.lib().spand_analyze(p.n, p.rowptr.ctypes.data, p.colind.ctypes.data, p.vals.ctypes.data, None, 0,
+                                   C.byref(o), C.byref(h))
+        if h.value:
+            L.spand_destroy(h.value)
+        assert rc == want, (comp, order, rc)

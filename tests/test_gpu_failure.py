@@ -62,3 +62,25 @@ def test_short_wait_limit_still_completes(cuda_ok):
         assert np.array_equal(s.apply(r).cpu().numpy(), z_ref)
     finally:
         s.close()
+
+
+def test_apply_shape_autotuner_keeps_bits(cuda_ok):
+    """The apply's launch shape (CTAs per SM) is autotuned at the first apply;
+    every candidate shape gives the same bits of z."""
+    import torch
+    p = I.laplacian_3d(16)
+    s = Solver.from_problem(p, levels=6, eps=1e-2, precision="fp32").factorize()
+    try:
+        assert s.stats().apply_ctas_per_sm == 0
+        r = torch.from_numpy(I.rhs(p.n, 9)).cuda()
+        z0 = s.apply(r).cpu().numpy()
+        tuned = s.stats().apply_ctas_per_sm
+        assert 1 <= tuned <= 4
+        for c in (1, 2, 3, 4):
+            L.spand_set_apply_shape(s.h, c)
+            assert np.array_equal(s.apply(r).cpu().numpy(), z0), c
+        L.spand_set_apply_shape(s.h, 0)  # back to the autotuner: it runs again at the next apply
+        s.factorize()
+        assert np.array_equal(s.apply(r).cpu().numpy(), z0)
+    finally:
+        s.close()

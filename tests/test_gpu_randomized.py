@@ -1,0 +1,102 @@
+"""Randomized compression on the GPU (SPAND_RANDOMIZED: OrthS with a
+Gaussian-sketch range finder in place of the column-pivoted QR, the
+randomized alternative of Sec. 2.6.2 and Sec. 5) against the oracle's
+"OrthS-rand" variant driven by the same counter-based sketches (Philox4x64-10
+keyed by (seed, step, cluster)).
+
+* FP64 form: ranks at every step equal to the oracle's per cluster (a near
+  tie in the sketch's pivoted QR may move one by one), PCG iterations within
+  +10 %, x within 1e-8 of the oracle's x at relative residual 1e-10;
+* eps = 0: the sketch grows to min(p, m) columns whose range is that of
+  A_pn, so the factorization is exact (one PCG iteration, dense solution);
+* mixed forms (FP32 factor with FP64 pivots, TF32 Schur operands) converge
+  to the same accuracy;
+* the option is refused with the simultaneous order.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import spand_oracle as O
+from paper_1901_02971_gb300 import Solver
+from paper_1901_02971_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+SEED = 7
+
+
+def _oracle(p, b, levels, eps, geo=True):
+    return O.solve(p, b, levels, eps, use_coords=geo, variant="OrthS-rand",
+                   sketch=lambda t, q, m, ell: O.sketch_philox(SEED, t, q, m, ell))
+
+
+CASES = [
+    ("lapl2d_48_L7_e1e-2", lambda: I.laplacian_2d(48), 7, 1e-2, True),
+    ("diff2d_40_L6_e1e-1", lambda: I.diffusion_2d(40, 3), 6, 1e-1, True),
+    ("lapl3d_16_L6_e1e-2", lambda: I.laplacian_3d(16), 6, 1e-2, True),
+    ("diff3d_14_L6_e1e-2", lambda: I.diffusion_3d(14, 5, block=2), 6, 1e-2, True),
+    ("knn_2500_L6_e1e-2", lambda: I.knn_laplacian(2500, 8, 4), 6, 1e-2, False),
+]
+
+
+@pytest.mark.parametrize("name,gen,levels,eps,geo", CASES, ids=[c[0] for c in CASES])
+def test_randomized_fp64_matches_oracle(cuda_ok, name, gen, levels, eps, geo):
+    import torch
+    p = gen()
+    b = I.rhs(p.n, 0)
+    ref = _oracle(p, b, levels, eps, geo)
+    s = Solver.from_problem(p, use_coords=geo, levels=levels, eps=eps, compression="randomized", sketch_seed=SEED)
+    try:
+        s.factorize()
+        xd, it, rr = s.solve(torch.from_numpy(b).cuda())
+        x = xd.cpu().numpy()
+        assert rr <= 1e-10
+        err = np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x)
+        assert err <= 1e-8, err
+        assert it <= math.ceil(1.1 * ref.iters), (it, ref.iters)
+        moved = 0
+        for t in range(1, levels + 1):
+            _, after = s.ranks(t)
+            want = ref.factor.sizes_after[t - 1]
+            d = np.abs(after.astype(np.int64) - want)
+            assert d.max() <= 1, (t, d.max())
+            moved += int(np.count_nonzero(d))
+        assert moved <= max(2, sum(len(a) for a in ref.factor.sizes_after) // 50), moved
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("gen,levels", [(lambda: I.laplacian_2d(20), 5), (lambda: I.diffusion_3d(8, 2, block=2), 4)])
+def test_randomized_eps0_is_exact(cuda_ok, gen, levels):
+    p = gen()
+    b = I.rhs(p.n, 1)
+    s = Solver.from_problem(p, levels=levels, eps=0.0, compression="randomized", sketch_seed=SEED)
+    try:
+        s.factorize()
+        x, it, rr = s.solve(b)
+        x_ref = np.linalg.solve(p.to_scipy().toarray(), b)
+        assert it == 1
+        assert np.linalg.norm(x - x_ref) <= 1e-9 * np.linalg.norm(x_ref)
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tf32"])
+def test_randomized_mixed_forms_converge(cuda_ok, precision):
+    import torch
+    p = I.laplacian_3d(20)
+    b = I.rhs(p.n, 2)
+    ref = _oracle(p, b, 7, 1e-2)
+    s = Solver.from_problem(p, levels=7, eps=1e-2, precision=precision, compression="randomized",
+                            sketch_seed=SEED)
+    try:
+        s.factorize()
+        xd, it, rr = s.solve(torch.from_numpy(b).cuda())
+        x = xd.cpu().numpy()
+        assert rr <= 1e-10
+        assert np.linalg.norm(x - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+        assert it <= 2 * ref.iters + 3, (it, ref.iters)
+    finally:
+        s.close()
