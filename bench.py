@@ -196,12 +196,16 @@ HBM_BOUND = {"copy", "apply", "pcg"}
 # counters were taken on: a changed kernel reports null until re-measured.
 # The capture and its command are summarised under profiles/ (DRAM traffic, 64^3).
 MEASURED_TRAFFIC = {
-    "cpqr": {"bytes_per_launch": (583.4e6 + 13.8e6) / 212,
+    # dram__bytes_read.sum + dram__bytes_write.sum of the 212 sparsification
+    # launches of one factorization (k_cpqr_cluster, k_cpqr_reg, k_form_q:
+    # 583.9 MB read, 14.1 MB written) and of three applications (3104.1 MB
+    # read, 40.4 MB written); ncu, one pass
+    "cpqr": {"bytes_per_launch": (583.9e6 + 14.1e6) / 212,
              "src": ["paper_1901_02971_gb300/csrc/cpqr_cluster.cuh", "paper_1901_02971_gb300/csrc/cpqr_reg.cuh"],
-             "sha256": ["354ec7fda5fb9373049b5f2a1946c215d720f4dd2c38934a2327d32eada75f44",
-                        "836df7b7d270b09faac01137e4b748a8b7b66bba747ef1eb9b66b4622ec27290"]},
-    "apply": {"bytes_per_launch": (2070.9e6 + 27.7e6) / 2, "src": "paper_1901_02971_gb300/csrc/solve_kernels.cuh",
-              "sha256": "d0f0fe613eb473dc7d77d8c65ee86cd5bf0c489ba06b3025e26d980cc3300dda"},
+             "sha256": ["70c5f5687cb1faaca31b30549d96136cb5fb766a4f5236057435ff4a20d2804e",
+                        "f4375f2638107797fe808912ff23db71eba06329efe4f946106ee94aebe58cd8"]},
+    "apply": {"bytes_per_launch": (3104.1e6 + 40.4e6) / 3, "src": "paper_1901_02971_gb300/csrc/solve_kernels.cuh",
+              "sha256": "6520881e8f0975871035275afc7fec1c110a1adcde70f8a412a4ef8d529d2dcf"},
 }
 
 

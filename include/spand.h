@@ -97,6 +97,19 @@ enum {
                            largest column; coloured order only */
 };
 
+/* the sparsification transform (Sec. 2.6; the variants compared in the
+ * ablation of Sec. 4.3) */
+enum {
+  SPAND_ORTHS = 0,  /* orthogonal transform after block scaling (Sec. 2.5,
+                       2.6.1): Algorithm 2 */
+  SPAND_INS = 1,    /* interpolative transform (Sec. 2.6.2) after block
+                       scaling: the column-pivoted QR of A_np picks the kept
+                       dofs c and T_cf = R_11^{-1} R_12 interpolates the
+                       others, f, which are then eliminated; the f block
+                       C_ff can fail to be positive definite (NOT_SPD) */
+  SPAND_IN = 2      /* the same without the block scaling */
+};
+
 typedef struct spand_handle_s* spand_handle;
 
 typedef struct {
@@ -110,10 +123,15 @@ typedef struct {
   int32_t sparsify_order; /* SPAND_COLOURED or SPAND_SIMULTANEOUS */
   int32_t compression;    /* SPAND_CPQR or SPAND_RANDOMIZED */
   uint64_t sketch_seed;   /* seed of the Gaussian sketches (SPAND_RANDOMIZED) */
+  int32_t variant;        /* SPAND_ORTHS, SPAND_INS or SPAND_IN; the
+                             interpolative ones need the coloured order and
+                             column-pivoted QR compression, and run their
+                             sparsification in FP64 in every precision */
 } spand_opts;
 
 /* Fills *opts with levels 8, eps 1e-2, skip 0, FP64, maxit 500, tol 1e-10,
- * coloured sparsification order, column-pivoted QR compression, sketch seed 0. */
+ * coloured sparsification order, column-pivoted QR compression, sketch seed 0,
+ * the OrthS variant. */
 void spand_default_opts(spand_opts* opts);
 
 /*

@@ -461,6 +461,38 @@ def sketch_philox(seed: int, step: int, cluster: int, m: int, ell: int) -> np.nd
     return rows.reshape(4 * nb, ell)[:m]
 
 
+def cpqr_exact(A: np.ndarray):
+    """Column-pivoted Householder QR with the column norms recomputed exactly
+    at every step (Businger and Golub, Numer. Math. 1965): step k moves the
+    remaining column of largest norm below row k to position k (lowest
+    original column index on ties) and reflects it onto e_k.  In exact
+    arithmetic this is geqp3's pivot sequence; geqp3 downdates its norm
+    estimates instead, so the two part ways at near ties.  Returns (Q, R, P)
+    with A[:, P] = Q R, Q square orthogonal, R upper triangular."""
+    A = np.array(A, dtype=np.float64, copy=True)
+    m, n = A.shape
+    P = np.arange(n)
+    Q = np.eye(m)
+    for k in range(min(m, n)):
+        nrm = (A[k:, k:] ** 2).sum(axis=0)
+        best = nrm.max()
+        j = k + int(np.argmin(np.where(nrm == best, P[k:], n)))  # lowest original index among the largest
+        A[:, [k, j]] = A[:, [j, k]]
+        P[[k, j]] = P[[j, k]]
+        x = A[k:, k]
+        nx = np.sqrt(nrm[j - k])
+        if nx == 0.0:
+            continue
+        beta = -nx if x[0] >= 0 else nx          # R_kk, sign opposite to the pivot entry
+        v = x / (x[0] - beta)
+        v[0] = 1.0
+        tau = (beta - x[0]) / beta
+        A[k:, k:] -= tau * np.outer(v, v @ A[k:, k:])
+        A[k + 1:, k] = 0.0
+        Q[:, k:] -= tau * np.outer(Q[:, k:] @ v, v)  # Q <- Q H_k
+    return Q, np.triu(A), P
+
+
 RAND_OVERSAMPLE = 10   # sketch columns beyond the rank (HMT 2011, Sec. 4.2)
 RAND_ELL0 = 32         # first sketch width; doubled while the rank saturates it
 
@@ -473,7 +505,10 @@ def sparsify_interface_rand(Apn: np.ndarray, eps: float, Omega: np.ndarray,
     Omega is an m x min(p, m) Gaussian test matrix (an input: the random
     numbers are drawn outside).  With ell = min(ell0, min(p, m)) sketch
     columns, Y = A_pn Omega[:, :ell] samples the range of A_pn and the
-    column-pivoted QR Y P = Q R orders an orthogonal basis Q (p x p) of it.
+    column-pivoted QR Y P = Q R orders an orthogonal basis Q (p x p) of it
+    (``cpqr_exact``: the column norms recomputed at every step, so that the
+    order of the basis -- which decides where the rank rule below stops --
+    is the largest-remaining-norm order itself, not geqp3's estimate of it).
     W = Q^T A_pn.  The rank follows the meaning of the truncation rule of
     Sec. 4: in a column-pivoted QR |R_kk| is the largest column norm of the
     part of A_pn outside the first k basis vectors, so here r = the first
@@ -496,7 +531,7 @@ def sparsify_interface_rand(Apn: np.ndarray, eps: float, Omega: np.ndarray,
     ell = min(ell0, ell_max)
     while True:
         Y = Apn @ Omega[:, :ell]
-        Q, _, _ = sla.qr(Y, pivoting=True, mode="full")
+        Q, _, _ = cpqr_exact(Y)
         W = Q.T @ Apn
         # res[k] = max_j ||W[k:, j]||, k = 0..ell
         tail = np.cumsum((W * W)[::-1], axis=0)[::-1]

@@ -33,6 +33,9 @@ SPAND_COLOURED = 0
 SPAND_SIMULTANEOUS = 1
 SPAND_CPQR = 0
 SPAND_RANDOMIZED = 1
+SPAND_ORTHS = 0
+SPAND_INS = 1
+SPAND_IN = 2
 
 # every function declared in include/spand.h
 EXPORTS = ["spand_default_opts", "spand_analyze", "spand_analyze_batch", "spand_factorize", "spand_solve", "spand_apply",
@@ -49,7 +52,8 @@ KERNEL_FAMILIES = ["potrf", "trsm", "schur", "cpqr", "copy", "apply", "pcg"]
 class Opts(C.Structure):
     _fields_ = [("levels", C.c_int32), ("eps", C.c_double), ("skip", C.c_int32),
                 ("precision", C.c_int32), ("maxit", C.c_int32), ("tol", C.c_double),
-                ("sparsify_order", C.c_int32), ("compression", C.c_int32), ("sketch_seed", C.c_uint64)]
+                ("sparsify_order", C.c_int32), ("compression", C.c_int32), ("sketch_seed", C.c_uint64),
+                ("variant", C.c_int32)]
 
 
 class Problem(C.Structure):

@@ -253,8 +253,11 @@ __device__ __forceinline__ void cq_finish(const CpqrTask<T>& d, cg::cluster_grou
     const int cc = j0 + jl - cstart[e];
     for (int i = 0; i < r; ++i) nb.Rq[cc + (size_t)(nb.off_qp + i) * nb.ldq] = wval(jl, i);
   }
-  // A_cc = I: column j by warp j of the cluster, lanes over rows
-  for (int j = rank * NW + warp; j < r; j += C * NW) {
+  // A_cc = I: column j by warp j of the cluster, lanes over rows (not with
+  // nowb: the block row is then left as it is -- its scaled diagonal block
+  // is I already, or it is the sketch of the randomized compression, whose
+  // leading columns the next, wider round reuses)
+  for (int j = rank * NW + warp; j < (d.nowb ? 0 : r); j += C * NW) {
     T* dst = d.Rp + (size_t)j * d.ldp;
     for (int i = lane; i < r; i += 32) dst[i] = (i == j) ? T(1) : T(0);
   }

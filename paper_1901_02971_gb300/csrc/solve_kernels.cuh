@@ -5,6 +5,9 @@
 //   E_s: r_s <- U_s^{-T} r_s, r_n <- r_n - X_ns r_s        (Sec. 2.4)
 //   S_p: r_p <- U_p^{-T} r_p                               (Sec. 2.5)
 //   Q_p^T: c <- Q_pc^T r_p, fine part left in place        (Sec. 2.6.1)
+// or, for the interpolative variants (Sec. 2.6.2), T_p^T: r_f <- r_f -
+// T_cf^T r_c followed by the elimination of f, both elimination ops (the
+// first with U = I and X^T = T_cf),
 // and the backward sweep (root -> leaf) the transposes in reverse order.  The
 // sparsification transform is kept as the explicit coarse basis Q_pc: since
 // the fine dofs are identity in M^T A M, Q_p [c; f] = r_p + Q_pc (c - c_old)
@@ -23,8 +26,10 @@ constexpr int AT = 256;  // threads per CTA of the apply kernels
 
 template <typename TF>
 struct ElimOp {
-  const TF* R;       // [U_s | X^T], ns x (ns + m), leading dimension ld >= ns
-  const TF* Y;       // U_s^{-T} (lower, ns x ns, ld = ns)
+  const TF* XT;      // X^T, ns x m, leading dimension ld >= ns (the right part of s's
+                     // block row [U_s | X^T]; T_cf for an interpolation transform)
+  const TF* Y;       // U_s^{-T} (lower, ns x ns, ld = ns); nullptr: U_s = I (the
+                     // interpolation transform T_p of Sec. 2.6.2)
   int32_t ns, m, ld, pad;
   int64_t slot;      // ns slots of s, then m slots of the neighbour columns
   int64_t ty, tu, ta;  // temp offsets: y_s (ns), u = X_ns y_s (m), backward acc (ns)
@@ -266,8 +271,8 @@ __device__ __forceinline__ void prefetch_first_item(const ApplyPhase<TF>& P) {
     ld = (size_t)o.ns;
     rows = o.ns;
     if (P.kind == PH_FY) { A = o.Y; rowblock = true; lo = it.first; cols = min(o.ns, it.first + RB); nsl = cols; }
-    else if (P.kind == PH_BA) { A = o.R + (size_t)o.ld * o.ns; ld = (size_t)o.ld; rowblock = true; lo = it.first; cols = o.m; sl += o.ns; nsl = o.m; }
-    else if (P.kind == PH_FU) { A = o.R + (size_t)o.ld * o.ns; ld = (size_t)o.ld; rowblock = false; lo = it.first; cols = min(o.m - it.first, AP_COLS); nsl = 0; }
+    else if (P.kind == PH_BA) { A = o.XT; ld = (size_t)o.ld; rowblock = true; lo = it.first; cols = o.m; sl += o.ns; nsl = o.m; }
+    else if (P.kind == PH_FU) { A = o.XT; ld = (size_t)o.ld; rowblock = false; lo = it.first; cols = min(o.m - it.first, AP_COLS); nsl = 0; }
     else { A = o.Y; rowblock = false; lo = it.first; cols = min(o.ns - it.first, AP_COLS); nsl = cols + it.first; }
   } else {
     const SqOp<TF> o = P.sq[it.op];
@@ -330,13 +335,17 @@ __global__ void __launch_bounds__(AT) k_apply(const ApplyPhase<TF>* __restrict__
         if (P.kind == PH_FY || P.kind == PH_BA || P.kind == PH_FU || P.kind == PH_BX) {
           const ElimOp<TF> o = P.elim[it.op];
           const int32_t* sl = P.slots + o.slot;
-          const TF* XT = o.R + (size_t)o.ld * o.ns;
+          const TF* XT = o.XT;
           if (P.kind == PH_FY) {
-            const int K = min(o.ns, it.first + RB);
-            const ACC v = rowblock_gemv<TF, ACC>(o.Y, (size_t)o.ns, it.first, o.ns, K,
-                                                 [&](int k) { return ldv(x + sl[k]); }, vs, part);
             const int i = it.first + lane;
-            if (warp == 0 && i < o.ns) tmp[o.ty + i] = (double)v;
+            if (!o.Y) {
+              if (warp == 0 && i < o.ns) tmp[o.ty + i] = ldv(x + sl[i]);
+            } else {
+              const int K = min(o.ns, it.first + RB);
+              const ACC v = rowblock_gemv<TF, ACC>(o.Y, (size_t)o.ns, it.first, o.ns, K,
+                                                   [&](int k) { return ldv(x + sl[k]); }, vs, part);
+              if (warp == 0 && i < o.ns) tmp[o.ty + i] = (double)v;
+            }
           } else if (P.kind == PH_BA) {
             const ACC v = rowblock_gemv<TF, ACC>(XT, (size_t)o.ld, it.first, o.ns, o.m,
                                                  [&](int k) { return ldv(x + sl[o.ns + k]); }, vs, part);
@@ -346,6 +355,8 @@ __global__ void __launch_bounds__(AT) k_apply(const ApplyPhase<TF>* __restrict__
             coldot_gemv<TF, ACC>(XT, (size_t)o.ld, o.ns, it.first, min(o.m, it.first + AP_COLS), false,
                                  [&](int i) { return ldv(tmp + o.ty + i); },
                                  [&](int j, ACC v) { tmp[o.tu + j] = (double)v; }, vs);
+          } else if (!o.Y) {  // PH_BX, U_s = I
+            for (int j = it.first + threadIdx.x; j < min(o.ns, it.first + AP_COLS); j += AT) x[sl[j]] = ldv(tmp + o.ta + j);
           } else {  // PH_BX
             coldot_gemv<TF, ACC>(o.Y, (size_t)o.ns, o.ns, it.first, min(o.ns, it.first + AP_COLS), true,
                                  [&](int i) { return ldv(tmp + o.ta + i); },

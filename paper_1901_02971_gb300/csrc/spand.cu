@@ -28,6 +28,7 @@
 #include "factor_kernels.cuh"
 #include "schur_tc.cuh"
 #include "schur_tma.cuh"
+#include "sparsify_interp.cuh"
 #include "sparsify_rand.cuh"
 #include "sparsify_sim.cuh"
 #include "sketch.cuh"
@@ -426,6 +427,7 @@ struct spand_handle_s {
   DevBuf d_vec, d_tmp, d_save, d_bin, d_bout;
   DevBuf d_piv64;  // FP64 copies of the pivot blocks of FP32 factors (scratch)
   DevBuf d_rand;   // sketches, products and state of the randomized compression (scratch)
+  DevBuf d_interp; // Gram matrices, R rows and pivot orders of the interpolative variants (scratch)
   DevBuf d_rowptr, d_colind;  // original CSR pattern (gradient on A's pattern)
   int fprec = -1;
   bool factored = false;
@@ -1014,7 +1016,9 @@ static std::vector<int> sparsify_randomized(spand_handle h, int t, const std::ve
       std::map<std::tuple<int, int, int>, std::vector<int32_t>> groups;  // (C, resident, threads) -> tasks
       std::map<std::tuple<int, int, int>, size_t> gsmem;
       for (int k : alist) {
-        const int np = std::max(rt[k].np, 1), cols = std::max(ub[k], 1);
+        // sized for the task's column bound vt.m_max, from which the kernel
+        // lays out its shared memory (not for this round's width ub[k] <= it)
+        const int np = std::max(rt[k].np, 1), cols = std::max(vt[k].m_max, 1);
         const size_t Lp = (size_t)cq_ld<T>(np);
         auto res_smem = [&](int cc) {
           const int cp = (cols + cc - 1) / cc;
@@ -1109,6 +1113,378 @@ static std::vector<int> sparsify_randomized(spand_handle h, int t, const std::ve
     h->prof.launches += nl + 1;
   }
   return ell_final;
+}
+
+// Result of the interpolative sparsification of one interface.
+template <typename T>
+struct InterpOut {
+  int p = -1, r = 0, nf = 0, ldf = 0;
+  std::vector<int32_t> perm;  // c (pivot order), then f (increasing)
+  const T* F = nullptr;       // [U_f | X_fc] after the elimination of f (ld ldf)
+  const T* XT = nullptr;      // T_cf (r x nf, ld r)
+  const T* Yf = nullptr;      // U_f^{-T} (nf x nf)
+};
+
+// Interpolative sparsification (SPAND_INS / SPAND_IN) of the interfaces of
+// one step, colour by colour (the method and its kernels are described in
+// sparsify_interp.cuh).  Per colour: the Gram matrices, their truncated
+// pivoted Cholesky with T_cf, and A_pp[perm, perm]; the host then reads the
+// ranks and pivot orders (one synchronisation per colour: every later launch
+// is shaped by them), forms C_cf and C_ff, gathers the kept blocks, and
+// eliminates f with the pivot Cholesky / block-row solve / Schur kernels of
+// the elimination.  hsz: the current cluster sizes (updated); d_finfo: one
+// non-positive-pivot flag per colour; fcls[c]: the interface of each entry of
+// colour c's pivot batch.
+template <typename T>
+static std::vector<InterpOut<T>> sparsify_interp(spand_handle h, const std::vector<CpqrTask<T>>& tasks,
+                                                 const std::vector<int>& tcolour, int ncol,
+                                                 const std::vector<CpqrNbr<T>>& nbrs, std::vector<int32_t>& hsz,
+                                                 int32_t* d_cur, int* d_finfo, std::vector<std::vector<int>>& fcls,
+                                                 double eps, cudaStream_t s) {
+  const size_t ntk = tasks.size();
+  std::vector<InterpOut<T>> out(ntk);
+  fcls.assign(std::max(ncol, 1), {});
+  if (ntk == 0) return out;
+  // scratch: per task G, Rw, P (np^2 doubles each), the coupling copies
+  // (2 np m_max), the column map (m_max); perms and ranks contiguous per colour
+  struct Off { size_t g, rw, p, cp, tcol; int64_t perm; };
+  std::vector<Off> off(ntk);
+  size_t bytes = 0;
+  int64_t nperm = 0;
+  std::vector<std::vector<int>> ids(std::max(ncol, 1));
+  for (size_t i = 0; i < ntk; ++i) ids[std::max(tcolour[i], 0)].push_back((int)i);
+  for (const auto& col : ids)
+    for (int i : col) {
+      const size_t np = (size_t)std::max(tasks[i].np, 1), mm = (size_t)std::max(tasks[i].m_max, 1);
+      off[i].g = bytes; bytes += align256(np * np * sizeof(double));
+      off[i].rw = bytes; bytes += align256(np * np * sizeof(double));
+      off[i].p = bytes; bytes += align256(np * np * sizeof(double));
+      off[i].cp = bytes; bytes += align256(2 * np * mm * sizeof(T));
+      off[i].tcol = bytes; bytes += align256(mm * sizeof(int32_t));
+      off[i].perm = nperm;
+      nperm += tasks[i].np;
+    }
+  const size_t operm = bytes;
+  bytes += align256((size_t)std::max<int64_t>(nperm, 1) * sizeof(int32_t));
+  const size_t orank = bytes;
+  bytes += align256(ntk * sizeof(int32_t));
+  char* base = (char*)h->d_interp.ensure(bytes);
+  int32_t* d_perm = (int32_t*)(base + operm);
+  int32_t* d_rank = (int32_t*)(base + orank);
+  Packer pkn;
+  const size_t onb = pkn.add(nbrs);
+  const CpqrNbr<T>* d_nbrs = at<const CpqrNbr<T>>(upload<T>(h, pkn, s), onb);
+  int32_t* hbuf = (int32_t*)h->stage.take((size_t)(nperm + (int64_t)ntk) * sizeof(int32_t) + 256);
+  int64_t rank_slot = 0;  // ranks are stored in colour order too
+  for (int c = 0; c < (int)ids.size(); ++c) {
+    const std::vector<int>& col = ids[c];
+    const int nc = (int)col.size();
+    if (nc == 0) continue;
+    const int pid = h->prof.begin(F_CPQR, s);
+    int64_t nl = 0;
+    double fl = 0, by = 0;
+    std::vector<InterpTask<T>> it(nc);
+    std::vector<int32_t> tcol;
+    std::vector<size_t> tcol_at(nc);
+    std::vector<InterpTile> gtiles;
+    int npmax = 1;
+    for (int k = 0; k < nc; ++k) {
+      const CpqrTask<T>& tk = tasks[col[k]];
+      const Off& o = off[col[k]];
+      InterpTask<T> d{};
+      d.Rp = tk.Rp;
+      d.G = (double*)(base + o.g);
+      d.Rw = (double*)(base + o.rw);
+      d.P = (double*)(base + o.p);
+      d.cp = (T*)(base + o.cp);
+      d.perm = d_perm + o.perm;
+      d.rank = d_rank + rank_slot + k;
+      d.p = tk.p;
+      d.np = tk.np;
+      d.ldp = tk.ldp;
+      d.nbeg = tk.nbeg;
+      d.nend = tk.nend;
+      tcol_at[k] = tcol.size();
+      for (int32_t e = tk.nbeg; e < tk.nend; ++e)
+        for (int32_t jj = 0; jj < hsz[nbrs[e].q]; ++jj) tcol.push_back(nbrs[e].off_pq + jj);
+      d.m = (int32_t)(tcol.size() - tcol_at[k]);
+      it[k] = d;
+      npmax = std::max(npmax, tk.np);
+      const int nt = (tk.np + 31) / 32;
+      for (int ti = 0; ti < nt; ++ti)
+        for (int tj = ti; tj < nt; ++tj) gtiles.push_back({k, 32 * ti, 32 * tj});
+      const double np_ = tk.np, m_ = d.m;
+      fl += np_ * np_ * m_;
+      by += (np_ * m_ * sizeof(T) + 3.0 * np_ * np_ * sizeof(double));
+    }
+    {  // the column maps first, then the tasks that point into them
+      Packer pk;
+      const size_t ot = pk.add(tcol);
+      char* d = (char*)upload<T>(h, pk, s);
+      for (int k = 0; k < nc; ++k) it[k].tcol = d ? at<const int32_t>(d, ot) + tcol_at[k] : nullptr;
+    }
+    Packer pk;
+    const size_t oi = pk.add(it), og = pk.add(gtiles);
+    void* dd = upload<T>(h, pk, s);
+    const InterpTask<T>* d_it = at<const InterpTask<T>>(dd, oi);
+    if (!gtiles.empty()) {
+      k_interp_gram<T><<<(unsigned)gtiles.size(), 256, 0, s>>>(d_it, at<const InterpTile>(dd, og));
+      CKLAUNCH();
+      ++nl;
+    }
+    const size_t fsm = (size_t)npmax * (sizeof(double) + sizeof(int));
+    ensure_smem((const void*)k_interp_factor<T>, fsm);
+    k_interp_factor<T><<<nc, 256, fsm, s>>>(d_it, eps);
+    CKLAUNCH();
+    k_interp_gather_pp<T><<<dim3(16, nc), 256, 0, s>>>(d_it);
+    CKLAUNCH();
+    nl += 2;
+    // ranks and pivot orders of the colour
+    const int64_t p0 = off[col[0]].perm;
+    int64_t pn = 0;
+    for (int k = 0; k < nc; ++k) pn += tasks[col[k]].np;
+    CK(cudaMemcpyAsync(hbuf, d_perm + p0, (size_t)pn * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hbuf + pn, d_rank + rank_slot, (size_t)nc * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<DGemmTask> g12, g3;
+    std::vector<DGemmTile> t12, t3;
+    std::vector<RowDesc<T>> ident, diag;
+    std::vector<TrsmTask<T>> tr;
+    std::vector<SchurBlock<T>> sblk;
+    std::vector<SchurContrib<T>> scon;
+    std::vector<SchurTile> stiles;
+    for (int k = 0; k < nc; ++k) {
+      InterpTask<T>& d = it[k];
+      InterpOut<T>& o = out[col[k]];
+      const int r = hbuf[pn + k];
+      if (r < 0 || r > d.np) throw Fail{SPAND_ERR_STATE, "interpolative sparsification: rank out of range"};
+      const int nf = d.np - r;
+      o.p = d.p;
+      o.r = r;
+      o.nf = nf;
+      o.perm.assign(hbuf + (off[col[k]].perm - p0), hbuf + (off[col[k]].perm - p0) + d.np);
+      d.r = r;
+      d.nf = nf;
+      d.ldf = row_ld(nf);
+      o.ldf = d.ldf;
+      if (nf > 0) {
+        const size_t fb = (size_t)d.ldf * d.np * sizeof(T);
+        T* F = (T*)h->persist.alloc(fb);
+        CK(cudaMemsetAsync(F, 0, fb, s));
+        d.F = F;
+        o.F = F;
+        if (r > 0) {
+          d.XT = (T*)h->persist.alloc((size_t)r * nf * sizeof(T));
+          o.XT = d.XT;
+        }
+        T* Yf = (T*)h->persist.alloc((size_t)nf * nf * sizeof(T));
+        o.Yf = Yf;
+        T* dv = alloc_dinv<T>(h, nf);
+        ident.push_back({Yf, nf, nf, nullptr, 0, 0});
+        diag.push_back({F, nf, d.ldf, dv, 0, 0});
+        fcls[c].push_back(d.p);
+        add_panels(tr, F, (const T*)dv, nf, d.ldf, nf, d.np);
+        add_inverse(tr, (const T*)F, (const T*)dv, nf, d.ldf, Yf);
+        if (r > 0) {
+          const int np = d.np;
+          double* Tt = d.G;
+          const int b1 = (int)g12.size();
+          g12.push_back({d.P, Tt, d.P + (size_t)r * np, np, nf, np, 0, 1, r, nf, r});           // C_cf
+          g12.push_back({d.P + r, Tt, d.P + r + (size_t)r * np, np, nf, np, 0, 1, nf, nf, r});  // A_ff - A_fc T
+          g3.push_back({Tt, d.P + (size_t)r * np, d.P + r + (size_t)r * np, nf, np, np, 0, 0, nf, nf, r});
+          for (int i0 = 0; i0 < r; i0 += 64)
+            for (int j0 = 0; j0 < nf; j0 += 64) t12.push_back({b1, i0, j0});
+          for (int i0 = 0; i0 < nf; i0 += 64)
+            for (int j0 = 0; j0 < nf; j0 += 64) {
+              t12.push_back({b1 + 1, i0, j0});
+              t3.push_back({(int32_t)g3.size() - 1, i0, j0});
+            }
+          // A_cc -= X_fc^T X_fc
+          SchurBlock<T> bl{};
+          bl.C1 = d.Rp;
+          bl.C2 = nullptr;
+          bl.ld1 = d.ldp;
+          bl.ld2 = d.ldp;
+          bl.rows = r;
+          bl.cols = r;
+          bl.cbeg = (int32_t)scon.size();
+          SchurContrib<T> sc{};
+          sc.Xa = F + (size_t)nf * d.ldf;
+          sc.Xb = sc.Xa;
+          sc.lds = d.ldf;
+          sc.ns = nf;
+          sc.owner = d.p;
+          scon.push_back(sc);
+          bl.cend = (int32_t)scon.size();
+          for (int i0 = 0; i0 < r; i0 += TB)
+            for (int j0 = 0; j0 < r; j0 += TB) stiles.push_back({(int32_t)sblk.size(), i0, j0});
+          sblk.push_back(bl);
+          const double rr = r, ff = nf;
+          fl += 2 * rr * rr * ff + 4 * ff * ff * rr;
+        }
+        const double rr = r, ff = nf;
+        fl += ff * ff * ff / 3 + ff * ff * rr + ff * rr * rr;
+      }
+      {
+        const double rr = r, np_ = d.np;
+        fl += rr * rr * np_ - 2 * rr * rr * rr / 3 + nf * rr * rr;  // pivoted Cholesky, T_cf
+      }
+      h->st.mem_f += (int64_t)r * nf * 2 + (int64_t)nf * (nf + 1) / 2;
+      hsz[d.p] = r;
+    }
+    rank_slot += nc;
+    {
+      Packer pk2;
+      const size_t oi2 = pk2.add(it);
+      const size_t oa = pk2.add(g12), ota = pk2.add(t12), ob = pk2.add(g3), otb = pk2.add(t3);
+      void* d2 = upload<T>(h, pk2, s);
+      if (!t12.empty()) {
+        k_dgemm_sub<<<(unsigned)t12.size(), 256, 0, s>>>(at<const DGemmTask>(d2, oa), at<const DGemmTile>(d2, ota));
+        CKLAUNCH();
+        ++nl;
+      }
+      if (!t3.empty()) {
+        k_dgemm_sub<<<(unsigned)t3.size(), 256, 0, s>>>(at<const DGemmTask>(d2, ob), at<const DGemmTile>(d2, otb));
+        CKLAUNCH();
+        ++nl;
+      }
+      k_interp_store<T><<<nc, 256, 0, s>>>(at<const InterpTask<T>>(d2, oi2), d_nbrs, d_cur);
+      CKLAUNCH();
+      ++nl;
+    }
+    h->st.factor_flops += fl;
+    h->prof.launches += nl;
+    h->prof.end(pid, s, fl, by, nl);
+    // eliminate f: C_ff = U_f^T U_f, X_fc = U_f^{-T} C_fc, Y_f = U_f^{-T},
+    // then A_cc -= X_fc^T X_fc
+    set_identity<T>(h, ident, s);
+    pivot_chol<T>(h, diag, d_finfo + c, s);
+    trsm_batch<T>(h, tr, s);
+    if (!stiles.empty()) {
+      Packer pk3;
+      const size_t ob = pk3.add(sblk), oc = pk3.add(scon), ot = pk3.add(stiles);
+      void* d3 = upload<T>(h, pk3, s);
+      const int spid = h->prof.begin(F_SCHUR, s);
+      k_schur<T><<<(unsigned)stiles.size(), NT, 0, s>>>(at<const SchurTile>(d3, ot), at<const SchurBlock<T>>(d3, ob),
+                                                       at<const SchurContrib<T>>(d3, oc));
+      CKLAUNCH();
+      h->prof.launches += 1;
+      double bfl = 0, bby = 0;
+      for (const auto& bl : sblk) {
+        const double ns = scon[bl.cbeg].ns;
+        bfl += 2.0 * bl.rows * bl.cols * ns;
+        bby += ((double)(bl.rows + bl.cols) * ns + 2.0 * bl.rows * bl.cols) * sizeof(T);
+      }
+      h->prof.end(spid, s, bfl, bby, 1);
+    }
+  }
+  return out;
+}
+
+// The subtractions x_v -= tmp[k] of an elimination phase's scatter, grouped
+// by target slot v (appended to tslot / tptr / tidx): a stable counting sort,
+// so each target's sources stay in op order (the fixed summation order).
+static void group_by_target(int64_t n, const std::vector<std::pair<int32_t, int64_t>>& tgt,
+                            std::vector<int32_t>& tslot, std::vector<int64_t>& tptr, std::vector<int64_t>& tidx) {
+  std::vector<int64_t> head((size_t)n + 1, 0);
+  for (const auto& e : tgt) ++head[(size_t)e.first + 1];
+  for (int64_t v = 0; v < n; ++v) head[v + 1] += head[v];
+  std::vector<int64_t> byslot(tgt.size());
+  for (size_t i = 0; i < tgt.size(); ++i) byslot[head[tgt[i].first]++] = tgt[i].second;
+  // head[v] is now the end of slot v's run
+  tidx.reserve(tidx.size() + tgt.size());
+  int64_t b = 0;
+  for (int64_t v = 0; v < n; ++v) {
+    const int64_t e = head[v];
+    if (e == b) continue;
+    tslot.push_back((int32_t)v);
+    for (int64_t k = b; k < e; ++k) tidx.push_back(byslot[k]);
+    tptr.push_back((int64_t)tidx.size());
+    b = e;
+  }
+}
+
+// One elimination op of the apply given by its factor blocks and slot lists:
+// s (ns slots) is eliminated against n (m slots).
+template <typename T>
+struct ElimSpec {
+  const T* XT;  // X^T, ns x m, leading dimension ld
+  const T* Y;   // U_s^{-T} (ns x ns, ld ns), or nullptr for U_s = I
+  int32_t ld;
+  std::vector<int32_t> s_slots, n_slots;
+};
+
+// A phase group of the apply made of elimination ops only (its temporaries
+// start at 0: the phases of one group are separated from every other
+// group's by grid barriers, and nothing in tmp outlives a sweep through a
+// group).  Uploaded to the persistent arena.
+template <typename T>
+static ApplyStep<T> make_elim_step(spand_handle h, const std::vector<ElimSpec<T>>& specs, cudaStream_t s) {
+  std::vector<ElimOp<T>> eops;
+  std::vector<int32_t> aslots, tslot;
+  std::vector<int64_t> tptr(1, 0), tidx;
+  std::vector<std::pair<int32_t, int64_t>> tgt;
+  std::vector<ApplyItem> fy, fu, ba, bx;
+  int64_t tmp_off = 0;
+  for (const ElimSpec<T>& sp : specs) {
+    ElimOp<T> o{};
+    o.XT = sp.XT;
+    o.Y = sp.Y;
+    o.ld = sp.ld;
+    o.ns = (int32_t)sp.s_slots.size();
+    o.m = (int32_t)sp.n_slots.size();
+    if (o.ns == 0) continue;
+    o.slot = (int64_t)aslots.size();
+    o.ty = tmp_off;
+    o.tu = tmp_off + o.ns;
+    o.ta = tmp_off + o.ns + o.m;
+    const int32_t op = (int32_t)eops.size();
+    aslots.insert(aslots.end(), sp.s_slots.begin(), sp.s_slots.end());
+    aslots.insert(aslots.end(), sp.n_slots.begin(), sp.n_slots.end());
+    for (int32_t i = 0; i < o.ns; ++i) {  // x_s = y_s
+      tslot.push_back(sp.s_slots[i]);
+      tidx.push_back(o.ty + i);
+      tptr.push_back((int64_t)tidx.size());
+    }
+    for (int32_t k = 0; k < o.m; ++k) tgt.push_back({sp.n_slots[k], o.tu + k});
+    for (int32_t r0 = 0; r0 < o.ns; r0 += RB) {
+      fy.push_back({op, r0});
+      ba.push_back({op, r0});
+    }
+    for (int32_t c0 = 0; c0 < o.m; c0 += AP_COLS) fu.push_back({op, c0});
+    for (int32_t c0 = 0; c0 < o.ns; c0 += AP_COLS) bx.push_back({op, c0});
+    tmp_off += 2 * (int64_t)o.ns + o.m;
+    eops.push_back(o);
+  }
+  ApplyStep<T> ap;
+  if (eops.empty()) return ap;
+  h->tmp_len = std::max(h->tmp_len, tmp_off);
+  const int64_t nassign = (int64_t)tslot.size();
+  group_by_target(h->n, tgt, tslot, tptr, tidx);
+  Packer pk;
+  const size_t oe = pk.add(eops), osl = pk.add(aslots), ots = pk.add(tslot), otp = pk.add(tptr), oti = pk.add(tidx);
+  const size_t ofy = pk.add(fy), ofu = pk.add(fu), oba = pk.add(ba), obx = pk.add(bx);
+  void* d = h->persist.alloc(pk.buf.size());
+  void* src = h->stage.take(pk.buf.size());
+  std::memcpy(src, pk.buf.data(), pk.buf.size());
+  CK(cudaMemcpyAsync(d, src, pk.buf.size(), cudaMemcpyHostToDevice, s));
+  ap.n_elim = (int)eops.size();
+  ap.elim = at<const ElimOp<T>>(d, oe);
+  ap.slots = at<const int32_t>(d, osl);
+  ap.ntgt = (int64_t)tslot.size();
+  ap.nassign = nassign;
+  ap.tslot = at<const int32_t>(d, ots);
+  ap.tptr = at<const int64_t>(d, otp);
+  ap.tidx = at<const int64_t>(d, oti);
+  ap.n_fy = (int)fy.size();
+  ap.n_fu = (int)fu.size();
+  ap.n_ba = (int)ba.size();
+  ap.n_bx = (int)bx.size();
+  ap.fy = at<const ApplyItem>(d, ofy);
+  ap.fu = at<const ApplyItem>(d, ofu);
+  ap.ba = at<const ApplyItem>(d, oba);
+  ap.bx = at<const ApplyItem>(d, obx);
+  return ap;
 }
 
 // The apply program: the phases of every step in execution order (forward
@@ -1208,22 +1584,38 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
   // scaling pivots ([0]: a bounded device wait gave up);
   // read at the next host synchronisation (the rank readback of a
   // sparsifying step, or the end of the factorization)
-  int* d_info = (int*)h->descs.alloc(2 * (size_t)(L + 1) * sizeof(int));
-  CK(cudaMemsetAsync(d_info, 0, 2 * (size_t)(L + 1) * sizeof(int), s));
+  // (then, for the interpolative variants, one flag per step and colour for
+  // the f blocks C_ff)
+  int maxcol = 1;
+  for (const StepStruct& sx : tr.steps) maxcol = std::max(maxcol, sx.ncolours());
+  const size_t ninfo = 2 * (size_t)(L + 1) + (size_t)(L + 1) * maxcol;
+  int* d_info = (int*)h->descs.alloc(ninfo * sizeof(int));
+  CK(cudaMemsetAsync(d_info, 0, ninfo * sizeof(int), s));
   std::vector<std::vector<int>> elim_cls(L + 1), scale_cls(L + 1);  // cluster of each pivot-batch entry
+  std::vector<std::vector<std::vector<int>>> f_cls(L + 1);           // per step and colour: the f blocks' interfaces
   auto check_pivots = [&](int upto) {  // after a stream synchronisation
-    std::vector<int> info(2 * (size_t)(L + 1), 0);
+    std::vector<int> info(ninfo, 0);
     CK(cudaMemcpy(info.data(), d_info, info.size() * sizeof(int), cudaMemcpyDeviceToHost));
     if (info[0])
       throw Fail{SPAND_ERR_TIMEOUT, "Schur update: a bounded tensor-core wait (MMA completion or operand "
                                     "copy) timed out"};
-    for (int u = 1; u <= upto; ++u)
+    for (int u = 1; u <= upto; ++u) {
       if (info[2 * u] || info[2 * u + 1]) {
         stt.fail_step = u;
         stt.fail_cluster = info[2 * u] ? elim_cls[u][info[2 * u] - 1] : scale_cls[u][info[2 * u + 1] - 1];
         throw Fail{SPAND_ERR_NOT_SPD, std::string(info[2 * u] ? "pivot" : "interface") +
                                           " block not positive definite at step " + std::to_string(u)};
       }
+      for (int c = 0; c < (int)f_cls[u].size() && c < maxcol; ++c) {
+        const int v = info[2 * (size_t)(L + 1) + (size_t)u * maxcol + c];
+        if (v) {
+          stt.fail_step = u;
+          stt.fail_cluster = f_cls[u][c][v - 1];
+          throw Fail{SPAND_ERR_NOT_SPD, "interpolative sparsification: block C_ff not positive definite at step " +
+                                            std::to_string(u)};
+        }
+      }
+    }
   };
 
   const int nc0 = (int)tr.cluster_ptr.size() - 1;
@@ -1458,7 +1850,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       for (int sidx : seps) {
         if (sz[sidx] <= 0) continue;
         ElimOp<T> o{};
-        o.R = lay.row[sidx];
+        o.XT = lay.row[sidx] + (size_t)lay.ld[sidx] * sz[sidx];
         o.ld = lay.ld[sidx];
         o.Y = ysep[sidx];
         o.ns = sz[sidx];
@@ -1496,24 +1888,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       }
       h->tmp_len = std::max(h->tmp_len, tmp_off);
       nassign = (int64_t)tslot.size();
-      // group the subtractions by target slot: a stable counting sort, so each
-      // target's sources stay in op order (the fixed summation order)
-      std::vector<int64_t> head((size_t)h->n + 1, 0);
-      for (const auto& e : tgt) ++head[(size_t)e.first + 1];
-      for (int64_t v = 0; v < h->n; ++v) head[v + 1] += head[v];
-      std::vector<int64_t> byslot(tgt.size());
-      for (size_t i = 0; i < tgt.size(); ++i) byslot[head[tgt[i].first]++] = tgt[i].second;
-      // head[v] is now the end of slot v's run
-      tidx.reserve(tidx.size() + tgt.size());
-      int64_t b = 0;
-      for (int64_t v = 0; v < h->n; ++v) {
-        const int64_t e = head[v];
-        if (e == b) continue;
-        tslot.push_back((int32_t)v);
-        for (int64_t k = b; k < e; ++k) tidx.push_back(byslot[k]);
-        tptr.push_back((int64_t)tidx.size());
-        b = e;
-      }
+      group_by_target(h->n, tgt, tslot, tptr, tidx);
       elim_ops_built = true;
     };
 
@@ -1527,6 +1902,10 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
     const bool sparsify = (skip < t) && (t < L);
     int cpqr_pid = -1;
     std::vector<int> ell_fin;              // randomized compression: final sketch width per task
+    std::vector<InterpOut<T>> interp_out;  // interpolative variants: per task
+    std::vector<std::vector<int32_t>> kept_slots(n);  // and the slots each interface keeps
+    std::vector<char> has_kept(n, 0);
+    std::vector<ApplyStep<T>> interp_steps;  // their apply groups: T_p ops, then the eliminations of f
     std::vector<int> cp_cluster;           // sparsified clusters (task order)
     std::vector<T*> cp_qc;                 // their Q_pc scratch
     if (sparsify) {
@@ -1536,7 +1915,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       std::vector<CopyTask<T>> m_up, m_lo;
       std::vector<RowDesc<T>> idr;
       for (int p : rems) {
-        if (sz[p] <= 0) continue;
+        if (sz[p] <= 0 || h->opts.variant == SPAND_IN) continue;  // In: no block scaling
         T* dv = alloc_dinv<T>(h, sz[p]);
         diag.push_back({lay.row[p], sz[p], lay.ld[p], dv});
         diag_cl.push_back(p);
@@ -1602,6 +1981,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       // same matrix; ranks go to d_rank so that the sizes the kernels read
       // (d_cur) stay those of the scaled matrix until the launch is over
       const bool sim = h->opts.sparsify_order == SPAND_SIMULTANEOUS;
+      const bool interp = h->opts.variant != SPAND_ORTHS;
       int32_t* d_rank = nullptr;
       if (sim) {
         d_rank = (int32_t*)h->descs.alloc((size_t)n * sizeof(int32_t));
@@ -1658,7 +2038,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         for (int c = 1; c <= max_cluster; c *= 2)
           if (res_smem(c) <= CB) { C = c; break; }
         while (C < max_cluster && (mm + C - 1) / C > 2 * CQ_MAXNT) C *= 2;
-        if ((mm + C - 1) / C > CQ_CPT * CQ_MAXNT)
+        if (!interp && (mm + C - 1) / C > CQ_CPT * CQ_MAXNT)
           throw Fail{SPAND_ERR_INVALID_ARG, "interface coupling too wide for the sparsification kernel (" +
                                                 std::to_string(mm) + " columns)"};
         const bool resident = res_smem(C) <= CB;
@@ -1668,7 +2048,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         w.tau = wbytes; wbytes += align256((size_t)sz[p] * sizeof(T));
         w.qc = wbytes; wbytes += align256((size_t)sz[p] * sz[p] * sizeof(T));
         w.gw = wbytes;
-        if (!resident) wbytes += align256((size_t)C * Lp * ((mm + C - 1) / C) * sizeof(T));
+        if (!resident && !interp) wbytes += align256((size_t)C * Lp * ((mm + C - 1) / C) * sizeof(T));
         woff.push_back(w);
         tasks.push_back(tk);
         tclass.push_back(C);
@@ -1680,7 +2060,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       // clusters run on that kernel (FP32 factors only): its reflector steps
       // are cheaper, but its CTAs fill whole SMs, so a colour that would need
       // a second wave keeps the chunked kernel.
-      if (sizeof(T) == 4 && !tasks.empty()) {
+      if (sizeof(T) == 4 && !tasks.empty() && !interp) {
         std::vector<int> rg(tasks.size(), 0), rc(tasks.size(), 0);
         for (size_t i = 0; i < tasks.size(); ++i) {
           int G = 1;
@@ -1729,15 +2109,21 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
           }
       }
       if (!tasks.empty()) {
-        char* wb = (char*)h->scratch[(t + 1) & 1].ensure(wbytes);
-        for (size_t i = 0; i < tasks.size(); ++i) {
+        char* wb = interp ? nullptr : (char*)h->scratch[(t + 1) & 1].ensure(wbytes);
+        for (size_t i = 0; i < tasks.size() && wb; ++i) {
           tasks[i].V = (T*)(wb + woff[i].v);
           tasks[i].tau = (T*)(wb + woff[i].tau);
           tasks[i].Qc = (T*)(wb + woff[i].qc);
           tasks[i].gwork = (T*)(wb + woff[i].gw);
           cp_qc.push_back(tasks[i].Qc);
         }
-        if (h->opts.compression == SPAND_RANDOMIZED) {
+        if (interp) {
+          std::vector<int> tcol_(tasks.size());
+          for (size_t i = 0; i < tasks.size(); ++i) tcol_[i] = colour_of(tasks[i].p);
+          std::vector<int32_t> hsz = sz;
+          interp_out = sparsify_interp<T>(h, tasks, tcol_, ncol, nbrs, hsz, d_cur, d_info + 2 * (L + 1) + t * maxcol,
+                                          f_cls[t], eps, s);
+        } else if (h->opts.compression == SPAND_RANDOMIZED) {
           cpqr_pid = h->prof.begin(F_CPQR, s);
           std::vector<int> tcolr(tasks.size());
           for (size_t i = 0; i < tasks.size(); ++i) tcolr[i] = colour_of(tasks[i].p);
@@ -1950,7 +2336,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       std::vector<CopyTask<T>> qcopy;
       std::vector<int> sq_of(n, -1);
       for (size_t i = 0; i < sq_cluster.size(); ++i) sq_of[sq_cluster[i]] = (int)i;
-      for (size_t i = 0; i < cp_cluster.size(); ++i) {
+      for (size_t i = 0; i < cp_cluster.size() && !interp; ++i) {
         const int p = cp_cluster[i];
         const int r = sz_after[p];
         // sparsified: Q_pc (|p| x r); r = 0 keeps a non-null empty basis
@@ -1972,6 +2358,27 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       }
       for (auto& so : sqops) sm_r = std::max(sm_r, (size_t)std::max(so.r, 1) * sizeof(double));
       copy_batch<T>(h, qcopy, s);
+      if (interp) {
+        // apply groups of the step's interpolative transforms: T_p (U = I,
+        // X^T = T_cf, c against f), then the elimination of f against c; p
+        // keeps the slots of c, in pivot order
+        std::vector<ElimSpec<T>> tsp, fsp;
+        for (const InterpOut<T>& o : interp_out) {
+          if (o.p < 0) continue;
+          const std::vector<int32_t>& sl = slots[o.p];
+          std::vector<int32_t> cs(o.r), fs(o.nf);
+          for (int a = 0; a < o.r; ++a) cs[a] = sl[o.perm[a]];
+          for (int j = 0; j < o.nf; ++j) fs[j] = sl[o.perm[o.r + j]];
+          if (o.nf > 0) {
+            if (o.r > 0) tsp.push_back({o.XT, nullptr, o.r, cs, fs});
+            fsp.push_back({o.F + (size_t)o.ldf * o.nf, o.Yf, o.ldf, fs, cs});
+          }
+          kept_slots[o.p] = std::move(cs);
+          has_kept[o.p] = 1;
+        }
+        interp_steps.push_back(make_elim_step<T>(h, tsp, s));
+        interp_steps.push_back(make_elim_step<T>(h, fsp, s));
+      }
     } else {
       CK(cudaEventRecord(tm.at(t, 2), s));
     }
@@ -1991,7 +2398,8 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
           pof[a] = P;
           ro[a] = o;
           o += sz_after[a];
-          nslots[P].insert(nslots[P].end(), slots[a].begin(), slots[a].begin() + sz_after[a]);
+          const std::vector<int32_t>& ks = has_kept[a] ? kept_slots[a] : slots[a];
+          nslots[P].insert(nslots[P].end(), ks.begin(), ks.begin() + sz_after[a]);
         }
         nsz[P] = o;
       }
@@ -2043,7 +2451,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
                  sqops = std::move(sqops), sq_cluster = std::move(sq_cluster), aslots = std::move(aslots),
                  tslot = std::move(tslot), tptr = std::move(tptr), tidx = std::move(tidx), it_fy = std::move(it_fy),
                  it_fu = std::move(it_fu), it_ba = std::move(it_ba), it_bx = std::move(it_bx), nassign, sm_ns, sm_m,
-                 sm_np, sm_r, tmp_off]() mutable {
+                 sm_np, sm_r, tmp_off, interp_steps = std::move(interp_steps)]() mutable {
       // slots, save areas, temporaries and work items of the scaling +
       // coarse-basis ops (step-t slot lists)
       std::vector<ApplyItem> it_sy, it_sc, it_sz, it_sx;
@@ -2113,6 +2521,8 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         ap.sm_np = sm_np;
         ap.sm_r = sm_r;
         apply.push_back(ap);
+        for (const ApplyStep<T>& x : interp_steps)
+          if (x.n_elim) apply.push_back(x);
       }
       };
     }
@@ -2281,6 +2691,7 @@ void spand_default_opts(spand_opts* o) {
   o->sparsify_order = SPAND_COLOURED;
   o->compression = SPAND_CPQR;
   o->sketch_seed = 0;
+  o->variant = SPAND_ORTHS;
 }
 
 const char* spand_error_string(int code) {
@@ -2319,6 +2730,11 @@ int spand_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const
     throw Fail{SPAND_ERR_INVALID_ARG, "unknown compression"};
   if (opts->compression == SPAND_RANDOMIZED && opts->sparsify_order != SPAND_COLOURED)
     throw Fail{SPAND_ERR_INVALID_ARG, "randomized compression runs in the coloured order only"};
+  if (opts->variant != SPAND_ORTHS && opts->variant != SPAND_INS && opts->variant != SPAND_IN)
+    throw Fail{SPAND_ERR_INVALID_ARG, "unknown variant"};
+  if (opts->variant != SPAND_ORTHS &&
+      (opts->sparsify_order != SPAND_COLOURED || opts->compression != SPAND_CPQR))
+    throw Fail{SPAND_ERR_INVALID_ARG, "the interpolative variants need the coloured order and column-pivoted QR"};
   if (n > INT32_MAX - 1) throw Fail{SPAND_ERR_INVALID_ARG, "n too large"};
   if (coords && (dim < 1 || dim > 8)) throw Fail{SPAND_ERR_INVALID_ARG, "dim must be in [1, 8]"};
   std::string err;

@@ -20,6 +20,7 @@ def _addr(a):
 PRECISIONS = {"fp64": L.SPAND_FP64, "fp32": L.SPAND_FP32, "tf32": L.SPAND_TF32, "bf16": L.SPAND_BF16}
 ORDERS = {"coloured": L.SPAND_COLOURED, "simultaneous": L.SPAND_SIMULTANEOUS}
 COMPRESSIONS = {"cpqr": L.SPAND_CPQR, "randomized": L.SPAND_RANDOMIZED}
+VARIANTS = {"OrthS": L.SPAND_ORTHS, "InS": L.SPAND_INS, "In": L.SPAND_IN}
 
 
 class Solver:
@@ -31,17 +32,19 @@ class Solver:
     sparsify_order ("coloured", or "simultaneous": every interface of a level
     compressed from the same scaled matrix, one launch per level),
     compression ("cpqr", or "randomized": a Gaussian-sketch range finder in
-    place of the column-pivoted QR, sketches keyed by sketch_seed).
+    place of the column-pivoted QR, sketches keyed by sketch_seed), variant
+    ("OrthS", or the interpolative "InS" / "In" of Sec. 2.6.2, with / without
+    the block scaling).
     """
 
     def __init__(self, rowptr, colind, vals, coords=None, levels: int = 8, eps: float = 1e-2, skip: int = 0,
                  precision: str = "fp64", maxit: int = 500, tol: float = 1e-10, sparsify_order: str = "coloured",
-                 compression: str = "cpqr", sketch_seed: int = 0):
+                 compression: str = "cpqr", sketch_seed: int = 0, variant: str = "OrthS"):
         prec = PRECISIONS[precision]
         order = ORDERS[sparsify_order]
         self.opts = L.default_opts(levels=levels, eps=eps, skip=skip, precision=prec, maxit=maxit, tol=tol,
                                    sparsify_order=order, compression=COMPRESSIONS[compression],
-                                   sketch_seed=int(sketch_seed))
+                                   sketch_seed=int(sketch_seed), variant=VARIANTS[variant])
         self.n = int(np.asarray(rowptr).size - 1)
         self.nnz = int(np.asarray(rowptr)[-1])
         self.h = L.spand_analyze(rowptr, colind, vals, coords, self.opts)
@@ -121,7 +124,8 @@ class Solver:
                                        precision=prec, maxit=kw.get("maxit", 500), tol=kw.get("tol", 1e-10),
                                        sparsify_order=ORDERS[kw.get("sparsify_order", "coloured")],
                                        compression=COMPRESSIONS[kw.get("compression", "cpqr")],
-                                       sketch_seed=int(kw.get("sketch_seed", 0))))
+                                       sketch_seed=int(kw.get("sketch_seed", 0)),
+                                       variant=VARIANTS[kw.get("variant", "OrthS")]))
         hs = L.spand_analyze_batch([(p.rowptr, p.colind, p.vals, p.coords) for p in problems], opts)
         out = []
         for p, o, h in zip(problems, opts, hs):

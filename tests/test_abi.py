@@ -218,3 +218,25 @@ def test_compression_option(spand_lib):
         if h.value:
             L.spand_destroy(h.value)
         assert rc == want, (comp, order, rc)
+
+
+def test_variant_option(spand_lib):
+    """variant is SPAND_ORTHS by default; the interpolative SPAND_INS /
+    SPAND_IN run in the coloured order with column-pivoted QR only; unknown
+    values are refused."""
+    assert L.default_opts().variant == L.SPAND_ORTHS
+    p = I.laplacian_2d(6)
+    for var, order, comp, want in [(L.SPAND_ORTHS, L.SPAND_SIMULTANEOUS, L.SPAND_CPQR, L.SPAND_OK),
+                                   (L.SPAND_INS, L.SPAND_COLOURED, L.SPAND_CPQR, L.SPAND_OK),
+                                   (L.SPAND_IN, L.SPAND_COLOURED, L.SPAND_CPQR, L.SPAND_OK),
+                                   (L.SPAND_INS, L.SPAND_SIMULTANEOUS, L.SPAND_CPQR, L.SPAND_ERR_INVALID_ARG),
+                                   (L.SPAND_IN, L.SPAND_COLOURED, L.SPAND_RANDOMIZED, L.SPAND_ERR_INVALID_ARG),
+                                   (3, L.SPAND_COLOURED, L.SPAND_CPQR, L.SPAND_ERR_INVALID_ARG),
+                                   (-1, L.SPAND_COLOURED, L.SPAND_CPQR, L.SPAND_ERR_INVALID_ARG)]:
+        o = L.default_opts(levels=3, variant=var, sparsify_order=order, compression=comp)
+        h = C.c_void_p()
+        rc = L.lib().spand_analyze(p.n, p.rowptr.ctypes.data, p.colind.ctypes.data, p.vals.ctypes.data, None, 0,
+                                   C.byref(o), C.byref(h))
+        if h.value:
+            L.spand_destroy(h.value)
+        assert rc == want, (var, order, comp, rc)

@@ -4,9 +4,12 @@ randomized alternative of Sec. 2.6.2 and Sec. 5) against the oracle's
 "OrthS-rand" variant driven by the same counter-based sketches (Philox4x64-10
 keyed by (seed, step, cluster)).
 
-* FP64 form: ranks at every step equal to the oracle's per cluster (a near
-  tie in the sketch's pivoted QR may move one by one), PCG iterations within
-  +10 %, x within 1e-8 of the oracle's x at relative residual 1e-10;
+* FP64 form: PCG iterations within +10 %, x within 1e-8 of the oracle's x
+  at relative residual 1e-10, and the ranks of every cluster at every step
+  equal to the oracle's, with at most one cluster in 50 one apart (a tail
+  max_j ||W[k:, j]|| within rounding of eps max_j ||a_j||).  Both sides
+  order the sketch's basis by the same pivot rule, the largest remaining
+  column norm recomputed at every step (the oracle's cpqr_exact);
 * eps = 0: the sketch grows to min(p, m) columns whose range is that of
   A_pn, so the factorization is exact (one PCG iteration, dense solution);
 * mixed forms (FP32 factor with FP64 pivots, TF32 Schur operands) converge
@@ -56,14 +59,13 @@ def test_randomized_fp64_matches_oracle(cuda_ok, name, gen, levels, eps, geo):
         err = np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x)
         assert err <= 1e-8, err
         assert it <= math.ceil(1.1 * ref.iters), (it, ref.iters)
-        moved = 0
         for t in range(1, levels + 1):
             _, after = s.ranks(t)
             want = ref.factor.sizes_after[t - 1]
+            got, tot = int(after.sum()), int(want.sum())
             d = np.abs(after.astype(np.int64) - want)
-            assert d.max() <= 1, (t, d.max())
-            moved += int(np.count_nonzero(d))
-        assert moved <= max(2, sum(len(a) for a in ref.factor.sizes_after) // 50), moved
+            nbad = int(np.count_nonzero(d))
+            assert d.size == 0 or (d.max() <= 1 and nbad <= max(1, d.size // 50)), (t, d.max(), nbad, got, tot)
     finally:
         s.close()
 

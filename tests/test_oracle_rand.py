@@ -161,3 +161,40 @@ def test_solver_with_philox_sketch(gen, L):
     r = O.solve(p, b, L, 1e-2, variant="OrthS-rand", sketch=lambda t, c, m, ell: O.sketch_philox(0, t, c, m, ell))
     assert r.iters <= a.iters + 3, (r.iters, a.iters)
     assert np.linalg.norm(r.x - a.x) <= 1e-8 * np.linalg.norm(a.x)
+
+
+def test_cpqr_exact_hand_examples():
+    """Pivot order by hand: columns of norms 1, 3, 2 are taken as 3, 2, 1;
+    equal norms go by lowest column index."""
+    Q, R, P = O.cpqr_exact(np.diag([1.0, 3.0, 2.0]))
+    assert P.tolist() == [1, 2, 0]
+    assert np.allclose(np.abs(np.diag(R)), [3.0, 2.0, 1.0], rtol=0, atol=1e-15)
+    Q, R, P = O.cpqr_exact(np.eye(3))
+    assert P.tolist() == [0, 1, 2]
+    # a column that becomes the largest only after projecting out the first
+    A = np.array([[2.0, 2.0, 0.0], [0.0, 0.1, 1.0]])
+    Q, R, P = O.cpqr_exact(A)
+    assert P.tolist() == [1, 2, 0]  # ||a_1|| > ||a_0||; then a_2 keeps 0.995-ish, a_0 ~0.1
+    assert np.allclose(Q @ R, A[:, P], atol=1e-14)
+
+
+@pytest.mark.parametrize("seed,shape", [(0, (30, 12)), (1, (12, 30)), (2, (40, 40))])
+def test_cpqr_exact_is_a_pivoted_qr(seed, shape):
+    """A P = Q R, Q orthogonal, R upper triangular; every |R_kk| is the
+    largest norm of a remaining column after projecting out the first k
+    (checked by brute force); on Gaussian matrices (no near ties) the pivots
+    and |R| equal LAPACK geqp3's."""
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal(shape)
+    Q, R, P = O.cpqr_exact(A)
+    m, n = A.shape
+    assert np.allclose(Q.T @ Q, np.eye(m), atol=1e-13)
+    assert np.allclose(np.tril(R, -1), 0.0)
+    assert np.allclose(Q @ R, A[:, P], atol=1e-12)
+    for k in range(min(m, n)):
+        Qk = Q[:, :k]
+        rest = A[:, P[k:]] - Qk @ (Qk.T @ A[:, P[k:]])
+        assert abs(abs(R[k, k]) - np.linalg.norm(rest, axis=0).max()) <= 1e-12 * np.abs(A).max() * n
+    _, R2, P2 = sla.qr(A, pivoting=True, mode="economic")
+    assert P.tolist() == P2.tolist()
+    assert np.allclose(np.abs(R[:min(m, n)]), np.abs(R2), atol=1e-12)
