@@ -21,13 +21,23 @@ constexpr int NT = 256;   // threads per CTA of the tile kernels (64-row tiles)
 constexpr int KC = 16;    // k-chunk staged in shared memory
 constexpr int TB2 = 32;   // tile edge of the FP64 pivot Cholesky (shorter dependent chains)
 
-// Tiles of edge B are processed by (B/4)^2 threads, each holding a 4 x 4
-// patch: rows tx + (B/4) ii, columns ty + (B/4) jj, tx = tid % (B/4),
-// ty = tid / (B/4).
+// Tiles of edge B are processed by PR x PC threads, each holding a 4 x CB
+// patch: rows tx + PR ii (ii < 4), columns ty + PC jj (jj < CB),
+// tx = tid % PR, ty = tid / PR.  64-tiles: 16 x 16 threads with 4 x 4
+// patches.  32-tiles (the FP64 pivot Cholesky): 8 x 16 threads with 4 x 2
+// patches -- four warps, one per SM sub-partition, because a warp-wide FP64
+// FMA occupies a sub-partition's FP64 unit for tens of cycles on this GPU,
+// so a tile held by two warps leaves half of the SM's FP64 units idle.
 template <int B>
 struct TileGeom {
-  static constexpr int P = B / 4;         // threads per side
-  static constexpr int NTH = P * P;       // threads per CTA
+  static constexpr int PR = B / 4;                  // threads along the rows
+  static constexpr int PC = B == 32 ? 16 : B / 4;   // threads along the columns
+  static constexpr int CB = B / PC;                 // columns per thread
+  static constexpr int NTH = PR * PC;               // threads per CTA
+  // row block ii lies entirely below column block jj (no element with row <= column)
+  __host__ __device__ static constexpr bool below(int ii, int jj) { return ii * PR >= PC * (jj + 1); }
+  // row block ii lies entirely above column block jj (no element with row >= column)
+  __host__ __device__ static constexpr bool above(int ii, int jj) { return (ii + 1) * PR <= jj * PC; }
 };
 
 template <typename T, int B = TB>
@@ -38,22 +48,23 @@ struct TileSmemB {  // two K chunks (double buffer)
 template <typename T>
 using TileSmem = TileSmemB<T, TB>;
 
-// acc[ii][jj] (row = tx + P ii, col = ty + P jj)
+// acc[ii][jj] (row = tx + PR ii, col = ty + PC jj)
 // += sum_{k < K} A[k + row*lda] * B[k + col*ldb]     ("TN": C += A^T B)
 // Rows >= mi and columns >= nj read as zero.
 // UPPER: only the outputs on or above the diagonal of a diagonal tile are
-// needed (rows tx + P ii > columns ty + P jj whenever ii > jj: those
-// products are skipped and their accumulators stay zero).
+// needed (the patches whose row block lies entirely below their column
+// block are skipped and their accumulators stay zero).
 template <typename T, bool UPPER = false, int B = TB>
-__device__ __forceinline__ void tn_acc(T (&acc)[4][4], const T* __restrict__ A, int lda, int mi,
+__device__ __forceinline__ void tn_acc(T (&acc)[4][TileGeom<B>::CB], const T* __restrict__ A, int lda, int mi,
                                        const T* __restrict__ Bm, int ldb, int nj, int K,
                                        TileSmemB<T, B>& sm) {
   // K in chunks of KC, double-buffered: chunk c + 1 is loaded into registers
   // while chunk c is multiplied from shared memory; one block barrier per chunk
-  constexpr int P = TileGeom<B>::P, NTH = TileGeom<B>::NTH;
+  using G = TileGeom<B>;
+  constexpr int PR = G::PR, PC = G::PC, CB = G::CB, NTH = G::NTH;
   constexpr int NL = KC * B / NTH;  // elements of each operand loaded per thread per chunk
   const int tid = threadIdx.x;
-  const int tx = tid % P, ty = tid / P;
+  const int tx = tid % PR, ty = tid / PR;
   T ra[NL], rb[NL];
   auto load = [&](int k0) {
 #pragma unroll
@@ -80,43 +91,42 @@ __device__ __forceinline__ void tn_acc(T (&acc)[4][4], const T* __restrict__ A, 
     if (k0 + KC < K) load(k0 + KC);
 #pragma unroll
     for (int kk = 0; kk < KC; ++kk) {
-      T av[4], bv[4];
+      T av[4], bv[CB];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        av[q] = sm.a[buf][kk][tx + P * q];
-        bv[q] = sm.b[buf][kk][ty + P * q];
-      }
+      for (int q = 0; q < 4; ++q) av[q] = sm.a[buf][kk][tx + PR * q];
+#pragma unroll
+      for (int q = 0; q < CB; ++q) bv[q] = sm.b[buf][kk][ty + PC * q];
 #pragma unroll
       for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj)
-          if (!UPPER || ii <= jj) acc[ii][jj] = fma(av[ii], bv[jj], acc[ii][jj]);
+        for (int jj = 0; jj < CB; ++jj)
+          if (!UPPER || !G::below(ii, jj)) acc[ii][jj] = fma(av[ii], bv[jj], acc[ii][jj]);
     }
     buf ^= 1;
   }
   __syncthreads();  // the caller may reuse the buffers
 }
 
-template <typename T>
-__device__ __forceinline__ void zero_acc(T (&acc)[4][4]) {
+template <typename T, int CB>
+__device__ __forceinline__ void zero_acc(T (&acc)[4][CB]) {
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int j = 0; j < CB; ++j) acc[i][j] = T(0);
 }
 
 // C[row + col*ldc] -= acc for row < mi, col < nj.
 template <int B = TB, typename T>
-__device__ __forceinline__ void sub_store(const T (&acc)[4][4], T* C, int ldc, int mi, int nj) {
-  constexpr int P = TileGeom<B>::P;
-  const int tx = threadIdx.x % P, ty = threadIdx.x / P;
+__device__ __forceinline__ void sub_store(const T (&acc)[4][TileGeom<B>::CB], T* C, int ldc, int mi, int nj) {
+  using G = TileGeom<B>;
+  const int tx = threadIdx.x % G::PR, ty = threadIdx.x / G::PR;
 #pragma unroll
-  for (int jj = 0; jj < 4; ++jj) {
-    const int c = ty + P * jj;
+  for (int jj = 0; jj < G::CB; ++jj) {
+    const int c = ty + G::PC * jj;
     if (c >= nj) continue;
 #pragma unroll
     for (int ii = 0; ii < 4; ++ii) {
-      const int r = tx + P * ii;
+      const int r = tx + G::PR * ii;
       if (r < mi) C[r + (size_t)c * ldc] -= acc[ii][jj];
     }
   }
@@ -156,8 +166,8 @@ __device__ __forceinline__ void store_tile(const SqTileB<T, B>& s, T* P, int ld,
 //   U_{k+1,k+1} = sqrt(A_{k+1,k+1} - U_{k,k+1}^2),
 //   U_{k+1,.} = (A_{k+1,.} - U_{k,k+1} U_k.) / U_{k+1,k+1},
 //   D_k. <- D_k. / U_kk,  D_{k+1,.} <- (D_{k+1,.} - U_{k,k+1} D_k.) / U_{k+1,k+1},
-// and updates the 4 x 4 elements it holds in registers (rows tx + P a,
-// columns ty + P b) with the rank-2 terms:
+// and updates the 4 x CB elements it holds in registers (rows tx + PR a,
+// columns ty + PC b) with the rank-2 terms:
 //   A_ij -= U_ki U_kj + U_{k+1,i} U_{k+1,j} (k + 1 < i <= j),
 //   D_i. -= U_ki D_k. + U_{k+1,i} D_{k+1,.} (i > k + 1)   (row ops of L^{-1}, L = U^T).
 // One block barrier per pair of rows (the row buffers alternate); 1 / U_kk
@@ -165,15 +175,16 @@ __device__ __forceinline__ void store_tile(const SqTileB<T, B>& s, T* P, int ld,
 // a pivot is not positive; nothing is stored then.
 template <typename T, int B>
 __device__ bool potrf_inv_tile(SqTileB<T, B>& s, SqTileB<T, B>& D, int nb) {
-  constexpr int P = TileGeom<B>::P;
+  using G = TileGeom<B>;
+  constexpr int PR = G::PR, PC = G::PC, CB = G::CB;
   __shared__ T rowA[2][2][B], rowD[2][2][B];
-  const int tx = threadIdx.x % P, ty = threadIdx.x / P;
-  T a[4][4], d[4][4];
+  const int tx = threadIdx.x % PR, ty = threadIdx.x / PR;
+  T a[4][CB], d[4][CB];
 #pragma unroll
   for (int p = 0; p < 4; ++p)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int i = tx + P * p, j = ty + P * q;
+    for (int q = 0; q < CB; ++q) {
+      const int i = tx + PR * p, j = ty + PC * q;
       a[p][q] = s.v[i][j];
       d[p][q] = (i == j) ? T(1) : T(0);
     }
@@ -183,13 +194,13 @@ __device__ bool potrf_inv_tile(SqTileB<T, B>& s, SqTileB<T, B>& D, int nb) {
     const int k1 = two ? k + 1 : k;  // a single last row repeats row k (unused)
 #pragma unroll
     for (int p = 0; p < 4; ++p) {  // owners of rows k, k + 1 publish them (compile-time register indices)
-      const int i = tx + P * p;
+      const int i = tx + PR * p;
       if (i == k || i == k1) {
         const int w = i == k ? 0 : 1;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          rowA[par][w][ty + P * q] = a[p][q];
-          rowD[par][w][ty + P * q] = d[p][q];
+        for (int q = 0; q < CB; ++q) {
+          rowA[par][w][ty + PC * q] = a[p][q];
+          rowD[par][w][ty + PC * q] = d[p][q];
         }
       }
     }
@@ -201,44 +212,50 @@ __device__ bool potrf_inv_tile(SqTileB<T, B>& s, SqTileB<T, B>& D, int nb) {
     const T s11 = two ? rowA[par][1][k1] - u01 * u01 : T(1);
     if (!(s11 > T(0))) return false;
     const T r1 = rsqrt(s11), u11 = s11 * r1;
-    T u0i[4], u1i[4], u0j[4], u1j[4], d0[4], d1[4];
+    T u0i[4], u1i[4], u0j[CB], u1j[CB], d0[CB], d1[CB];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int ci = tx + P * q, cj = ty + P * q;
+      const int ci = tx + PR * q;
       u0i[q] = rowA[par][0][ci] * r0;
+      u1i[q] = two ? (rowA[par][1][ci] - u01 * u0i[q]) * r1 : T(0);
+    }
+#pragma unroll
+    for (int q = 0; q < CB; ++q) {
+      const int cj = ty + PC * q;
       u0j[q] = rowA[par][0][cj] * r0;
       d0[q] = rowD[par][0][cj] * r0;
-      u1i[q] = two ? (rowA[par][1][ci] - u01 * u0i[q]) * r1 : T(0);
       u1j[q] = two ? (rowA[par][1][cj] - u01 * u0j[q]) * r1 : T(0);
       d1[q] = two ? (rowD[par][1][cj] - u01 * d0[q]) * r1 : T(0);
     }
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
-      const int i = tx + P * p;
+      const int i = tx + PR * p;
       if (i == k) {  // finalise row k of U and of D
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int j = ty + P * q;
+        for (int q = 0; q < CB; ++q) {
+          const int j = ty + PC * q;
           if (j == k) a[p][q] = u00;
           else if (j > k) a[p][q] = u0j[q];
           d[p][q] = d0[q];
         }
       } else if (two && i == k1) {  // finalise row k + 1
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int j = ty + P * q;
+        for (int q = 0; q < CB; ++q) {
+          const int j = ty + PC * q;
           if (j == k1) a[p][q] = u11;
           else if (j > k1) a[p][q] = u1j[q];
           d[p][q] = d1[q];
         }
       } else if (i > k1) {
-        // U's upper triangle: column block q >= row block p; D's lower
-        // triangle: q <= p (the other blocks are zero in D and unused in U)
+        // U's upper triangle and D's lower triangle: patches entirely on the
+        // other side of the diagonal are skipped (they are zero in D and
+        // unused in U); D's entries above the diagonal stay zero because
+        // rows k, k + 1 of D are zero there
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int j = ty + P * q;
-          if (q >= p && j >= i) a[p][q] = fma(-u1i[p], u1j[q], fma(-u0i[p], u0j[q], a[p][q]));
-          if (q <= p) d[p][q] = fma(-u1i[p], d1[q], fma(-u0i[p], d0[q], d[p][q]));
+        for (int q = 0; q < CB; ++q) {
+          const int j = ty + PC * q;
+          if (!G::below(p, q) && j >= i) a[p][q] = fma(-u1i[p], u1j[q], fma(-u0i[p], u0j[q], a[p][q]));
+          if (!G::above(p, q)) d[p][q] = fma(-u1i[p], d1[q], fma(-u0i[p], d0[q], d[p][q]));
         }
       }
     }
@@ -246,8 +263,8 @@ __device__ bool potrf_inv_tile(SqTileB<T, B>& s, SqTileB<T, B>& D, int nb) {
 #pragma unroll
   for (int p = 0; p < 4; ++p)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int i = tx + P * p, j = ty + P * q;
+    for (int q = 0; q < CB; ++q) {
+      const int i = tx + PR * p, j = ty + PC * q;
       if (i <= j) s.v[i][j] = a[p][q];
       D.v[i][j] = d[p][q];
     }
@@ -260,96 +277,101 @@ __device__ bool potrf_inv_tile(SqTileB<T, B>& s, SqTileB<T, B>& D, int nb) {
 // D part of potrf_inv_tile, with the rows of U taken from the tile.
 template <typename T, int B>
 __device__ void inv_tile(const SqTileB<T, B>& U, SqTileB<T, B>& D, int nb) {
-  constexpr int P = TileGeom<B>::P;
+  using G = TileGeom<B>;
+  constexpr int PR = G::PR, PC = G::PC, CB = G::CB;
   __shared__ T rowD[2][2][B];
-  const int tx = threadIdx.x % P, ty = threadIdx.x / P;
-  T d[4][4];
+  const int tx = threadIdx.x % PR, ty = threadIdx.x / PR;
+  T d[4][CB];
 #pragma unroll
   for (int p = 0; p < 4; ++p)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) d[p][q] = (tx + P * p == ty + P * q) ? T(1) : T(0);
+    for (int q = 0; q < CB; ++q) d[p][q] = (tx + PR * p == ty + PC * q) ? T(1) : T(0);
   for (int k = 0; k < nb; k += 2) {
     const int par = (k >> 1) & 1;
     const bool two = k + 1 < nb;
     const int k1 = two ? k + 1 : k;
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
-      const int i = tx + P * p;
+      const int i = tx + PR * p;
       if (i == k || i == k1) {
         const int w = i == k ? 0 : 1;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) rowD[par][w][ty + P * q] = d[p][q];
+        for (int q = 0; q < CB; ++q) rowD[par][w][ty + PC * q] = d[p][q];
       }
     }
     __syncthreads();
     const T r0 = T(1) / U.v[k][k];
     const T u01 = two ? U.v[k][k1] : T(0);
     const T r1 = two ? T(1) / U.v[k1][k1] : T(0);
-    T d0[4], d1[4], u0i[4], u1i[4];
+    T d0[CB], d1[CB], u0i[4], u1i[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int cj = ty + P * q, ci = tx + P * q;
+    for (int q = 0; q < CB; ++q) {
+      const int cj = ty + PC * q;
       d0[q] = rowD[par][0][cj] * r0;
       d1[q] = two ? (rowD[par][1][cj] - u01 * d0[q]) * r1 : T(0);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int ci = tx + PR * q;
       u0i[q] = U.v[k][ci];
       u1i[q] = two ? U.v[k1][ci] : T(0);
     }
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
-      const int i = tx + P * p;
+      const int i = tx + PR * p;
       if (i == k) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) d[p][q] = d0[q];
+        for (int q = 0; q < CB; ++q) d[p][q] = d0[q];
       } else if (two && i == k1) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) d[p][q] = d1[q];
+        for (int q = 0; q < CB; ++q) d[p][q] = d1[q];
       } else if (i > k1) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (q <= p) d[p][q] = fma(-u1i[p], d1[q], fma(-u0i[p], d0[q], d[p][q]));
+        for (int q = 0; q < CB; ++q)
+          if (!G::above(p, q)) d[p][q] = fma(-u1i[p], d1[q], fma(-u0i[p], d0[q], d[p][q]));
       }
     }
   }
 #pragma unroll
   for (int p = 0; p < 4; ++p)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) D.v[tx + P * p][ty + P * q] = d[p][q];
+    for (int q = 0; q < CB; ++q) D.v[tx + PR * p][ty + PC * q] = d[p][q];
   __syncthreads();
 }
 
 // B <- D B with D = U^{-T} the stored inverse of a diagonal tile (lower,
 // zero above the diagonal), i.e. B <- U^{-T} B as one small GEMM instead of a
 // serial substitution.  D, B in shared memory; each thread produces a 4x4
-// patch; starts and ends synchronised.  For l in the P-row block lb, the rows
-// tx + P ii with ii < lb lie above l, where D is zero, so their products are
-// skipped (uniformly over the CTA).
+// patch; starts and ends synchronised.  For l in the PR-row block lb, the
+// rows tx + PR ii with ii < lb lie above l, where D is zero, so their
+// products are skipped (uniformly over the CTA).
 template <typename T, int B>
 __device__ void apply_inv_tile(const SqTileB<T, B>& D, SqTileB<T, B>& Bt, int nb) {
-  constexpr int P = TileGeom<B>::P;
-  const int tx = threadIdx.x % P, ty = threadIdx.x / P;
-  T acc[4][4];
+  using G = TileGeom<B>;
+  constexpr int PR = G::PR, PC = G::PC, CB = G::CB;
+  const int tx = threadIdx.x % PR, ty = threadIdx.x / PR;
+  T acc[4][CB];
   zero_acc(acc);
 #pragma unroll
   for (int lb = 0; lb < 4; ++lb) {
-    const int le = min(nb, P * lb + P);
-    for (int l = P * lb; l < le; ++l) {
-      T dv[4], bv[4];
+    const int le = min(nb, PR * lb + PR);
+    for (int l = PR * lb; l < le; ++l) {
+      T dv[4], bv[CB];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        dv[q] = D.v[tx + P * q][l];
-        bv[q] = Bt.v[l][ty + P * q];
-      }
+      for (int q = 0; q < 4; ++q) dv[q] = D.v[tx + PR * q][l];
+#pragma unroll
+      for (int q = 0; q < CB; ++q) bv[q] = Bt.v[l][ty + PC * q];
 #pragma unroll
       for (int ii = lb; ii < 4; ++ii)
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) acc[ii][jj] = fma(dv[ii], bv[jj], acc[ii][jj]);
+        for (int jj = 0; jj < CB; ++jj) acc[ii][jj] = fma(dv[ii], bv[jj], acc[ii][jj]);
     }
   }
   __syncthreads();
 #pragma unroll
   for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj) Bt.v[tx + P * ii][ty + P * jj] = acc[ii][jj];
+    for (int jj = 0; jj < CB; ++jj) Bt.v[tx + PR * ii][ty + PC * jj] = acc[ii][jj];
   __syncthreads();
 }
 

@@ -144,12 +144,12 @@ __global__ void __launch_bounds__(TileGeom<B>::NTH) k_potrf_update(const RowDesc
   if (d.bw > 0 && j + 1 > d.bw) return;  // U_kj is a zero tile: nothing to subtract
   const int i0 = (k + 1 + i) * B, j0 = (k + 1 + j) * B, k0 = k * B;
   const int mi = min(B, d.n - i0), nj = min(B, d.n - j0), kb = min(B, d.n - k0);
-  T acc[4][4];
+  T acc[4][TileGeom<B>::CB];
   zero_acc(acc);
   if (i == j)  // diagonal tile: only its upper triangle is used
-    tn_acc<T, true>(acc, d.R + k0 + (size_t)i0 * d.ld, d.ld, mi, d.R + k0 + (size_t)j0 * d.ld, d.ld, nj, kb, sm);
+    tn_acc<T, true, B>(acc, d.R + k0 + (size_t)i0 * d.ld, d.ld, mi, d.R + k0 + (size_t)j0 * d.ld, d.ld, nj, kb, sm);
   else
-    tn_acc<T, false>(acc, d.R + k0 + (size_t)i0 * d.ld, d.ld, mi, d.R + k0 + (size_t)j0 * d.ld, d.ld, nj, kb, sm);
+    tn_acc<T, false, B>(acc, d.R + k0 + (size_t)i0 * d.ld, d.ld, mi, d.R + k0 + (size_t)j0 * d.ld, d.ld, nj, kb, sm);
   sub_store<B>(acc, d.R + i0 + (size_t)j0 * d.ld, d.ld, mi, nj);
 }
 
