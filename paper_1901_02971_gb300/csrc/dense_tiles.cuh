@@ -160,24 +160,34 @@ __device__ __forceinline__ void store_tile(const SqTileB<T, B>& s, T* P, int ld,
 // Upper Cholesky of the nb x nb diagonal tile s (A = U^T U, upper triangle
 // read and overwritten with U, lower triangle left as loaded) fused with the
 // inverse D = U^{-T} (lower, B x B, identity beyond nb).  Right-looking,
-// two pivot rows per step: rows k and k + 1 of A and of D are published to
-// shared memory, every thread forms the 2 x 2 pivot block from them,
+// two pivot rows per step.  The owners of rows k and k + 1 of A and of D
+// publish them to shared memory; after a block barrier warp 0 alone forms
+// the 2 x 2 pivot block and the scaled rows (lane l takes the columns
+// l, l + 32, ...),
 //   U_kk = sqrt(A_kk), U_k. = A_k. / U_kk,
 //   U_{k+1,k+1} = sqrt(A_{k+1,k+1} - U_{k,k+1}^2),
 //   U_{k+1,.} = (A_{k+1,.} - U_{k,k+1} U_k.) / U_{k+1,k+1},
 //   D_k. <- D_k. / U_kk,  D_{k+1,.} <- (D_{k+1,.} - U_{k,k+1} D_k.) / U_{k+1,k+1},
-// and updates the 4 x CB elements it holds in registers (rows tx + PR a,
-// columns ty + PC b) with the rank-2 terms:
+// and publishes them; after a second barrier every thread updates the
+// 4 x CB elements it holds in registers (rows tx + PR a, columns ty + PC b)
+// with the rank-2 terms:
 //   A_ij -= U_ki U_kj + U_{k+1,i} U_{k+1,j} (k + 1 < i <= j),
 //   D_i. -= U_ki D_k. + U_{k+1,i} D_{k+1,.} (i > k + 1)   (row ops of L^{-1}, L = U^T).
-// One block barrier per pair of rows (the row buffers alternate); 1 / U_kk
-// comes from one reciprocal square root.  Returns false (for every thread) if
-// a pivot is not positive; nothing is stored then.
+// The pivot scalars and the row scalings are FP64 work that every warp
+// would otherwise repeat on its own sub-partition (on this GPU a warp-wide
+// FP64 instruction occupies a sub-partition for tens of cycles), so one warp
+// does them once: fewer FP64 instructions per step on the critical path and
+// in total.  The row and result buffers alternate with the step parity.
+// 1 / U_kk comes from one reciprocal square root.  Returns false (for every
+// thread) if a pivot is not positive; nothing is stored then.
 template <typename T, int B>
 __device__ bool potrf_inv_tile(SqTileB<T, B>& s, SqTileB<T, B>& D, int nb) {
   using G = TileGeom<B>;
   constexpr int PR = G::PR, PC = G::PC, CB = G::CB;
-  __shared__ T rowA[2][2][B], rowD[2][2][B];
+  __shared__ T rowA[2][2][B], rowD[2][2][B];        // raw rows k, k + 1
+  __shared__ T scU[2][2][B], scD[2][2][B];          // scaled rows of U and of D
+  __shared__ T scP[2][2];                           // U_kk, U_{k+1,k+1}
+  __shared__ int okP[2];
   const int tx = threadIdx.x % PR, ty = threadIdx.x / PR;
   T a[4][CB], d[4][CB];
 #pragma unroll
@@ -205,27 +215,41 @@ __device__ bool potrf_inv_tile(SqTileB<T, B>& s, SqTileB<T, B>& D, int nb) {
       }
     }
     __syncthreads();
-    const T a00 = rowA[par][0][k];
-    if (!(a00 > T(0))) return false;  // uniform: every thread read the same pivot
-    const T r0 = rsqrt(a00), u00 = a00 * r0;
-    const T u01 = two ? rowA[par][0][k1] * r0 : T(0);
-    const T s11 = two ? rowA[par][1][k1] - u01 * u01 : T(1);
-    if (!(s11 > T(0))) return false;
-    const T r1 = rsqrt(s11), u11 = s11 * r1;
+    if (threadIdx.x < 32) {  // warp 0: the pivot block and the scaled rows
+      const T a00 = rowA[par][0][k];
+      const T r0 = rsqrt(a00), u00 = a00 * r0;
+      const T u01 = two ? rowA[par][0][k1] * r0 : T(0);
+      const T s11 = two ? rowA[par][1][k1] - u01 * u01 : T(1);
+      const T r1 = rsqrt(s11), u11 = s11 * r1;
+      for (int j = threadIdx.x; j < B; j += 32) {
+        const T v0 = rowA[par][0][j] * r0, e0 = rowD[par][0][j] * r0;
+        scU[par][0][j] = v0;
+        scD[par][0][j] = e0;
+        scU[par][1][j] = two ? (rowA[par][1][j] - u01 * v0) * r1 : T(0);
+        scD[par][1][j] = two ? (rowD[par][1][j] - u01 * e0) * r1 : T(0);
+      }
+      if (threadIdx.x == 0) {
+        scP[par][0] = u00;
+        scP[par][1] = u11;
+        okP[par] = (a00 > T(0)) && (s11 > T(0));
+      }
+    }
+    __syncthreads();
+    if (!okP[par]) return false;  // uniform: every thread reads the same flag
     T u0i[4], u1i[4], u0j[CB], u1j[CB], d0[CB], d1[CB];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int ci = tx + PR * q;
-      u0i[q] = rowA[par][0][ci] * r0;
-      u1i[q] = two ? (rowA[par][1][ci] - u01 * u0i[q]) * r1 : T(0);
+      u0i[q] = scU[par][0][ci];
+      u1i[q] = scU[par][1][ci];
     }
 #pragma unroll
     for (int q = 0; q < CB; ++q) {
       const int cj = ty + PC * q;
-      u0j[q] = rowA[par][0][cj] * r0;
-      d0[q] = rowD[par][0][cj] * r0;
-      u1j[q] = two ? (rowA[par][1][cj] - u01 * u0j[q]) * r1 : T(0);
-      d1[q] = two ? (rowD[par][1][cj] - u01 * d0[q]) * r1 : T(0);
+      u0j[q] = scU[par][0][cj];
+      u1j[q] = scU[par][1][cj];
+      d0[q] = scD[par][0][cj];
+      d1[q] = scD[par][1][cj];
     }
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
@@ -234,7 +258,7 @@ __device__ bool potrf_inv_tile(SqTileB<T, B>& s, SqTileB<T, B>& D, int nb) {
 #pragma unroll
         for (int q = 0; q < CB; ++q) {
           const int j = ty + PC * q;
-          if (j == k) a[p][q] = u00;
+          if (j == k) a[p][q] = scP[par][0];
           else if (j > k) a[p][q] = u0j[q];
           d[p][q] = d0[q];
         }
@@ -242,7 +266,7 @@ __device__ bool potrf_inv_tile(SqTileB<T, B>& s, SqTileB<T, B>& D, int nb) {
 #pragma unroll
         for (int q = 0; q < CB; ++q) {
           const int j = ty + PC * q;
-          if (j == k1) a[p][q] = u11;
+          if (j == k1) a[p][q] = scP[par][1];
           else if (j > k1) a[p][q] = u1j[q];
           d[p][q] = d1[q];
         }

@@ -1384,8 +1384,23 @@ static std::vector<InterpOut<T>> sparsify_interp(spand_handle h, const std::vect
 // The subtractions x_v -= tmp[k] of an elimination phase's scatter, grouped
 // by target slot v (appended to tslot / tptr / tidx): a stable counting sort,
 // so each target's sources stay in op order (the fixed summation order).
+// Few targets against many slots (the upper levels): a comparison sort on
+// (slot, position) gives the same grouping and order without the O(n) passes.
 static void group_by_target(int64_t n, const std::vector<std::pair<int32_t, int64_t>>& tgt,
                             std::vector<int32_t>& tslot, std::vector<int64_t>& tptr, std::vector<int64_t>& tidx) {
+  if ((double)tgt.size() * 32.0 < (double)n) {
+    std::vector<std::pair<int32_t, int64_t>> key(tgt.size());
+    for (size_t i = 0; i < tgt.size(); ++i) key[i] = {tgt[i].first, (int64_t)i};
+    std::sort(key.begin(), key.end());
+    tidx.reserve(tidx.size() + tgt.size());
+    for (size_t i = 0; i < key.size();) {
+      const int32_t v = key[i].first;
+      tslot.push_back(v);
+      for (; i < key.size() && key[i].first == v; ++i) tidx.push_back(tgt[(size_t)key[i].second].second);
+      tptr.push_back((int64_t)tidx.size());
+    }
+    return;
+  }
   std::vector<int64_t> head((size_t)n + 1, 0);
   for (const auto& e : tgt) ++head[(size_t)e.first + 1];
   for (int64_t v = 0; v < n; ++v) head[v + 1] += head[v];
