@@ -292,8 +292,26 @@ __device__ __forceinline__ void cq_finish(const CpqrTask<T>& d, cg::cluster_grou
 //   4. every thread applies H_k to its live columns and recomputes their
 //      trailing norms.
 //
-// Column ownership: thread t owns the local columns t + c * NT, c < CQ_CPT.
-template <typename T, bool RES, int NT>
+// Column ownership: with LG lanes per column, thread t belongs to group
+// t / LG, which owns the local columns t / LG + c * (NT / LG), c < CQ_CPT;
+// lane t % LG of the group takes the vectors gs + lane, gs + lane + LG, ...
+// of a column (gs: the vector holding row k), and the group's partial dot
+// products and norms are summed over its lanes with xor shuffles (every lane
+// ends with the same bits).  LG > 1 spends otherwise idle threads of a CTA
+// with fewer columns than threads on shortening each step's per-column
+// sweep, which is the step's latency.
+template <int LG, typename T>
+__device__ __forceinline__ T cq_group_sum(T v) {
+  if constexpr (LG > 1) {
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned mask = ((1u << LG) - 1u) << (lane & ~(unsigned)(LG - 1));
+#pragma unroll
+    for (int o = 1; o < LG; o <<= 1) v += __shfl_xor_sync(mask, v, o);
+  }
+  return v;
+}
+
+template <typename T, bool RES, int NT, int LG = 1>
 __global__ void __launch_bounds__(NT) k_cpqr_cluster(const CpqrTask<T>* __restrict__ tasks,
                                                        const int32_t* __restrict__ list,
                                                        const CpqrNbr<T>* __restrict__ nbrs,
@@ -332,6 +350,8 @@ __global__ void __launch_bounds__(NT) k_cpqr_cluster(const CpqrTask<T>* __restri
   T* schunk = reinterpret_cast<T*>(smraw + off);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = NT / 32;
+  constexpr int NG = NT / LG;             // column groups
+  const int grp = tid / LG, lg = tid % LG;
 
   // neighbour descriptors and their current sizes (cur_size of neighbours of
   // earlier colours already holds their ranks), loaded in parallel
@@ -395,17 +415,17 @@ __global__ void __launch_bounds__(NT) k_cpqr_cluster(const CpqrTask<T>* __restri
   T nrm[CQ_CPT];
 #pragma unroll
   for (int c = 0; c < CQ_CPT; ++c) {
-    const int jl = tid + c * NT;
+    const int jl = grp + c * NG;
     nrm[c] = T(-1);
-    if (jl < nc) {
+    if (jl < nc) {  // uniform over the group
       const V* cv = reinterpret_cast<const V*>(chunk + (size_t)jl * L);
       T s = 0;
-      for (int g = 0; g < ng; ++g) {
+      for (int g = lg; g < ng; g += LG) {
         const V x = cv[g];
         if constexpr (VW == 4) s += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
         else s += x.x * x.x + x.y * x.y;
       }
-      nrm[c] = s;
+      nrm[c] = cq_group_sum<LG>(s);
     }
   }
 
@@ -420,7 +440,7 @@ __global__ void __launch_bounds__(NT) k_cpqr_cluster(const CpqrTask<T>* __restri
     for (int c = 0; c < CQ_CPT; ++c)
       if (nrm[c] > bv) {
         bv = nrm[c];
-        bj = j0 + tid + c * NT;
+        bj = j0 + grp + c * NG;
       }
     cq_warp_argmax(bv, bj);
     if (lane == 0) {
@@ -462,7 +482,7 @@ __global__ void __launch_bounds__(NT) k_cpqr_cluster(const CpqrTask<T>* __restri
     }
 #pragma unroll
     for (int c = 0; c < CQ_CPT; ++c)
-      if (j0 + tid + c * NT == gj) nrm[c] = T(-1);  // the pivot column leaves the live set
+      if (j0 + grp + c * NG == gj) nrm[c] = T(-1);  // the pivot column leaves the live set
     // 3. the raw pivot column (never written again) and the reflector
     const T* pcol = C == 1 ? chunk + (size_t)(gj - j0) * L
                            : cbuf + ((size_t)(k & 1) * C + min(C - 1, gj / cols_per)) * L;
@@ -491,10 +511,66 @@ __global__ void __launch_bounds__(NT) k_cpqr_cluster(const CpqrTask<T>* __restri
     const V* __restrict__ pv = reinterpret_cast<const V*>(pcol);
 #pragma unroll
     for (int c = 0; c < CQ_CPT; ++c) {
-      if (nrm[c] < T(0)) continue;
-      T* colp = chunk + (size_t)(tid + c * NT) * L;
+      if (nrm[c] < T(0)) continue;  // uniform over the group
+      T* colp = chunk + (size_t)(grp + c * NG) * L;
       V* __restrict__ cv = reinterpret_cast<V*>(colp);
       const T xk = colp[k];
+      if constexpr (LG > 1) {
+        // the group's lanes take interleaved vectors; lane 0 holds vector gs
+        T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        for (int g = gs + lg; g < ng; g += LG) {
+          const V x = cv[g], p = pv[g];
+          if (g == gs) {
+            if (rb > k) a0 = fma(x.x, p.x, a0);
+            if (rb + 1 > k) a1 = fma(x.y, p.y, a1);
+            if constexpr (VW == 4) {
+              if (rb + 2 > k) a2 = fma(x.z, p.z, a2);
+              if (rb + 3 > k) a3 = fma(x.w, p.w, a3);
+            }
+          } else {
+            a0 = fma(x.x, p.x, a0);
+            a1 = fma(x.y, p.y, a1);
+            if constexpr (VW == 4) {
+              a2 = fma(x.z, p.z, a2);
+              a3 = fma(x.w, p.w, a3);
+            }
+          }
+        }
+        const T dot = cq_group_sum<LG>((a0 + a1) + (a2 + a3));
+        const T w = tau * fma(scal, dot, xk);
+        const T ws = w * scal;
+        T q0 = 0, q1 = 0, q2 = 0, q3 = 0;
+        for (int g = gs + lg; g < ng; g += LG) {
+          V x = cv[g];
+          const V p = pv[g];
+          if (g == gs) {  // row k takes -w, rows > k take -ws p and enter the norm
+            if (rb == k) x.x -= w;
+            else if (rb > k) { x.x = fma(-ws, p.x, x.x); q0 = x.x * x.x; }
+            if (rb + 1 == k) x.y -= w;
+            else if (rb + 1 > k) { x.y = fma(-ws, p.y, x.y); q1 = x.y * x.y; }
+            if constexpr (VW == 4) {
+              if (rb + 2 == k) x.z -= w;
+              else if (rb + 2 > k) { x.z = fma(-ws, p.z, x.z); q2 = x.z * x.z; }
+              if (rb + 3 == k) x.w -= w;
+              else if (rb + 3 > k) { x.w = fma(-ws, p.w, x.w); q3 = x.w * x.w; }
+            }
+          } else {
+            x.x = fma(-ws, p.x, x.x);
+            x.y = fma(-ws, p.y, x.y);
+            q0 = fma(x.x, x.x, q0);
+            q1 = fma(x.y, x.y, q1);
+            if constexpr (VW == 4) {
+              x.z = fma(-ws, p.z, x.z);
+              x.w = fma(-ws, p.w, x.w);
+              q2 = fma(x.z, x.z, q2);
+              q3 = fma(x.w, x.w, q3);
+            }
+          }
+          cv[g] = x;
+        }
+        nrm[c] = cq_group_sum<LG>((q0 + q1) + (q2 + q3));
+        continue;
+      }
       T a0 = 0, a1 = 0, a2 = 0, a3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
       {  // first vector: only rows > k
         const V x = cv[gs], p = pv[gs];
