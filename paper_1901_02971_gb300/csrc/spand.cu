@@ -175,14 +175,28 @@ struct DevBuf {
 };
 
 // Host-side packer for one upload of descriptor arrays.
+// It records each array's place (256-byte aligned) without copying, and
+// write() copies them straight into the destination (the pinned staging
+// buffer): no intermediate host buffer is allocated, zero-filled and copied
+// again (at the leaf level the apply program alone is several MB per step).
+// The arrays must stay alive and unchanged until write().
 struct Packer {
-  std::vector<char> buf;
+  struct Part {
+    const void* p;
+    size_t off, bytes;
+  };
+  std::vector<Part> parts;
+  size_t size = 0;
   template <typename X>
   size_t add(const std::vector<X>& v) {
-    size_t off = align256(buf.size());
-    buf.resize(off + v.size() * sizeof(X));
-    if (!v.empty()) std::memcpy(buf.data() + off, v.data(), v.size() * sizeof(X));
+    const size_t off = align256(size), bytes = v.size() * sizeof(X);
+    if (bytes) parts.push_back({v.data(), off, bytes});
+    size = off + bytes;
     return off;
+  }
+  bool empty() const { return size == 0; }
+  void write(void* dst) const {
+    for (const Part& q : parts) std::memcpy((char*)dst + q.off, q.p, q.bytes);
   }
 };
 
@@ -398,6 +412,25 @@ struct KProf {
 
 using namespace spand;
 
+// Host arrays handed back after use and reused by later steps and
+// factorizations: the apply program's per-step arrays run to megabytes at
+// the leaf level, and fresh allocations of that size pay first-touch page
+// faults on every factorization.
+template <typename X>
+struct VecPool {
+  std::vector<std::vector<X>> free;
+  std::vector<X> take() {
+    if (free.empty()) return {};
+    std::vector<X> v = std::move(free.back());
+    free.pop_back();
+    v.clear();
+    return v;
+  }
+  void give(std::vector<X>&& v) {
+    if (v.capacity() && free.size() < 64) free.push_back(std::move(v));
+  }
+};
+
 struct spand_handle_s {
   spand_opts opts{};
   int64_t n = 0, nnz = 0;
@@ -428,6 +461,12 @@ struct spand_handle_s {
   DevBuf d_piv64;  // FP64 copies of the pivot blocks of FP32 factors (scratch)
   DevBuf d_rand;   // sketches, products and state of the randomized compression (scratch)
   DevBuf d_interp; // Gram matrices, R rows and pivot orders of the interpolative variants (scratch)
+  // host scratch reused across steps and factorizations
+  VecPool<int32_t> pool32;
+  VecPool<int64_t> pool64;
+  VecPool<std::pair<int32_t, int64_t>> poolpair;
+  VecPool<ApplyItem> poolitem;
+  std::vector<int64_t> gb_head, gb_byslot;  // the scatter grouping's counting sort
   DevBuf d_rowptr, d_colind;  // original CSR pattern (gradient on A's pattern)
   int fprec = -1;
   bool factored = false;
@@ -545,11 +584,11 @@ static void ensure_streams(spand_handle h) {
 
 template <typename T>
 static void* upload(spand_handle h, const Packer& pk, cudaStream_t s) {
-  if (pk.buf.empty()) return nullptr;
-  void* d = h->descs.alloc(pk.buf.size());
-  void* src = h->stage.take(pk.buf.size());
-  std::memcpy(src, pk.buf.data(), pk.buf.size());
-  CK(cudaMemcpyAsync(d, src, pk.buf.size(), cudaMemcpyHostToDevice, s));
+  if (pk.empty()) return nullptr;
+  void* d = h->descs.alloc(pk.size);
+  void* src = h->stage.take(pk.size);
+  pk.write(src);
+  CK(cudaMemcpyAsync(d, src, pk.size, cudaMemcpyHostToDevice, s));
   return d;
 }
 
@@ -973,25 +1012,20 @@ static std::vector<int> sparsify_randomized(spand_handle h, int t, const std::ve
         throw Fail{SPAND_ERR_INVALID_ARG, "randomized compression: an interface with more than 256 neighbours"};
     }
     // device state: [vcur | vrank | active] ints, then the task arrays
-    const size_t ist = 0;
     Packer pk;
-    const size_t ostate = pk.add(std::vector<int32_t>((size_t)3 * nc, 0));
-    (void)ist;
+    const std::vector<int32_t> state0((size_t)3 * nc, 0);
+    const size_t ostate = pk.add(state0);
     const size_t ort = pk.add(rt), ovn = pk.add(vn);
     const size_t ovt = pk.add(vt);
-    void* dev = h->descs.alloc(pk.buf.size());
+    void* dev = h->descs.alloc(pk.size);
     int32_t* d_vcur = at<int32_t>(dev, ostate);
     int32_t* d_vrank = d_vcur + nc;
     int32_t* d_active = d_vcur + 2 * nc;
-    for (int k = 0; k < nc; ++k) {
-      CpqrTask<T> v = vt[k];
-      v.rank_out = d_vrank;
-      std::memcpy(pk.buf.data() + ovt + k * sizeof(CpqrTask<T>), &v, sizeof(CpqrTask<T>));
-    }
+    for (int k = 0; k < nc; ++k) vt[k].rank_out = d_vrank;  // the device copy's rank array
     {
-      void* src = h->stage.take(pk.buf.size());
-      std::memcpy(src, pk.buf.data(), pk.buf.size());
-      CK(cudaMemcpyAsync(dev, src, pk.buf.size(), cudaMemcpyHostToDevice, s));
+      void* src = h->stage.take(pk.size);
+      pk.write(src);
+      CK(cudaMemcpyAsync(dev, src, pk.size, cudaMemcpyHostToDevice, s));
     }
     RandTask<T>* d_rt = at<RandTask<T>>(dev, ort);
     CpqrTask<T>* d_vt = at<CpqrTask<T>>(dev, ovt);
@@ -1390,7 +1424,7 @@ static std::vector<InterpOut<T>> sparsify_interp(spand_handle h, const std::vect
 // so each target's sources stay in op order (the fixed summation order).
 // Few targets against many slots (the upper levels): a comparison sort on
 // (slot, position) gives the same grouping and order without the O(n) passes.
-static void group_by_target(int64_t n, const std::vector<std::pair<int32_t, int64_t>>& tgt,
+static void group_by_target(spand_handle h, int64_t n, const std::vector<std::pair<int32_t, int64_t>>& tgt,
                             std::vector<int32_t>& tslot, std::vector<int64_t>& tptr, std::vector<int64_t>& tidx) {
   if ((double)tgt.size() * 32.0 < (double)n) {
     std::vector<std::pair<int32_t, int64_t>> key(tgt.size());
@@ -1405,10 +1439,12 @@ static void group_by_target(int64_t n, const std::vector<std::pair<int32_t, int6
     }
     return;
   }
-  std::vector<int64_t> head((size_t)n + 1, 0);
+  std::vector<int64_t>& head = h->gb_head;
+  head.assign((size_t)n + 1, 0);
   for (const auto& e : tgt) ++head[(size_t)e.first + 1];
   for (int64_t v = 0; v < n; ++v) head[v + 1] += head[v];
-  std::vector<int64_t> byslot(tgt.size());
+  std::vector<int64_t>& byslot = h->gb_byslot;
+  byslot.resize(tgt.size());
   for (size_t i = 0; i < tgt.size(); ++i) byslot[head[tgt[i].first]++] = tgt[i].second;
   // head[v] is now the end of slot v's run
   tidx.reserve(tidx.size() + tgt.size());
@@ -1479,14 +1515,14 @@ static ApplyStep<T> make_elim_step(spand_handle h, const std::vector<ElimSpec<T>
   if (eops.empty()) return ap;
   h->tmp_len = std::max(h->tmp_len, tmp_off);
   const int64_t nassign = (int64_t)tslot.size();
-  group_by_target(h->n, tgt, tslot, tptr, tidx);
+  group_by_target(h, h->n, tgt, tslot, tptr, tidx);
   Packer pk;
   const size_t oe = pk.add(eops), osl = pk.add(aslots), ots = pk.add(tslot), otp = pk.add(tptr), oti = pk.add(tidx);
   const size_t ofy = pk.add(fy), ofu = pk.add(fu), oba = pk.add(ba), obx = pk.add(bx);
-  void* d = h->persist.alloc(pk.buf.size());
-  void* src = h->stage.take(pk.buf.size());
-  std::memcpy(src, pk.buf.data(), pk.buf.size());
-  CK(cudaMemcpyAsync(d, src, pk.buf.size(), cudaMemcpyHostToDevice, s));
+  void* d = h->persist.alloc(pk.size);
+  void* src = h->stage.take(pk.size);
+  pk.write(src);
+  CK(cudaMemcpyAsync(d, src, pk.size, cudaMemcpyHostToDevice, s));
   ap.n_elim = (int)eops.size();
   ap.elim = at<const ElimOp<T>>(d, oe);
   ap.slots = at<const int32_t>(d, osl);
@@ -1854,12 +1890,14 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
     CK(cudaEventRecord(tm.at(t, 1), s));
     // ------------------------------------------------ apply ops of the elimination
     ApplyStep<T> ap;
-    std::vector<int32_t> aslots;
+    std::vector<int32_t> aslots = h->pool32.take();
     std::vector<ElimOp<T>> eops;
-    std::vector<std::pair<int32_t, int64_t>> tgt;  // (target slot, tmp index) of the subtractions
-    std::vector<int32_t> tslot;
-    std::vector<int64_t> tptr(1, 0), tidx;
-    std::vector<ApplyItem> it_fy, it_fu, it_ba, it_bx;
+    std::vector<std::pair<int32_t, int64_t>> tgt = h->poolpair.take();  // (target slot, tmp index) of the subtractions
+    std::vector<int32_t> tslot = h->pool32.take();
+    std::vector<int64_t> tptr = h->pool64.take(), tidx = h->pool64.take();
+    tptr.push_back(0);
+    std::vector<ApplyItem> it_fy = h->poolitem.take(), it_fu = h->poolitem.take(), it_ba = h->poolitem.take(),
+                           it_bx = h->poolitem.take();
     int64_t tmp_off = 0;
     size_t sm_ns = 0, sm_m = 0;
     int64_t nassign = 0;
@@ -1907,7 +1945,8 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       }
       h->tmp_len = std::max(h->tmp_len, tmp_off);
       nassign = (int64_t)tslot.size();
-      group_by_target(h->n, tgt, tslot, tptr, tidx);
+      group_by_target(h, h->n, tgt, tslot, tptr, tidx);
+      h->poolpair.give(std::move(tgt));
       elim_ops_built = true;
     };
 
@@ -2483,7 +2522,8 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
                  sm_np, sm_r, tmp_off, interp_steps = std::move(interp_steps)]() mutable {
       // slots, save areas, temporaries and work items of the scaling +
       // coarse-basis ops (step-t slot lists)
-      std::vector<ApplyItem> it_sy, it_sc, it_sz, it_sx;
+      std::vector<ApplyItem> it_sy = h->poolitem.take(), it_sc = h->poolitem.take(), it_sz = h->poolitem.take(),
+                             it_sx = h->poolitem.take();
       {
         int64_t save = h->save_len;
         for (size_t i = 0; i < sqops.size(); ++i) {
@@ -2513,11 +2553,11 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         size_t ots = pk.add(tslot), otp = pk.add(tptr), oti = pk.add(tidx);
         size_t ofy = pk.add(it_fy), ofu = pk.add(it_fu), oba = pk.add(it_ba), obx = pk.add(it_bx);
         void* d = nullptr;
-        if (!pk.buf.empty()) {
-          d = h->persist.alloc(pk.buf.size());
-          void* src = h->stage.take(pk.buf.size());
-          std::memcpy(src, pk.buf.data(), pk.buf.size());
-          CK(cudaMemcpyAsync(d, src, pk.buf.size(), cudaMemcpyHostToDevice, s));
+        if (!pk.empty()) {
+          d = h->persist.alloc(pk.size);
+          void* src = h->stage.take(pk.size);
+          pk.write(src);
+          CK(cudaMemcpyAsync(d, src, pk.size, cudaMemcpyHostToDevice, s));
         }
         ap.n_elim = (int)eops.size();
         ap.n_sq = (int)sqops.size();
@@ -2553,6 +2593,12 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         for (const ApplyStep<T>& x : interp_steps)
           if (x.n_elim) apply.push_back(x);
       }
+      // the host arrays have been copied to pinned staging: back to the pools
+      h->pool32.give(std::move(aslots));
+      h->pool32.give(std::move(tslot));
+      h->pool64.give(std::move(tptr));
+      h->pool64.give(std::move(tidx));
+      for (auto* v : {&it_fy, &it_fu, &it_ba, &it_bx, &it_sy, &it_sc, &it_sz, &it_sx}) h->poolitem.give(std::move(*v));
       };
     }
 
