@@ -86,6 +86,15 @@ __global__ void k_assemble(const double* __restrict__ vals, const int32_t* __res
 // smaller tile shortens every link of that chain).  dinv holds ceil(n/B)
 // tiles of B x B (the inverses U_kk^{-T} of phase 1); bw counts B-tiles.
 
+// Programmatic dependent launch: the tile Cholesky's phases are launched so
+// that a phase's CTAs may be scheduled while the previous phase drains.
+// Every CTA first waits for the previous grid's completion (and visibility of
+// its writes) -- also the CTAs that then find no work, so that a grid never
+// completes before its predecessor -- and signals the next grid once its own
+// stores are issued.  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Tile step k, phase 1: factor diagonal tile (k, k) of every block and store
 // the inverse of its factor, U_kk^{-T}, for the tile solves of phase 2.
 template <typename T, int B = TB>
@@ -94,6 +103,7 @@ __global__ void __launch_bounds__(TileGeom<B>::NTH) k_potrf_diag(const RowDesc<T
   extern __shared__ __align__(16) unsigned char smraw[];
   SqTileB<T, B>& s = *reinterpret_cast<SqTileB<T, B>*>(smraw);
   SqTileB<T, B>& Id = *reinterpret_cast<SqTileB<T, B>*>(smraw + sizeof(SqTileB<T, B>));
+  pdl_wait();
   const RowDesc<T> d = rows[blockIdx.x];
   const int k0 = k * B;
   if (k0 >= d.n) return;
@@ -107,6 +117,7 @@ __global__ void __launch_bounds__(TileGeom<B>::NTH) k_potrf_diag(const RowDesc<T
   }
   store_tile(s, P, d.ld, nb, nb);
   store_tile(Id, d.dinv + (size_t)k * B * B, B, B, B);
+  pdl_trigger();
 }
 
 // Tile step k, phase 2: U_kj = U_kk^{-T} A_kj for the tiles j > k of the diagonal block.
@@ -115,6 +126,7 @@ __global__ void __launch_bounds__(TileGeom<B>::NTH) k_potrf_trsm(const RowDesc<T
   extern __shared__ __align__(16) unsigned char smraw[];
   SqTileB<T, B>& D = *reinterpret_cast<SqTileB<T, B>*>(smraw);
   SqTileB<T, B>& Bt = *reinterpret_cast<SqTileB<T, B>*>(smraw + sizeof(SqTileB<T, B>));
+  pdl_wait();
   const RowDesc<T> d = rows[blockIdx.y];
   const int k0 = k * B;
   const int j0 = k0 + B * (1 + blockIdx.x);
@@ -125,12 +137,14 @@ __global__ void __launch_bounds__(TileGeom<B>::NTH) k_potrf_trsm(const RowDesc<T
   __syncthreads();
   apply_inv_tile(D, Bt, nb);
   store_tile(Bt, d.R + k0 + (size_t)j0 * d.ld, d.ld, nb, nc);
+  pdl_trigger();
 }
 
 // Tile step k, phase 3: A_ij -= U_ki^T U_kj for k < i <= j (upper trailing tiles).
 template <typename T, int B = TB>
 __global__ void __launch_bounds__(TileGeom<B>::NTH) k_potrf_update(const RowDesc<T>* __restrict__ rows, int k) {
   __shared__ TileSmemB<T, B> sm;
+  pdl_wait();
   const RowDesc<T> d = rows[blockIdx.y];
   const int nt = (d.n + B - 1) / B;
   const int m = nt - k - 1;  // trailing tiles per side
@@ -151,6 +165,7 @@ __global__ void __launch_bounds__(TileGeom<B>::NTH) k_potrf_update(const RowDesc
   else
     tn_acc<T, false, B>(acc, d.R + k0 + (size_t)i0 * d.ld, d.ld, mi, d.R + k0 + (size_t)j0 * d.ld, d.ld, nj, kb, sm);
   sub_store<B>(acc, d.R + i0 + (size_t)j0 * d.ld, d.ld, mi, nj);
+  pdl_trigger();
 }
 
 // The inverses U_kk^{-T} of the 64 x 64 diagonal tiles of a factored pivot

@@ -595,8 +595,27 @@ static void* upload(spand_handle h, const Packer& pk, cudaStream_t s) {
 template <typename X>
 static X* at(void* base, size_t off) { return reinterpret_cast<X*>((char*)base + off); }
 
+// Launch with programmatic stream serialization: the kernel may be scheduled
+// before its predecessor on the stream completes; the kernel itself waits
+// for that completion (griddepcontrol.wait) before touching its data.
+template <typename... P, typename... A>
+static void launch_pdl(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  CK(cudaLaunchKernelEx(&cfg, kern, args...));
+}
+
 // Tiled upper Cholesky of a batch of diagonal blocks (right-looking over
-// B x B tiles; dinv and bw of the rows in B-tiles).
+// B x B tiles; dinv and bw of the rows in B-tiles).  The phases of the tile
+// steps are launched back to back as programmatic dependent launches.
 template <typename T, int B = TB>
 static void potrf_batch(spand_handle h, const std::vector<RowDesc<T>>& rows, int* d_info, cudaStream_t s,
                         const std::vector<double>* row_flops = nullptr) {
@@ -623,14 +642,11 @@ static void potrf_batch(spand_handle h, const std::vector<RowDesc<T>>& rows, int
   int64_t nl = 0;
   for (int k = 0; k < nt; ++k) {
     nl += (nt - k - 1 > 0) ? 3 : 1;
-    k_potrf_diag<T, B><<<nb, nth, sm1, s>>>(dr, k, d_info);
-    CKLAUNCH();
+    launch_pdl(k_potrf_diag<T, B>, dim3(nb), dim3(nth), sm1, s, dr, k, d_info);
     const int m = nt - k - 1;
     if (m > 0) {
-      k_potrf_trsm<T, B><<<dim3(m, nb), nth, sm2, s>>>(dr, k);
-      CKLAUNCH();
-      k_potrf_update<T, B><<<dim3(m * (m + 1) / 2, nb), nth, 0, s>>>(dr, k);
-      CKLAUNCH();
+      launch_pdl(k_potrf_trsm<T, B>, dim3(m, nb), dim3(nth), sm2, s, dr, k);
+      launch_pdl(k_potrf_update<T, B>, dim3(m * (m + 1) / 2, nb), dim3(nth), (size_t)0, s, dr, k);
     }
   }
   h->prof.launches += nl;
