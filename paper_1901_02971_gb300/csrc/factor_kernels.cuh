@@ -25,6 +25,8 @@ struct RowDesc {      // a cluster's block row or its diagonal block
   T* dinv;            // ceil(n/64) tiles of 64x64: inverses U_kk^{-T} of the diagonal tiles
   int32_t bw;         // tile bandwidth of U in 64-tiles (0 = dense)
   int32_t bw2;        // the same in 32-tiles (FP64 pivot factorization)
+  int32_t band;       // element half-bandwidth of the block (0 = dense or not known)
+  int32_t pad;
 };
 
 template <typename T>
@@ -66,6 +68,16 @@ struct CopyTile {
   int32_t task, r0, c0;
 };
 
+// Programmatic dependent launch: the tile Cholesky's phases (and the banded
+// Cholesky) are launched so that a kernel's CTAs may be scheduled while the
+// previous kernel drains.
+// Every CTA first waits for the previous grid's completion (and visibility of
+// its writes) -- also the CTAs that then find no work, so that a grid never
+// completes before its predecessor -- and signals the next grid once its own
+// stores are issued.  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ---------------------------------------------------------------- assembly
 
 // Scatter A's values into the step-1 block rows: rows[dst_row[e]][dst_off[e]] = vals[e].
@@ -85,15 +97,6 @@ __global__ void k_assemble(const double* __restrict__ vals, const int32_t* __res
 // diagonal-tile factor -> tile solve -> trailing tile update the cost: a
 // smaller tile shortens every link of that chain).  dinv holds ceil(n/B)
 // tiles of B x B (the inverses U_kk^{-T} of phase 1); bw counts B-tiles.
-
-// Programmatic dependent launch: the tile Cholesky's phases are launched so
-// that a phase's CTAs may be scheduled while the previous phase drains.
-// Every CTA first waits for the previous grid's completion (and visibility of
-// its writes) -- also the CTAs that then find no work, so that a grid never
-// completes before its predecessor -- and signals the next grid once its own
-// stores are issued.  Without the launch attribute both are no-ops.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Tile step k, phase 1: factor diagonal tile (k, k) of every block and store
 // the inverse of its factor, U_kk^{-T}, for the tile solves of phase 2.
@@ -165,6 +168,132 @@ __global__ void __launch_bounds__(TileGeom<B>::NTH) k_potrf_update(const RowDesc
   else
     tn_acc<T, false, B>(acc, d.R + k0 + (size_t)i0 * d.ld, d.ld, mi, d.R + k0 + (size_t)j0 * d.ld, d.ld, nj, kb, sm);
   sub_store<B>(acc, d.R + i0 + (size_t)j0 * d.ld, d.ld, mi, nj);
+  pdl_trigger();
+}
+
+// Banded upper Cholesky (Sec. 2.4) of the step-1 pivot blocks, FP64, one
+// CTA per block.  A step-1 pivot is the restriction of A to one leaf
+// cluster, vertices in increasing id (lexicographic on grids), so its
+// nonzeros lie within a half-bandwidth b of the diagonal (b = 49-64 for the
+// 7³-8³ leaves of a 3D grid); the Cholesky factor keeps that band, and the
+// right-looking elimination touches only the (b + 2)-column window ahead of
+// the pivot.  The window lives in shared memory as a ring of b + 2 columns
+// (column j at slot j mod (b + 2), its rows j - b .. j); per step two pivot
+// rows k, k + 1:
+//   1. one thread forms the 2 x 2 pivot block, U_kk = sqrt(A_kk),
+//      U_{k,k+1} = A_{k,k+1} / U_kk, U_{k+1,k+1} = sqrt(A_{k+1,k+1} - U_{k,k+1}^2);
+//   2. the rows U_k. and U_{k+1,.} across the band, one column per thread;
+//   3. the rank-2 update A_ij -= U_ki U_kj + U_{k+1,i} U_{k+1,j} of the
+//      b (b + 1) / 2 window entries k + 1 < i <= j <= k + 1 + b, spread evenly
+//      over the threads by a table of (i, j) offsets;
+//   4. columns k, k + 1 are final: each thread stores its element of them
+//      and loads in its place the element of column k + b + 2 (or k + b + 3),
+//      which no step has touched yet.
+// The tiled kernels would do about four times the arithmetic on such a band
+// (a 32 x 32 tile step covers rows k .. k + 95 in full).  A pivot that is not
+// positive is reported like the tiled kernels' (the block's batch index + 1).
+constexpr int BAND_MAX = 96;   // widest band taken by this kernel
+constexpr int BAND_NT = 256;
+
+struct BandTask {
+  double* R;        // the block, column-major, leading dimension ld (upper triangle read and overwritten)
+  int32_t n, ld, band, entry;  // entry: index of the block in its pivot batch (for the failure flag)
+};
+
+__host__ __device__ inline size_t band_smem(int b) {
+  return (size_t)(b + 2) * (b + 1) * sizeof(double) + 2 * (size_t)(b + 2) * sizeof(double) +
+         (((size_t)b * (b + 1) / 2 * sizeof(uint16_t) + 15) & ~size_t(15));
+}
+
+__global__ void __launch_bounds__(BAND_NT) k_potrf_band(const BandTask* __restrict__ tasks, int* info) {
+  pdl_wait();
+  const BandTask d = tasks[blockIdx.x];
+  const int n = d.n, b = d.band, ld = d.ld, tid = threadIdx.x;
+  const int WS = b + 2, CL = b + 1;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* win = reinterpret_cast<double*>(smraw);
+  double* u0 = win + (size_t)WS * CL;  // u0[x] = U(k, k + x), x = 0 .. b + 1
+  double* u1 = u0 + WS;                // u1[x] = U(k + 1, k + x)
+  uint16_t* pairs = reinterpret_cast<uint16_t*>(u1 + WS);  // (xi << 8) | xj, 2 <= xi <= xj <= b + 1
+  __shared__ double sc[4];
+  __shared__ int ok;
+  const int npairs = b * (b + 1) / 2;
+  // pair table: column xj = 2 .. b + 1 holds rows xi = 2 .. xj
+  for (int xj = 2 + tid; xj <= b + 1; xj += BAND_NT) {
+    int e = (xj - 2) * (xj - 1) / 2;
+    for (int xi = 2; xi <= xj; ++xi) pairs[e++] = (uint16_t)((xi << 8) | xj);
+  }
+  // initial window: columns 0 .. min(n, WS) - 1 into slots 0 ..
+  for (int e = tid; e < min(n, WS) * CL; e += BAND_NT) {
+    const int j = e / CL, r = e % CL, i = j - b + r;
+    win[(size_t)j * CL + r] = i >= 0 ? d.R[i + (size_t)j * ld] : 0.0;
+  }
+  __syncthreads();
+  for (int k = 0; k < n; k += 2) {
+    const bool two = k + 1 < n;
+    const int k1 = k + 1;
+    if (tid == 0) {  // 1. the pivot block
+      const double a00 = win[(size_t)(k % WS) * CL + b];
+      const double r0 = rsqrt(a00), u00 = a00 * r0;
+      const double u01 = two ? win[(size_t)(k1 % WS) * CL + b - 1] * r0 : 0.0;
+      const double s11 = two ? win[(size_t)(k1 % WS) * CL + b] - u01 * u01 : 1.0;
+      const double r1 = rsqrt(s11), u11 = s11 * r1;
+      sc[0] = r0;
+      sc[1] = u01;
+      sc[2] = r1;
+      sc[3] = u11;
+      u0[0] = u00;
+      ok = (a00 > 0.0) && (s11 > 0.0);
+    }
+    __syncthreads();
+    if (!ok) {
+      if (tid == 0) atomicCAS(info, 0, d.entry + 1);
+      return;  // uniform
+    }
+    // 2. rows k and k + 1 of U across the band (x = j - k)
+    for (int x = 1 + tid; x <= b + 1; x += BAND_NT) {
+      const int j = k + x;
+      double v0 = 0.0, v1 = 0.0;
+      if (j < n) {
+        double* col = win + (size_t)(j % WS) * CL;
+        if (x <= b) {
+          v0 = col[k - j + b] * sc[0];
+          col[k - j + b] = v0;
+        }
+        if (two) {
+          v1 = x == 1 ? sc[3] : (col[k1 - j + b] - sc[1] * v0) * sc[2];
+          col[k1 - j + b] = v1;
+        }
+      }
+      u0[x] = v0;
+      u1[x] = v1;
+    }
+    if (tid == 0) win[(size_t)(k % WS) * CL + b] = u0[0];
+    __syncthreads();
+    // 3. rank-2 update of the window ahead of the pivot rows
+    // (a single last row, n = k + 1, has nothing after it to update)
+    if (two)
+      for (int e = tid; e < npairs; e += BAND_NT) {
+        const int xi = pairs[e] >> 8, xj = pairs[e] & 0xff;
+        const int j = k + xj;
+        if (j >= n) continue;
+        const int i = k + xi;
+        double& a = win[(size_t)(j % WS) * CL + (i - j + b)];
+        a = fma(-u1[xi], u1[xj], fma(-u0[xi], u0[xj], a));
+      }
+    __syncthreads();
+    // 4. columns k, k + 1 are final: store them, load k + WS, k + 1 + WS in their slots
+    for (int e = tid; e < 2 * CL; e += BAND_NT) {
+      const int c = k + e / CL, r = e % CL;
+      if (c >= n) continue;
+      double* slot = win + (size_t)(c % WS) * CL;
+      const int i = c - b + r;
+      if (i >= 0) d.R[i + (size_t)c * ld] = slot[r];
+      const int cn = c + WS, in = cn - b + r;
+      if (cn < n) slot[r] = in >= 0 ? d.R[in + (size_t)cn * ld] : 0.0;
+    }
+    __syncthreads();
+  }
   pdl_trigger();
 }
 

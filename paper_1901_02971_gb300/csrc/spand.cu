@@ -445,6 +445,7 @@ struct spand_handle_s {
   // are dense): per initial cluster, U's tile bandwidth (0 = dense), the
   // Cholesky flops sum_j r_j^2 over U's row lengths r_j, and nnz(U)
   std::vector<int32_t> env_bw, env_bw32;  // in 64-tiles and in 32-tiles
+  std::vector<int32_t> env_band;          // element half-bandwidth max_i (i - f(i)) (0 = dense)
   std::vector<double> env_flops, env_nnz;
   // A in the cluster order (for the SpMV of PCG)
   std::vector<int64_t> prow;
@@ -705,6 +706,21 @@ static void pivot_chol(spand_handle h, const std::vector<RowDesc<T>>& rows, int*
     if (wide) r64.push_back({W, r.n, r.n, D, r.bw2, 0});
     else r64.push_back({(double*)r.R, r.n, r.ld, D, r.bw2, 0});
   }
+  // banded blocks (step-1 pivots with a narrow band) go to the banded
+  // kernel; the tiled batch skips them (n = 0 keeps the batch indices, which
+  // the failure flag reports)
+  std::vector<BandTask> bands;
+  int bmax = 0;
+  for (size_t i = 0; i < rows.size(); ++i) {
+    const RowDesc<T>& r = rows[i];
+    if (r.band > 0 && r.band <= BAND_MAX && r.band + 1 < r.n) {
+      bands.push_back({r64[i].R, r.n, r64[i].ld, r.band, (int32_t)i});
+      bmax = std::max(bmax, r.band);
+      r64[i].n = 0;
+    }
+  }
+  bool dense_left = false;
+  for (const auto& r : r64) dense_left = dense_left || r.n > 0;
   const PivotCopy* dc = nullptr;
   if (wide) {
     Packer pk;
@@ -718,7 +734,26 @@ static void pivot_chol(spand_handle h, const std::vector<RowDesc<T>>& rows, int*
       ++h->prof.launches;
     }
   }
-  potrf_batch<double, TB2>(h, r64, d_info, s, row_flops);
+  if (!bands.empty()) {
+    Packer pk;
+    const size_t ob = pk.add(bands);
+    void* d = upload<T>(h, pk, s);
+    const size_t sm = band_smem(bmax);
+    ensure_smem((const void*)k_potrf_band, sm);
+    const int pid = h->prof.begin(F_POTRF, s);
+    for (size_t b0 = 0; b0 < bands.size(); b0 += 65535) {
+      const unsigned cnt = (unsigned)std::min<size_t>(bands.size() - b0, 65535);
+      launch_pdl(k_potrf_band, dim3(cnt), dim3(BAND_NT), sm, s, at<const BandTask>(d, ob) + b0, d_info);
+      ++h->prof.launches;
+    }
+    double fl = 0, by = 0;
+    for (const BandTask& b : bands) {
+      fl += row_flops ? (*row_flops)[b.entry] : (double)b.n * b.band * b.band;
+      by += 2.0 * b.n * (b.band + 1) * sizeof(double);
+    }
+    h->prof.end(pid, s, fl, by, (int64_t)((bands.size() + 65534) / 65535));
+  }
+  if (dense_left) potrf_batch<double, TB2>(h, r64, d_info, s, row_flops);
   if (wide) {
     for (size_t b0 = 0; b0 < cps.size(); b0 += 65535) {
       const unsigned cnt = (unsigned)std::min<size_t>(cps.size() - b0, 65535);
@@ -1747,10 +1782,11 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         // step 1: the pivot is a piece of A, with the envelope found at analysis
         const bool env = t == 1 && !h->env_bw.empty();
         const int bw = env ? h->env_bw[sidx] : 0, bw2 = env ? h->env_bw32[sidx] : 0;
+        const int band = env ? h->env_band[sidx] : 0;
         const double cfl = env ? h->env_flops[sidx] : ns * ns * ns / 3;
         const double nnzU = env ? h->env_nnz[sidx] : ns * (ns + 1) / 2;
         T* dv = alloc_dinv<T>(h, sz[sidx]);
-        diag.push_back({lay.row[sidx], sz[sidx], lay.ld[sidx], dv, bw, bw2});
+        diag.push_back({lay.row[sidx], sz[sidx], lay.ld[sidx], dv, bw, bw2, band, 0});
         diag_cl.push_back(sidx);
         diag_fl.push_back(cfl);
         add_panels(tr_tasks, lay.row[sidx], (const T*)dv, sz[sidx], lay.ld[sidx], sz[sidx], lay.W[sidx], bw, &tr_fl,
@@ -2895,6 +2931,7 @@ int spand_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const
   // r_j = #{i >= j : f(i) <= j} of U give the Cholesky flops sum_j r_j^2.
   h->env_bw.assign(nc, 0);
   h->env_bw32.assign(nc, 0);
+  h->env_band.assign(nc, 0);
   h->env_flops.assign(nc, 0.0);
   h->env_nnz.assign(nc, 0.0);
   if (n > 0) {
@@ -2913,12 +2950,13 @@ int spand_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const
         }
         f[i] = fi;
       }
-      int32_t bw = 0, bw32 = 0;
+      int32_t bw = 0, bw32 = 0, band = 0;
       double nnzU = 0;
       cnt.assign((size_t)sz + 1, 0);
       for (int32_t i = 0; i < sz; ++i) {
         bw = std::max(bw, i / 64 - f[i] / 64);
         bw32 = std::max(bw32, i / 32 - f[i] / 32);
+        band = std::max(band, i - f[i]);
         nnzU += i - f[i] + 1;
         ++cnt[f[i]];  // column i covers rows f(i) .. i
         --cnt[i + 1];
@@ -2931,6 +2969,7 @@ int spand_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const
       const int32_t ntile = (sz + 63) / 64, ntile32 = (sz + 31) / 32;
       h->env_bw[c] = (bw + 1 >= ntile) ? 0 : bw;  // 0: dense (no tile is structurally zero)
       h->env_bw32[c] = (bw32 + 1 >= ntile32) ? 0 : bw32;
+      h->env_band[c] = (band + 1 >= sz) ? 0 : band;
       h->env_flops[c] = fl;
       h->env_nnz[c] = nnzU;
     }
