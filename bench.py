@@ -198,13 +198,13 @@ HBM_BOUND = {"copy", "apply", "pcg"}
 MEASURED_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of the 212 sparsification
     # launches of one factorization (k_cpqr_cluster, k_cpqr_reg, k_form_q:
-    # 583.9 MB read, 14.1 MB written) and of three applications (3104.1 MB
-    # read, 40.4 MB written); ncu, one pass
-    "cpqr": {"bytes_per_launch": (583.9e6 + 14.1e6) / 212,
+    # 583.9 MB read, 14.0 MB written) and of three applications (3100.6 MB
+    # read, 40.1 MB written); ncu, one pass
+    "cpqr": {"bytes_per_launch": (583.9e6 + 14.0e6) / 212,
              "src": ["paper_1901_02971_gb300/csrc/cpqr_cluster.cuh", "paper_1901_02971_gb300/csrc/cpqr_reg.cuh"],
-             "sha256": ["70c5f5687cb1faaca31b30549d96136cb5fb766a4f5236057435ff4a20d2804e",
+             "sha256": ["df1a284e74542b5aa3f39bc25ec90beb14e91cbaa13b15fbeed6c93563a1f421",
                         "f4375f2638107797fe808912ff23db71eba06329efe4f946106ee94aebe58cd8"]},
-    "apply": {"bytes_per_launch": (3104.1e6 + 40.4e6) / 3, "src": "paper_1901_02971_gb300/csrc/solve_kernels.cuh",
+    "apply": {"bytes_per_launch": (3100.6e6 + 40.1e6) / 3, "src": "paper_1901_02971_gb300/csrc/solve_kernels.cuh",
               "sha256": "6520881e8f0975871035275afc7fec1c110a1adcde70f8a412a4ef8d529d2dcf"},
 }
 
