@@ -187,21 +187,30 @@ __global__ void __launch_bounds__(TileGeom<B>::NTH) k_potrf_update(const RowDesc
 //      b (b + 1) / 2 window entries k + 1 < i <= j <= k + 1 + b, spread evenly
 //      over the threads by a table of (i, j) offsets;
 //   4. columns k, k + 1 are final: each thread stores its element of them
-//      and loads in its place the element of column k + b + 2 (or k + b + 3),
-//      which no step has touched yet.
+//      and puts in its place the element of column k + b + 2 (or k + b + 3),
+//      which no step has touched yet; the global load is issued before 3
+//      and the store after it (3 touches only columns k + 2 and up), so its
+//      latency hides behind the update.
 // The tiled kernels would do about four times the arithmetic on such a band
 // (a 32 x 32 tile step covers rows k .. k + 95 in full).  A pivot that is not
 // positive is reported like the tiled kernels' (the block's batch index + 1).
 constexpr int BAND_MAX = 96;   // widest band taken by this kernel
-constexpr int BAND_NT = 256;
+constexpr int BAND_NT = 256;   // >= 2 (BAND_MAX + 1): one element of step 4 per thread
+static_assert(BAND_NT >= 2 * (BAND_MAX + 1), "one element of step 4 per thread");
 
 struct BandTask {
   double* R;        // the block, column-major, leading dimension ld (upper triangle read and overwritten)
   int32_t n, ld, band, entry;  // entry: index of the block in its pivot batch (for the failure flag)
 };
 
+// Column stride of the window: b + 1 entries, rounded up to an even count of
+// doubles.  Step 2's threads walk the window diagonally (column + 1, row - 1:
+// a stride of one column less one element), which must be odd for the
+// threads of a warp to spread over the shared-memory banks.
+__host__ __device__ inline int band_cl(int b) { return (b + 2) & ~1; }
+
 __host__ __device__ inline size_t band_smem(int b) {
-  return (size_t)(b + 2) * (b + 1) * sizeof(double) + 2 * (size_t)(b + 2) * sizeof(double) +
+  return (size_t)(b + 2) * band_cl(b) * sizeof(double) + 2 * (size_t)(b + 2) * sizeof(double) +
          (((size_t)b * (b + 1) / 2 * sizeof(uint16_t) + 15) & ~size_t(15));
 }
 
@@ -209,7 +218,7 @@ __global__ void __launch_bounds__(BAND_NT) k_potrf_band(const BandTask* __restri
   pdl_wait();
   const BandTask d = tasks[blockIdx.x];
   const int n = d.n, b = d.band, ld = d.ld, tid = threadIdx.x;
-  const int WS = b + 2, CL = b + 1;
+  const int WS = b + 2, CL = band_cl(b), CB = b + 1;  // CB: entries used per column
   extern __shared__ __align__(16) unsigned char smraw[];
   double* win = reinterpret_cast<double*>(smraw);
   double* u0 = win + (size_t)WS * CL;  // u0[x] = U(k, k + x), x = 0 .. b + 1
@@ -224,8 +233,8 @@ __global__ void __launch_bounds__(BAND_NT) k_potrf_band(const BandTask* __restri
     for (int xi = 2; xi <= xj; ++xi) pairs[e++] = (uint16_t)((xi << 8) | xj);
   }
   // initial window: columns 0 .. min(n, WS) - 1 into slots 0 ..
-  for (int e = tid; e < min(n, WS) * CL; e += BAND_NT) {
-    const int j = e / CL, r = e % CL, i = j - b + r;
+  for (int e = tid; e < min(n, WS) * CB; e += BAND_NT) {
+    const int j = e / CB, r = e % CB, i = j - b + r;
     win[(size_t)j * CL + r] = i >= 0 ? d.R[i + (size_t)j * ld] : 0.0;
   }
   __syncthreads();
@@ -270,6 +279,19 @@ __global__ void __launch_bounds__(BAND_NT) k_potrf_band(const BandTask* __restri
     }
     if (tid == 0) win[(size_t)(k % WS) * CL + b] = u0[0];
     __syncthreads();
+    // 4. (issued first, it overlaps 3: disjoint columns) columns k, k + 1
+    // are final: each thread reads the element of column k + WS or
+    // k + 1 + WS it will put in place of its element of column k or k + 1
+    const int e4 = tid;  // 2 (b + 1) <= 2 (BAND_MAX + 1) < BAND_NT elements
+    const bool has4 = e4 < 2 * CB && k + e4 / CB < n;
+    double nv = 0.0;
+    int c4 = 0, r4 = 0;
+    if (has4) {
+      c4 = k + e4 / CB;
+      r4 = e4 % CB;
+      const int cn = c4 + WS, in = cn - b + r4;
+      if (cn < n && in >= 0) nv = d.R[in + (size_t)cn * ld];
+    }
     // 3. rank-2 update of the window ahead of the pivot rows
     // (a single last row, n = k + 1, has nothing after it to update)
     if (two)
@@ -281,16 +303,11 @@ __global__ void __launch_bounds__(BAND_NT) k_potrf_band(const BandTask* __restri
         double& a = win[(size_t)(j % WS) * CL + (i - j + b)];
         a = fma(-u1[xi], u1[xj], fma(-u0[xi], u0[xj], a));
       }
-    __syncthreads();
-    // 4. columns k, k + 1 are final: store them, load k + WS, k + 1 + WS in their slots
-    for (int e = tid; e < 2 * CL; e += BAND_NT) {
-      const int c = k + e / CL, r = e % CL;
-      if (c >= n) continue;
-      double* slot = win + (size_t)(c % WS) * CL;
-      const int i = c - b + r;
-      if (i >= 0) d.R[i + (size_t)c * ld] = slot[r];
-      const int cn = c + WS, in = cn - b + r;
-      if (cn < n) slot[r] = in >= 0 ? d.R[in + (size_t)cn * ld] : 0.0;
+    if (has4) {
+      double* slot = win + (size_t)(c4 % WS) * CL;
+      const int i = c4 - b + r4;
+      if (i >= 0) d.R[i + (size_t)c4 * ld] = slot[r4];
+      if (c4 + WS < n) slot[r4] = nv;
     }
     __syncthreads();
   }
