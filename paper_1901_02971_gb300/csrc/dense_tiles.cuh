@@ -149,6 +149,25 @@ __device__ __forceinline__ void load_tile(SqTileB<T, B>& s, const T* P, int ld, 
   }
 }
 
+// The same load issued as asynchronous copies (cp.async, one element each,
+// zero-filled outside mi x nj); complete with cp_async_wait_all() and a block
+// barrier before reading the tile.
+template <typename T, int B>
+__device__ __forceinline__ void load_tile_async(SqTileB<T, B>& s, const T* P, int ld, int mi, int nj) {
+  for (int e = threadIdx.x; e < B * B; e += TileGeom<B>::NTH) {
+    const int i = e % B, j = e / B;
+    const bool in = i < mi && j < nj;
+    const T* src = in ? P + i + (size_t)j * ld : P;
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(&s.v[i][j]);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(dst), "l"(src), "n"(sizeof(T)),
+                 "r"(in ? (int)sizeof(T) : 0)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 template <typename T, int B>
 __device__ __forceinline__ void store_tile(const SqTileB<T, B>& s, T* P, int ld, int mi, int nj) {
   for (int e = threadIdx.x; e < B * B; e += TileGeom<B>::NTH) {

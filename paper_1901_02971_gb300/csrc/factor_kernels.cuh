@@ -198,8 +198,9 @@ constexpr int BAND_MAX = 96;   // widest band taken by this kernel
 constexpr int BAND_NT = 256;   // >= 2 (BAND_MAX + 1): one element of step 4 per thread
 static_assert(BAND_NT >= 2 * (BAND_MAX + 1), "one element of step 4 per thread");
 
+template <typename TS>
 struct BandTask {
-  double* R;        // the block, column-major, leading dimension ld (upper triangle read and overwritten)
+  TS* R;            // the block, column-major, leading dimension ld (upper triangle read and overwritten)
   int32_t n, ld, band, entry;  // entry: index of the block in its pivot batch (for the failure flag)
 };
 
@@ -214,9 +215,13 @@ __host__ __device__ inline size_t band_smem(int b) {
          (((size_t)b * (b + 1) / 2 * sizeof(uint16_t) + 15) & ~size_t(15));
 }
 
-__global__ void __launch_bounds__(BAND_NT) k_potrf_band(const BandTask* __restrict__ tasks, int* info) {
+// TS: the factor's storage type; the block is read from it and U written
+// back to it directly (an FP32 factor needs no FP64 copy: the window is
+// FP64), all arithmetic in FP64.
+template <typename TS>
+__global__ void __launch_bounds__(BAND_NT) k_potrf_band(const BandTask<TS>* __restrict__ tasks, int* info) {
   pdl_wait();
-  const BandTask d = tasks[blockIdx.x];
+  const BandTask<TS> d = tasks[blockIdx.x];
   const int n = d.n, b = d.band, ld = d.ld, tid = threadIdx.x;
   const int WS = b + 2, CL = band_cl(b), CB = b + 1;  // CB: entries used per column
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -235,7 +240,7 @@ __global__ void __launch_bounds__(BAND_NT) k_potrf_band(const BandTask* __restri
   // initial window: columns 0 .. min(n, WS) - 1 into slots 0 ..
   for (int e = tid; e < min(n, WS) * CB; e += BAND_NT) {
     const int j = e / CB, r = e % CB, i = j - b + r;
-    win[(size_t)j * CL + r] = i >= 0 ? d.R[i + (size_t)j * ld] : 0.0;
+    win[(size_t)j * CL + r] = i >= 0 ? (double)d.R[i + (size_t)j * ld] : 0.0;
   }
   __syncthreads();
   for (int k = 0; k < n; k += 2) {
@@ -290,7 +295,7 @@ __global__ void __launch_bounds__(BAND_NT) k_potrf_band(const BandTask* __restri
       c4 = k + e4 / CB;
       r4 = e4 % CB;
       const int cn = c4 + WS, in = cn - b + r4;
-      if (cn < n && in >= 0) nv = d.R[in + (size_t)cn * ld];
+      if (cn < n && in >= 0) nv = (double)d.R[in + (size_t)cn * ld];
     }
     // 3. rank-2 update of the window ahead of the pivot rows
     // (a single last row, n = k + 1, has nothing after it to update)
@@ -306,7 +311,7 @@ __global__ void __launch_bounds__(BAND_NT) k_potrf_band(const BandTask* __restri
     if (has4) {
       double* slot = win + (size_t)(c4 % WS) * CL;
       const int i = c4 - b + r4;
-      if (i >= 0) d.R[i + (size_t)c4 * ld] = slot[r4];
+      if (i >= 0) d.R[i + (size_t)c4 * ld] = (TS)slot[r4];
       if (c4 + WS < n) slot[r4] = nv;
     }
     __syncthreads();
@@ -334,7 +339,9 @@ __global__ void __launch_bounds__(NT) k_inv_diag(const RowDesc<T>* __restrict__ 
 
 // B <- U^{-T} B for one panel of at most 64 columns, left-looking over the
 // row tiles (B_i -= sum_{l<i} U_li^T X_l; X_i = U_ii^{-T} B_i).  Rows of B
-// above i_start are zero (identity right-hand sides) and are skipped.
+// above i_start are zero (identity right-hand sides) and are skipped.  The
+// next row tile's U_ii^{-T} and B_i (neither written by this tile) are
+// copied asynchronously while this tile's GEMM with the solved rows runs.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_trsm_cols(const TrsmTask<T>* __restrict__ tasks) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -347,6 +354,10 @@ __global__ void __launch_bounds__(NT) k_trsm_cols(const TrsmTask<T>* __restrict_
   T* X = d.B;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int is = (d.i_start / TB) * TB;
+  if (is < d.n) {
+    load_tile_async(U, d.dinv + (size_t)(is / TB) * TB * TB, TB, TB, TB);  // U_ii^{-T}
+    load_tile_async(B, X + is, d.ldb, min(TB, d.n - is), nc);
+  }
   for (int i0 = is; i0 < d.n; i0 += TB) {
     const int nb = min(TB, d.n - i0);
     T acc[4][4];
@@ -354,8 +365,7 @@ __global__ void __launch_bounds__(NT) k_trsm_cols(const TrsmTask<T>* __restrict_
     // rows of U's column block i0 above the band are zero tiles
     const int ls = d.bw > 0 ? max(is, i0 - d.bw * TB) : is;
     if (i0 > ls) tn_acc(acc, d.U + ls + (size_t)i0 * d.ldu, d.ldu, nb, X + ls, d.ldb, nc, i0 - ls, sm);
-    load_tile(U, d.dinv + (size_t)(i0 / TB) * TB * TB, TB, TB, TB);  // U_ii^{-T}
-    load_tile(B, X + i0, d.ldb, nb, nc);
+    cp_async_wait_all();  // this tile's U_ii^{-T} and B_i
     __syncthreads();
 #pragma unroll
     for (int ii = 0; ii < 4; ++ii)
@@ -368,6 +378,11 @@ __global__ void __launch_bounds__(NT) k_trsm_cols(const TrsmTask<T>* __restrict_
     apply_inv_tile(U, B, nb);
     store_tile(B, X + i0, d.ldb, nb, nc);
     __syncthreads();
+    const int i1 = i0 + TB;
+    if (i1 < d.n) {
+      load_tile_async(U, d.dinv + (size_t)(i1 / TB) * TB * TB, TB, TB, TB);
+      load_tile_async(B, X + i1, d.ldb, min(TB, d.n - i1), nc);
+    }
   }
 }
 

@@ -693,8 +693,20 @@ static void pivot_chol(spand_handle h, const std::vector<RowDesc<T>>& rows, int*
   std::vector<RowDesc<double>> r64;
   std::vector<PivotCopy> cps;
   r64.reserve(rows.size());
+  // banded blocks (step-1 pivots with a narrow band) go to the banded kernel,
+  // on their own storage (no FP64 copy); the tiled batch skips them (n = 0
+  // keeps the batch indices, which the failure flag reports)
+  std::vector<BandTask<T>> bands;
+  int bmax = 0;
   size_t o = 0;
-  for (auto& r : rows) {
+  for (size_t i = 0; i < rows.size(); ++i) {
+    const RowDesc<T>& r = rows[i];
+    if (r.band > 0 && r.band <= BAND_MAX && r.band + 1 < r.n) {
+      bands.push_back({r.R, r.n, r.ld, r.band, (int32_t)i});
+      bmax = std::max(bmax, r.band);
+      r64.push_back({nullptr, 0, 1, nullptr, 0, 0});
+      continue;
+    }
     double* W = nullptr;
     if (wide) {
       W = base + o;
@@ -706,23 +718,10 @@ static void pivot_chol(spand_handle h, const std::vector<RowDesc<T>>& rows, int*
     if (wide) r64.push_back({W, r.n, r.n, D, r.bw2, 0});
     else r64.push_back({(double*)r.R, r.n, r.ld, D, r.bw2, 0});
   }
-  // banded blocks (step-1 pivots with a narrow band) go to the banded
-  // kernel; the tiled batch skips them (n = 0 keeps the batch indices, which
-  // the failure flag reports)
-  std::vector<BandTask> bands;
-  int bmax = 0;
-  for (size_t i = 0; i < rows.size(); ++i) {
-    const RowDesc<T>& r = rows[i];
-    if (r.band > 0 && r.band <= BAND_MAX && r.band + 1 < r.n) {
-      bands.push_back({r64[i].R, r.n, r64[i].ld, r.band, (int32_t)i});
-      bmax = std::max(bmax, r.band);
-      r64[i].n = 0;
-    }
-  }
   bool dense_left = false;
   for (const auto& r : r64) dense_left = dense_left || r.n > 0;
   const PivotCopy* dc = nullptr;
-  if (wide) {
+  if (wide && !cps.empty()) {
     Packer pk;
     const size_t oc = pk.add(cps);
     void* d = upload<T>(h, pk, s);
@@ -739,22 +738,22 @@ static void pivot_chol(spand_handle h, const std::vector<RowDesc<T>>& rows, int*
     const size_t ob = pk.add(bands);
     void* d = upload<T>(h, pk, s);
     const size_t sm = band_smem(bmax);
-    ensure_smem((const void*)k_potrf_band, sm);
+    ensure_smem((const void*)k_potrf_band<T>, sm);
     const int pid = h->prof.begin(F_POTRF, s);
     for (size_t b0 = 0; b0 < bands.size(); b0 += 65535) {
       const unsigned cnt = (unsigned)std::min<size_t>(bands.size() - b0, 65535);
-      launch_pdl(k_potrf_band, dim3(cnt), dim3(BAND_NT), sm, s, at<const BandTask>(d, ob) + b0, d_info);
+      launch_pdl(k_potrf_band<T>, dim3(cnt), dim3(BAND_NT), sm, s, at<const BandTask<T>>(d, ob) + b0, d_info);
       ++h->prof.launches;
     }
     double fl = 0, by = 0;
-    for (const BandTask& b : bands) {
+    for (const BandTask<T>& b : bands) {
       fl += row_flops ? (*row_flops)[b.entry] : (double)b.n * b.band * b.band;
-      by += 2.0 * b.n * (b.band + 1) * sizeof(double);
+      by += 2.0 * b.n * (b.band + 1) * sizeof(T);
     }
     h->prof.end(pid, s, fl, by, (int64_t)((bands.size() + 65534) / 65535));
   }
   if (dense_left) potrf_batch<double, TB2>(h, r64, d_info, s, row_flops);
-  if (wide) {
+  if (wide && !cps.empty()) {
     for (size_t b0 = 0; b0 < cps.size(); b0 += 65535) {
       const unsigned cnt = (unsigned)std::min<size_t>(cps.size() - b0, 65535);
       k_narrow_pivot<<<dim3(8, cnt), 256, 0, s>>>(dc + b0);
