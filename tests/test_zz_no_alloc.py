@@ -50,7 +50,10 @@ def test_noalloc_apply_in_place(cuda_ok):
 
 
 def test_noalloc_rejects_work_space_beyond_the_fixed_array(cuda_ok):
-    """2.25M unknowns alone exceed the 2^21-double array: clear error, no GPU work."""
+    """2.25M unknowns alone exceed the 2^21-double array: clear error, no GPU
+    work in the call.  The check itself is host arithmetic on n and the
+    apply's temporaries, but reaching it needs a factorization of that size
+    (about a second of GPU time, the heaviest case of this file)."""
     import torch
     p = I.laplacian_2d(1500)
     s = Solver.from_problem(p, levels=14, eps=1e-1, precision="fp32").factorize()
