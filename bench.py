@@ -50,12 +50,20 @@ p = I.laplacian_3d(%(grid)d); b = I.rhs(p.n, %(seed)d)
 t0 = time.perf_counter(); tr = O.analyze(p.n, p.rowptr, p.colind, p.coords, %(levels)d); t_p = time.perf_counter() - t0
 print(json.dumps(dict(kind="analysis", t_p=t_p, n=p.n, nnz=p.nnz)), flush=True)
 A = O.permuted_matrix(p.rowptr, p.colind, p.vals, tr.perm)
+W = %(workers)d
+if W > 1:  # the all-core leg: the independent blocks of each level and colour on a spawn pool
+    from oracle import spand_parallel as OP
+    pool = OP.make_pool(W)
+    list(pool.map(abs, range(4 * W)))  # workers started (and the oracle imported) before the clock
+    fact = lambda: OP.factorize(p.rowptr, p.colind, p.vals, tr, %(eps)r, pool, W)
+else:
+    fact = lambda: O.factorize(p.rowptr, p.colind, p.vals, tr, %(eps)r)
 start = time.perf_counter(); last = 0.0
 for i in range(%(steps)d):
     if i > 0 and time.perf_counter() - start + last > %(budget)r:
         break
     t1 = time.perf_counter()
-    F = O.factorize(p.rowptr, p.colind, p.vals, tr, %(eps)r)
+    F = fact()
     t2 = time.perf_counter()
     x, it, rr = O.pcg(A, b[tr.perm], lambda r: O.apply(F, r))
     t3 = time.perf_counter()
@@ -66,15 +74,18 @@ for i in range(%(steps)d):
 
 
 def oracle_runs(steps: int = 1, budget_s: float = 1e30, threads: int = 1, grid: int = GRID,
-                levels: int = LEVELS) -> dict:
+                levels: int = LEVELS, workers: int = 1) -> dict:
     """Times the FP64 oracle on the whole workload in a fresh process
     (started before any CUDA work in this one; its BLAS/LAPACK limited to
-    `threads` threads): the analysis once, then up to `steps` full
-    factorizations + PCG solves, stopping early when the next one would run
-    past `budget_s` (at least one always runs).  Returns t_P and the list of
-    per-step t_F, t_S, n_CG."""
+    `threads` threads per process): the analysis once, then up to `steps`
+    full factorizations + PCG solves, stopping early when the next one would
+    run past `budget_s` (at least one always runs).  With workers > 1 the
+    factorization is the all-core leg (oracle/spand_parallel.py: the
+    independent blocks of each level and colour on a pool of that many
+    processes); the PCG stays serial.  Returns t_P and the list of per-step
+    t_F, t_S, n_CG."""
     code = _ORACLE_RUN % dict(root=ROOT, grid=grid, seed=SEED, levels=levels, steps=max(1, steps),
-                              budget=float(budget_s), eps=EPS)
+                              budget=float(budget_s), eps=EPS, workers=int(workers))
     t = str(int(threads))
     env = dict(os.environ, OPENBLAS_NUM_THREADS=t, OMP_NUM_THREADS=t, MKL_NUM_THREADS=t)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=7200)
@@ -492,9 +503,14 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     rank, world, local = dist_env()
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and (args.grid, args.levels) == (GRID, LEVELS):
         cpu = oracle_runs(steps=1)  # the whole workload, once, 1 thread; before any CUDA work here
+        ncores = os.cpu_count() or 1
+        try:
+            cpu_all = (oracle_runs(steps=1, workers=ncores), ncores) if ncores > 1 else None
+        except RuntimeError as e:  # reported, never fatal to the headline line
+            cpu_all = ({"error": str(e)[-300:]}, ncores)
     import numpy as np
     import torch
 
@@ -526,8 +542,9 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def run_form(precision, steps, warmup, timed_clocks=False, skip=0, order="coloured"):
-        s = Solver.from_problem(p, levels=levels, eps=EPS, precision=precision, skip=skip, sparsify_order=order)
+    def run_form(precision, steps, warmup, timed_clocks=False, skip=0, order="coloured", **kw):
+        s = Solver.from_problem(p, levels=levels, eps=EPS, precision=precision, skip=skip, sparsify_order=order,
+                                **kw)
         for _ in range(warmup):
             s.factorize(vals_d)
             s.solve(b_d, x_d)
@@ -593,6 +610,21 @@ def main():
         ssim.close()
     except Exception as e:  # reported, never fatal to the headline line
         sim = {"error": str(e)[:300]}
+    # the other compressions of the interfaces, same form and workload: the
+    # randomized range finder (sketch in place of the QR of A_pn) and the
+    # interpolative variants InS / In (Sec. 2.6.2)
+    alt = {}
+    for name, kw in (("randomized", {"compression": "randomized", "sketch_seed": 7}),
+                     ("InS", {"variant": "InS"}), ("In", {"variant": "In"})):
+        try:
+            sa, ta, ita, rra, _, _ = run_form(args.form, 2, 1, **kw)
+            pha = sa.phase_times()
+            alt[name] = {"s_per_step": statistics.mean(ta), "iters": ita[-1], "relres": rra,
+                         "t_factor_ms_phases": list(pha[:4]), "apply_ms": pha[4], "size_top": sa.stats().size_top,
+                         "mem_f": sa.stats().mem_f}
+            sa.close()
+        except Exception as e:  # reported, never fatal to the headline line
+            alt[name] = {"error": str(e)[:300]}
     st64 = s64.stats()
     ph64 = s64.phase_times()
     # accuracy of x of each form against each other (FP64 reference on the GPU)
@@ -652,6 +684,7 @@ def main():
             "x_vs_fp64_oracle": vs_oracle,
             "skip_sweep_mixed_" + args.form: sweep,
             "mixed_" + args.form + "_simultaneous_order": sim,
+            "mixed_" + args.form + "_compressions": alt,
         },
         "e2e": {"value": ve, "unit": "s", "h2d_bytes_per_step": int(p.nnz * 8 + p.n * 8),
                 "d2h_bytes_per_step": int(p.n * 8)},
@@ -672,6 +705,19 @@ def main():
                                          f"cube (L={LEVELS}) on 1 host core ({cpu_model()}), {ph['n_cg']} "
                                          f"iterations; analysis t_P {ph['t_p_s']:.1f} s not in the metric",
                                "phases": ph}
+    if cpu_all is not None:
+        run_all, ncores = cpu_all
+        if "error" in run_all:
+            out["cpu_baseline_all_cores"] = {"error": run_all["error"], "cores": ncores}
+        else:
+            pa = oracle_phases(run_all)
+            out["cpu_baseline_all_cores"] = {
+                "value": pa["t_f_s"] + pa["t_s_s"], "unit": "s", "cores": ncores, "kind": "oracle",
+                "sample": f"the whole workload, once: the oracle's factorization with the independent blocks of "
+                          f"each level and colour on a pool of {ncores} processes (spawn; blocks pickled to and "
+                          f"from the workers; oracle/spand_parallel.py), then the serial PCG; "
+                          f"{pa['n_cg']} iterations; analysis t_P {pa['t_p_s']:.1f} s not in the metric",
+                "phases": pa}
     print(json.dumps(out))
     s32.close()
     s64.close()
