@@ -50,6 +50,23 @@ __device__ __forceinline__ void philox_gauss4(uint64_t k0, uint64_t k1, uint64_t
   z[3] = rb * sinpi(2.0 * u[3]);
 }
 
+// The same four entries from the same Philox words with Box-Muller in FP32
+// (for FP32 sketches): u = (w >> 11) 2^-53 + 2^-54 rounded to float, then
+// CUDA's logf / sqrtf / cospif / sinpif; within about 1e-6 of
+// philox_gauss4's entries.
+__device__ __forceinline__ void philox_gauss4f(uint64_t k0, uint64_t k1, uint64_t j, uint64_t b, float z[4]) {
+  uint64_t x[4] = {j, b, 0ull, 0ull};
+  philox4x64_10(x, k0, k1);
+  float u[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) u[k] = fmaf(__ull2float_rn(x[k] >> 11), 0x1.0p-53f, 0x1.0p-54f);
+  const float ra = sqrtf(-2.0f * logf(u[0])), rb = sqrtf(-2.0f * logf(u[2]));
+  z[0] = ra * cospif(2.0f * u[1]);
+  z[1] = ra * sinpif(2.0f * u[1]);
+  z[2] = rb * cospif(2.0f * u[3]);
+  z[3] = rb * sinpif(2.0f * u[3]);
+}
+
 // out: m x ell, column-major (leading dimension m); one thread per 4-row block
 // of one column (grid-stride).
 __global__ void k_sketch_philox(uint64_t k0, uint64_t k1, int m, int ell, double* __restrict__ out) {

@@ -1095,7 +1095,7 @@ static std::vector<int> sparsify_randomized(spand_handle h, int t, const std::ve
           maxnew = std::max(maxnew, ub[k] - prev[k]);
         }
       if (alist.empty()) break;
-      k_rand_omega<T><<<dim3(16, nc), 256, 0, s>>>(d_rt, seed, t);
+      k_rand_omega<T><<<dim3(32, nc), 256, 0, s>>>(d_rt, seed, t);
       CKLAUNCH();
       const int tiles = ((npmax + 31) / 32) * ((maxnew + 31) / 32);
       k_rand_sketch<T><<<dim3(tiles, nc), 256, 0, s>>>(d_rt);
@@ -1196,7 +1196,8 @@ static std::vector<int> sparsify_randomized(spand_handle h, int t, const std::ve
         }
       }
     }
-    k_rand_writeback<T><<<nc, 256, 0, s>>>(d_rt, d_nbrs, d_cur);
+    k_rand_writeback<T><<<dim3((unsigned)std::min(32, (mmax + npmax + 63) / 64), nc), 256, 0, s>>>(d_rt, d_nbrs,
+                                                                                                  d_cur);
     CKLAUNCH();
     h->prof.launches += nl + 1;
   }
@@ -1436,9 +1437,16 @@ static std::vector<InterpOut<T>> sparsify_interp(spand_handle h, const std::vect
         CKLAUNCH();
         ++nl;
       }
-      k_interp_store<T><<<nc, 256, 0, s>>>(at<const InterpTask<T>>(d2, oi2), d_nbrs, d_cur);
+      // copies, then gathers: the warps of a task's CTAs take columns (about
+      // eight each)
+      int cols = 1;
+      for (const InterpTask<T>& d : it) cols = std::max(cols, d.m + d.np);
+      const dim3 grid((unsigned)std::min(32, (cols + 63) / 64), (unsigned)nc);
+      k_interp_copy<T><<<grid, 256, 0, s>>>(at<const InterpTask<T>>(d2, oi2), d_nbrs, d_cur);
       CKLAUNCH();
-      ++nl;
+      k_interp_store<T><<<grid, 256, 0, s>>>(at<const InterpTask<T>>(d2, oi2), d_nbrs, d_cur);
+      CKLAUNCH();
+      nl += 2;
     }
     h->st.factor_flops += fl;
     h->prof.launches += nl;

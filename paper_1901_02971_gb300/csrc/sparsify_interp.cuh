@@ -275,70 +275,77 @@ __global__ void __launch_bounds__(256) k_dgemm_sub(const DGemmTask* __restrict__
     }
 }
 
-// Step 4 (one CTA per task): the factor blocks F = [C_ff | C_fc] (from P,
-// rounded to the factor's type) and X^T = T_cf (r x nf, ld r) of the apply's
-// T_p; p keeps A_cc (P's leading r x r block), the rows c (pivot order) of
-// its coupling blocks, and every neighbour q the columns c of its block A_qp;
-// the size of p becomes r.  The coupling blocks are first copied (the gather
-// is in place).
+// Step 4a: copies of the coupling blocks before the in-place gathers of step
+// 4b: p's coupling columns (np x m, column j of A_pn at cp[j np]), then each
+// neighbour's block A_qp (w_q x np, column a at w_q a after the previous
+// neighbours' blocks).  Grid (CTAs per task, tasks): the warps of a task's
+// CTAs take columns, the lanes rows.
+template <typename T>
+__global__ void __launch_bounds__(256) k_interp_copy(const InterpTask<T>* __restrict__ tasks,
+                                                     const CpqrNbr<T>* __restrict__ nbrs,
+                                                     const int32_t* __restrict__ cur_size) {
+  const InterpTask<T> d = tasks[blockIdx.y];
+  const int np = d.np, m = d.m, lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * 8 + (threadIdx.x >> 5), nw = gridDim.x * 8;
+  for (int j = gw; j < m; j += nw) {
+    const T* src = d.Rp + (size_t)d.tcol[j] * d.ldp;
+    T* dst = d.cp + (size_t)j * np;
+    for (int i = lane; i < np; i += 32) dst[i] = src[i];
+  }
+  T* cpq = d.cp + (size_t)np * m;
+  for (int e = d.nbeg; e < d.nend; ++e) {
+    const CpqrNbr<T> nb = nbrs[e];
+    const int w = cur_size[nb.q];
+    for (int a = gw; a < np; a += nw) {
+      const T* src = nb.Rq + (size_t)(nb.off_qp + a) * nb.ldq;
+      T* dst = cpq + (size_t)a * w;
+      for (int jj = lane; jj < w; jj += 32) dst[jj] = src[jj];
+    }
+    cpq += (size_t)w * np;
+  }
+}
+
+// Step 4b, grid (CTAs per task, tasks), after k_interp_copy: the factor
+// blocks F = [C_ff | C_fc] (from P, rounded to the factor's type) and
+// X^T = T_cf (r x nf, ld r) of the apply's T_p; p keeps A_cc (P's leading
+// r x r block), the rows c (pivot order) of its coupling blocks, and every
+// neighbour q the columns c of its block A_qp, all gathered from the copies;
+// the size of p becomes r (no other task of the colour reads it: the
+// interfaces of one colour are not adjacent).
 template <typename T>
 __global__ void __launch_bounds__(256) k_interp_store(const InterpTask<T>* __restrict__ tasks,
                                                       const CpqrNbr<T>* __restrict__ nbrs,
                                                       int32_t* __restrict__ cur_size) {
-  const InterpTask<T> d = tasks[blockIdx.x];
-  const int np = d.np, r = d.r, nf = d.nf, m = d.m, tid = threadIdx.x;
+  const InterpTask<T> d = tasks[blockIdx.y];
+  const int np = d.np, r = d.r, nf = d.nf, m = d.m, lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * 8 + (threadIdx.x >> 5), nw = gridDim.x * 8;
   const double* P = d.P;
-  // copies: p's coupling columns (np x m), then the neighbours' blocks (w_q x np each)
-  T* cpp = d.cp;
-  T* cpq = d.cp + (size_t)np * m;
-  for (int64_t e = tid; e < (int64_t)np * m; e += 256) {
-    const int i = (int)(e % np), j = (int)(e / np);
-    cpp[e] = d.Rp[i + (size_t)d.tcol[j] * d.ldp];
-  }
-  {
-    int64_t o = 0;
-    for (int e = d.nbeg; e < d.nend; ++e) {
-      const CpqrNbr<T> nb = nbrs[e];
-      const int w = cur_size[nb.q];
-      for (int64_t t = tid; t < (int64_t)w * np; t += 256) {
-        const int jj = (int)(t % w), a = (int)(t / w);
-        cpq[o + t] = nb.Rq[jj + (size_t)(nb.off_qp + a) * nb.ldq];
-      }
-      o += (int64_t)w * np;
+  for (int b = gw; b < r; b += nw)  // A_cc
+    for (int a = lane; a < r; a += 32) d.Rp[a + (size_t)b * d.ldp] = (T)P[a + (size_t)b * np];
+  for (int j = gw; j < np; j += nw)  // [C_ff | C_fc]
+    for (int i = lane; i < nf; i += 32) {
+      const double v = j < nf ? P[(r + i) + (size_t)(r + j) * np] : P[(j - nf) + (size_t)(r + i) * np];
+      d.F[i + (size_t)j * d.ldf] = (T)v;
     }
+  for (int j = gw; j < nf; j += nw)  // T_cf, column-major ld r
+    for (int a = lane; a < r; a += 32) d.XT[a + (size_t)j * r] = (T)d.G[(size_t)a * nf + j];
+  for (int j = gw; j < m; j += nw) {  // rows c of p's coupling blocks
+    T* dst = d.Rp + (size_t)d.tcol[j] * d.ldp;
+    const T* src = d.cp + (size_t)j * np;
+    for (int a = lane; a < r; a += 32) dst[a] = src[d.perm[a]];
   }
-  __syncthreads();
-  for (int64_t e = tid; e < (int64_t)r * r; e += 256) {  // A_cc
-    const int a = (int)(e % r), b = (int)(e / r);
-    d.Rp[a + (size_t)b * d.ldp] = (T)P[a + (size_t)b * np];
-  }
-  for (int64_t e = tid; e < (int64_t)nf * np; e += 256) {  // [C_ff | C_fc]
-    const int i = (int)(e % nf), j = (int)(e / nf);
-    const double v = j < nf ? P[(r + i) + (size_t)(r + j) * np] : P[(j - nf) + (size_t)(r + i) * np];
-    d.F[i + (size_t)j * d.ldf] = (T)v;
-  }
-  for (int64_t e = tid; e < (int64_t)r * nf; e += 256) {  // T_cf, column-major ld r
-    const int a = (int)(e % r), j = (int)(e / r);
-    d.XT[e] = (T)d.G[(size_t)a * nf + j];
-  }
-  for (int64_t e = tid; e < (int64_t)r * m; e += 256) {  // rows c of p's coupling blocks
-    const int a = (int)(e % r), j = (int)(e / r);
-    d.Rp[a + (size_t)d.tcol[j] * d.ldp] = cpp[d.perm[a] + (size_t)j * np];
-  }
-  {
-    int64_t o = 0;
-    for (int e = d.nbeg; e < d.nend; ++e) {  // columns c of the neighbours' blocks
-      const CpqrNbr<T> nb = nbrs[e];
-      const int w = cur_size[nb.q];
-      for (int64_t t = tid; t < (int64_t)w * r; t += 256) {
-        const int jj = (int)(t % w), a = (int)(t / w);
-        nb.Rq[jj + (size_t)(nb.off_qp + a) * nb.ldq] = cpq[o + jj + (size_t)d.perm[a] * w];
-      }
-      o += (int64_t)w * np;
+  const T* cpq = d.cp + (size_t)np * m;
+  for (int e = d.nbeg; e < d.nend; ++e) {  // columns c of the neighbours' blocks
+    const CpqrNbr<T> nb = nbrs[e];
+    const int w = cur_size[nb.q];
+    for (int a = gw; a < r; a += nw) {
+      T* dst = nb.Rq + (size_t)(nb.off_qp + a) * nb.ldq;
+      const T* src = cpq + (size_t)d.perm[a] * w;
+      for (int jj = lane; jj < w; jj += 32) dst[jj] = src[jj];
     }
+    cpq += (size_t)w * np;
   }
-  __syncthreads();
-  if (tid == 0) cur_size[d.p] = r;
+  if (blockIdx.x == 0 && threadIdx.x == 0) cur_size[d.p] = r;
 }
 
 }  // namespace spand

@@ -78,12 +78,14 @@ __global__ void __launch_bounds__(256) k_rand_init(RandTask<T>* __restrict__ tas
     for (int jj = tid; jj < cst[e + 1] - cst[e]; jj += 256) d.tcol[cst[e] + jj] = nb.off_pq + jj;
   }
   __syncthreads();
-  double mx = 0.0;
-  for (int j = tid; j < m; j += 256) {
+  double mx = 0.0;  // max_j ||A_j||^2: a warp per column, lanes over rows (sums in T)
+  for (int j = tid >> 5; j < m; j += 8) {
     const T* col = d.Rp + (size_t)d.tcol[j] * d.ldp;
-    double s = 0.0;
-    for (int i = 0; i < d.np; ++i) s += (double)col[i] * (double)col[i];
-    mx = fmax(mx, s);
+    T s = T(0);
+    for (int i = tid & 31; i < d.np; i += 32) s = fma(col[i], col[i], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    mx = fmax(mx, (double)s);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -104,23 +106,32 @@ __global__ void __launch_bounds__(256) k_rand_init(RandTask<T>* __restrict__ tas
   }
 }
 
-// Om[:, ell_prev:ell] of every active task (entries as spand_sketch_gaussian
-// draws them, key (seed, step, cluster)).
+// Om[:, ell_prev:ell] of every active task (key (seed, step, cluster);
+// FP64 sketches: entries as spand_sketch_gaussian draws them; FP32 sketches:
+// the same Philox words, Box-Muller in FP32).
 template <typename T>
 __global__ void k_rand_omega(const RandTask<T>* __restrict__ tasks, uint64_t seed, int step) {
   const RandTask<T>& d = tasks[blockIdx.y];
   if (!d.active) return;
   const int m = d.m, nb = (m + 3) / 4, c0 = d.ell_prev, nc = d.ell - d.ell_prev;
   const uint64_t k1 = ((uint64_t)(uint32_t)step << 32) + (uint64_t)(uint32_t)d.p;
-  const int64_t total = (int64_t)nb * nc;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int j = c0 + (int)(t / nb), b = (int)(t % nb);
-    double z[4];
-    philox_gauss4(seed, k1, (uint64_t)j, (uint64_t)b, z);
+  const int total = nb * nc;  // <= (m_max / 4 + 1) * np
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const int j = c0 + t / nb, b = t - (t / nb) * nb;
     T* col = d.Om + (size_t)j * d.m_max;
+    if constexpr (sizeof(T) == 4) {
+      float z[4];
+      philox_gauss4f(seed, k1, (uint64_t)j, (uint64_t)b, z);
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (4 * b + k < m) col[4 * b + k] = (T)z[k];
+      for (int k = 0; k < 4; ++k)
+        if (4 * b + k < m) col[4 * b + k] = z[k];
+    } else {
+      double z[4];
+      philox_gauss4(seed, k1, (uint64_t)j, (uint64_t)b, z);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (4 * b + k < m) col[4 * b + k] = (T)z[k];
+    }
   }
 }
 
@@ -139,11 +150,13 @@ __global__ void __launch_bounds__(256) k_rand_sketch(const RandTask<T>* __restri
   T acc[4] = {T(0), T(0), T(0), T(0)};
   for (int k0 = 0; k0 < d.m; k0 += 32) {
     for (int e = tid; e < 1024; e += 256) {
-      const int i = e & 31, kk = e >> 5;  // a[i][kk] = A(r0 + i, k0 + kk); b[kk][c] = Om(k0 + kk, c0 + c)
+      // a[i][kk] = A(r0 + i, k0 + kk) and b[kk][c] = Om(k0 + kk, c0 + c), the
+      // lanes of a warp along the rows of A and of Om (contiguous in both)
+      const int i = e & 31, kk = e >> 5;
       const int k = k0 + kk;
       a[i][kk] = (r0 + i < d.np && k < d.m) ? d.Rp[(r0 + i) + (size_t)d.tcol[k] * d.ldp] : T(0);
-      const int c = i;
-      b[kk][c] = (k < d.m && c0 + c < d.ell) ? d.Om[k + (size_t)(c0 + c) * d.m_max] : T(0);
+      const int kb = k0 + i, c = kk;
+      b[i][c] = (kb < d.m && c0 + c < d.ell) ? d.Om[kb + (size_t)(c0 + c) * d.m_max] : T(0);
     }
     __syncthreads();
 #pragma unroll 8
@@ -207,14 +220,18 @@ __global__ void __launch_bounds__(256) k_rand_project(RandTask<T>* __restrict__ 
       wsq[4 * ty + s][tx] = (live && i < ell) ? (double)acc[s] * (double)acc[s] : 0.0;
     }
     __syncthreads();
-    if (ty == 0) {  // the warp of ty = 0 walks the block's 32 rows in order
-      for (int ii = 0; ii < 32 && i0 + ii < ell; ++ii) {
-        double t = live ? fmax(nrm - pre, 0.0) : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
-        if (tx == 0) rd_atomic_max(&d.res[i0 + ii], t);
-        pre += wsq[ii][tx];
+    if (ty == 0)  // per column, t_j(k) for the block's rows k in order (wsq[k] becomes t_j(k))
+      for (int ii = 0; ii < 32; ++ii) {
+        const double w2 = wsq[ii][tx];
+        wsq[ii][tx] = live ? fmax(nrm - pre, 0.0) : 0.0;
+        pre += w2;  // rows at or beyond ell hold 0
       }
+    __syncthreads();
+    for (int ii = ty; ii < 32 && i0 + ii < ell; ii += 8) {  // max over the block's columns, a warp per row
+      double t = wsq[ii][tx];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
+      if (tx == 0) rd_atomic_max(&d.res[i0 + ii], t);
     }
     __syncthreads();
   }
@@ -260,23 +277,29 @@ __global__ void k_rand_decide(RandTask<T>* __restrict__ tasks, int n, double eps
   active[i] = d.active;
 }
 
-// Step 6 for every task of the colour (one CTA each): W_cn into p's row and
-// its transposes into the neighbours' rows, A_cc = I, the size of p; a task
-// with nothing to compress against keeps p whole with Q_pc = I.
+// Step 6 for every task of the colour, grid (CTAs per task, tasks): W_cn
+// into p's row and its transposes into the neighbours' rows, A_cc = I, the
+// size of p (no other task of the colour reads it: the interfaces of one
+// colour are not adjacent); a task with nothing to compress against keeps
+// p whole with Q_pc = I.  The warps of a task's CTAs take columns, the
+// lanes rows.
 template <typename T>
 __global__ void __launch_bounds__(256) k_rand_writeback(const RandTask<T>* __restrict__ tasks,
                                                         const CpqrNbr<T>* __restrict__ nbrs,
                                                         int32_t* __restrict__ cur_size) {
-  const RandTask<T>& d = tasks[blockIdx.x];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const RandTask<T>& d = tasks[blockIdx.y];
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * 8 + (threadIdx.x >> 5), nw = gridDim.x * 8;
   const int np = d.np;
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
   if (d.m == 0 || np == 0) {
-    for (int e = tid; e < np * np; e += 256) d.Qc[e] = (e % np == e / np) ? T(1) : T(0);
-    if (tid == 0) cur_size[d.p] = np;
+    for (int c = gw; c < np; c += nw)
+      for (int i = lane; i < np; i += 32) d.Qc[i + (size_t)c * np] = (i == c) ? T(1) : T(0);
+    if (lead) cur_size[d.p] = np;
     return;
   }
   const int r = d.rank;
-  for (int j = warp; j < d.m; j += 8) {  // p's row: one warp per column, lanes over rows
+  for (int j = gw; j < d.m; j += nw) {  // p's row
     T* dst = d.Rp + (size_t)d.tcol[j] * d.ldp;
     for (int i = lane; i < r; i += 32) dst[i] = d.W[i + (size_t)j * np];
   }
@@ -284,18 +307,15 @@ __global__ void __launch_bounds__(256) k_rand_writeback(const RandTask<T>* __res
   for (int e = d.nbeg; e < d.nend; ++e) {
     const CpqrNbr<T> nb = nbrs[e];
     const int w = cur_size[nb.q];
-    for (int t = tid; t < w * r; t += 256) {
-      const int jj = t % w, i = t / w;
-      nb.Rq[jj + (size_t)(nb.off_qp + i) * nb.ldq] = d.W[i + (size_t)(j + jj) * np];
+    for (int i = gw; i < r; i += nw) {
+      T* dst = nb.Rq + (size_t)(nb.off_qp + i) * nb.ldq;
+      for (int jj = lane; jj < w; jj += 32) dst[jj] = d.W[i + (size_t)(j + jj) * np];
     }
     j += w;
   }
-  for (int t = tid; t < r * r; t += 256) {
-    const int i = t % r, c = t / r;
-    d.Rp[i + (size_t)c * d.ldp] = (i == c) ? T(1) : T(0);
-  }
-  __syncthreads();
-  if (tid == 0) cur_size[d.p] = r;
+  for (int c = gw; c < r; c += nw)
+    for (int i = lane; i < r; i += 32) d.Rp[i + (size_t)c * d.ldp] = (i == c) ? T(1) : T(0);
+  if (lead) cur_size[d.p] = r;
 }
 
 }  // namespace spand
