@@ -62,8 +62,9 @@ static inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 static inline int32_t row_ld(int32_t size) { return (std::max<int32_t>(size, 1) + 3) / 4 * 4; }
 
 constexpr size_t kCpqrChunkBudget = 224 * 1024;  // shared memory per sparsification CTA (chunk included)
+constexpr size_t kSmemPerSM = 228 * 1024;        // shared memory of one SM (each resident CTA also reserves 1 KB)
 constexpr int kCpqrMaxCluster = 8;              // thread-block cluster size (broadcasts to 16 CTAs cost 3.5x more)
-constexpr int kAuxStreams = 4;
+constexpr int kAuxStreams = 8;
 constexpr int kApplyCtasPerSm = 4;  // the most CTAs per SM the apply autotuner tries
 
 // Chunked bump allocator over cudaMalloc; reset() keeps the chunks for reuse.
@@ -2250,19 +2251,13 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         // launch groups: (colour, cluster size)
         struct Group { int colour, C, res, G = 0; std::vector<int32_t> ids; size_t smem = 0; int maxm = 0; };
         // one pass: tasks bucketed by (colour, kernel, lane group, cluster
-        // size, residency); within a colour the register-resident groups come
-        // first
-        std::map<std::tuple<int, int, int, int, int>, Group> buckets;
+        // size, residency, CTAs per SM that their shared memory allows, 1-4):
+        // a launch gives every CTA its group's largest need, so interfaces
+        // with small chunks are not held to one CTA per SM by a few wide
+        // ones; within a colour the register-resident groups come first
+        std::map<std::tuple<int, int, int, int, int, int>, Group> buckets;
         for (size_t i = 0; i < tasks.size(); ++i) {
           const int c = colour_of(tasks[i].p), C = tclass[i], Gr = treg[i], res = tres[i];
-          Group& g = buckets[std::make_tuple(c, Gr ? 0 : 1, Gr, C, -res)];
-          if (g.ids.empty()) {
-            g.colour = c;
-            g.C = C;
-            g.res = res;
-            g.G = Gr;
-          }
-          g.ids.push_back((int32_t)i);
           const int np_ = tasks[i].np, mm = tasks[i].m_max, nnb_ = tasks[i].nend - tasks[i].nbeg;
           size_t need;
           if (Gr) {
@@ -2271,6 +2266,15 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
             need = cq_fixed_smem<T>(nnb_, np_, (mm + C - 1) / C, C);
             if (res) need += (size_t)cq_ld<T>(np_) * ((mm + C - 1) / C) * sizeof(T);
           }
+          const int per_sm = Gr ? 1 : (int)std::min<size_t>(4, std::max<size_t>(1, kSmemPerSM / (need + 1024)));
+          Group& g = buckets[std::make_tuple(c, Gr ? 0 : 1, Gr, C, -res, -per_sm)];
+          if (g.ids.empty()) {
+            g.colour = c;
+            g.C = C;
+            g.res = res;
+            g.G = Gr;
+          }
+          g.ids.push_back((int32_t)i);
           g.smem = std::max(g.smem, need);
           g.maxm = std::max(g.maxm, mm);
         }
