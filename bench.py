@@ -494,6 +494,8 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=REF_BUDGET_S,
                     help="wall-clock budget (s) of the reference arm's full-size oracle steps")
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--headline-only", action="store_true",
+                    help="skip the skip sweep, the simultaneous order and the other compressions (profiling runs)")
     ap.add_argument("--grid", type=int, default=GRID, help="cube edge (small cases for profiling only)")
     ap.add_argument("--levels", type=int, default=LEVELS)
     ap.add_argument("--form", default="tf32", choices=["fp32", "tf32", "bf16"],
@@ -594,7 +596,7 @@ def main():
     # sparsification for the first `skip` steps)
     sweep = {"0": {"s_per_step": statistics.mean(t32), "iters": it32[-1], "size_top": s32.stats().size_top,
                    "mem_f": s32.stats().mem_f}}
-    for sk in (2, 4):
+    for sk in (() if args.headline_only else (2, 4)):
         ss, ts, its, _, _, _ = run_form(args.form, 2, 1, skip=sk)
         sst = ss.stats()
         sweep[str(sk)] = {"s_per_step": statistics.mean(ts), "iters": its[-1], "size_top": sst.size_top,
@@ -603,6 +605,8 @@ def main():
     # the simultaneous sparsification order (an option: every interface of a
     # level compressed from the same scaled matrix in one launch), same form
     try:
+        if args.headline_only:
+            raise RuntimeError("not run (--headline-only)")
         ssim, tsim, itsim, rrsim, _, _ = run_form(args.form, 2, 1, order="simultaneous")
         phs = ssim.phase_times()
         sim = {"s_per_step": statistics.mean(tsim), "iters": itsim[-1], "relres": rrsim,
@@ -614,8 +618,9 @@ def main():
     # randomized range finder (sketch in place of the QR of A_pn) and the
     # interpolative variants InS / In (Sec. 2.6.2)
     alt = {}
-    for name, kw in (("randomized", {"compression": "randomized", "sketch_seed": 7}),
-                     ("InS", {"variant": "InS"}), ("In", {"variant": "In"})):
+    for name, kw in (() if args.headline_only else
+                     (("randomized", {"compression": "randomized", "sketch_seed": 7}),
+                      ("InS", {"variant": "InS"}), ("In", {"variant": "In"}))):
         try:
             sa, ta, ita, rra, _, _ = run_form(args.form, 2, 1, **kw)
             pha = sa.phase_times()
