@@ -64,9 +64,6 @@ struct CopyTask {     // dst[r + c*ldd] = src[r + c*lds] (trans = 0) or src[c + 
   int32_t lds, ldd, rows, cols, trans, pad;
 };
 
-struct CopyTile {
-  int32_t task, r0, c0;
-};
 
 // Programmatic dependent launch: the tile Cholesky's phases (and the banded
 // Cholesky) are launched so that a kernel's CTAs may be scheduled while the
@@ -441,28 +438,47 @@ __global__ void __launch_bounds__(NT) k_schur(const SchurTile* __restrict__ tile
 
 // ---------------------------------------------------------------- copies
 
+// Block copies in 32 x 32 tiles, one warp per tile: tile g = CP_WARPS
+// blockIdx.x + warp belongs to the task i with tptr[i] <= g < tptr[i + 1]
+// (tptr: prefix sums of the tasks' tile counts, ntask + 1 entries; every task
+// has at least one tile).  cidx[c] is the task holding tile 32 c, and the
+// tasks that start after it within g's chunk of 32 tiles are found with one
+// ballot over the next 32 entries of tptr (at most 31 start there).  A task's
+// tiles run down its rows first.
+constexpr int CP_WARPS = 4;
 template <typename T>
-__global__ void __launch_bounds__(NT) k_copy(const CopyTile* __restrict__ tiles, const CopyTask<T>* __restrict__ tasks) {
-  __shared__ T s[32][33];
-  const CopyTile t = tiles[blockIdx.x];
-  const CopyTask<T> d = tasks[t.task];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+__global__ void __launch_bounds__(32 * CP_WARPS) k_copy(const int32_t* __restrict__ tptr,
+                                                        const int32_t* __restrict__ cidx, int ntask, int32_t ntile,
+                                                        const CopyTask<T>* __restrict__ tasks) {
+  __shared__ T s[CP_WARPS][32][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int32_t g = (int32_t)blockIdx.x * CP_WARPS + w;
+  if (g >= ntile) return;  // uniform over the warp; the warps never synchronise with each other
+  int i = cidx[g >> 5];
+  const int j = i + 1 + lane;
+  i += __popc(__ballot_sync(0xffffffffu, j < ntask && tptr[j] <= g));
+  const CopyTask<T> d = tasks[i];
+  const int32_t local = g - tptr[i], nr = (d.rows + 31) >> 5;
+  const int r0 = (local % nr) * 32, c0 = (local / nr) * 32;
+  const int nc = min(32, d.cols - c0);
   if (!d.trans) {
-    for (int c = ty; c < 32; c += 8) {
-      const int rr = t.r0 + tx, cc = t.c0 + c;
-      if (rr < d.rows && cc < d.cols) d.dst[rr + (size_t)cc * d.ldd] = d.src[rr + (size_t)cc * d.lds];
+    const int rr = r0 + lane;
+    if (rr < d.rows) {
+#pragma unroll 8
+      for (int c = 0; c < nc; ++c) d.dst[rr + (size_t)(c0 + c) * d.ldd] = d.src[rr + (size_t)(c0 + c) * d.lds];
     }
     return;
   }
-  // dst (rows x cols) = transpose of src (cols x rows)
-  for (int c = ty; c < 32; c += 8) {   // read src rows = dst cols
-    const int sr = t.c0 + tx, sc = t.r0 + c;
-    if (sr < d.cols && sc < d.rows) s[c][tx] = d.src[sr + (size_t)sc * d.lds];
-  }
-  __syncthreads();
-  for (int c = ty; c < 32; c += 8) {
-    const int rr = t.r0 + tx, cc = t.c0 + c;
-    if (rr < d.rows && cc < d.cols) d.dst[rr + (size_t)cc * d.ldd] = s[tx][c];
+  // dst (rows x cols) = transpose of src (cols x rows): lanes along src's
+  // rows (dst's columns) on the way in, along dst's rows on the way out
+  const int nrr = min(32, d.rows - r0);
+#pragma unroll 8
+  for (int c = 0; c < nrr; ++c)
+    if (lane < nc) s[w][c][lane] = d.src[(c0 + lane) + (size_t)(r0 + c) * d.lds];
+  __syncwarp();
+  if (lane < nrr) {
+#pragma unroll 8
+    for (int c = 0; c < nc; ++c) d.dst[(r0 + lane) + (size_t)(c0 + c) * d.ldd] = s[w][lane][c];
   }
 }
 

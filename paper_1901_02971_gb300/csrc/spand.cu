@@ -846,29 +846,54 @@ static T* alloc_dinv(spand_handle h, int n) {
 }
 
 template <typename T>
-static void copy_batch(spand_handle h, const std::vector<CopyTask<T>>& tasks, cudaStream_t s) {
+static void copy_batch(spand_handle h, const std::vector<CopyTask<T>>& tasks_in, cudaStream_t s) {
+  if (tasks_in.empty()) return;
+  // tasks without tiles are left out (the kernel's search assumes none)
+  const std::vector<CopyTask<T>>* tp = &tasks_in;
+  std::vector<CopyTask<T>> kept;
+  for (const CopyTask<T>& c : tasks_in)
+    if (c.rows <= 0 || c.cols <= 0) {
+      for (const CopyTask<T>& k : tasks_in)
+        if (k.rows > 0 && k.cols > 0) kept.push_back(k);
+      tp = &kept;
+      break;
+    }
+  const std::vector<CopyTask<T>>& tasks = *tp;
   if (tasks.empty()) return;
-  std::vector<CopyTile> tiles;
-  for (int32_t i = 0; i < (int32_t)tasks.size(); ++i)
-    for (int r0 = 0; r0 < tasks[i].rows; r0 += 32)
-      for (int c0 = 0; c0 < tasks[i].cols; c0 += 32) tiles.push_back({i, r0, c0});
-  if (tiles.empty()) return;
+  // prefix sums of the tasks' 32 x 32 tile counts, and the task of every 32nd tile
+  std::vector<int32_t> tptr = h->pool32.take(), cidx = h->pool32.take();
+  tptr.resize(tasks.size() + 1);
+  int64_t ntile = 0;
+  for (size_t i = 0; i < tasks.size(); ++i) {
+    tptr[i] = (int32_t)std::min<int64_t>(ntile, INT32_MAX);
+    ntile += (int64_t)((tasks[i].rows + 31) / 32) * ((tasks[i].cols + 31) / 32);
+  }
+  if (ntile > INT32_MAX - 64) {
+    h->pool32.give(std::move(tptr));
+    h->pool32.give(std::move(cidx));
+    throw Fail{SPAND_ERR_INVALID_ARG, "block copy batch too large"};
+  }
+  tptr[tasks.size()] = (int32_t)ntile;
+  cidx.resize((size_t)((ntile + 31) / 32));
+  for (size_t c = 0, i = 0; c < cidx.size(); ++c) {
+    const int64_t g = (int64_t)c * 32;
+    while (tptr[i + 1] <= g) ++i;
+    cidx[c] = (int32_t)i;
+  }
   Packer pk;
-  size_t ot = pk.add(tasks), oi = pk.add(tiles);
+  size_t ot = pk.add(tasks), op = pk.add(tptr), oc = pk.add(cidx);
   void* d = upload<T>(h, pk, s);
-  const size_t nt = tiles.size();
+  h->pool32.give(std::move(tptr));  // copied to pinned staging by upload
+  h->pool32.give(std::move(cidx));
   double by = 0;
   for (auto& t : tasks) by += 2.0 * t.rows * t.cols * sizeof(T);
   const int pid = h->prof.begin(F_COPY, s);
-  int64_t nl = 0;
-  for (size_t b = 0; b < nt; b += 1u << 30) {
-    const unsigned cnt = (unsigned)std::min<size_t>(nt - b, 1u << 30);
-    k_copy<T><<<cnt, NT, 0, s>>>(at<const CopyTile>(d, oi) + b, at<const CopyTask<T>>(d, ot));
-    CKLAUNCH();
-    ++nl;
-  }
-  h->prof.launches += nl;
-  h->prof.end(pid, s, 0.0, by, nl);
+  const unsigned nb = (unsigned)((ntile + CP_WARPS - 1) / CP_WARPS);
+  k_copy<T><<<nb, 32 * CP_WARPS, 0, s>>>(at<const int32_t>(d, op), at<const int32_t>(d, oc), (int)tasks.size(),
+                                          (int32_t)ntile, at<const CopyTask<T>>(d, ot));
+  CKLAUNCH();
+  h->prof.launches += 1;
+  h->prof.end(pid, s, 0.0, by, 1);
 }
 
 template <typename T>
@@ -2536,6 +2561,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       }
       nxt = make_layout<T>(h, t + 1, nsz, s);
       std::vector<CopyTask<T>> cps;
+      cps.reserve(rems.size() + lay.nidx.size());
       for (int a : rems) {
         if (sz_after[a] <= 0) continue;
         const int P = pof[a];
