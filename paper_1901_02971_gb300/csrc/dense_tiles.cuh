@@ -315,73 +315,6 @@ __device__ bool potrf_inv_tile(SqTileB<T, B>& s, SqTileB<T, B>& D, int nb) {
   return true;
 }
 
-// D = U^{-T} (lower, identity beyond nb) of an already factored upper
-// triangular nb x nb tile U held in shared memory (U is only read): the
-// D part of potrf_inv_tile, with the rows of U taken from the tile.
-template <typename T, int B>
-__device__ void inv_tile(const SqTileB<T, B>& U, SqTileB<T, B>& D, int nb) {
-  using G = TileGeom<B>;
-  constexpr int PR = G::PR, PC = G::PC, CB = G::CB;
-  __shared__ T rowD[2][2][B];
-  const int tx = threadIdx.x % PR, ty = threadIdx.x / PR;
-  T d[4][CB];
-#pragma unroll
-  for (int p = 0; p < 4; ++p)
-#pragma unroll
-    for (int q = 0; q < CB; ++q) d[p][q] = (tx + PR * p == ty + PC * q) ? T(1) : T(0);
-  for (int k = 0; k < nb; k += 2) {
-    const int par = (k >> 1) & 1;
-    const bool two = k + 1 < nb;
-    const int k1 = two ? k + 1 : k;
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const int i = tx + PR * p;
-      if (i == k || i == k1) {
-        const int w = i == k ? 0 : 1;
-#pragma unroll
-        for (int q = 0; q < CB; ++q) rowD[par][w][ty + PC * q] = d[p][q];
-      }
-    }
-    __syncthreads();
-    const T r0 = T(1) / U.v[k][k];
-    const T u01 = two ? U.v[k][k1] : T(0);
-    const T r1 = two ? T(1) / U.v[k1][k1] : T(0);
-    T d0[CB], d1[CB], u0i[4], u1i[4];
-#pragma unroll
-    for (int q = 0; q < CB; ++q) {
-      const int cj = ty + PC * q;
-      d0[q] = rowD[par][0][cj] * r0;
-      d1[q] = two ? (rowD[par][1][cj] - u01 * d0[q]) * r1 : T(0);
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int ci = tx + PR * q;
-      u0i[q] = U.v[k][ci];
-      u1i[q] = two ? U.v[k1][ci] : T(0);
-    }
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const int i = tx + PR * p;
-      if (i == k) {
-#pragma unroll
-        for (int q = 0; q < CB; ++q) d[p][q] = d0[q];
-      } else if (two && i == k1) {
-#pragma unroll
-        for (int q = 0; q < CB; ++q) d[p][q] = d1[q];
-      } else if (i > k1) {
-#pragma unroll
-        for (int q = 0; q < CB; ++q)
-          if (!G::above(p, q)) d[p][q] = fma(-u1i[p], d1[q], fma(-u0i[p], d0[q], d[p][q]));
-      }
-    }
-  }
-#pragma unroll
-  for (int p = 0; p < 4; ++p)
-#pragma unroll
-    for (int q = 0; q < CB; ++q) D.v[tx + PR * p][ty + PC * q] = d[p][q];
-  __syncthreads();
-}
-
 // B <- D B with D = U^{-T} the stored inverse of a diagonal tile (lower,
 // zero above the diagonal), i.e. B <- U^{-T} B as one small GEMM instead of a
 // serial substitution.  D, B in shared memory; each thread produces a 4x4

@@ -318,20 +318,67 @@ __global__ void __launch_bounds__(BAND_NT) k_potrf_band(const BandTask<TS>* __re
 
 // The inverses U_kk^{-T} of the 64 x 64 diagonal tiles of a factored pivot
 // block (for the block-row solves of k_trsm_cols), tile k = blockIdx.x of
-// block blockIdx.y, from U itself.
+// block blockIdx.y, from U itself (rows and columns beyond n: the identity).
+// In 32 x 32 blocks, U^{-1} = [D11, -D11 U12 D22; 0, D22]: each diagonal
+// block is inverted by one warp, a lane per column by back substitution in
+// registers (no block barrier inside), then the corner by two 32 x 32
+// products, four 32 x 32 warps; the result is stored transposed.
+constexpr int INV_NT = 128;
 template <typename T>
-__global__ void __launch_bounds__(NT) k_inv_diag(const RowDesc<T>* __restrict__ rows) {
+__global__ void __launch_bounds__(INV_NT) k_inv_diag(const RowDesc<T>* __restrict__ rows) {
   extern __shared__ __align__(16) unsigned char smraw[];
   SqTile<T>& U = *reinterpret_cast<SqTile<T>*>(smraw);
-  SqTile<T>& D = *reinterpret_cast<SqTile<T>*>(smraw + sizeof(SqTile<T>));
+  SqTile<T>& D = *reinterpret_cast<SqTile<T>*>(smraw + sizeof(SqTile<T>));  // U^{-1}; its lower-left block: W
   const RowDesc<T> d = rows[blockIdx.y];
   const int k0 = blockIdx.x * TB;
   if (k0 >= d.n) return;
   const int nb = min(TB, d.n - k0);
-  load_tile(U, d.R + k0 + (size_t)k0 * d.ld, d.ld, nb, nb);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < TB * TB; e += INV_NT) {
+    const int i = e & (TB - 1), j = e / TB;
+    U.v[i][j] = (i < nb && j < nb) ? d.R[(k0 + i) + (size_t)(k0 + j) * d.ld] : (i == j ? T(1) : T(0));
+  }
   __syncthreads();
-  inv_tile(U, D, nb);
-  store_tile(D, d.dinv + (size_t)blockIdx.x * TB * TB, TB, TB, TB);
+  if (warp < 2) {  // D_bb = U_bb^{-1}: column j = lane, rows i <= j
+    const int o = 32 * warp, j = lane;
+    const T rinv = T(1) / U.v[o + lane][o + lane];
+    T x[32];
+#pragma unroll
+    for (int i = 31; i >= 0; --i) {
+      T acc = (i == j) ? T(1) : T(0);
+#pragma unroll
+      for (int k = i + 1; k < 32; ++k) acc = fma(-U.v[o + i][o + k], x[k], acc);
+      const T ri = __shfl_sync(0xffffffffu, rinv, i);
+      x[i] = (i > j) ? T(0) : acc * ri;
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) D.v[o + i][o + j] = x[i];
+  }
+  __syncthreads();
+  // W = U12 D22 into D's lower-left block (rows 32.., columns ..31)
+  const int jc = lane, i0 = warp;  // thread: column jc, rows i0 + 4 m
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int i = i0 + 4 * m;
+    T acc = T(0);
+    for (int k = 0; k <= jc; ++k) acc = fma(U.v[i][32 + k], D.v[32 + k][32 + jc], acc);
+    D.v[32 + i][jc] = acc;
+  }
+  __syncthreads();
+  // D12 = -D11 W
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int i = i0 + 4 * m;
+    T acc = T(0);
+    for (int k = i; k < 32; ++k) acc = fma(D.v[i][k], D.v[32 + k][jc], acc);
+    D.v[i][32 + jc] = -acc;
+  }
+  __syncthreads();
+  T* out = d.dinv + (size_t)blockIdx.x * TB * TB;  // out(i, j) = U^{-1}(j, i), column-major, zero above
+  for (int e = tid; e < TB * TB; e += INV_NT) {
+    const int i = e & (TB - 1), j = e / TB;
+    out[e] = i >= j ? D.v[j][i] : T(0);
+  }
 }
 
 // B <- U^{-T} B for one panel of at most 64 columns, left-looking over the

@@ -671,7 +671,7 @@ static void inv_diag_batch(spand_handle h, const std::vector<RowDesc<T>>& rows, 
   const size_t nb = rows.size();
   for (size_t b0 = 0; b0 < nb; b0 += 65535) {
     const unsigned cnt = (unsigned)std::min<size_t>(nb - b0, 65535);
-    k_inv_diag<T><<<dim3(nt, cnt), NT, sm, s>>>(at<const RowDesc<T>>(d, o) + b0);
+    k_inv_diag<T><<<dim3(nt, cnt), INV_NT, sm, s>>>(at<const RowDesc<T>>(d, o) + b0);
     CKLAUNCH();
     ++h->prof.launches;
   }
