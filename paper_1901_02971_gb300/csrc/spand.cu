@@ -465,6 +465,15 @@ struct spand_handle_s {
   DevBuf d_interp; // Gram matrices, R rows and pivot orders of the interpolative variants (scratch)
   // host scratch reused across steps and factorizations
   VecPool<int32_t> pool32;
+  // Per step, the structure of the elimination's Schur update (which target
+  // blocks, which contributions, in which order): fixed by the analysis, so
+  // built at the first factorization and reused by every later one.
+  struct SchurPlan {
+    bool built = false;
+    std::vector<int32_t> a, b, eab, eba;      // target block (a, b), a's edge to b and b's edge to a (-1: a == b)
+    std::vector<int32_t> cptr, csep, cea, ceb;  // its contributions: separator, its edges to a and to b
+  };
+  std::vector<SchurPlan> splan;
   VecPool<int64_t> pool64;
   VecPool<std::pair<int32_t, int64_t>> poolpair;
   VecPool<ApplyItem> poolitem;
@@ -515,6 +524,12 @@ struct Layout {
   std::vector<T*> row;
   std::vector<int32_t> ld, W;
   std::vector<int32_t> nptr, nidx, noff;  // neighbour lists with column offsets
+  int32_t edge_of(int i, int q) const {  // index of q in i's neighbour list, or -1
+    const int32_t* b = nidx.data() + nptr[i];
+    const int32_t* e = nidx.data() + nptr[i + 1];
+    const int32_t* it = std::lower_bound(b, e, q);
+    return (it == e || *it != q) ? -1 : nptr[i] + (int32_t)(it - b);
+  }
   int32_t off_of(int i, int q) const {
     if (q == i) return 0;
     const int32_t* b = nidx.data() + nptr[i];
@@ -1834,58 +1849,90 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
       pivot_chol<T>(h, diag, d_info + 2 * t, s, &diag_fl);
       elim_cls[t] = diag_cl;
       trsm_batch<T>(h, tr_tasks, s, &tr_fl);
-      // pull-form Schur update of every pair of neighbours
-      std::vector<SchurBlock<T>> blocks;
-      std::vector<std::vector<SchurContrib<T>>> contr;
-      std::unordered_map<int64_t, int32_t> bid;
-      for (int sidx : seps) {
-        if (sz[sidx] <= 0) continue;
-        const int32_t nb0 = lay.nptr[sidx], nb1 = lay.nptr[sidx + 1];
-        for (int32_t ea = nb0; ea < nb1; ++ea) {
-          const int32_t a = lay.nidx[ea];
-          if (sz[a] <= 0) continue;
-          for (int32_t eb = ea; eb < nb1; ++eb) {
-            const int32_t b = lay.nidx[eb];
-            if (sz[b] <= 0) continue;
-            const int64_t key = (int64_t)a * n + b;
-            auto it = bid.find(key);
-            int32_t id;
-            if (it == bid.end()) {
-              id = (int32_t)blocks.size();
-              bid.emplace(key, id);
-              const int32_t oab = lay.off_of(a, b), oba = lay.off_of(b, a);
-              if (oab < 0 || oba < 0) throw Fail{SPAND_ERR_STATE, "fill block missing from the layout"};
-              SchurBlock<T> bl;
-              bl.C1 = lay.row[a] + (size_t)oab * lay.ld[a];
-              bl.C2 = (a == b) ? nullptr : lay.row[b] + (size_t)oba * lay.ld[b];
-              bl.ld1 = lay.ld[a];
-              bl.ld2 = lay.ld[b];
-              bl.rows = sz[a];
-              bl.cols = sz[b];
-              blocks.push_back(bl);
-              contr.emplace_back();
-            } else {
-              id = it->second;
+      // pull-form Schur update of every pair of neighbours: target blocks in
+      // the order of their first contribution (separators in order, then
+      // their neighbour pairs), each with its contributions in separator
+      // order; clusters reduced to nothing are left out
+      if (h->splan.size() < (size_t)L + 1) h->splan.resize((size_t)L + 1);
+      auto& plan = h->splan[t];
+      if (!plan.built) {
+        std::unordered_map<int64_t, int32_t> bid;
+        std::vector<std::vector<int32_t>> cl;  // per block: contribution triples (sep, ea, eb)
+        for (int sidx : seps) {
+          const int32_t nb0 = lay.nptr[sidx], nb1 = lay.nptr[sidx + 1];
+          for (int32_t ea = nb0; ea < nb1; ++ea)
+            for (int32_t eb = ea; eb < nb1; ++eb) {
+              const int32_t a = lay.nidx[ea], b = lay.nidx[eb];
+              const int64_t key = (int64_t)a * n + b;
+              auto it = bid.find(key);
+              int32_t id;
+              if (it == bid.end()) {
+                id = (int32_t)plan.a.size();
+                bid.emplace(key, id);
+                const int32_t eab = a == b ? -1 : lay.edge_of(a, b), eba = a == b ? -1 : lay.edge_of(b, a);
+                if (a != b && (eab < 0 || eba < 0)) throw Fail{SPAND_ERR_STATE, "fill block missing from the layout"};
+                plan.a.push_back(a);
+                plan.b.push_back(b);
+                plan.eab.push_back(eab);
+                plan.eba.push_back(eba);
+                cl.emplace_back();
+              } else {
+                id = it->second;
+              }
+              cl[id].insert(cl[id].end(), {sidx, ea, eb});
             }
-            SchurContrib<T> c;
-            c.Xa = lay.row[sidx] + (size_t)lay.noff[ea] * lay.ld[sidx];
-            c.Xb = lay.row[sidx] + (size_t)lay.noff[eb] * lay.ld[sidx];
-            c.lds = lay.ld[sidx];
-            c.ns = sz[sidx];
-            c.owner = sidx;
-            contr[id].push_back(c);
-          }
         }
+        plan.cptr.assign(1, 0);
+        for (const auto& v : cl) {
+          for (size_t k = 0; k < v.size(); k += 3) {
+            plan.csep.push_back(v[k]);
+            plan.cea.push_back(v[k + 1]);
+            plan.ceb.push_back(v[k + 2]);
+          }
+          plan.cptr.push_back((int32_t)plan.csep.size());
+        }
+        plan.built = true;
+      }
+      std::vector<SchurBlock<T>> blocks;
+      std::vector<SchurContrib<T>> flat;
+      blocks.reserve(plan.a.size());
+      flat.reserve(plan.csep.size());
+      for (size_t id = 0; id < plan.a.size(); ++id) {
+        const int32_t a = plan.a[id], b = plan.b[id];
+        if (sz[a] <= 0 || sz[b] <= 0) continue;
+        const int32_t cb = (int32_t)flat.size();
+        for (int32_t k = plan.cptr[id]; k < plan.cptr[id + 1]; ++k) {
+          const int32_t sidx = plan.csep[k];
+          if (sz[sidx] <= 0) continue;
+          SchurContrib<T> c;
+          c.Xa = lay.row[sidx] + (size_t)lay.noff[plan.cea[k]] * lay.ld[sidx];
+          c.Xb = lay.row[sidx] + (size_t)lay.noff[plan.ceb[k]] * lay.ld[sidx];
+          c.lds = lay.ld[sidx];
+          c.ns = sz[sidx];
+          c.owner = sidx;
+          flat.push_back(c);
+        }
+        if ((int32_t)flat.size() == cb) continue;
+        SchurBlock<T> bl;
+        bl.C1 = lay.row[a] + (size_t)(a == b ? 0 : lay.noff[plan.eab[id]]) * lay.ld[a];
+        bl.C2 = (a == b) ? nullptr : lay.row[b] + (size_t)lay.noff[plan.eba[id]] * lay.ld[b];
+        bl.ld1 = lay.ld[a];
+        bl.ld2 = lay.ld[b];
+        bl.rows = sz[a];
+        bl.cols = sz[b];
+        bl.cbeg = cb;
+        bl.cend = (int32_t)flat.size();
+        blocks.push_back(bl);
       }
       if (!blocks.empty()) {
-        std::vector<SchurContrib<T>> flat;
         std::vector<SchurTile> tiles;
         // tensor cores for the TF32 / BF16 forms: 128 x 64 tiles; FP32 and
         // FP64 on the SIMT pipes: 64 x 64 tiles
         bool tc = sizeof(T) == 4 && (h->opts.precision == SPAND_TF32 || h->opts.precision == SPAND_BF16);
-        for (size_t b = 0; tc && b < contr.size(); ++b)  // the kernel loads 16-byte vectors of X
-          for (const auto& c : contr[b])
-            if (c.lds % 4 != 0 || ((uintptr_t)c.Xa | (uintptr_t)c.Xb) % 16 != 0) tc = false;
+        for (size_t k = 0; tc && k < flat.size(); ++k) {  // the kernel loads 16-byte vectors of X
+          const SchurContrib<T>& c = flat[k];
+          if (c.lds % 4 != 0 || ((uintptr_t)c.Xa | (uintptr_t)c.Xb) % 16 != 0) tc = false;
+        }
         // TF32: operands through the copy engine (one tensor map pair per
         // separator row); BF16 converts in registers (k_schur_tc)
         std::vector<CUtensorMap> tmaps;
@@ -1904,9 +1951,6 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         }
         const int ti = tc ? TC_M : TB, tj = tc ? TC_N : TB;
         for (size_t b = 0; b < blocks.size(); ++b) {
-          blocks[b].cbeg = (int32_t)flat.size();
-          flat.insert(flat.end(), contr[b].begin(), contr[b].end());
-          blocks[b].cend = (int32_t)flat.size();
           for (int i0 = 0; i0 < blocks[b].rows; i0 += ti)
             for (int j0 = 0; j0 < blocks[b].cols; j0 += tj) tiles.push_back({(int32_t)b, i0, j0});
         }
