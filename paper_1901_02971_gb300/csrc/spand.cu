@@ -474,6 +474,15 @@ struct spand_handle_s {
     std::vector<int32_t> cptr, csep, cea, ceb;  // its contributions: separator, its edges to a and to b
   };
   std::vector<SchurPlan> splan;
+  // Per step, the block copies of the merge (Sec. 2.7): for every remaining
+  // cluster a, its own block and each neighbour b, with b's edge in a's row
+  // (-1: a itself) and the edge of the parents (P, Q) in the next layout (-1:
+  // P == Q; -2: not adjacent there, nothing to copy); fixed by the analysis.
+  struct MergePlan {
+    bool built = false;
+    std::vector<int32_t> ptr, b, src, tgt;  // per entry of rems: ptr[i] .. ptr[i + 1]
+  };
+  std::vector<MergePlan> mplan;
   VecPool<int64_t> pool64;
   VecPool<std::pair<int32_t, int64_t>> poolpair;
   VecPool<ApplyItem> poolitem;
@@ -2604,24 +2613,44 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         nsz[P] = o;
       }
       nxt = make_layout<T>(h, t + 1, nsz, s);
+      if (h->mplan.size() < (size_t)L + 1) h->mplan.resize((size_t)L + 1);
+      auto& mp = h->mplan[t];
+      if (!mp.built) {
+        mp.ptr.assign(1, 0);
+        for (int a : rems) {
+          const int P = pof[a];
+          auto add = [&](int b, int32_t e) {
+            const int Q = pof[b];
+            int32_t tg = -1;
+            if (Q != P) {
+              tg = nxt.edge_of(P, Q);
+              if (tg < 0) tg = -2;
+            }
+            mp.b.push_back(b);
+            mp.src.push_back(e);
+            mp.tgt.push_back(tg);
+          };
+          add(a, -1);
+          for (int32_t e = lay.nptr[a]; e < lay.nptr[a + 1]; ++e) add(lay.nidx[e], e);
+          mp.ptr.push_back((int32_t)mp.b.size());
+        }
+        mp.built = true;
+      }
       std::vector<CopyTask<T>> cps;
-      cps.reserve(rems.size() + lay.nidx.size());
-      for (int a : rems) {
+      cps.reserve(mp.b.size());
+      for (size_t ia = 0; ia < rems.size(); ++ia) {
+        const int a = rems[ia];
         if (sz_after[a] <= 0) continue;
         const int P = pof[a];
-        auto add = [&](int b, int32_t src_col) {
-          if (sz_after[b] <= 0) return;
-          const int Q = pof[b];
-          int32_t tc;
-          if (Q == P) tc = ro[b];
-          else {
-            const int32_t o = nxt.off_of(P, Q);
-            if (o < 0) return;
-            tc = o + ro[b];
-          }
+        T* const dst0 = nxt.row[P] + ro[a];
+        for (int32_t k = mp.ptr[ia]; k < mp.ptr[ia + 1]; ++k) {
+          const int b = mp.b[k], tg = mp.tgt[k];
+          if (sz_after[b] <= 0 || tg == -2) continue;
+          const int32_t tc = (tg < 0 ? 0 : nxt.noff[tg]) + ro[b];
+          const int32_t src_col = mp.src[k] < 0 ? 0 : lay.noff[mp.src[k]];
           CopyTask<T> c;
           c.src = lay.row[a] + (size_t)src_col * lay.ld[a];
-          c.dst = nxt.row[P] + ro[a] + (size_t)tc * nxt.ld[P];
+          c.dst = dst0 + (size_t)tc * nxt.ld[P];
           c.lds = lay.ld[a];
           c.ldd = nxt.ld[P];
           c.rows = sz_after[a];
@@ -2629,9 +2658,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
           c.trans = 0;
           c.pad = 0;
           cps.push_back(c);
-        };
-        add(a, 0);
-        for (int32_t e = lay.nptr[a]; e < lay.nptr[a + 1]; ++e) add(lay.nidx[e], lay.noff[e]);
+        }
       }
       copy_batch<T>(h, cps, s);
       sz = nsz;
