@@ -483,6 +483,79 @@ __global__ void __launch_bounds__(NT) k_schur(const SchurTile* __restrict__ tile
   }
 }
 
+// ---------------------------------------------------------------- two-sided scaling, second side
+
+// Scaling of an adjacent pair p < q (Sec. 2.5), second side: with
+// B = U_p^{-T} A_pq (|p| x |q|, the first side's block-row solve) and the
+// pivot inverse Y_q = U_q^{-T} (|q| x |q|, lower triangular, zero above the
+// diagonal in memory), the scaled block in q's row is
+// O = (U_p^{-T} A_pq U_q^{-1})^T = Y_q B^T (|q| x |p|).  One 64 x 64 tile of
+// O per CTA (tile list: task, i0, j0); K stops at the tile's last row, past
+// which Y_q is zero.
+template <typename T>
+struct ScaleTask {
+  const T* B;  // p's row at q's columns, leading dimension ldb
+  const T* Y;  // Y_q, leading dimension nq
+  T* O;        // q's row at p's columns, leading dimension ldo
+  int32_t ldb, ldo, np, nq;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_scale_gemm(const SchurTile* __restrict__ tiles,
+                                                   const ScaleTask<T>* __restrict__ tasks) {
+  constexpr int KC2 = 16;
+  __shared__ T ys[KC2][TB + 1], bs[KC2][TB + 1];
+  const SchurTile tl = tiles[blockIdx.x];
+  const ScaleTask<T> d = tasks[tl.block];
+  const int i0 = tl.i0, j0 = tl.j0, tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  T acc[4][4];
+  zero_acc(acc);
+  const int kend = min(d.nq, i0 + TB);
+  constexpr int NL = TB * KC2 / NT;  // elements of each operand per thread and chunk
+  T ry[NL], rb[NL];
+  auto load = [&](int k0) {  // Y(i0 + i, k0 + kk), B(j0 + i, k0 + kk): lanes along i
+#pragma unroll
+    for (int r = 0; r < NL; ++r) {
+      const int e = tid + NT * r, i = e & (TB - 1), k = k0 + e / TB;
+      ry[r] = (i0 + i < d.nq && k < kend) ? d.Y[(i0 + i) + (size_t)k * d.nq] : T(0);
+      rb[r] = (j0 + i < d.np && k < kend) ? d.B[(j0 + i) + (size_t)k * d.ldb] : T(0);
+    }
+  };
+  if (kend > 0) load(0);
+  for (int k0 = 0; k0 < kend; k0 += KC2) {
+#pragma unroll
+    for (int r = 0; r < NL; ++r) {
+      const int e = tid + NT * r;
+      ys[e / TB][e & (TB - 1)] = ry[r];
+      bs[e / TB][e & (TB - 1)] = rb[r];
+    }
+    __syncthreads();
+    if (k0 + KC2 < kend) load(k0 + KC2);  // the next chunk's loads overlap this chunk's products
+#pragma unroll
+    for (int kk = 0; kk < KC2; ++kk) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        av[q] = ys[kk][tx + 16 * q];
+        bv[q] = bs[kk][ty + 16 * q];
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = i0 + tx + 16 * a, j = j0 + ty + 16 * b;
+      if (i < d.nq && j < d.np) d.O[i + (size_t)j * d.ldo] = acc[a][b];
+    }
+}
+
 // ---------------------------------------------------------------- copies
 
 // Block copies in 32 x 32 tiles, one warp per tile: tile g = CP_WARPS

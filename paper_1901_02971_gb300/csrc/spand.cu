@@ -2107,8 +2107,8 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
     if (sparsify) {
       std::vector<RowDesc<T>> diag, ident;
       std::vector<int> diag_cl;
-      std::vector<TrsmTask<T>> up, lo;
-      std::vector<CopyTask<T>> m_up, m_lo;
+      std::vector<TrsmTask<T>> up;
+      std::vector<CopyTask<T>> m_up, m_lo;  // per pair p < q: p -> q (the product's operands), q -> p
       std::vector<RowDesc<T>> idr;
       for (int p : rems) {
         if (sz[p] <= 0 || h->opts.variant == SPAND_IN) continue;  // In: no block scaling
@@ -2117,7 +2117,6 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         diag_cl.push_back(p);
         const int fu = lay.first_upper(p);
         add_panels(up, lay.row[p], (const T*)dv, sz[p], lay.ld[p], fu, lay.W[p]);
-        add_panels(lo, lay.row[p], (const T*)dv, sz[p], lay.ld[p], sz[p], fu);
         for (int32_t e = lay.nptr[p]; e < lay.nptr[p + 1]; ++e) {
           const int32_t q = lay.nidx[e];
           if (q <= p || sz[q] <= 0) continue;
@@ -2157,12 +2156,54 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         stt.mem_f += (int64_t)sz[p] * (sz[p] + 1) / 2;
         sm_np = std::max(sm_np, (size_t)sz[p] * sizeof(double));
       }
+      // second side of every pair p < q from the first side's block and Y_q:
+      // O = Y_q (U_p^{-T} A_pq)^T into q's row (the scaled A_qp)
+      std::vector<ScaleTask<T>> sct;
+      std::vector<SchurTile> sctl;
+      {
+        std::vector<const T*> yof(n, nullptr);
+        for (size_t i = 0; i < sq_cluster.size(); ++i) yof[sq_cluster[i]] = sqops[i].Y;
+        for (const CopyTask<T>& c : m_up) {  // one per pair p < q: src = p's block, dst = q's block
+          ScaleTask<T> k;
+          k.B = c.src;
+          k.O = c.dst;
+          k.ldb = c.lds;
+          k.ldo = c.ldd;
+          k.np = c.cols;
+          k.nq = c.rows;
+          k.Y = nullptr;
+          sct.push_back(k);
+        }
+        size_t i = 0;
+        for (int p : rems) {
+          if (sz[p] <= 0 || h->opts.variant == SPAND_IN) continue;
+          for (int32_t e = lay.nptr[p]; e < lay.nptr[p + 1]; ++e) {
+            const int32_t q = lay.nidx[e];
+            if (q <= p || sz[q] <= 0) continue;
+            sct[i++].Y = yof[q];
+          }
+        }
+        for (size_t k = 0; k < sct.size(); ++k)
+          for (int i0 = 0; i0 < sct[k].nq; i0 += TB)
+            for (int j0 = 0; j0 < sct[k].np; j0 += TB) sctl.push_back({(int32_t)k, i0, j0});
+      }
       set_identity<T>(h, ident, s);
       pivot_chol<T>(h, diag, d_info + 2 * t + 1, s);
       scale_cls[t] = diag_cl;
       trsm_batch<T>(h, up, s);   // upper blocks U_p^{-T} A_pq and the inverses Y_p
-      copy_batch<T>(h, m_up, s);
-      trsm_batch<T>(h, lo, s);
+      if (!sctl.empty()) {
+        Packer pks;
+        const size_t okt = pks.add(sct), okl = pks.add(sctl);
+        void* dks = upload<T>(h, pks, s);
+        double fl = 0;
+        for (const ScaleTask<T>& k : sct) fl += (double)k.nq * k.nq * k.np;
+        const int pid = h->prof.begin(F_TRSM, s);
+        k_scale_gemm<T><<<(unsigned)sctl.size(), NT, 0, s>>>(at<const SchurTile>(dks, okl),
+                                                             at<const ScaleTask<T>>(dks, okt));
+        CKLAUNCH();
+        h->prof.launches += 1;
+        h->prof.end(pid, s, fl, 0.0, 1);
+      }
       copy_batch<T>(h, m_lo, s);
       set_identity<T>(h, idr, s);
       CK(cudaEventRecord(tm.at(t, 2), s));
