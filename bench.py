@@ -206,12 +206,14 @@ HBM_BOUND = {"copy", "apply", "pcg"}
 # of one factorization or solve), with the SHA-256 of the kernel source the
 # counters were taken on: a changed kernel reports null until re-measured.
 # The capture and its command are summarised under profiles/ (DRAM traffic, 64^3).
+CPQR_DRAM_BYTES = 583.09e6 + 5.74e6  # read + written by the 265 launches of one factorization
 MEASURED_TRAFFIC = {
-    # dram__bytes_read.sum + dram__bytes_write.sum of the 212 sparsification
-    # launches of one factorization (k_cpqr_cluster, k_cpqr_reg, k_form_q:
-    # 583.9 MB read, 14.0 MB written) and of three applications (3100.6 MB
-    # read, 40.1 MB written); ncu, one pass
-    "cpqr": {"bytes_per_launch": (583.9e6 + 14.0e6) / 212,
+    # dram__bytes_read.sum + dram__bytes_write.sum: "cpqr", of all the
+    # sparsification launches of one factorization (k_cpqr_cluster,
+    # k_cpqr_reg, k_form_q), divided by the family's launch count of the
+    # profiled run; "apply", of three applications (one launch each); ncu,
+    # one pass
+    "cpqr": {"bytes_per_step": CPQR_DRAM_BYTES,
              "src": ["paper_1901_02971_gb300/csrc/cpqr_cluster.cuh", "paper_1901_02971_gb300/csrc/cpqr_reg.cuh"],
              "sha256": ["df1a284e74542b5aa3f39bc25ec90beb14e91cbaa13b15fbeed6c93563a1f421",
                         "f4375f2638107797fe808912ff23db71eba06329efe4f946106ee94aebe58cd8"]},
@@ -220,7 +222,7 @@ MEASURED_TRAFFIC = {
 }
 
 
-def measured_traffic(fam: str, grid: int):
+def measured_traffic(fam: str, grid: int, launches: int = 1):
     t = MEASURED_TRAFFIC.get(fam)
     if t is None or grid != GRID:
         return None
@@ -235,6 +237,8 @@ def measured_traffic(fam: str, grid: int):
                     return None
         except OSError:
             return None
+    if "bytes_per_step" in t:
+        return t["bytes_per_step"] / max(int(launches), 1)
     return t["bytes_per_launch"]
 
 
@@ -245,7 +249,7 @@ def make_roofline(prof: dict, peaks: dict, dtype_peak_tflops: float = FP32_ALU_T
     fam = max(prof, key=lambda k: prof[k]["ms"])
     f = prof[fam]
     sec = f["ms"] / 1e3
-    traffic = measured_traffic(fam, grid)
+    traffic = measured_traffic(fam, grid, f["launches"])
     if fam in HBM_BOUND:
         ach = f["bytes"] / sec / 1e9
         pk = float(peaks["hbm_gbs"])
