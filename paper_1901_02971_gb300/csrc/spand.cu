@@ -2370,7 +2370,7 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
         // launch groups: (colour, cluster size)
         struct Group { int colour, C, res, G = 0; std::vector<int32_t> ids; size_t smem = 0; int maxm = 0; };
         // one pass: tasks bucketed by (colour, kernel, lane group, cluster
-        // size, residency, CTAs per SM that their shared memory allows, 1-4):
+        // size, residency, CTAs per SM that their shared memory allows, 1-2):
         // a launch gives every CTA its group's largest need, so interfaces
         // with small chunks are not held to one CTA per SM by a few wide
         // ones; within a colour the register-resident groups come first
@@ -2385,7 +2385,8 @@ static int factorize_impl(spand_handle h, cudaStream_t s) {
             need = cq_fixed_smem<T>(nnb_, np_, (mm + C - 1) / C, C);
             if (res) need += (size_t)cq_ld<T>(np_) * ((mm + C - 1) / C) * sizeof(T);
           }
-          const int per_sm = Gr ? 1 : (int)std::min<size_t>(4, std::max<size_t>(1, kSmemPerSM / (need + 1024)));
+          // (at most two: the chunked kernel's registers hold two 256-thread CTAs per SM)
+          const int per_sm = Gr ? 1 : (int)std::min<size_t>(2, std::max<size_t>(1, kSmemPerSM / (need + 1024)));
           Group& g = buckets[std::make_tuple(c, Gr ? 0 : 1, Gr, C, -res, -per_sm)];
           if (g.ids.empty()) {
             g.colour = c;
