@@ -57,3 +57,34 @@ def test_x_vs_oracle_against_stored_samples():
     assert r["samples"] == 256 and r["oracle_iters"] == g["iters"]
     assert r["a"]["sampled_rel_err"] == 0.0 and r["a"]["norm_rel_err"] < 1e-14
     assert abs(r["b"]["sampled_rel_err"] - 1e-6) < 1e-12
+
+
+def test_measured_traffic_per_step_divided_by_live_launches(tmp_path, monkeypatch):
+    """A family measured per factorization (all its launches in one capture)
+    reports that total over the launch count of the profiled run, so the
+    per-launch figure follows a change of launch grouping; the roofline line
+    carries it."""
+    src = tmp_path / "q.cuh"
+    src.write_text("qr")
+    import hashlib
+    good = hashlib.sha256(b"qr").hexdigest()
+    monkeypatch.setattr(bench, "MEASURED_TRAFFIC",
+                        {"cpqr": {"bytes_per_step": 600e6, "src": [str(src)], "sha256": [good]}})
+    assert bench.measured_traffic("cpqr", bench.GRID, 240) == 2.5e6
+    assert bench.measured_traffic("cpqr", bench.GRID, 300) == 2e6
+    peaks = {"hbm_gbs": 8000.0, "bf16_tflops": 2000.0, "_source": "test"}
+    prof = _prof()
+    prof["cpqr"]["launches"] = 240
+    r = bench.make_roofline(prof, peaks, grid=bench.GRID)
+    assert r["kernel"] == "cpqr" and r["traffic"] == 2.5e6 and r["launches"] == 240
+    assert abs(r["achieved"] - 2.0) < 1e-12 and r["bound"] == "alu"
+
+
+def test_oracle_runs_all_core_leg_matches_single_core():
+    """The all-core leg of the CPU baseline (the oracle's factorization on a
+    process pool) runs through the same subprocess recipe as the single-core
+    leg and reaches the same iterations, rank structure and memory."""
+    one = bench.oracle_phases(bench.oracle_runs(grid=12, levels=4))
+    two = bench.oracle_phases(bench.oracle_runs(grid=12, levels=4, workers=2))
+    assert (one["n_cg"], one["size_top"], one["mem_f"]) == (two["n_cg"], two["size_top"], two["mem_f"])
+    assert one["relres"] <= 1e-10 and two["relres"] <= 1e-10
